@@ -1,0 +1,224 @@
+"""ctypes wrapper of the plain FP64 CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and
+by the cpu_baseline / reference leg of bench.py. The product path never
+imports this package. It shares no code with the CUDA library.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAXC = 32
+
+
+class OrcConfig(ct.Structure):
+    _fields_ = [
+        ("P", ct.c_int32), ("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
+        ("N", ct.c_int64),
+        ("kinetic_eV", ct.c_double), ("mass_eV", ct.c_double), ("charge_e", ct.c_double),
+        ("bunch_charge_C", ct.c_double),
+        ("eps_n", ct.c_double * 3), ("alpha", ct.c_double * 3), ("beta", ct.c_double * 3),
+        ("twiss_slot", ct.c_int32 * 6),
+        ("L", ct.c_double * 5), ("g", ct.c_double * 2),
+        ("kicks", ct.c_int32 * 5), ("lat_slot", ct.c_int32 * 7),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        dp = ct.POINTER(ct.c_double)
+        cp = ct.POINTER(OrcConfig)
+        sig = {
+            "orc_constants": (None, [cp, dp]),
+            "orc_dual_op": (None, [ct.c_int, ct.c_int, dp, dp, dp]),
+            "orc_testfn": (None, [dp, dp]),
+            "orc_fft1d": (ct.c_int, [dp, dp, ct.c_int, ct.c_int]),
+            "orc_igf": (ct.c_double, [ct.c_double] * 6),
+            "orc_beam_init": (ct.c_int, [cp, dp, dp]),
+            "orc_half_map": (None, [cp, ct.c_int64, dp]),
+            "orc_apply_half_map": (None, [cp, dp, ct.c_int64]),
+            "orc_geometry": (ct.c_int, [cp, dp, dp]),
+            "orc_deposit": (ct.c_int, [cp, dp, dp, dp]),
+            "orc_green": (None, [cp, dp, dp]),
+            "orc_solve": (ct.c_int, [cp, dp, dp, dp]),
+            "orc_solve_direct": (ct.c_int, [cp, dp, dp, dp]),
+            "orc_field": (None, [cp, dp, dp, dp]),
+            "orc_gather": (ct.c_int, [cp, dp, dp, dp, dp]),
+            "orc_kick": (ct.c_int, [cp, dp, dp, dp, ct.c_int64]),
+            "orc_moments": (None, [cp, dp, dp]),
+            "orc_emittance": (None, [cp, dp, dp]),
+            "orc_run": (ct.c_int, [cp, dp, ct.c_int64, ct.c_int, dp, dp, ct.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _check(st, what):
+    if st < 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+    return st
+
+
+class Oracle:
+    """FP64 oracle bound to one configuration (a plain dict of the fields of OrcConfig)."""
+
+    def __init__(self, **kw):
+        c = OrcConfig()
+        for k, v in kw.items():
+            f = getattr(c, k)
+            if isinstance(f, ct.Array):
+                for i, x in enumerate(v):
+                    f[i] = x
+            else:
+                setattr(c, k, v)
+        self.cfg = c
+        self.C = c.P + 1
+        self.N = c.N
+        self.n = (c.nx, c.ny, c.nz)
+        self._L = lib()
+
+    @property
+    def ref(self):
+        return ct.byref(self.cfg)
+
+    def constants(self):
+        out = np.zeros(8)
+        self._L.orc_constants(self.ref, _p(out))
+        keys = ["gamma0", "beta0", "p0", "brho", "kappa_perp", "kappa_z", "q_macro", "q"]
+        return dict(zip(keys, out.tolist()))
+
+    def state_shape(self):
+        return (6, self.N, self.C)
+
+    def grid_shape(self):
+        nx, ny, nz = self.n
+        return (self.C, nz, ny, nx)
+
+    def beam_init(self, normals):
+        normals = np.ascontiguousarray(normals, dtype=np.float64)
+        assert normals.shape == (6, self.N)
+        st = np.zeros(self.state_shape())
+        _check(self._L.orc_beam_init(self.ref, _p(normals), _p(st)), "beam_init")
+        return st
+
+    def half_map(self, kick):
+        m = np.zeros((3, 4, self.C))
+        self._L.orc_half_map(self.ref, kick, _p(m))
+        return m
+
+    def apply_half_map(self, state, kick):
+        self._L.orc_apply_half_map(self.ref, _p(state), kick)
+
+    def geometry(self, state):
+        g = np.zeros(6)
+        _check(self._L.orc_geometry(self.ref, _p(state), _p(g)), "geometry")
+        return g
+
+    def deposit(self, state, geom):
+        rho = np.zeros(self.grid_shape())
+        _check(self._L.orc_deposit(self.ref, _p(state), _p(np.ascontiguousarray(geom)), _p(rho)), "deposit")
+        return rho
+
+    def green(self, geom):
+        nx, ny, nz = self.n
+        G = np.zeros((2 * nz, 2 * ny, 2 * nx))
+        self._L.orc_green(self.ref, _p(np.ascontiguousarray(geom)), _p(G))
+        return G
+
+    def solve(self, geom, rho):
+        phi = np.zeros(self.grid_shape())
+        _check(self._L.orc_solve(self.ref, _p(np.ascontiguousarray(geom)), _p(np.ascontiguousarray(rho)), _p(phi)),
+               "solve")
+        return phi
+
+    def solve_direct(self, geom, rho):
+        phi = np.zeros(self.grid_shape())
+        _check(self._L.orc_solve_direct(self.ref, _p(np.ascontiguousarray(geom)), _p(np.ascontiguousarray(rho)),
+                                        _p(phi)), "solve_direct")
+        return phi
+
+    def field(self, geom, phi):
+        E = np.zeros((3,) + self.grid_shape())
+        self._L.orc_field(self.ref, _p(np.ascontiguousarray(geom)), _p(np.ascontiguousarray(phi)), _p(E))
+        return E
+
+    def gather(self, state, geom, E):
+        Ep = np.zeros((3, self.N, self.C))
+        _check(self._L.orc_gather(self.ref, _p(state), _p(np.ascontiguousarray(geom)),
+                                  _p(np.ascontiguousarray(E)), _p(Ep)), "gather")
+        return Ep
+
+    def kick(self, state, geom, E, kick):
+        _check(self._L.orc_kick(self.ref, _p(state), _p(np.ascontiguousarray(geom)),
+                                _p(np.ascontiguousarray(E)), kick), "kick")
+
+    def moments(self, state):
+        m = np.zeros((3, 5, self.C))
+        self._L.orc_moments(self.ref, _p(state), _p(m))
+        return m
+
+    def emittance(self, mom):
+        e = np.zeros((3, self.C))
+        self._L.orc_emittance(self.ref, _p(np.ascontiguousarray(mom)), _p(e))
+        return e
+
+    def run(self, state, n_kicks, kick0=0, geom=None, geom_mode=0):
+        """Advance `state` in place; returns (moment records [R][3][5][C], geometry [n_kicks][6])."""
+        kpp = sum(self.cfg.kicks)
+        nrec = n_kicks // max(kpp, 1) + 2
+        hist = np.zeros((nrec, 3, 5, self.C))
+        if geom is None:
+            geom = np.zeros((max(n_kicks, 1), 6))
+        r = _check(self._L.orc_run(self.ref, _p(state), kick0, n_kicks, _p(hist), _p(geom), geom_mode), "run")
+        return hist[:r], geom[:n_kicks]
+
+
+def dual_op(op, f, g=None):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.zeros_like(f) if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros_like(f)
+    ops = {"add": 0, "sub": 1, "mul": 2, "div": 3, "sqrt": 4, "sin": 5, "cos": 6, "sinh": 7, "cosh": 8, "exp": 9}
+    lib().orc_dual_op(ops[op], f.size, _p(f), _p(g), _p(out))
+    return out
+
+
+def testfn(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(6)
+    lib().orc_testfn(_p(x), _p(out))
+    return out
+
+
+def fft1d(z, sign=-1):
+    re = np.ascontiguousarray(z.real, dtype=np.float64).copy()
+    im = np.ascontiguousarray(z.imag, dtype=np.float64).copy()
+    _check(lib().orc_fft1d(_p(re), _p(im), re.size, sign), "fft1d")
+    return re + 1j * im
+
+
+def igf(x, y, z, hx, hy, hz):
+    return lib().orc_igf(x, y, z, hx, hy, hz)
+
+
+def threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))

@@ -1,0 +1,859 @@
+/*
+ * Plain FP64 CPU oracle for the dual-number 3D space-charge PIC step.
+ * TEST INFRASTRUCTURE ONLY: see adpic_oracle.h. This file shares no code
+ * with the CUDA library and must never be linked into it.
+ *
+ * Built with -ffp-contract=off so that every written operation rounds on
+ * its own, identically on x86-64 and aarch64.
+ */
+#include "adpic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 exact or recommended values */
+static const double C_LIGHT = 299792458.0;      /* m/s */
+static const double Q_E = 1.602176634e-19;      /* C */
+static const double EPS0 = 8.8541878128e-12;    /* F/m */
+static const double PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------ */
+/* Dual numbers, Sec. 2. A dual is an array D[0..C-1]: D[0] is the     */
+/* value, D[k] (k >= 1) the derivative with respect to parameter k.    */
+/* ------------------------------------------------------------------ */
+
+typedef double dual[ORC_MAXC];
+
+static void d_const(int C, double v, double* out) {
+    out[0] = v;
+    for (int k = 1; k < C; ++k) out[k] = 0.0;
+}
+
+static void d_copy(int C, const double* f, double* out) {
+    for (int k = 0; k < C; ++k) out[k] = f[k];
+}
+
+/* Eq. 1: componentwise sum */
+static void d_add(int C, const double* f, const double* g, double* out) {
+    for (int k = 0; k < C; ++k) out[k] = f[k] + g[k];
+}
+
+static void d_sub(int C, const double* f, const double* g, double* out) {
+    for (int k = 0; k < C; ++k) out[k] = f[k] - g[k];
+}
+
+/* Eq. 2: (f g, g f_k + f g_k) */
+static void d_mul(int C, const double* f, const double* g, double* out) {
+    double v = f[0] * g[0];
+    double t[ORC_MAXC];
+    for (int k = 1; k < C; ++k) t[k] = g[0] * f[k] + f[0] * g[k];
+    out[0] = v;
+    for (int k = 1; k < C; ++k) out[k] = t[k];
+}
+
+/* Eq. 3: (f/g, (f_k g - g_k f) / g^2) */
+static void d_div(int C, const double* f, const double* g, double* out) {
+    double v = f[0] / g[0];
+    double g2 = g[0] * g[0];
+    double t[ORC_MAXC];
+    for (int k = 1; k < C; ++k) t[k] = (f[k] * g[0] - g[k] * f[0]) / g2;
+    out[0] = v;
+    for (int k = 1; k < C; ++k) out[k] = t[k];
+}
+
+/* Eq. 4: h(F) = (h(f), h'(f) f_k), given h(f) and h'(f) */
+static void d_fn(int C, const double* f, double h, double hp, double* out) {
+    double t[ORC_MAXC];
+    for (int k = 1; k < C; ++k) t[k] = hp * f[k];
+    out[0] = h;
+    for (int k = 1; k < C; ++k) out[k] = t[k];
+}
+
+static void d_sqrt(int C, const double* f, double* out) {
+    double s = sqrt(f[0]);
+    d_fn(C, f, s, 0.5 / s, out);
+}
+static void d_sin(int C, const double* f, double* out) { d_fn(C, f, sin(f[0]), cos(f[0]), out); }
+static void d_cos(int C, const double* f, double* out) { d_fn(C, f, cos(f[0]), -sin(f[0]), out); }
+static void d_sinh(int C, const double* f, double* out) { d_fn(C, f, sinh(f[0]), cosh(f[0]), out); }
+static void d_cosh(int C, const double* f, double* out) { d_fn(C, f, cosh(f[0]), sinh(f[0]), out); }
+static void d_exp(int C, const double* f, double* out) {
+    double e = exp(f[0]);
+    d_fn(C, f, e, e, out);
+}
+
+/* a constant times a dual: Eq. 2 with g = (a, 0, ..., 0) */
+static void d_cmul(int C, double a, const double* f, double* out) {
+    dual g;
+    d_const(C, a, g);
+    d_mul(C, f, g, out);
+}
+
+/* an independent variable X_i = (x, 0, .., 1 at slot i+1, ..) (Sec. 2); slot < 0: constant */
+static void d_var(int C, double v, int slot, double* out) {
+    d_const(C, v, out);
+    if (slot >= 0 && slot + 1 < C) out[slot + 1] = 1.0;
+}
+
+void orc_dual_op(int op, int C, const double* f, const double* g, double* out) {
+    switch (op) {
+        case 0: d_add(C, f, g, out); break;
+        case 1: d_sub(C, f, g, out); break;
+        case 2: d_mul(C, f, g, out); break;
+        case 3: d_div(C, f, g, out); break;
+        case 4: d_sqrt(C, f, out); break;
+        case 5: d_sin(C, f, out); break;
+        case 6: d_cos(C, f, out); break;
+        case 7: d_sinh(C, f, out); break;
+        case 8: d_cosh(C, f, out); break;
+        case 9: d_exp(C, f, out); break;
+        default: break;
+    }
+}
+
+/* f = x3 (2 cos(x1/x2) + x1/x2 + e^{x2}) + 2 x4 + sinh(x4) + x5^2, Sec. 3 */
+void orc_testfn(const double x[5], double out[6]) {
+    const int C = 6;
+    dual X[5], q, t, u, v, two, f;
+    for (int i = 0; i < 5; ++i) d_var(C, x[i], i, X[i]);
+    d_const(C, 2.0, two);
+    d_div(C, X[0], X[1], q);      /* x1/x2 */
+    d_cos(C, q, t);
+    d_mul(C, two, t, t);          /* 2 cos(x1/x2) */
+    d_add(C, t, q, t);            /* + x1/x2 */
+    d_exp(C, X[1], u);
+    d_add(C, t, u, t);            /* + e^{x2} */
+    d_mul(C, X[2], t, f);         /* x3 ( ... ) */
+    d_mul(C, two, X[3], u);
+    d_add(C, f, u, f);            /* + 2 x4 */
+    d_sinh(C, X[3], u);
+    d_add(C, f, u, f);            /* + sinh(x4) */
+    d_mul(C, X[4], X[4], v);
+    d_add(C, f, v, f);            /* + x5^2 */
+    d_copy(C, f, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Physical constants of the reference particle                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double gamma0, beta0, p0, brho, kperp, kz, qm, q;
+} consts;
+
+static consts get_consts(const orc_config* cfg) {
+    consts k;
+    double mass_kg = cfg->mass_eV * Q_E / (C_LIGHT * C_LIGHT);
+    k.q = cfg->charge_e * Q_E;
+    k.gamma0 = 1.0 + cfg->kinetic_eV / cfg->mass_eV;
+    k.beta0 = sqrt(1.0 - 1.0 / (k.gamma0 * k.gamma0));
+    k.p0 = k.gamma0 * k.beta0 * mass_kg * C_LIGHT;
+    k.brho = k.p0 / k.q;
+    double v0 = k.beta0 * C_LIGHT;
+    /* transverse: rest-frame E_perp over gamma0 (electric and magnetic
+       forces of the co-moving bunch combined); longitudinal: E_z,rest */
+    k.kperp = k.q / (k.gamma0 * k.p0 * v0);
+    k.kz = k.q / (k.p0 * v0);
+    k.qm = cfg->N > 0 ? cfg->bunch_charge_C / (double)cfg->N : 0.0;
+    return k;
+}
+
+void orc_constants(const orc_config* cfg, double out[8]) {
+    consts k = get_consts(cfg);
+    out[0] = k.gamma0; out[1] = k.beta0; out[2] = k.p0; out[3] = k.brho;
+    out[4] = k.kperp; out[5] = k.kz; out[6] = k.qm; out[7] = k.q;
+}
+
+/* ------------------------------------------------------------------ */
+/* Lattice: element of a kick, dual step length, half-step maps         */
+/* ------------------------------------------------------------------ */
+
+static int kicks_per_period(const orc_config* cfg) {
+    int s = 0;
+    for (int e = 0; e < 5; ++e) s += cfg->kicks[e];
+    return s;
+}
+
+static int element_of_kick(const orc_config* cfg, int64_t kick) {
+    int kpp = kicks_per_period(cfg);
+    int s = (int)(kick % kpp);
+    for (int e = 0; e < 5; ++e) {
+        if (s < cfg->kicks[e]) return e;
+        s -= cfg->kicks[e];
+    }
+    return 4;
+}
+
+/* parameter index of each element length in lat_slot */
+static const int LEN_PARAM[5] = {0, 1, 3, 4, 6};
+
+/* D tau = D L_e / n_e (Sec. 4: step size = element length over the number of steps) */
+static void dual_tau(const orc_config* cfg, int e, double* tau) {
+    const int C = cfg->P + 1;
+    dual L, n;
+    d_var(C, cfg->L[e], cfg->lat_slot[LEN_PARAM[e]], L);
+    d_const(C, (double)cfg->kicks[e], n);
+    d_div(C, L, n, tau);
+}
+
+/* 2x2 dual map of one transverse plane over a step t for focusing strength kp */
+static void plane_map(int C, const double* kp, const double* t, double m[4][ORC_MAXC]) {
+    dual w, th, c, s, negk;
+    if (kp[0] > 0.0) {                 /* focusing plane, Eq. quadtr */
+        d_sqrt(C, kp, w);
+        d_mul(C, w, t, th);
+        d_cos(C, th, c);
+        d_sin(C, th, s);
+        d_copy(C, c, m[0]);
+        d_div(C, s, w, m[1]);
+        d_mul(C, w, s, m[2]);
+        for (int k = 0; k < C; ++k) m[2][k] = -m[2][k];
+        d_copy(C, c, m[3]);
+    } else if (kp[0] < 0.0) {          /* defocusing plane */
+        for (int k = 0; k < C; ++k) negk[k] = -kp[k];
+        d_sqrt(C, negk, w);
+        d_mul(C, w, t, th);
+        d_cosh(C, th, c);
+        d_sinh(C, th, s);
+        d_copy(C, c, m[0]);
+        d_div(C, s, w, m[1]);
+        d_mul(C, w, s, m[2]);
+        d_copy(C, c, m[3]);
+    } else {                           /* field-free: drift */
+        d_const(C, 1.0, m[0]);
+        d_copy(C, t, m[1]);
+        d_const(C, 0.0, m[2]);
+        d_const(C, 1.0, m[3]);
+    }
+}
+
+/* M1(tau/2) of the element owning this kick: m[plane][entry][C] with
+   entries (m11, m12, m21, m22) for planes (x,px), (y,py), (z,delta). */
+void orc_half_map(const orc_config* cfg, int64_t kick, double* mflat) {
+    const int C = cfg->P + 1;
+    consts K = get_consts(cfg);
+    int e = element_of_kick(cfg, kick);
+    dual tau, t, kx, ky, zero;
+    double m[4][ORC_MAXC];
+    dual_tau(cfg, e, tau);
+    d_cmul(C, 0.5, tau, t);
+    d_const(C, 0.0, zero);
+    if (e == 1 || e == 3) {
+        int gi = (e == 1) ? 0 : 1;
+        int gslot = cfg->lat_slot[(e == 1) ? 2 : 5];
+        dual g, br;
+        d_var(C, cfg->g[gi], gslot, g);
+        d_const(C, K.brho, br);
+        d_div(C, g, br, kx);                  /* k = q g / p0 = g / Brho */
+        for (int k = 0; k < C; ++k) ky[k] = -kx[k];
+    } else {
+        d_copy(C, zero, kx);
+        d_copy(C, zero, ky);
+    }
+    plane_map(C, kx, t, m);
+    for (int i = 0; i < 4; ++i) d_copy(C, m[i], mflat + (0 * 4 + i) * C);
+    plane_map(C, ky, t, m);
+    for (int i = 0; i < 4; ++i) d_copy(C, m[i], mflat + (1 * 4 + i) * C);
+    /* longitudinal: z += t delta / gamma0^2 */
+    dual g2, tz;
+    d_const(C, K.gamma0 * K.gamma0, g2);
+    d_div(C, t, g2, tz);
+    d_const(C, 1.0, mflat + (2 * 4 + 0) * C);
+    d_copy(C, tz, mflat + (2 * 4 + 1) * C);
+    d_const(C, 0.0, mflat + (2 * 4 + 2) * C);
+    d_const(C, 1.0, mflat + (2 * 4 + 3) * C);
+}
+
+static inline double* coord(double* state, int64_t N, int C, int c, int64_t i) {
+    return state + ((int64_t)c * N + i) * C;
+}
+static inline const double* ccoord(const double* state, int64_t N, int C, int c, int64_t i) {
+    return state + ((int64_t)c * N + i) * C;
+}
+
+void orc_apply_half_map(const orc_config* cfg, double* state, int64_t kick) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    double m[3 * 4 * ORC_MAXC];
+    orc_half_map(cfg, kick, m);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        for (int pl = 0; pl < 3; ++pl) {
+            double* u = coord(state, N, C, 2 * pl, i);
+            double* p = coord(state, N, C, 2 * pl + 1, i);
+            const double* m11 = m + (pl * 4 + 0) * C;
+            const double* m12 = m + (pl * 4 + 1) * C;
+            const double* m21 = m + (pl * 4 + 2) * C;
+            const double* m22 = m + (pl * 4 + 3) * C;
+            dual a, b, un, pn;
+            d_mul(C, m11, u, a);
+            d_mul(C, m12, p, b);
+            d_add(C, a, b, un);
+            d_mul(C, m21, u, a);
+            d_mul(C, m22, p, b);
+            d_add(C, a, b, pn);
+            d_copy(C, un, u);
+            d_copy(C, pn, p);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial distribution with Twiss parameters as dual variables         */
+/* (Sec. 4: initial distribution parameters may be AD variables)        */
+/* ------------------------------------------------------------------ */
+
+int orc_beam_init(const orc_config* cfg, const double* normals, double* state) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    if (C < 1 || C > ORC_MAXC || N < 0) return -1;
+    consts K = get_consts(cfg);
+    double bg = K.beta0 * K.gamma0;
+    for (int pl = 0; pl < 3; ++pl) {
+        dual al, be, ep, epsn, bgd, a, b, t;
+        int sa = pl < 2 ? cfg->twiss_slot[3 * pl + 0] : -1;
+        int sb = pl < 2 ? cfg->twiss_slot[3 * pl + 1] : -1;
+        int se = pl < 2 ? cfg->twiss_slot[3 * pl + 2] : -1;
+        d_var(C, cfg->alpha[pl], sa, al);
+        d_var(C, cfg->beta[pl], sb, be);
+        d_const(C, cfg->eps_n[pl], epsn);
+        d_const(C, bg, bgd);
+        d_div(C, epsn, bgd, ep);              /* geometric emittance */
+        if (se >= 0) d_var(C, ep[0], se, ep);
+        d_mul(C, ep, be, t);
+        d_sqrt(C, t, a);                      /* sqrt(eps beta) */
+        d_div(C, ep, be, t);
+        d_sqrt(C, t, b);                      /* sqrt(eps / beta) */
+        const double* n1 = normals + (int64_t)(2 * pl) * N;
+        const double* n2 = normals + (int64_t)(2 * pl + 1) * N;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            dual u1, u2, x, p, s;
+            d_const(C, n1[i], u1);
+            d_const(C, n2[i], u2);
+            d_mul(C, a, u1, x);               /* x = sqrt(eps beta) u1 */
+            d_mul(C, al, u1, s);
+            d_sub(C, u2, s, s);
+            d_mul(C, b, s, p);                /* p = sqrt(eps/beta) (u2 - alpha u1) */
+            d_copy(C, x, coord(state, N, C, 2 * pl, i));
+            d_copy(C, p, coord(state, N, C, 2 * pl + 1, i));
+        }
+    }
+    /* subtract the sample mean of every coordinate (dual) */
+    if (N > 0) {
+        for (int c = 0; c < 6; ++c) {
+            dual sum, mean, invn;
+            d_const(C, 0.0, sum);
+            for (int64_t i = 0; i < N; ++i) d_add(C, sum, ccoord(state, N, C, c, i), sum);
+            d_const(C, (double)N, invn);
+            d_div(C, sum, invn, mean);
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < N; ++i) {
+                double* x = coord(state, N, C, c, i);
+                d_sub(C, x, mean, x);
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Grid geometry from the value part (not differentiated)              */
+/* ------------------------------------------------------------------ */
+
+int orc_geometry(const orc_config* cfg, const double* state, double* geom) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
+    for (int d = 0; d < 3; ++d) {
+        double lo = 0.0, hi = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double v = ccoord(state, N, C, 2 * d, i)[0];
+            if (!isfinite(v)) return -5;
+            if (i == 0 || v < lo) lo = v;
+            if (i == 0 || v > hi) hi = v;
+        }
+        double w = hi - lo;
+        if (!(w > 0.0)) w = 1e-6;
+        double h = w / (double)(n[d] - 4);
+        geom[d] = lo - 1.5 * h;
+        geom[3 + d] = h;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cloud-in-cell weights (linear shape, two nodes per dimension)        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int idx[3];
+    double w[3][2][ORC_MAXC];   /* dual weights of the lower/upper node per dimension */
+} cic;
+
+static int cic_weights(int C, const double* state, int64_t N, int64_t i, const double* geom,
+                       const int n[3], cic* out) {
+    for (int d = 0; d < 3; ++d) {
+        const double* x = ccoord(state, N, C, 2 * d, i);
+        dual o, h, u, f, one;
+        if (!isfinite(x[0])) return -5;
+        d_const(C, geom[d], o);
+        d_const(C, geom[3 + d], h);
+        d_sub(C, x, o, u);
+        d_div(C, u, h, u);                      /* u = (x - origin) / h */
+        double fl = floor(u[0]);
+        if (fl < 1.0 || fl > (double)(n[d] - 3)) return -6;
+        int id = (int)fl;                       /* floor is not differentiated */
+        dual idd;
+        d_const(C, (double)id, idd);
+        d_sub(C, u, idd, f);                    /* fractional offset in the cell */
+        d_const(C, 1.0, one);
+        d_sub(C, one, f, out->w[d][0]);
+        d_copy(C, f, out->w[d][1]);
+        out->idx[d] = id;
+    }
+    return 0;
+}
+
+int orc_deposit(const orc_config* cfg, const double* state, const double* geom, double* rho) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
+    const int64_t nn = (int64_t)n[0] * n[1] * n[2];
+    consts K = get_consts(cfg);
+    int status = 0;
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    double* priv = (double*)calloc((size_t)nthreads * C * nn, sizeof(double));
+    if (!priv) return -1;
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* my = priv + (int64_t)tid * C * nn;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            cic w;
+            int st = cic_weights(C, state, N, i, geom, n, &w);
+            if (st) {
+#pragma omp critical
+                status = st;
+                continue;
+            }
+            for (int c = 0; c < 2; ++c)
+                for (int b = 0; b < 2; ++b)
+                    for (int a = 0; a < 2; ++a) {
+                        dual W, Q;
+                        d_mul(C, w.w[0][a], w.w[1][b], W);
+                        d_mul(C, W, w.w[2][c], W);
+                        d_cmul(C, K.qm, W, Q);  /* macroparticle charge times weight */
+                        int64_t node = ((int64_t)(w.idx[2] + c) * n[1] + (w.idx[1] + b)) * n[0] +
+                                       (w.idx[0] + a);
+                        for (int k = 0; k < C; ++k) my[(int64_t)k * nn + node] += Q[k];
+                    }
+        }
+    }
+    memset(rho, 0, sizeof(double) * C * nn);
+    for (int t = 0; t < nthreads; ++t)
+        for (int64_t j = 0; j < C * nn; ++j) rho[j] += priv[(int64_t)t * C * nn + j];
+    free(priv);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Integrated Green's function of the open-boundary Poisson problem    */
+/* ------------------------------------------------------------------ */
+
+/* An antiderivative of 1/r: d^3 F / dx dy dz = 1/sqrt(x^2+y^2+z^2). */
+static double igf_F(double x, double y, double z) {
+    double r = sqrt(x * x + y * y + z * z);
+    return y * z * log(x + r) + x * z * log(y + r) + x * y * log(z + r) -
+           0.5 * x * x * atan(y * z / (x * r)) - 0.5 * y * y * atan(x * z / (y * r)) -
+           0.5 * z * z * atan(x * y / (z * r));
+}
+
+double orc_igf(double x, double y, double z, double hx, double hy, double hz) {
+    double xs[2] = {x - 0.5 * hx, x + 0.5 * hx};
+    double ys[2] = {y - 0.5 * hy, y + 0.5 * hy};
+    double zs[2] = {z - 0.5 * hz, z + 0.5 * hz};
+    double s = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                double sgn = ((a + b + c) % 2 == 1) ? 1.0 : -1.0;   /* + at the (x2,y2,z2) corner */
+                s += sgn * igf_F(xs[a], ys[b], zs[c]);
+            }
+    return s / (4.0 * PI * EPS0 * hx * hy * hz);
+}
+
+/* G on the doubled grid (2nx x 2ny x 2nz), even extension: index i maps to
+   offset i for i <= n and i - 2n above. Rest-frame spacings (hx, hy, gamma0 hz). */
+void orc_green(const orc_config* cfg, const double* geom, double* G) {
+    consts K = get_consts(cfg);
+    const int mx = 2 * cfg->nx, my = 2 * cfg->ny, mz = 2 * cfg->nz;
+    const double hx = geom[3], hy = geom[4], hz = geom[5] * K.gamma0;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < mz; ++k) {
+        int ok = k <= cfg->nz ? k : k - mz;
+        for (int j = 0; j < my; ++j) {
+            int oj = j <= cfg->ny ? j : j - my;
+            for (int i = 0; i < mx; ++i) {
+                int oi = i <= cfg->nx ? i : i - mx;
+                /* the integral depends on |offset| only; evaluate at |offset| */
+                G[((int64_t)k * my + j) * mx + i] =
+                    orc_igf(fabs((double)oi) * hx, fabs((double)oj) * hy, fabs((double)ok) * hz, hx, hy, hz);
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Radix-2 complex FFT (iterative, bit reversal, unnormalised)          */
+/* ------------------------------------------------------------------ */
+
+int orc_fft1d(double* re, double* im, int n, int sign) {
+    if (n < 1 || (n & (n - 1))) return -1;
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double t = re[i]; re[i] = re[j]; re[j] = t;
+            t = im[i]; im[i] = im[j]; im[j] = t;
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len >> 1;
+        for (int k = 0; k < half; ++k) {
+            double ang = sign * 2.0 * PI * (double)k / (double)len;
+            double wr = cos(ang), wi = sin(ang);
+            for (int s = 0; s < n; s += len) {
+                int a = s + k, b = s + k + half;
+                double tr = re[b] * wr - im[b] * wi;
+                double ti = re[b] * wi + im[b] * wr;
+                re[b] = re[a] - tr; im[b] = im[a] - ti;
+                re[a] = re[a] + tr; im[a] = im[a] + ti;
+            }
+        }
+    }
+    return 0;
+}
+
+/* 3D FFT of a complex array [mz][my][mx] (split re/im), along x, then y, then z */
+static void fft3d(double* re, double* im, int mx, int my, int mz, int sign) {
+#pragma omp parallel
+    {
+        int mmax = mx > my ? mx : my;
+        if (mz > mmax) mmax = mz;
+        double* lr = (double*)malloc(sizeof(double) * mmax);
+        double* li = (double*)malloc(sizeof(double) * mmax);
+#pragma omp for schedule(static)
+        for (int64_t line = 0; line < (int64_t)my * mz; ++line) {
+            int64_t base = line * mx;
+            for (int i = 0; i < mx; ++i) { lr[i] = re[base + i]; li[i] = im[base + i]; }
+            orc_fft1d(lr, li, mx, sign);
+            for (int i = 0; i < mx; ++i) { re[base + i] = lr[i]; im[base + i] = li[i]; }
+        }
+#pragma omp for schedule(static)
+        for (int64_t line = 0; line < (int64_t)mx * mz; ++line) {
+            int64_t k = line / mx, i = line % mx;
+            for (int j = 0; j < my; ++j) {
+                int64_t a = (k * my + j) * mx + i;
+                lr[j] = re[a]; li[j] = im[a];
+            }
+            orc_fft1d(lr, li, my, sign);
+            for (int j = 0; j < my; ++j) {
+                int64_t a = (k * my + j) * mx + i;
+                re[a] = lr[j]; im[a] = li[j];
+            }
+        }
+#pragma omp for schedule(static)
+        for (int64_t line = 0; line < (int64_t)mx * my; ++line) {
+            for (int k = 0; k < mz; ++k) {
+                int64_t a = (int64_t)k * mx * my + line;
+                lr[k] = re[a]; li[k] = im[a];
+            }
+            orc_fft1d(lr, li, mz, sign);
+            for (int k = 0; k < mz; ++k) {
+                int64_t a = (int64_t)k * mx * my + line;
+                re[a] = lr[k]; im[a] = li[k];
+            }
+        }
+        free(lr);
+        free(li);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Hockney convolution phi_c = G * rho_c for every channel (Sec. 4: the  */
+/* Poisson equation is solved for the value and for every derivative)   */
+/* ------------------------------------------------------------------ */
+
+int orc_solve(const orc_config* cfg, const double* geom, const double* rho, double* phi) {
+    const int C = cfg->P + 1;
+    const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+    const int mx = 2 * nx, my = 2 * ny, mz = 2 * nz;
+    const int64_t M = (int64_t)mx * my * mz, nn = (int64_t)nx * ny * nz;
+    double* gr = (double*)malloc(sizeof(double) * M);
+    double* gi = (double*)calloc(M, sizeof(double));
+    double* ar = (double*)malloc(sizeof(double) * M);
+    double* ai = (double*)malloc(sizeof(double) * M);
+    if (!gr || !gi || !ar || !ai) { free(gr); free(gi); free(ar); free(ai); return -1; }
+    orc_green(cfg, geom, gr);
+    fft3d(gr, gi, mx, my, mz, -1);
+    for (int c = 0; c < C; ++c) {
+        memset(ar, 0, sizeof(double) * M);
+        memset(ai, 0, sizeof(double) * M);
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    ar[((int64_t)k * my + j) * mx + i] = rho[(int64_t)c * nn + ((int64_t)k * ny + j) * nx + i];
+        fft3d(ar, ai, mx, my, mz, -1);
+        for (int64_t q = 0; q < M; ++q) {
+            double r = ar[q] * gr[q] - ai[q] * gi[q];
+            double s = ar[q] * gi[q] + ai[q] * gr[q];
+            ar[q] = r;
+            ai[q] = s;
+        }
+        fft3d(ar, ai, mx, my, mz, +1);
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    phi[(int64_t)c * nn + ((int64_t)k * ny + j) * nx + i] =
+                        ar[((int64_t)k * my + j) * mx + i] / (double)M;
+    }
+    free(gr); free(gi); free(ar); free(ai);
+    return 0;
+}
+
+/* brute-force direct sum phi_c(i) = sum_j rho_c(j) G(i - j) (pins the FFT path) */
+int orc_solve_direct(const orc_config* cfg, const double* geom, const double* rho, double* phi) {
+    const int C = cfg->P + 1;
+    const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+    const int64_t nn = (int64_t)nx * ny * nz;
+    consts K = get_consts(cfg);
+    const double hx = geom[3], hy = geom[4], hz = geom[5] * K.gamma0;
+#pragma omp parallel for schedule(static)
+    for (int64_t a = 0; a < nn; ++a) {
+        int ia = (int)(a % nx), ja = (int)((a / nx) % ny), ka = (int)(a / ((int64_t)nx * ny));
+        for (int c = 0; c < C; ++c) phi[(int64_t)c * nn + a] = 0.0;
+        for (int64_t b = 0; b < nn; ++b) {
+            int ib = (int)(b % nx), jb = (int)((b / nx) % ny), kb = (int)(b / ((int64_t)nx * ny));
+            double G = orc_igf(fabs((double)(ia - ib)) * hx, fabs((double)(ja - jb)) * hy,
+                               fabs((double)(ka - kb)) * hz, hx, hy, hz);
+            for (int c = 0; c < C; ++c) phi[(int64_t)c * nn + a] += G * rho[(int64_t)c * nn + b];
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Central finite-difference field E = -grad(phi), rest-frame spacing  */
+/* ------------------------------------------------------------------ */
+
+void orc_field(const orc_config* cfg, const double* geom, const double* phi, double* E) {
+    const int C = cfg->P + 1;
+    const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+    const int64_t nn = (int64_t)nx * ny * nz;
+    consts K = get_consts(cfg);
+    const double hx = geom[3], hy = geom[4], hz = geom[5] * K.gamma0;
+    memset(E, 0, sizeof(double) * 3 * C * nn);
+    for (int c = 0; c < C; ++c) {
+        const double* f = phi + (int64_t)c * nn;
+        double* ex = E + ((int64_t)0 * C + c) * nn;
+        double* ey = E + ((int64_t)1 * C + c) * nn;
+        double* ez = E + ((int64_t)2 * C + c) * nn;
+        for (int k = 1; k < nz - 1; ++k)
+            for (int j = 1; j < ny - 1; ++j)
+                for (int i = 1; i < nx - 1; ++i) {
+                    int64_t a = ((int64_t)k * ny + j) * nx + i;
+                    ex[a] = -(f[a + 1] - f[a - 1]) / (2.0 * hx);
+                    ey[a] = -(f[a + nx] - f[a - nx]) / (2.0 * hy);
+                    ez[a] = -(f[a + (int64_t)nx * ny] - f[a - (int64_t)nx * ny]) / (2.0 * hz);
+                }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Gather (same linear shape as the deposit) and the space-charge kick  */
+/* M2(tau): r fixed, p += kappa tau E (Sec. 4, Eqs. for map M2)         */
+/* ------------------------------------------------------------------ */
+
+int orc_gather(const orc_config* cfg, const double* state, const double* geom, const double* E,
+               double* Ep) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
+    const int64_t nn = (int64_t)n[0] * n[1] * n[2];
+    int status = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        cic w;
+        int st = cic_weights(C, state, N, i, geom, n, &w);
+        if (st) {
+#pragma omp critical
+            status = st;
+            continue;
+        }
+        for (int d = 0; d < 3; ++d) {
+            dual acc, W, En, t;
+            d_const(C, 0.0, acc);
+            for (int c = 0; c < 2; ++c)
+                for (int b = 0; b < 2; ++b)
+                    for (int a = 0; a < 2; ++a) {
+                        d_mul(C, w.w[0][a], w.w[1][b], W);
+                        d_mul(C, W, w.w[2][c], W);
+                        int64_t node = ((int64_t)(w.idx[2] + c) * n[1] + (w.idx[1] + b)) * n[0] +
+                                       (w.idx[0] + a);
+                        for (int k = 0; k < C; ++k) En[k] = E[((int64_t)d * C + k) * nn + node];
+                        d_mul(C, W, En, t);
+                        d_add(C, acc, t, acc);
+                    }
+            d_copy(C, acc, Ep + ((int64_t)d * N + i) * C);
+        }
+    }
+    return status;
+}
+
+int orc_kick(const orc_config* cfg, double* state, const double* geom, const double* E, int64_t kick) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    consts K = get_consts(cfg);
+    double* Ep = (double*)malloc(sizeof(double) * 3 * N * C + 8);
+    if (!Ep) return -1;
+    int st = orc_gather(cfg, state, geom, E, Ep);
+    if (st) { free(Ep); return st; }
+    dual tau, a[3];
+    dual_tau(cfg, element_of_kick(cfg, kick), tau);
+    d_cmul(C, K.kperp, tau, a[0]);
+    d_cmul(C, K.kperp, tau, a[1]);
+    d_cmul(C, K.kz, tau, a[2]);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            dual dp;
+            double* p = coord(state, N, C, 2 * d + 1, i);
+            d_mul(C, a[d], Ep + ((int64_t)d * N + i) * C, dp);
+            d_add(C, p, dp, p);
+        }
+    }
+    free(Ep);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Dual beam moments and emittance (Sec. 4, D eps_x)                    */
+/* ------------------------------------------------------------------ */
+
+void orc_moments(const orc_config* cfg, const double* state, double* mom) {
+    const int C = cfg->P + 1;
+    const int64_t N = cfg->N;
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    double* part = (double*)malloc(sizeof(double) * nthreads * 5 * ORC_MAXC);
+    for (int pl = 0; pl < 3; ++pl) {
+        dual s[5];
+        for (int q = 0; q < 5; ++q) d_const(C, 0.0, s[q]);
+#pragma omp parallel
+        {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            double* t = part + (int64_t)tid * 5 * ORC_MAXC;
+            dual a;
+            for (int q = 0; q < 5; ++q) d_const(C, 0.0, t + q * ORC_MAXC);
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < N; ++i) {
+                const double* u = ccoord(state, N, C, 2 * pl, i);
+                const double* p = ccoord(state, N, C, 2 * pl + 1, i);
+                d_add(C, t + 0 * ORC_MAXC, u, t + 0 * ORC_MAXC);
+                d_add(C, t + 1 * ORC_MAXC, p, t + 1 * ORC_MAXC);
+                d_mul(C, u, u, a); d_add(C, t + 2 * ORC_MAXC, a, t + 2 * ORC_MAXC);
+                d_mul(C, u, p, a); d_add(C, t + 3 * ORC_MAXC, a, t + 3 * ORC_MAXC);
+                d_mul(C, p, p, a); d_add(C, t + 4 * ORC_MAXC, a, t + 4 * ORC_MAXC);
+            }
+        }
+        /* partial sums combined in thread order: the result is reproducible */
+        for (int th = 0; th < nthreads; ++th)
+            for (int q = 0; q < 5; ++q) d_add(C, s[q], part + ((int64_t)th * 5 + q) * ORC_MAXC, s[q]);
+        for (int q = 0; q < 5; ++q) {
+            dual nd;
+            d_const(C, N > 0 ? (double)N : 1.0, nd);
+            d_div(C, s[q], nd, mom + (pl * 5 + q) * C);
+        }
+    }
+    free(part);
+}
+
+void orc_emittance(const orc_config* cfg, const double* mom, double* eps) {
+    const int C = cfg->P + 1;
+    for (int pl = 0; pl < 3; ++pl) {
+        const double* mu = mom + (pl * 5 + 0) * C;
+        const double* mp = mom + (pl * 5 + 1) * C;
+        const double* uu = mom + (pl * 5 + 2) * C;
+        const double* up = mom + (pl * 5 + 3) * C;
+        const double* pp = mom + (pl * 5 + 4) * C;
+        dual a, b, c, t, d;
+        d_mul(C, mu, mu, t); d_sub(C, uu, t, a);     /* centred <u^2> */
+        d_mul(C, mu, mp, t); d_sub(C, up, t, b);     /* centred <u p> */
+        d_mul(C, mp, mp, t); d_sub(C, pp, t, c);     /* centred <p^2> */
+        d_mul(C, a, c, t);
+        d_mul(C, b, b, d);
+        d_sub(C, t, d, t);
+        d_sqrt(C, t, eps + pl * C);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* The split-operator run                                               */
+/* ------------------------------------------------------------------ */
+
+int orc_run(const orc_config* cfg, double* state, int64_t kick0, int n_kicks, double* mom_hist,
+            double* geom_io, int geom_mode) {
+    const int C = cfg->P + 1;
+    if (C < 1 || C > ORC_MAXC || n_kicks < 0) return -1;
+    const int64_t nn = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+    const int kpp = kicks_per_period(cfg);
+    double* rho = (double*)malloc(sizeof(double) * C * nn);
+    double* phi = (double*)malloc(sizeof(double) * C * nn);
+    double* E = (double*)malloc(sizeof(double) * 3 * C * nn);
+    if (!rho || !phi || !E) { free(rho); free(phi); free(E); return -1; }
+    int rec = 0, st = 0;
+    for (int s = 0; s < n_kicks; ++s) {
+        int64_t kick = kick0 + s;
+        double geom[6];
+        orc_apply_half_map(cfg, state, kick);             /* M1(tau/2) */
+        if (geom_mode == 2) {
+            memcpy(geom, geom_io + 6 * s, sizeof(geom));
+        } else {
+            st = orc_geometry(cfg, state, geom);
+            if (st) break;
+            if (geom_mode == 1) memcpy(geom_io + 6 * s, geom, sizeof(geom));
+        }
+        st = orc_deposit(cfg, state, geom, rho);          /* D rho */
+        if (st) break;
+        st = orc_solve(cfg, geom, rho, phi);              /* D phi */
+        if (st) break;
+        orc_field(cfg, geom, phi, E);                     /* D E */
+        st = orc_kick(cfg, state, geom, E, kick);         /* M2(tau) */
+        if (st) break;
+        orc_apply_half_map(cfg, state, kick);             /* M1(tau/2) */
+        if (((kick + 1) % kpp == 0) || s == n_kicks - 1) {
+            if (mom_hist) orc_moments(cfg, state, mom_hist + (int64_t)rec * 15 * C);
+            ++rec;
+        }
+    }
+    free(rho); free(phi); free(E);
+    return st ? st : rec;
+}

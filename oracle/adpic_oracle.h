@@ -1,0 +1,96 @@
+/*
+ * Plain FP64 CPU oracle for the dual-number 3D space-charge PIC step.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path (the CUDA library,
+ * its Python binding) may include, link or call this code. Only the tests,
+ * __graft_entry__.smoke() and the cpu_baseline leg of bench.py use it.
+ *
+ * The oracle is written for readability against the paper, not for speed:
+ * a runtime-sized dual number (value plus P first derivatives, Sec. 2,
+ * Eqs. 1-4), the split-operator step M1(tau/2) M2(tau) M1(tau/2) (Sec. 4,
+ * Eq. "map"), the thick-quadrupole maps (Eq. "quadtr" and its defocusing
+ * twin, written in dual variables as in the equation following "Dk, Dtau"),
+ * cloud-in-cell deposition and gathering (Sec. 4, linear deposition), an
+ * open-boundary Hockney convolution with an integrated Green's function,
+ * central finite-difference fields, and the dual emittance of Sec. 4
+ * (Eqs. for D<x^2>, D<px^2>, D<x px>).
+ *
+ * Where the paper is silent (3D, rest frame, Green's function, grid geometry,
+ * longitudinal map) the oracle takes one written reading; every such reading
+ * is listed with the repository's design notes.
+ *
+ * Layouts (all row-major, all FP64):
+ *   particle state  [6][N][C]   coordinates (x, px, y, py, z, delta)
+ *   grid channel    [C][nz][ny][nx]
+ *   field           [3][C][nz][ny][nx]   (Ex, Ey, Ez), rest-frame V/m
+ *   moments         [3][5][C]   planes (x,y,z) x (<u>,<p>,<u^2>,<u p>,<p^2>)
+ *   geometry        [6]         origin x,y,z (m, lab), spacing hx,hy,hz (lab)
+ *
+ * Return codes: 0 ok, -1 invalid argument, -5 non-finite value,
+ * -6 particle outside the grid.
+ */
+#ifndef ADPIC_ORACLE_H
+#define ADPIC_ORACLE_H
+#include <stdint.h>
+
+#define ORC_MAXC 32
+
+typedef struct {
+    int32_t P;            /* derivative slots; C = P + 1 channels */
+    int32_t nx, ny, nz;   /* grid nodes per dimension (powers of two, >= 8) */
+    int64_t N;            /* macroparticles */
+    double kinetic_eV;    /* reference kinetic energy (eV) */
+    double mass_eV;       /* rest energy (eV) */
+    double charge_e;      /* particle charge in units of e */
+    double bunch_charge_C;/* physical bunch charge (C) */
+    double eps_n[3];      /* normalized rms emittance per plane (m rad) */
+    double alpha[3];      /* Twiss alpha per plane at the start */
+    double beta[3];       /* Twiss beta per plane at the start (m) */
+    int32_t twiss_slot[6];/* slots of (alpha_x, beta_x, eps_x, alpha_y, beta_y, eps_y); -1 = constant */
+    double L[5];          /* element lengths D1, QF, D2, QD, D3 (m) */
+    double g[2];          /* gradients of QF, QD (T/m) */
+    int32_t kicks[5];     /* space-charge kicks per element */
+    int32_t lat_slot[7];  /* slots of (L_D1, L_QF, g_QF, L_D2, L_QD, g_QD, L_D3); -1 = constant */
+} orc_config;
+
+/* derived constants: gamma0, beta0, p0 (kg m/s), Brho (T m), kappa_perp, kappa_z, q_macro (C), q (C) */
+void orc_constants(const orc_config* cfg, double out[8]);
+
+/* dual arithmetic, exposed for the pins: op 0 add, 1 sub, 2 mul, 3 div,
+   4 sqrt, 5 sin, 6 cos, 7 sinh, 8 cosh, 9 exp (g ignored for unary ops) */
+void orc_dual_op(int op, int C, const double* f, const double* g, double* out);
+/* the five-variable test function of Sec. 3, with all five seeded: out[6] */
+void orc_testfn(const double x[5], double out[6]);
+
+/* FFT of one complex sequence of power-of-two length n (sign -1 forward,
+   +1 inverse, unnormalised), in place on split re/im arrays */
+int orc_fft1d(double* re, double* im, int n, int sign);
+
+/* cell-averaged 1/(4 pi eps0 r) over the box of size (hx,hy,hz) centred at (x,y,z) */
+double orc_igf(double x, double y, double z, double hx, double hy, double hz);
+
+int orc_beam_init(const orc_config* cfg, const double* normals /*[6][N]*/, double* state);
+void orc_half_map(const orc_config* cfg, int64_t kick, double* m /*[3][4][C]*/);
+void orc_apply_half_map(const orc_config* cfg, double* state, int64_t kick);
+int orc_geometry(const orc_config* cfg, const double* state, double* geom);
+int orc_deposit(const orc_config* cfg, const double* state, const double* geom, double* rho);
+void orc_green(const orc_config* cfg, const double* geom, double* G /*[2nz][2ny][2nx]*/);
+int orc_solve(const orc_config* cfg, const double* geom, const double* rho, double* phi);
+int orc_solve_direct(const orc_config* cfg, const double* geom, const double* rho, double* phi);
+void orc_field(const orc_config* cfg, const double* geom, const double* phi, double* E);
+int orc_gather(const orc_config* cfg, const double* state, const double* geom, const double* E,
+               double* Ep /*[3][N][C]*/);
+int orc_kick(const orc_config* cfg, double* state, const double* geom, const double* E, int64_t kick);
+void orc_moments(const orc_config* cfg, const double* state, double* mom);
+void orc_emittance(const orc_config* cfg, const double* mom, double* eps /*[3][C]*/);
+
+/* Run n_kicks split steps starting at global kick index kick0.
+   geom_mode 0: geometry from the particles; 1: same and record into
+   geom_io[n_kicks][6]; 2: replay geom_io (frozen geometry).
+   Moments are recorded into mom_hist[r][3][5][C] at every period end and
+   after the last kick; the return value is the number of records (>= 0)
+   or a negative status. */
+int orc_run(const orc_config* cfg, double* state, int64_t kick0, int n_kicks,
+            double* mom_hist, double* geom_io, int geom_mode);
+
+#endif
