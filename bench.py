@@ -1,0 +1,345 @@
+"""Benchmark of the dual-number 3D space-charge PIC step on GB300.
+
+Workload: the 1M-particle FODO run - 1,048,576 macroparticles, 64^3 grid,
+P = 7 lattice derivatives, 1 GeV protons. One step = one FODO period: 20
+space-charge kicks (each: geometry, CIC deposit of 8 dual channels, Green's
+function, Hockney FFT convolution, FD field, gather + kick + maps) and the
+period-end FP64 dual moment reduction. Metric: dual particle-steps/s =
+particles x kicks / time, whole job.
+
+  python bench.py [--gpus N --steps K --warmup W]         CUDA path (FP32 bulk + FP64 reductions;
+                                                           the plain FP64 path is measured beside it)
+  python bench.py --impl reference [...]                   the FP64 CPU oracle on the host cores
+Multi-GPU (torchrun): independent replicas, one instance per rank (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dual particle-steps/s (1M p, 64³, P=7), FP32/batched vs plain FP64 at fixed error"
+UNIT = "dual particle-steps/s"
+WORKLOAD = "fodo_1m_64"
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": f"{w.name}: FODO period (D 0.5 / QF 0.1 m +10 T/m / D 1.0 / QD 0.1 m -10 T/m / D 0.5), "
+                       f"1 GeV protons, {w.n_particles} macroparticles, {w.grid[0]}x{w.grid[1]}x{w.grid[2]} grid, "
+                       f"P={w.n_deriv}, step = one period of {w.kicks_per_period} kicks + FP64 moments",
+           "particles": w.n_particles, "grid": list(w.grid), "n_deriv": w.n_deriv,
+           "kicks_per_step": w.kicks_per_period,
+           "l2": "inputs larger than L2: the dual particle state is 403 MB (FP32) / 805 MB (FP64)",
+           "parallelism": "replicas (one independent instance per GPU, no collective)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def oracle_rate(w, kicks, threads=None):
+    """Time the FP64 oracle on the host cores on `kicks` kicks of the workload; particle-steps/s."""
+    import oracle
+    from paper_2511_21839_gb300 import inputs as I
+
+    o = oracle.Oracle(**I.orc_kwargs(w))
+    st = o.beam_init(I.normals(w.seed, w.n_particles))
+    t0 = time.perf_counter()
+    o.run(st, kicks)
+    dt = time.perf_counter() - t0
+    return w.n_particles * kicks / dt, dt
+
+
+def host_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2511_21839_gb300 import inputs as I
+
+    w = I.workload(WORKLOAD)
+    kicks_per_step = 1
+    for _ in range(args.warmup):
+        oracle_rate(w, kicks_per_step)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(w, kicks_per_step)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = w.n_particles * kicks_per_step / (ms / 1000.0)
+    sample = (f"each step: {kicks_per_step} kick of the {w.name} workload ({w.n_particles} particles, 64^3, P=7), "
+              f"FP64 oracle, OpenMP over particles")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, {"kicks_per_step": kicks_per_step}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- native arm
+
+def traffic_from_profile(kernel_src_hash):
+    """Per-launch DRAM traffic of the push kernel from the committed ncu summary, if it was taken
+    on the current kernel source (else null)."""
+    path = os.path.join(ROOT, "profiles", "push_fodo_1m_64.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_src_sha256") != kernel_src_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("particles.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2511_21839_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measure(sim, steps, warmup, kicks, torch, timing_mask=0):
+    for _ in range(warmup):
+        sim.run(kicks)
+    sim.set_timing(timing_mask)
+    sim.run(kicks)          # capture the timed graph shape outside the timed region
+    sim.set_timing(timing_mask)
+    l0 = sim.launches()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        sim.run(kicks)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, sim.launches() - l0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from paper_2511_21839_gb300 import adpic, build
+    from paper_2511_21839_gb300 import inputs as I
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    build.build()
+    dev = torch.cuda.current_device()
+    w = I.workload(WORKLOAD)
+    kicks = w.kicks_per_period
+    nrm = I.normals(w.seed + 1000 * rank, w.n_particles)
+    stream = torch.cuda.Stream()        # one non-default stream shared by the library and the events
+    torch.cuda.set_stream(stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make(prec):
+        sim = adpic.ADPIC(w.grid, w.n_particles, w.n_deriv, prec)
+        sim.set_stream(stream.cuda_stream)
+        sim.set_beam(w.beam, nrm)
+        sim.set_lattice(w.lattice)
+        return sim
+
+    # ---- FP32 bulk / FP64 reductions (headline)
+    sim = make(adpic.AD_PIC_FP32_MIXED)
+    push_mask = 1 << 0
+    for _ in range(args.warmup):
+        sim.run(kicks)
+    sim.set_timing(push_mask)
+    sim.run(kicks)                      # captures the timed graph shape outside the timed region
+    sim.set_timing(push_mask)           # same mask: resets the accumulators, keeps the graph
+    clocks = ClockSampler(dev)
+    barrier()
+    l0 = sim.launches()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sim.run(kicks)
+    e1.record()
+    barrier()
+    ck = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    launches = sim.launches() - l0
+    tpush = sim.timing()["push"]
+    push_ms = tpush[0] / max(tpush[1], 1)
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * w.n_particles * kicks / (ms_step / 1000.0)
+
+    # ---- end to end through the public API with host buffers: upload the step's dual state
+    # from pinned host memory, run the period, read the emittances back
+    state = torch.empty((6, w.n_particles, w.n_deriv + 1), dtype=torch.float64, pin_memory=True)
+    state.numpy()[...] = sim.get_particles()
+    for _ in range(2):
+        sim.set_particles(state.numpy())
+        sim.run(kicks)
+        sim.moments()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_particles(state.numpy())
+        sim.run(kicks)
+        vals, der = sim.moments()
+    barrier()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
+    h2d = state.numel() * 8
+    d2h = 8 * (2 + 2 * w.n_deriv) + 15 * 8 * (w.n_deriv + 1) + 4
+    e2e_value = ws * w.n_particles * kicks / (e2e_ms / 1000.0)
+    fp32_eps = vals
+    sim.close()
+
+    # ---- plain FP64 path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        sim64 = make(adpic.AD_PIC_FP64)
+        ms64, _ = measure(sim64, max(2, args.steps // 3), min(args.warmup, 3), kicks, torch)
+        sim64.close()
+        v64 = w.n_particles * kicks / (ms64 / 1000.0)
+        fp64 = {"value": ws * v64, "ms_per_step": ms64, "dtype": "f64",
+                "fp32_speedup": (ws * v64 and value / (ws * v64))}
+
+    # ---- roofline of the dominant kernel (gather + kick + push): algorithmic bytes per launch
+    # = particles x (read + write of 6 coordinates x C channels x 4 B) + one read of the
+    #   rest-frame field grid (3 x C x n^3 x 4 B)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    C = w.n_deriv + 1
+    nodes = w.grid[0] * w.grid[1] * w.grid[2]
+    alg_bytes = w.n_particles * 2 * 6 * C * 4 + 3 * C * nodes * 4
+    achieved = alg_bytes / (push_ms / 1000.0) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "kernel": "push_kernel (CIC gather + kick + dual maps)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": push_ms,
+            "traffic": traffic_from_profile(kernel_src_hash())}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        kicks_cpu = args.cpu_kicks
+        rate, dt = oracle_rate(w, kicks_cpu)
+        cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"{kicks_cpu} kicks of the {w.name} workload on the host cores ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(w, {"precision": "FP32 particles/deposit/FFT/field/push, FP64 geometry, "
+                                                           "Green's-function integrals and moment reductions"}),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": e2e_ms},
+                "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64,
+                "final_eps_fp32": [float(v) for v in fp32_eps]}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-kicks", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

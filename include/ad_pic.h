@@ -1,0 +1,174 @@
+/*
+ * ad_pic.h - C ABI of the GB300 dual-number 3D space-charge PIC library.
+ *
+ * The method (Qiang, Hao, Qiang, Wan, "A multi-language auto-differentiation
+ * module and its application to a parallel particle-in-cell code on
+ * distributed computers"):
+ *   - every particle coordinate, grid density, potential and field value is a
+ *     first-order dual number (value plus P derivatives), Sec. 2, Eqs. 1-4, and
+ *     Sec. 4 ("D r_i, D p_i", "D rho, D phi");
+ *   - one step is the split map M1(tau/2) M2(tau) M1(tau/2), Sec. 4, Eq. "map";
+ *   - M1 is the drift / thick-quadrupole map with dual k and dual tau, Sec. 4,
+ *     Eq. "quadtr" and its dual form; M2 is the space-charge kick, Sec. 4,
+ *     Eqs. for r(tau), p(tau);
+ *   - the Poisson equation is solved for the value and every derivative
+ *     channel (Sec. 4); here in 3D with open boundaries by a Hockney FFT
+ *     convolution with an integrated Green's function (the paper's 2D pipe
+ *     solver is not this path);
+ *   - each period ends with the dual emittance D eps = sqrt(D<x^2> D<px^2> -
+ *     (D<x px>)^2), Sec. 4.
+ *
+ * Conventions for every entry point:
+ *   - return 0 on success or a negative AD_PIC_ERR_* status; a failed call
+ *     leaves the handle destroyable; ad_pic_strerror() names the status;
+ *   - all pointers are HOST pointers unless a name ends in "_dev"; the caller
+ *     owns every buffer it passes, the library owns all device memory it
+ *     allocates and frees it in ad_pic_destroy();
+ *   - a handle is not thread-safe; it launches on one CUDA stream (its own,
+ *     or the one given to ad_pic_set_stream) and every call that returns
+ *     results synchronizes that stream before returning;
+ *   - coordinates are (x, px, y, py, z, delta): positions in m (lab frame,
+ *     z relative to the reference particle), momenta normalised by p0
+ *     (Sec. 4), delta = dp/p0;
+ *   - the particle state layout is [6][N][C] doubles, C = n_deriv + 1,
+ *     channel 0 the value and channel k the derivative w.r.t. parameter k.
+ */
+#ifndef AD_PIC_H
+#define AD_PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    AD_PIC_OK = 0,
+    AD_PIC_ERR_INVALID_ARG = -1, /* a size, pointer or enum is out of range */
+    AD_PIC_ERR_OOM = -2,         /* a device or host allocation failed */
+    AD_PIC_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    AD_PIC_ERR_STATE = -4,       /* call out of order (e.g. run before set_beam) */
+    AD_PIC_ERR_NONFINITE = -5,   /* a particle coordinate became NaN or Inf */
+    AD_PIC_ERR_OUT_OF_GRID = -6, /* a particle fell outside the grid stencil */
+    AD_PIC_ERR_TIMEOUT = -7,     /* a bounded device wait gave up */
+    AD_PIC_ERR_UNSUPPORTED = -8  /* valid request this build does not implement */
+};
+
+enum { AD_PIC_FP64 = 0, AD_PIC_FP32_MIXED = 1 };
+
+typedef struct ad_pic ad_pic; /* opaque handle */
+
+/* Grid nodes per dimension: powers of two in [8, 128]. */
+typedef struct {
+    int nx, ny, nz;
+} ad_pic_grid;
+
+/* The FODO period of Sec. 1 / Sec. 4: drift D1, focusing quad QF, drift D2,
+   defocusing quad QD, drift D3. deriv_slot[j] is the derivative slot
+   (0 .. n_deriv-1) of parameter j in the order (L_D1, L_QF, g_QF, L_D2, L_QD,
+   g_QD, L_D3) - the order of Sec. 3 and Sec. 4 - or -1 to hold it constant.
+   Derivatives are w.r.t. the gradient g in T/m; the normalised strength of
+   Sec. 4 is k = q g / p0 = g / (B rho). */
+typedef struct {
+    double L[5];       /* element lengths (m), > 0 */
+    double g[2];       /* QF, QD gradients (T/m), nonzero */
+    int kicks[5];      /* space-charge kicks per element, >= 1 */
+    int deriv_slot[7];
+} ad_pic_lattice;
+
+/* Reference particle and initial distribution. Per plane (x, y, z) the
+   initial particles are u = sqrt(eps beta) n1, p = sqrt(eps/beta) (n2 - alpha n1)
+   with eps = eps_n / (beta0 gamma0), then the sample mean is removed
+   (Sec. 4: initial distribution parameters may be AD variables).
+   twiss_deriv_slot gives the slots of (alpha_x, beta_x, eps_x, alpha_y,
+   beta_y, eps_y), eps the geometric rms emittance, or -1. */
+typedef struct {
+    double kinetic_eV, mass_eV, charge_e, bunch_charge_C;
+    double eps_n[3];   /* normalised rms emittances (m rad), > 0 */
+    double alpha[3];
+    double beta[3];    /* m, > 0 */
+    int twiss_deriv_slot[6];
+} ad_pic_beam;
+
+/* Create a handle for n_particles >= 1 macroparticles on the given grid with
+   n_deriv in {7, 13} derivative slots and precision AD_PIC_FP64 (every step
+   in FP64) or AD_PIC_FP32_MIXED (particles, deposit, FFT, field and push in
+   FP32; grid geometry, Green's-function integrals and all moment reductions
+   in FP64). Allocates every device buffer; *out is NULL on failure. */
+int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int precision, ad_pic** out);
+
+/* Set the reference particle and bunch charge. If normals is not NULL it is
+   [6][N] standard-normal draws (n1,n2 per plane x, y, z) and the initial
+   dual particles are generated on the device from them; if NULL only the
+   physics constants are set and particles must come from ad_pic_set_particles. */
+int ad_pic_set_beam(ad_pic* h, const ad_pic_beam* beam, const double* normals);
+
+/* Upload / download the dual particle state [6][N][C] (FP64 on the host,
+   rounded to the handle's precision on upload). Resets the kick counter
+   only in ad_pic_set_particles. */
+int ad_pic_set_particles(ad_pic* h, const double* state);
+int ad_pic_get_particles(const ad_pic* h, double* state);
+
+/* Set the lattice and recompute the per-kick dual map coefficients (FP64 on
+   the host, Eqs. 1-4 applied to the quad matrices of Sec. 4). */
+int ad_pic_set_lattice(ad_pic* h, const ad_pic_lattice* lattice);
+
+/* Advance n_steps >= 0 space-charge kicks (each M1(tau/2) M2(tau) M1(tau/2)),
+   continuing the kick counter; moments are reduced at every period end and
+   after the last kick. Synchronizes before returning; returns
+   AD_PIC_ERR_OUT_OF_GRID / _NONFINITE if a kernel flagged a particle. */
+int ad_pic_run(ad_pic* h, int n_steps);
+
+/* Emittances of the latest moment record: values[2] = (eps_x, eps_y),
+   geometric rms (m rad), centred moments; derivs[2*n_deriv] row-major
+   d eps_x / d p_k then d eps_y / d p_k. */
+int ad_pic_moments(const ad_pic* h, double* values, double* derivs);
+
+/* Raw dual moments of the latest record, mom[3][5][C]: per plane (x, y, z)
+   the means <u>, <p>, <u^2>, <u p>, <p^2> over particles (FP64). */
+int ad_pic_moments_full(const ad_pic* h, double* mom);
+
+/* Number of moment records kept since the last set_beam/set_particles and
+   a copy of them, hist[n][3][5][C]; record 0 is the initial state. */
+int ad_pic_history(const ad_pic* h, double* hist, int max_records, int* n_records);
+
+/* Use an external CUDA stream (a cudaStream_t passed as void*); NULL returns
+   to the handle's own stream. Drops captured graphs. */
+int ad_pic_set_stream(ad_pic* h, void* stream);
+
+/* Capture each distinct run shape in a CUDA graph and replay it (default on). */
+int ad_pic_set_graphs(ad_pic* h, int enable);
+
+/* Per-kernel device timing with CUDA events recorded on the handle's stream
+   around every launch of the selected kernel classes (bit i = class i, see
+   ad_pic_kernel_name). ad_pic_timing returns per class the accumulated
+   milliseconds and launch counts since the mask was last set; setting the
+   same mask again only resets the accumulators. */
+int ad_pic_set_timing(ad_pic* h, unsigned mask);
+int ad_pic_timing(const ad_pic* h, double* ms, int64_t* launches, int n_classes);
+const char* ad_pic_kernel_name(int cls);
+int ad_pic_kernel_classes(void);
+
+/* Kernels launched by ad_pic_run on this handle so far (graph replays count
+   every kernel node they run). */
+int ad_pic_launches(const ad_pic* h, int64_t* n);
+
+/* Run one stage of the step on the current state and copy its output, for
+   parity tests. stage 0: grid geometry, out[6] = origin x,y,z (m), h x,y,z
+   (lab, m); 1: deposit, out[C][nz][ny][nx] node charges (C); 2: potential,
+   out[C][nz][ny][nx] (V); 3: field, out[3][C][nz][ny][nx] rest-frame V/m;
+   4: gather+kick M2(tau) of kick index `kick` with no map, particles updated
+   in place (out unused). Stages 1-4 use the geometry of the current state. */
+int ad_pic_stage(ad_pic* h, int stage, int64_t kick, double* out);
+
+/* Derived constants: out[8] = gamma0, beta0, p0 (kg m/s), B rho (T m),
+   kappa_perp, kappa_z (1/(V/m * m)), macroparticle charge (C), q (C). */
+int ad_pic_constants(const ad_pic* h, double* out);
+
+void ad_pic_destroy(ad_pic* h);
+const char* ad_pic_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

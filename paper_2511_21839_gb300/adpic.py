@@ -1,0 +1,287 @@
+"""Thin ctypes binding of the C ABI in include/ad_pic.h (argument marshalling only).
+
+Every entry point keeps its C name. The library must be built (see build.py);
+importing this module on a machine where libadpic.so is missing raises at
+load time: there is no CPU fallback.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadpic.so")
+
+AD_PIC_FP64 = 0
+AD_PIC_FP32_MIXED = 1
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error", -4: "call out of order",
+          -5: "non-finite particle coordinate", -6: "particle outside the grid stencil",
+          -7: "bounded device wait timed out", -8: "unsupported"}
+
+
+class ad_pic_grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int)]
+
+
+class ad_pic_lattice(ct.Structure):
+    _fields_ = [("L", ct.c_double * 5), ("g", ct.c_double * 2), ("kicks", ct.c_int * 5), ("deriv_slot", ct.c_int * 7)]
+
+
+class ad_pic_beam(ct.Structure):
+    _fields_ = [("kinetic_eV", ct.c_double), ("mass_eV", ct.c_double), ("charge_e", ct.c_double),
+                ("bunch_charge_C", ct.c_double), ("eps_n", ct.c_double * 3), ("alpha", ct.c_double * 3),
+                ("beta", ct.c_double * 3), ("twiss_deriv_slot", ct.c_int * 6)]
+
+
+class AdPicError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libadpic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (paper_2511_21839_gb300/build.py)")
+        L = ct.CDLL(LIB_PATH)
+        vp = ct.c_void_p
+        dp = ct.POINTER(ct.c_double)
+        sig = {
+            "ad_pic_create": (ct.c_int, [ct.POINTER(ad_pic_grid), ct.c_int64, ct.c_int, ct.c_int, ct.POINTER(vp)]),
+            "ad_pic_set_beam": (ct.c_int, [vp, ct.POINTER(ad_pic_beam), dp]),
+            "ad_pic_set_particles": (ct.c_int, [vp, dp]),
+            "ad_pic_get_particles": (ct.c_int, [vp, dp]),
+            "ad_pic_set_lattice": (ct.c_int, [vp, ct.POINTER(ad_pic_lattice)]),
+            "ad_pic_run": (ct.c_int, [vp, ct.c_int]),
+            "ad_pic_moments": (ct.c_int, [vp, dp, dp]),
+            "ad_pic_moments_full": (ct.c_int, [vp, dp]),
+            "ad_pic_history": (ct.c_int, [vp, dp, ct.c_int, ct.POINTER(ct.c_int)]),
+            "ad_pic_set_stream": (ct.c_int, [vp, vp]),
+            "ad_pic_set_graphs": (ct.c_int, [vp, ct.c_int]),
+            "ad_pic_set_timing": (ct.c_int, [vp, ct.c_uint]),
+            "ad_pic_timing": (ct.c_int, [vp, dp, ct.POINTER(ct.c_int64), ct.c_int]),
+            "ad_pic_kernel_name": (ct.c_char_p, [ct.c_int]),
+            "ad_pic_kernel_classes": (ct.c_int, []),
+            "ad_pic_stage": (ct.c_int, [vp, ct.c_int, ct.c_int64, dp]),
+            "ad_pic_constants": (ct.c_int, [vp, dp]),
+            "ad_pic_launches": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
+            "ad_pic_destroy": (None, [vp]),
+            "ad_pic_strerror": (ct.c_char_p, [ct.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _ck(fn, st):
+    if st != 0:
+        raise AdPicError(fn, st)
+
+
+# ------------------------------------------------------------------ C names
+
+def ad_pic_create(grid, n_particles, n_deriv, precision):
+    h = ct.c_void_p()
+    g = ad_pic_grid(*grid)
+    _ck("ad_pic_create", lib().ad_pic_create(ct.byref(g), int(n_particles), int(n_deriv), int(precision), ct.byref(h)))
+    return h
+
+
+def ad_pic_set_beam(h, beam: ad_pic_beam, normals=None):
+    nrm = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64)
+    _ck("ad_pic_set_beam", lib().ad_pic_set_beam(h, ct.byref(beam), None if nrm is None else _p(nrm)))
+
+
+def ad_pic_set_particles(h, state):
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    _ck("ad_pic_set_particles", lib().ad_pic_set_particles(h, _p(s)))
+
+
+def ad_pic_get_particles(h, out):
+    _ck("ad_pic_get_particles", lib().ad_pic_get_particles(h, _p(out)))
+    return out
+
+
+def ad_pic_set_lattice(h, lat: ad_pic_lattice):
+    _ck("ad_pic_set_lattice", lib().ad_pic_set_lattice(h, ct.byref(lat)))
+
+
+def ad_pic_run(h, n_steps):
+    st = lib().ad_pic_run(h, int(n_steps))
+    _ck("ad_pic_run", st)
+
+
+def ad_pic_moments(h, P):
+    v = np.zeros(2)
+    d = np.zeros(2 * P)
+    _ck("ad_pic_moments", lib().ad_pic_moments(h, _p(v), _p(d)))
+    return v, d.reshape(2, P)
+
+
+def ad_pic_moments_full(h, C):
+    m = np.zeros((3, 5, C))
+    _ck("ad_pic_moments_full", lib().ad_pic_moments_full(h, _p(m)))
+    return m
+
+
+def ad_pic_history(h, C):
+    n = ct.c_int()
+    _ck("ad_pic_history", lib().ad_pic_history(h, None, 0, ct.byref(n)))
+    out = np.zeros((n.value, 3, 5, C))
+    if n.value:
+        _ck("ad_pic_history", lib().ad_pic_history(h, _p(out), n.value, ct.byref(n)))
+    return out
+
+
+def ad_pic_set_stream(h, stream_ptr):
+    _ck("ad_pic_set_stream", lib().ad_pic_set_stream(h, ct.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def ad_pic_set_graphs(h, enable):
+    _ck("ad_pic_set_graphs", lib().ad_pic_set_graphs(h, int(bool(enable))))
+
+
+def ad_pic_set_timing(h, mask):
+    _ck("ad_pic_set_timing", lib().ad_pic_set_timing(h, int(mask)))
+
+
+def ad_pic_timing(h):
+    n = lib().ad_pic_kernel_classes()
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _ck("ad_pic_timing", lib().ad_pic_timing(h, _p(ms), cnt.ctypes.data_as(ct.POINTER(ct.c_int64)), n))
+    return {lib().ad_pic_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+
+def ad_pic_kernel_classes():
+    return int(lib().ad_pic_kernel_classes())
+
+
+def ad_pic_kernel_name(cls):
+    return lib().ad_pic_kernel_name(int(cls)).decode()
+
+
+def ad_pic_stage(h, stage, kick, out=None):
+    _ck("ad_pic_stage", lib().ad_pic_stage(h, int(stage), int(kick), None if out is None else _p(out)))
+    return out
+
+
+def ad_pic_launches(h):
+    n = ct.c_int64()
+    _ck("ad_pic_launches", lib().ad_pic_launches(h, ct.byref(n)))
+    return n.value
+
+
+def ad_pic_constants(h):
+    out = np.zeros(8)
+    _ck("ad_pic_constants", lib().ad_pic_constants(h, _p(out)))
+    keys = ["gamma0", "beta0", "p0", "brho", "kappa_perp", "kappa_z", "q_macro", "q"]
+    return dict(zip(keys, out.tolist()))
+
+
+def ad_pic_destroy(h):
+    if h:
+        lib().ad_pic_destroy(h)
+
+
+def ad_pic_strerror(status):
+    return lib().ad_pic_strerror(int(status)).decode()
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+def make_beam(b) -> ad_pic_beam:
+    """ad_pic_beam from any object with the fields of inputs.Beam."""
+    return ad_pic_beam(b.kinetic_eV, b.mass_eV, b.charge_e, b.bunch_charge_C, (ct.c_double * 3)(*b.eps_n),
+                       (ct.c_double * 3)(*b.alpha), (ct.c_double * 3)(*b.beta), (ct.c_int * 6)(*b.twiss_slot))
+
+
+def make_lattice(lat) -> ad_pic_lattice:
+    """ad_pic_lattice from any object with the fields of inputs.Lattice."""
+    return ad_pic_lattice((ct.c_double * 5)(*lat.L), (ct.c_double * 2)(*lat.g), (ct.c_int * 5)(*lat.kicks),
+                          (ct.c_int * 7)(*lat.deriv_slot))
+
+
+class ADPIC:
+    """One simulation handle (owns the device memory of one dual PIC instance)."""
+
+    def __init__(self, grid, n_particles, n_deriv=7, precision=AD_PIC_FP64):
+        self.grid = tuple(grid)
+        self.N = int(n_particles)
+        self.P = int(n_deriv)
+        self.C = self.P + 1
+        self.precision = precision
+        self.h = ad_pic_create(self.grid, self.N, self.P, precision)
+
+    def close(self):
+        if self.h:
+            ad_pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_beam(self, beam, normals=None):
+        ad_pic_set_beam(self.h, make_beam(beam), normals)
+
+    def set_lattice(self, lat):
+        ad_pic_set_lattice(self.h, make_lattice(lat))
+
+    def set_particles(self, state):
+        ad_pic_set_particles(self.h, state)
+
+    def get_particles(self):
+        return ad_pic_get_particles(self.h, np.zeros((6, self.N, self.C)))
+
+    def run(self, n_steps):
+        ad_pic_run(self.h, n_steps)
+
+    def moments(self):
+        return ad_pic_moments(self.h, self.P)
+
+    def moments_full(self):
+        return ad_pic_moments_full(self.h, self.C)
+
+    def history(self):
+        return ad_pic_history(self.h, self.C)
+
+    def stage(self, stage, kick=0):
+        nx, ny, nz = self.grid
+        shapes = {0: (6,), 1: (self.C, nz, ny, nx), 2: (self.C, nz, ny, nx), 3: (3, self.C, nz, ny, nx)}
+        out = np.zeros(shapes[stage]) if stage in shapes else None
+        return ad_pic_stage(self.h, stage, kick, out)
+
+    def constants(self):
+        return ad_pic_constants(self.h)
+
+    def launches(self):
+        return ad_pic_launches(self.h)
+
+    def set_stream(self, ptr):
+        ad_pic_set_stream(self.h, ptr)
+
+    def set_graphs(self, on):
+        ad_pic_set_graphs(self.h, on)
+
+    def set_timing(self, mask):
+        ad_pic_set_timing(self.h, mask)
+
+    def timing(self):
+        return ad_pic_timing(self.h)

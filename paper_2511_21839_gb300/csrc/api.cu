@@ -1,0 +1,908 @@
+// Host runtime behind the C ABI of include/ad_pic.h: handle and device memory,
+// per-kick dual map coefficients (host FP64 dual arithmetic, Sec. 2 Eqs. 1-4
+// applied to the quadrupole maps of Sec. 4), the split-step sequence of one
+// run (Sec. 4, Eq. "map"), CUDA-graph capture and replay, per-kernel event
+// timing, and the stage entry points used by the parity tests.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "ad_pic.h"
+#include "common.cuh"
+
+using namespace adpic;
+
+namespace {
+
+// CODATA 2018
+constexpr double kC = 299792458.0;
+constexpr double kQE = 1.602176634e-19;
+
+constexpr int kMaxCP = 16;
+constexpr int kClasses = 8;
+const char* kClassNames[kClasses] = {"push", "boundary", "deposit", "green", "fft", "field", "geometry", "misc"};
+enum { K_PUSH = 0, K_BOUNDARY, K_DEPOSIT, K_GREEN, K_FFT, K_FIELD, K_GEOM, K_MISC };
+
+// ------------------------------------------------------------------ host dual numbers
+// value v[0] and derivatives v[1..]; all 16 slots are carried, unused ones stay 0
+struct HD {
+    double v[kMaxCP];
+};
+HD hc(double x) { HD r{}; r.v[0] = x; return r; }
+HD hvar(double x, int slot) { HD r = hc(x); if (slot >= 0) r.v[slot + 1] = 1.0; return r; }
+HD hadd(const HD& a, const HD& b) { HD r; for (int k = 0; k < kMaxCP; ++k) r.v[k] = a.v[k] + b.v[k]; return r; }
+HD hneg(const HD& a) { HD r; for (int k = 0; k < kMaxCP; ++k) r.v[k] = -a.v[k]; return r; }
+HD hmul(const HD& a, const HD& b) {           // Eq. 2
+    HD r;
+    r.v[0] = a.v[0] * b.v[0];
+    for (int k = 1; k < kMaxCP; ++k) r.v[k] = b.v[0] * a.v[k] + a.v[0] * b.v[k];
+    return r;
+}
+HD hdiv(const HD& a, const HD& b) {           // Eq. 3
+    HD r;
+    r.v[0] = a.v[0] / b.v[0];
+    for (int k = 1; k < kMaxCP; ++k) r.v[k] = (a.v[k] * b.v[0] - b.v[k] * a.v[0]) / (b.v[0] * b.v[0]);
+    return r;
+}
+HD hfn(const HD& a, double h, double hp) {    // Eq. 4
+    HD r;
+    r.v[0] = h;
+    for (int k = 1; k < kMaxCP; ++k) r.v[k] = hp * a.v[k];
+    return r;
+}
+HD hsqrt(const HD& a) { double s = std::sqrt(a.v[0]); return hfn(a, s, 0.5 / s); }
+HD hsin(const HD& a) { return hfn(a, std::sin(a.v[0]), std::cos(a.v[0])); }
+HD hcos(const HD& a) { return hfn(a, std::cos(a.v[0]), -std::sin(a.v[0])); }
+HD hsinh(const HD& a) { return hfn(a, std::sinh(a.v[0]), std::cosh(a.v[0])); }
+HD hcosh(const HD& a) { return hfn(a, std::cosh(a.v[0]), std::sinh(a.v[0])); }
+
+struct HMap { HD m[3][4]; };   // per plane (m11, m12, m21, m22)
+
+// one transverse plane over step t with focusing strength kp (Sec. 4: cos/sin
+// in the focusing plane, cosh/sinh in the defocusing plane, drift at kp = 0)
+void plane_map(const HD& kp, const HD& t, HD* m) {
+    if (kp.v[0] > 0.0) {
+        HD w = hsqrt(kp), th = hmul(w, t), c = hcos(th), s = hsin(th);
+        m[0] = c; m[1] = hdiv(s, w); m[2] = hneg(hmul(w, s)); m[3] = c;
+    } else if (kp.v[0] < 0.0) {
+        HD w = hsqrt(hneg(kp)), th = hmul(w, t), c = hcosh(th), s = hsinh(th);
+        m[0] = c; m[1] = hdiv(s, w); m[2] = hmul(w, s); m[3] = c;
+    } else {
+        m[0] = hc(1.0); m[1] = t; m[2] = hc(0.0); m[3] = hc(1.0);
+    }
+}
+
+HMap compose(const HMap& B, const HMap& A) {   // B after A
+    HMap r;
+    for (int p = 0; p < 3; ++p) {
+        const HD* a = A.m[p];
+        const HD* b = B.m[p];
+        r.m[p][0] = hadd(hmul(b[0], a[0]), hmul(b[1], a[2]));
+        r.m[p][1] = hadd(hmul(b[0], a[1]), hmul(b[1], a[3]));
+        r.m[p][2] = hadd(hmul(b[2], a[0]), hmul(b[3], a[2]));
+        r.m[p][3] = hadd(hmul(b[2], a[1]), hmul(b[3], a[3]));
+    }
+    return r;
+}
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+}  // namespace
+
+struct ad_pic {
+    int prec = 0, P = 7, C = 8, CP = 8;
+    int nx = 0, ny = 0, nz = 0;
+    int64_t N = 0;
+    bool beam_set = false, particles_set = false, lattice_set = false, coef_dirty = true;
+    double gamma0 = 0, beta0 = 0, p0 = 0, brho = 0, kperp = 0, kz = 0, qm = 0, q = 0;
+    ad_pic_lattice lat{};
+    int kpp = 0;
+    int64_t kick = 0;
+    bool first_record = true;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    // device memory
+    void* state = nullptr;
+    void* rho = nullptr;
+    void* phi = nullptr;
+    void* E = nullptr;
+    void* X1 = nullptr;
+    void* X2 = nullptr;
+    void* G = nullptr;
+    void* Gtmp = nullptr;
+    void* Ghat = nullptr;
+    double* corner = nullptr;
+    void* dct[3] = {nullptr, nullptr, nullptr};
+    void* tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    GeomDev* geom = nullptr;
+    void* mm = nullptr;
+    void* chmax = nullptr;
+    int* err = nullptr;
+    double* partial = nullptr;
+    double* records = nullptr;
+    int records_cap = 0;
+    double* staging = nullptr;      // FP64 [6][N][C] staging buffer of set/get_particles
+    int64_t launches = 0;           // kernels launched by ad_pic_run so far
+    std::map<std::tuple<int, int, int, unsigned>, int64_t> graph_launches;
+    std::vector<void*> allocs;
+    // per-kick coefficients of the handle's precision (raw MapCoef / KickCoef)
+    std::vector<unsigned char> half, comp, kcoef;
+    std::vector<double> hist;   // records [3][5][C]
+    // graphs
+    bool use_graphs = true;
+    std::map<std::tuple<int, int, int, unsigned>, cudaGraphExec_t> graphs;
+    // timing
+    unsigned tmask = 0;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> ev_class;
+    int ev_used = 0;
+    double tms[kClasses] = {0};
+    int64_t tcount[kClasses] = {0};
+};
+
+namespace {
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            std::fprintf(stderr, "ad_pic: %s failed: %s\n", #call, cudaGetErrorString(e_));   \
+            return AD_PIC_ERR_CUDA;                                                            \
+        }                                                                                      \
+    } while (0)
+
+int dalloc(ad_pic* h, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; cudaGetLastError(); return AD_PIC_ERR_OOM; }
+    h->allocs.push_back(*p);
+    return AD_PIC_OK;
+}
+
+void free_graphs(ad_pic* h) {
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+// event timing around the launches of the selected kernel classes
+void tbegin(ad_pic* h, int cls, bool capturing) {
+    if (!((h->tmask >> cls) & 1u)) return;
+    while ((int)h->events.size() < h->ev_used + 2) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->events.push_back(e);
+    }
+    if ((int)h->ev_class.size() < (h->ev_used + 2) / 2) h->ev_class.resize((h->ev_used + 2) / 2);
+    h->ev_class[h->ev_used / 2] = cls;
+    if (capturing) cudaEventRecordWithFlags(h->events[h->ev_used], h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(h->events[h->ev_used], h->stream);
+}
+void tend(ad_pic* h, int cls, bool capturing) {
+    if (!((h->tmask >> cls) & 1u)) return;
+    if (capturing) cudaEventRecordWithFlags(h->events[h->ev_used + 1], h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(h->events[h->ev_used + 1], h->stream);
+    h->ev_used += 2;
+}
+void tcollect(ad_pic* h, int pairs) {
+    for (int j = 0; j < pairs; ++j) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->events[2 * j], h->events[2 * j + 1]) == cudaSuccess) {
+            h->tms[h->ev_class[j]] += ms;
+            h->tcount[h->ev_class[j]] += 1;
+        }
+    }
+    cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ typed implementation
+
+template <typename T, int C, int CP>
+struct Impl {
+    using M = MapCoef<T, CP>;
+    using K = KickCoef<T, CP>;
+
+    static T* st(ad_pic* h) { return (T*)h->state; }
+
+    static M to_map(const HMap& a) {
+        M r;
+        for (int p = 0; p < 3; ++p)
+            for (int e = 0; e < 4; ++e)
+                for (int k = 0; k < CP; ++k) r.m[p][e][k] = (T)a.m[p][e].v[k];
+        return r;
+    }
+    static M identity() {
+        HMap I;
+        for (int p = 0; p < 3; ++p) { I.m[p][0] = hc(1); I.m[p][1] = hc(0); I.m[p][2] = hc(0); I.m[p][3] = hc(1); }
+        return to_map(I);
+    }
+
+    // per-kick dual coefficients of one period
+    static void build_coef(ad_pic* h) {
+        const ad_pic_lattice& L = h->lat;
+        const int len_param[5] = {0, 1, 3, 4, 6};
+        int kpp = 0;
+        for (int e = 0; e < 5; ++e) kpp += L.kicks[e];
+        h->kpp = kpp;
+        std::vector<HMap> halfm(kpp);
+        std::vector<K> kc(kpp);
+        int s = 0;
+        for (int e = 0; e < 5; ++e) {
+            HD Le = hvar(L.L[e], L.deriv_slot[len_param[e]]);
+            HD tau = hdiv(Le, hc((double)L.kicks[e]));        // D tau = D L / n (Sec. 4)
+            HD t = hmul(tau, hc(0.5));
+            HD kx = hc(0.0), ky = hc(0.0);
+            if (e == 1 || e == 3) {
+                const int gi = e == 1 ? 0 : 1;
+                HD g = hvar(L.g[gi], L.deriv_slot[e == 1 ? 2 : 5]);
+                kx = hdiv(g, hc(h->brho));                   // k = q g / p0
+                ky = hneg(kx);
+            }
+            HMap m;
+            plane_map(kx, t, m.m[0]);
+            plane_map(ky, t, m.m[1]);
+            m.m[2][0] = hc(1.0);
+            m.m[2][1] = hdiv(t, hc(h->gamma0 * h->gamma0));   // z += t delta / gamma0^2
+            m.m[2][2] = hc(0.0);
+            m.m[2][3] = hc(1.0);
+            HD ap = hmul(hc(h->kperp), tau), az = hmul(hc(h->kz), tau);
+            K kk;
+            for (int k = 0; k < CP; ++k) { kk.a[0][k] = (T)ap.v[k]; kk.a[1][k] = (T)ap.v[k]; kk.a[2][k] = (T)az.v[k]; }
+            for (int j = 0; j < L.kicks[e]; ++j, ++s) { halfm[s] = m; kc[s] = kk; }
+        }
+        h->half.resize(sizeof(M) * kpp);
+        h->comp.resize(sizeof(M) * kpp);
+        h->kcoef.resize(sizeof(K) * kpp);
+        for (int i = 0; i < kpp; ++i) {
+            M a = to_map(halfm[i]);
+            M c = to_map(compose(halfm[(i + 1) % kpp], halfm[i]));
+            std::memcpy(h->half.data() + sizeof(M) * i, &a, sizeof(M));
+            std::memcpy(h->comp.data() + sizeof(M) * i, &c, sizeof(M));
+            std::memcpy(h->kcoef.data() + sizeof(K) * i, &kc[i], sizeof(K));
+        }
+        h->coef_dirty = false;
+    }
+    static const M& half(ad_pic* h, int64_t g) { return ((const M*)h->half.data())[g % h->kpp]; }
+    static const M& comp(ad_pic* h, int64_t g) { return ((const M*)h->comp.data())[g % h->kpp]; }
+    static const K& kick(ad_pic* h, int64_t g) { return ((const K*)h->kcoef.data())[g % h->kpp]; }
+
+    static FFTDims dims(ad_pic* h) {
+        FFTDims d;
+        d.nx = h->nx; d.ny = h->ny; d.nz = h->nz;
+        d.Mx = 2 * h->nx; d.My = 2 * h->ny; d.Mz = 2 * h->nz;
+        d.lx = ilog2(d.Mx); d.ly = ilog2(d.My); d.lz = ilog2(d.Mz);
+        d.C = C; d.CP = CP; d.npair = C / 2;
+        return d;
+    }
+
+    // geometry -> deposit -> Green -> convolution -> field for the current state
+    static void enqueue_field(ad_pic* h, bool cap) {
+        cudaStream_t s = h->stream;
+        const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
+        tbegin(h, K_GEOM, cap);
+        launch_geom<T>((Ord<T>*)h->mm, h->nx, h->ny, h->nz, h->gamma0, h->geom, (Ord<T>*)h->chmax, CP, s);
+        tend(h, K_GEOM, cap);
+        tbegin(h, K_MISC, cap);
+        cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s);
+        tend(h, K_MISC, cap);
+        tbegin(h, K_DEPOSIT, cap);
+        launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err, s);
+        tend(h, K_DEPOSIT, cap);
+        tbegin(h, K_MISC, cap);
+        launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
+        tend(h, K_MISC, cap);
+        tbegin(h, K_GREEN, cap);
+        launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
+                        (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2], s);
+        tend(h, K_GREEN, cap);
+        tbegin(h, K_FFT, cap);
+        FFTDims d = dims(h);
+        launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
+                           (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
+                           (const V2<T>*)h->tw[3], (const V2<T>*)h->tw[4], (const V2<T>*)h->tw[5],
+                           (const Ord<T>*)h->chmax, s);
+        tend(h, K_FFT, cap);
+        tbegin(h, K_FIELD, cap);
+        launch_field<T>((const T*)h->phi, h->geom, h->nx, h->ny, h->nz, CP, (T*)h->E, s);
+        tend(h, K_FIELD, cap);
+    }
+
+    static void record(ad_pic* h, int r, bool cap) {
+        tbegin(h, K_MISC, cap);
+        launch_moments_reduce(h->partial, boundary_blocks(), CP, h->N, h->records + (int64_t)r * 15 * CP, h->stream);
+        tend(h, K_MISC, cap);
+    }
+
+    // kernels launched by one enqueue_field (geometry 1, deposit 1, chmax 1,
+    // Green's function 5, convolution 5, field 1; the memset is not a kernel)
+    static constexpr int kFieldLaunches = 14;
+
+    // the launch sequence of one run; returns the number of moment records
+    static int enqueue_run(ad_pic* h, int64_t g0, int n, bool first, bool cap) {
+        cudaStream_t s = h->stream;
+        const int nb = boundary_blocks();
+        int nrec = 0;
+        cudaMemsetAsync(h->err, 0, sizeof(int), s);
+        if (n == 0) {
+            tbegin(h, K_BOUNDARY, cap);
+            launch_boundary<T, C, CP>(st(h), h->N, identity(), false, true, h->partial, nb, (Ord<T>*)h->mm, s);
+            tend(h, K_BOUNDARY, cap);
+            record(h, nrec++, cap);
+            return nrec;
+        }
+        // opening half map M1(tau/2) of the first kick (+ initial moments)
+        tbegin(h, K_BOUNDARY, cap);
+        launch_boundary<T, C, CP>(st(h), h->N, half(h, g0), true, first, h->partial, nb, (Ord<T>*)h->mm, s);
+        tend(h, K_BOUNDARY, cap);
+        if (first) record(h, nrec++, cap);
+        for (int i = 0; i < n; ++i) {
+            const int64_t g = g0 + i;
+            enqueue_field(h, cap);
+            const bool last = i == n - 1;
+            const bool pend = ((g + 1) % h->kpp) == 0;
+            if (last || pend) {
+                // M2(tau) then the closing M1(tau/2); moments at the period end,
+                // then the next kick's opening M1(tau/2)
+                tbegin(h, K_PUSH, cap);
+                launch_push<T, C, CP>(st(h), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, half(h, g),
+                                      kick(h, g), false, (Ord<T>*)h->mm, h->err, s);
+                tend(h, K_PUSH, cap);
+                tbegin(h, K_BOUNDARY, cap);
+                launch_boundary<T, C, CP>(st(h), h->N, half(h, g + 1), !last, true, h->partial, nb, (Ord<T>*)h->mm,
+                                          s);
+                tend(h, K_BOUNDARY, cap);
+                record(h, nrec++, cap);
+            } else {
+                // M2(tau) then M1(tau/2) of this kick composed with M1(tau/2) of the next
+                tbegin(h, K_PUSH, cap);
+                launch_push<T, C, CP>(st(h), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, comp(h, g),
+                                      kick(h, g), true, (Ord<T>*)h->mm, h->err, s);
+                tend(h, K_PUSH, cap);
+            }
+        }
+        return nrec;
+    }
+
+    static int run(ad_pic* h, int n) {
+        if (h->coef_dirty) build_coef(h);
+        const int64_t g0 = h->kick;
+        const bool first = h->first_record;
+        // records needed
+        int need = (first ? 1 : 0) + 1 + (int)(n / (h->kpp > 0 ? h->kpp : 1)) + 1;
+        if (need > h->records_cap) {
+            if (h->records) cudaFree(h->records);
+            for (auto& p : h->allocs) if (p == h->records) p = nullptr;
+            h->records = nullptr;
+            int st_ = dalloc(h, (void**)&h->records, sizeof(double) * 15 * CP * need);
+            if (st_) return st_;
+            h->records_cap = need;
+            free_graphs(h);
+        }
+        h->ev_used = 0;
+        int nrec = 0;
+        {
+            // kernel launches of this run: opening boundary (+ reduce), per kick the field
+            // kernels and the push, per moment record a boundary and a reduce
+            const int nr = count_records(h, g0, n, first);
+            int64_t l = 0;
+            if (n == 0) l = 2;
+            else l = 1 + (int64_t)n * (kFieldLaunches + 1) + 2 * (int64_t)nr - (first ? 1 : 0);
+            h->launches += l;
+        }
+        if (h->use_graphs) {
+            auto key = std::make_tuple((int)(g0 % h->kpp), n, first ? 1 : 0, h->tmask);
+            auto it = h->graphs.find(key);
+            if (it == h->graphs.end()) {
+                cudaGraph_t graph;
+                CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+                nrec = enqueue_run(h, g0, n, first, true);
+                CK(cudaStreamEndCapture(h->stream, &graph));
+                cudaGraphExec_t ex;
+                CK(cudaGraphInstantiate(&ex, graph, 0));
+                cudaGraphDestroy(graph);
+                it = h->graphs.emplace(key, ex).first;
+            } else {
+                // replay: recompute the record count and event use without launching
+                nrec = count_records(h, g0, n, first);
+                h->ev_used = count_events(h, n, first, nrec);
+            }
+            CK(cudaGraphLaunch(it->second, h->stream));
+        } else {
+            nrec = enqueue_run(h, g0, n, first, false);
+            CK(cudaGetLastError());
+        }
+        std::vector<double> rec((size_t)nrec * 15 * CP);
+        int errw = 0;
+        CK(cudaMemcpyAsync(rec.data(), h->records, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&errw, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (h->tmask) tcollect(h, h->ev_used / 2);
+        for (int r = 0; r < nrec; ++r)
+            for (int q = 0; q < 15; ++q)
+                for (int k = 0; k < C; ++k) h->hist.push_back(rec[((size_t)r * 15 + q) * CP + k]);
+        h->kick += n;
+        h->first_record = false;
+        if (errw & kErrNonfinite) return AD_PIC_ERR_NONFINITE;
+        if (errw & kErrOutOfGrid) return AD_PIC_ERR_OUT_OF_GRID;
+        return AD_PIC_OK;
+    }
+
+    static int count_records(ad_pic* h, int64_t g0, int n, bool first) {
+        if (n == 0) return 1;
+        int r = first ? 1 : 0;
+        for (int i = 0; i < n; ++i) {
+            const int64_t g = g0 + i;
+            if (i == n - 1 || ((g + 1) % h->kpp) == 0) ++r;
+        }
+        return r;
+    }
+    static int count_events(ad_pic* h, int n, bool first, int nrec) {
+        auto on = [&](int c) { return (int)((h->tmask >> c) & 1u); };
+        if (n == 0) return 2 * (on(K_BOUNDARY) + on(K_MISC));
+        int pend = nrec - (first ? 1 : 0);   // boundary+record pairs inside the loop
+        int e = on(K_BOUNDARY) + (first ? on(K_MISC) : 0);
+        e += n * (on(K_GEOM) + 2 * on(K_MISC) + on(K_DEPOSIT) + on(K_GREEN) + on(K_FFT) + on(K_FIELD) + on(K_PUSH));
+        e += pend * (on(K_BOUNDARY) + on(K_MISC));
+        return 2 * e;
+    }
+
+    static int set_beam(ad_pic* h, const ad_pic_beam* b, const double* normals) {
+        h->q = b->charge_e * kQE;
+        const double mass_kg = b->mass_eV * kQE / (kC * kC);
+        h->gamma0 = 1.0 + b->kinetic_eV / b->mass_eV;
+        h->beta0 = std::sqrt(1.0 - 1.0 / (h->gamma0 * h->gamma0));
+        h->p0 = h->gamma0 * h->beta0 * mass_kg * kC;
+        h->brho = h->p0 / h->q;
+        const double v0 = h->beta0 * kC;
+        h->kperp = h->q / (h->gamma0 * h->p0 * v0);
+        h->kz = h->q / (h->p0 * v0);
+        h->qm = b->bunch_charge_C / (double)h->N;
+        h->beam_set = true;
+        h->coef_dirty = true;
+        free_graphs(h);
+        if (!normals) return AD_PIC_OK;
+        // per-plane dual coefficients u = a n1, p = b (n2 - alpha n1)
+        std::vector<double> coef(3 * 3 * CP + 6, 0.0);
+        const double bg = h->beta0 * h->gamma0;
+        for (int pl = 0; pl < 3; ++pl) {
+            const int sa = pl < 2 ? b->twiss_deriv_slot[3 * pl + 0] : -1;
+            const int sb = pl < 2 ? b->twiss_deriv_slot[3 * pl + 1] : -1;
+            const int se = pl < 2 ? b->twiss_deriv_slot[3 * pl + 2] : -1;
+            HD al = hvar(b->alpha[pl], sa), be = hvar(b->beta[pl], sb);
+            HD ep = hvar(b->eps_n[pl] / bg, se);
+            HD a = hsqrt(hmul(ep, be)), bb = hsqrt(hdiv(ep, be));
+            for (int k = 0; k < CP; ++k) {
+                coef[(pl * 3 + 0) * CP + k] = a.v[k];
+                coef[(pl * 3 + 1) * CP + k] = bb.v[k];
+                coef[(pl * 3 + 2) * CP + k] = al.v[k];
+            }
+        }
+        for (int c = 0; c < 6; ++c) {
+            double s = 0.0;
+            for (int64_t i = 0; i < h->N; ++i) s += normals[(int64_t)c * h->N + i];
+            coef[3 * 3 * CP + c] = s / (double)h->N;
+        }
+        double *nd = nullptr, *cd = nullptr;
+        if (cudaMalloc(&nd, sizeof(double) * 6 * h->N) != cudaSuccess) { cudaGetLastError(); return AD_PIC_ERR_OOM; }
+        if (cudaMalloc(&cd, sizeof(double) * coef.size()) != cudaSuccess) {
+            cudaFree(nd);
+            cudaGetLastError();
+            return AD_PIC_ERR_OOM;
+        }
+        cudaError_t e1 = cudaMemcpyAsync(nd, normals, sizeof(double) * 6 * h->N, cudaMemcpyHostToDevice, h->stream);
+        cudaError_t e2 = cudaMemcpyAsync(cd, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e1 == cudaSuccess && e2 == cudaSuccess) launch_init<T, C, CP>(nd, h->N, cd, st(h), h->stream);
+        cudaError_t e3 = cudaStreamSynchronize(h->stream);
+        cudaFree(nd);
+        cudaFree(cd);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || cudaGetLastError() != cudaSuccess)
+            return AD_PIC_ERR_CUDA;
+        h->particles_set = true;
+        h->kick = 0;
+        h->first_record = true;
+        h->hist.clear();
+        return AD_PIC_OK;
+    }
+
+    static int staging(ad_pic* h, double** out) {
+        if (!h->staging) {
+            int r = dalloc(h, (void**)&h->staging, sizeof(double) * 6 * h->N * C);
+            if (r) return r;
+        }
+        *out = h->staging;
+        return AD_PIC_OK;
+    }
+
+    static int set_particles(ad_pic* h, const double* src) {
+        double* tmp = nullptr;
+        const size_t bytes = sizeof(double) * 6 * h->N * C;
+        int r = staging(h, &tmp);
+        if (r) return r;
+        cudaError_t e1 = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, h->stream);
+        if (e1 == cudaSuccess) launch_convert_in<T, CP>(tmp, st(h), h->N, C, h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || cudaGetLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
+        h->particles_set = true;
+        h->kick = 0;
+        h->first_record = true;
+        h->hist.clear();
+        return AD_PIC_OK;
+    }
+
+    static int get_particles(const ad_pic* hc_, double* dst) {
+        ad_pic* h = const_cast<ad_pic*>(hc_);
+        double* tmp = nullptr;
+        const size_t bytes = sizeof(double) * 6 * h->N * C;
+        int r = staging(h, &tmp);
+        if (r) return r;
+        launch_convert_out<T, CP>(st(h), tmp, h->N, C, h->stream);
+        cudaError_t e1 = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || cudaGetLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
+        return AD_PIC_OK;
+    }
+
+    template <typename U>
+    static void grid_out(const std::vector<U>& src, int comps, int64_t nodes, double* out) {
+        // [node][comps][CP] -> [comps][C][node]
+        for (int q = 0; q < comps; ++q)
+            for (int k = 0; k < C; ++k)
+                for (int64_t a = 0; a < nodes; ++a) out[((int64_t)q * C + k) * nodes + a] = (double)src[(a * comps + q) * CP + k];
+    }
+
+    static int stage(ad_pic* h, int which, int64_t kk, double* out) {
+        if (h->coef_dirty) build_coef(h);
+        cudaStream_t s = h->stream;
+        const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
+        CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+        launch_boundary<T, C, CP>(st(h), h->N, identity(), true, false, h->partial, boundary_blocks(),
+                                  (Ord<T>*)h->mm, s);
+        launch_geom<T>((Ord<T>*)h->mm, h->nx, h->ny, h->nz, h->gamma0, h->geom, (Ord<T>*)h->chmax, CP, s);
+        if (which == 0) {
+            GeomDev g;
+            CK(cudaMemcpyAsync(&g, h->geom, sizeof(g), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int d = 0; d < 3; ++d) { out[d] = g.o[d]; out[3 + d] = g.h[d]; }
+            return AD_PIC_OK;
+        }
+        // the geometry kernel already ran: do not run it twice (it resets the extrema)
+        CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s));
+        launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err, s);
+        std::vector<T> buf;
+        if (which == 1) {
+            buf.resize(nodes * CP);
+            CK(cudaMemcpyAsync(buf.data(), h->rho, sizeof(T) * buf.size(), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            grid_out(buf, 1, nodes, out);
+            return check_err(h);
+        }
+        launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
+        launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
+                        (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2], s);
+        FFTDims d = dims(h);
+        launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
+                           (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
+                           (const V2<T>*)h->tw[3], (const V2<T>*)h->tw[4], (const V2<T>*)h->tw[5],
+                           (const Ord<T>*)h->chmax, s);
+        if (which == 2) {
+            buf.resize(nodes * CP);
+            CK(cudaMemcpyAsync(buf.data(), h->phi, sizeof(T) * buf.size(), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            grid_out(buf, 1, nodes, out);
+            return check_err(h);
+        }
+        launch_field<T>((const T*)h->phi, h->geom, h->nx, h->ny, h->nz, CP, (T*)h->E, s);
+        if (which == 3) {
+            buf.resize(nodes * 3 * CP);
+            CK(cudaMemcpyAsync(buf.data(), h->E, sizeof(T) * buf.size(), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            grid_out(buf, 3, nodes, out);
+            return check_err(h);
+        }
+        launch_push<T, C, CP>(st(h), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, identity(), kick(h, kk),
+                              false, (Ord<T>*)h->mm, h->err, s);
+        CK(cudaStreamSynchronize(s));
+        return check_err(h);
+    }
+
+    static int check_err(ad_pic* h) {
+        int errw = 0;
+        CK(cudaMemcpy(&errw, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaGetLastError());
+        if (errw & kErrNonfinite) return AD_PIC_ERR_NONFINITE;
+        if (errw & kErrOutOfGrid) return AD_PIC_ERR_OUT_OF_GRID;
+        return AD_PIC_OK;
+    }
+
+    static int allocate(ad_pic* h) {
+        const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
+        const int64_t gnodes = (int64_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
+        const int npair = C / 2;
+        const int Mx = 2 * h->nx, My = 2 * h->ny, Mz = 2 * h->nz;
+        int r = 0;
+        r |= dalloc(h, &h->state, sizeof(T) * 6 * h->N * CP);
+        r |= dalloc(h, &h->rho, sizeof(T) * nodes * CP);
+        r |= dalloc(h, &h->phi, sizeof(T) * nodes * CP);
+        r |= dalloc(h, &h->E, sizeof(T) * nodes * 3 * CP);
+        r |= dalloc(h, &h->X1, sizeof(V2<T>) * npair * h->nz * h->ny * Mx);
+        r |= dalloc(h, &h->X2, sizeof(V2<T>) * npair * h->nz * My * Mx);
+        r |= dalloc(h, &h->G, sizeof(T) * gnodes);
+        r |= dalloc(h, &h->Gtmp, sizeof(T) * gnodes);
+        r |= dalloc(h, &h->Ghat, sizeof(T) * gnodes);
+        r |= dalloc(h, (void**)&h->corner, sizeof(double) * (h->nx + 2) * (h->ny + 2) * (h->nz + 2));
+        const int ns[3] = {h->nx, h->ny, h->nz};
+        for (int d = 0; d < 3; ++d) r |= dalloc(h, &h->dct[d], sizeof(T) * (ns[d] + 1) * (ns[d] + 1));
+        const int Ms[3] = {Mx, My, Mz};
+        for (int d = 0; d < 3; ++d) {
+            r |= dalloc(h, &h->tw[2 * d], sizeof(V2<T>) * Ms[d] / 2);
+            r |= dalloc(h, &h->tw[2 * d + 1], sizeof(V2<T>) * Ms[d] / 2);
+        }
+        r |= dalloc(h, (void**)&h->geom, sizeof(GeomDev));
+        r |= dalloc(h, &h->mm, sizeof(Ord<T>) * 6);
+        r |= dalloc(h, &h->chmax, sizeof(Ord<T>) * CP);
+        r |= dalloc(h, (void**)&h->err, sizeof(int));
+        r |= dalloc(h, (void**)&h->partial, sizeof(double) * boundary_blocks() * 15 * CP);
+        if (r) return AD_PIC_ERR_OOM;
+        CK(cudaMemsetAsync(h->state, 0, sizeof(T) * 6 * h->N * CP, h->stream));
+        CK(cudaMemsetAsync(h->E, 0, sizeof(T) * nodes * 3 * CP, h->stream));
+        std::vector<Ord<T>> mm0 = {~(Ord<T>)0, ~(Ord<T>)0, ~(Ord<T>)0, 0, 0, 0};
+        CK(cudaMemcpyAsync(h->mm, mm0.data(), sizeof(Ord<T>) * 6, cudaMemcpyHostToDevice, h->stream));
+        // DCT-I matrices D[k][l] = w_l cos(pi l k / n) and FFT twiddles exp(-+ 2 pi i j / M)
+        for (int d = 0; d < 3; ++d) {
+            const int n = ns[d];
+            std::vector<T> D((size_t)(n + 1) * (n + 1));
+            for (int k = 0; k <= n; ++k)
+                for (int l = 0; l <= n; ++l) {
+                    const double w = (l == 0 || l == n) ? 1.0 : 2.0;
+                    const long long m = ((long long)l * k) % (2LL * n);   // exact argument reduction
+                    D[(size_t)k * (n + 1) + l] = (T)(w * std::cos(M_PI * (double)m / (double)n));
+                }
+            CK(cudaMemcpy(h->dct[d], D.data(), sizeof(T) * D.size(), cudaMemcpyHostToDevice));
+            const int M = Ms[d];
+            std::vector<V2<T>> f(M / 2), i(M / 2);
+            for (int j = 0; j < M / 2; ++j) {
+                const double a = 2.0 * M_PI * (double)j / (double)M;
+                f[j].x = (T)std::cos(a); f[j].y = (T)(-std::sin(a));
+                i[j].x = (T)std::cos(a); i[j].y = (T)std::sin(a);
+            }
+            CK(cudaMemcpy(h->tw[2 * d], f.data(), sizeof(V2<T>) * f.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->tw[2 * d + 1], i.data(), sizeof(V2<T>) * i.size(), cudaMemcpyHostToDevice));
+        }
+        setup_fft_attrs<T>();
+        CK(cudaStreamSynchronize(h->stream));
+        return AD_PIC_OK;
+    }
+};
+
+// call Impl<T,C,CP>::fn for the handle's precision and derivative count
+#define DISPATCH(h, expr)                                                      \
+    do {                                                                       \
+        if ((h)->prec == AD_PIC_FP64 && (h)->P == 7) { using I = Impl<double, 8, 8>; return expr; }   \
+        if ((h)->prec == AD_PIC_FP64 && (h)->P == 13) { using I = Impl<double, 14, 16>; return expr; } \
+        if ((h)->prec == AD_PIC_FP32_MIXED && (h)->P == 7) { using I = Impl<float, 8, 8>; return expr; } \
+        if ((h)->prec == AD_PIC_FP32_MIXED && (h)->P == 13) { using I = Impl<float, 14, 16>; return expr; } \
+        return AD_PIC_ERR_INVALID_ARG;                                         \
+    } while (0)
+
+// host dual emittance from one record [3][5][C]: centred moments, Eqs. for D eps
+void emittance(const double* rec, int C, double* eps /*[3][C]*/) {
+    for (int pl = 0; pl < 3; ++pl) {
+        HD m[5];
+        for (int q = 0; q < 5; ++q) {
+            m[q] = hc(0.0);
+            for (int k = 0; k < C; ++k) m[q].v[k] = rec[(pl * 5 + q) * C + k];
+        }
+        HD a = hadd(m[2], hneg(hmul(m[0], m[0])));
+        HD b = hadd(m[3], hneg(hmul(m[0], m[1])));
+        HD c = hadd(m[4], hneg(hmul(m[1], m[1])));
+        HD e = hsqrt(hadd(hmul(a, c), hneg(hmul(b, b))));
+        for (int k = 0; k < C; ++k) eps[pl * C + k] = e.v[k];
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int precision, ad_pic** out) {
+    if (!out) return AD_PIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || n_particles < 1 || n_particles > ((int64_t)1 << 34)) return AD_PIC_ERR_INVALID_ARG;
+    if (n_deriv != 7 && n_deriv != 13) return AD_PIC_ERR_INVALID_ARG;
+    if (precision != AD_PIC_FP64 && precision != AD_PIC_FP32_MIXED) return AD_PIC_ERR_INVALID_ARG;
+    if (!pow2_in(grid->nx, 8, 128) || !pow2_in(grid->ny, 8, 128) || !pow2_in(grid->nz, 8, 128))
+        return AD_PIC_ERR_INVALID_ARG;
+    ad_pic* h = new (std::nothrow) ad_pic();
+    if (!h) return AD_PIC_ERR_OOM;
+    h->prec = precision;
+    h->P = n_deriv;
+    h->C = n_deriv + 1;
+    h->CP = n_deriv == 7 ? 8 : 16;
+    h->nx = grid->nx; h->ny = grid->ny; h->nz = grid->nz;
+    h->N = n_particles;
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return AD_PIC_ERR_CUDA;
+    }
+    h->stream = h->own_stream;
+    int st;
+    auto alloc = [&]() -> int { DISPATCH(h, I::allocate(h)); };
+    st = alloc();
+    if (st) { ad_pic_destroy(h); return st; }
+    *out = h;
+    return AD_PIC_OK;
+}
+
+int ad_pic_set_beam(ad_pic* h, const ad_pic_beam* b, const double* normals) {
+    if (!h || !b) return AD_PIC_ERR_INVALID_ARG;
+    if (!(b->kinetic_eV > 0) || !(b->mass_eV > 0) || b->charge_e == 0 || !(b->bunch_charge_C >= 0))
+        return AD_PIC_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(b->eps_n[d] > 0) || !(b->beta[d] > 0) || !std::isfinite(b->alpha[d])) return AD_PIC_ERR_INVALID_ARG;
+    for (int j = 0; j < 6; ++j)
+        if (b->twiss_deriv_slot[j] < -1 || b->twiss_deriv_slot[j] >= h->P) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::set_beam(h, b, normals));
+}
+
+int ad_pic_set_particles(ad_pic* h, const double* state) {
+    if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::set_particles(h, state));
+}
+
+int ad_pic_get_particles(const ad_pic* h, double* state) {
+    if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::get_particles(h, state));
+}
+
+int ad_pic_set_lattice(ad_pic* h, const ad_pic_lattice* L) {
+    if (!h || !L) return AD_PIC_ERR_INVALID_ARG;
+    for (int e = 0; e < 5; ++e)
+        if (!(L->L[e] > 0) || L->kicks[e] < 1 || L->kicks[e] > 100000) return AD_PIC_ERR_INVALID_ARG;
+    if (!(L->g[0] != 0) || !(L->g[1] != 0) || !std::isfinite(L->g[0]) || !std::isfinite(L->g[1]))
+        return AD_PIC_ERR_INVALID_ARG;
+    for (int j = 0; j < 7; ++j)
+        if (L->deriv_slot[j] < -1 || L->deriv_slot[j] >= h->P) return AD_PIC_ERR_INVALID_ARG;
+    h->lat = *L;
+    h->lattice_set = true;
+    h->coef_dirty = true;
+    free_graphs(h);
+    return AD_PIC_OK;
+}
+
+int ad_pic_run(ad_pic* h, int n_steps) {
+    if (!h || n_steps < 0) return AD_PIC_ERR_INVALID_ARG;
+    if (!h->beam_set || !h->lattice_set || !h->particles_set) return AD_PIC_ERR_STATE;
+    DISPATCH(h, I::run(h, n_steps));
+}
+
+int ad_pic_moments_full(const ad_pic* h, double* mom) {
+    if (!h || !mom) return AD_PIC_ERR_INVALID_ARG;
+    const size_t rs = (size_t)15 * h->C;
+    if (h->hist.size() < rs) return AD_PIC_ERR_STATE;
+    std::memcpy(mom, h->hist.data() + h->hist.size() - rs, sizeof(double) * rs);
+    return AD_PIC_OK;
+}
+
+int ad_pic_moments(const ad_pic* h, double* values, double* derivs) {
+    if (!h || !values) return AD_PIC_ERR_INVALID_ARG;
+    const size_t rs = (size_t)15 * h->C;
+    if (h->hist.size() < rs) return AD_PIC_ERR_STATE;
+    double eps[3 * kMaxCP];
+    emittance(h->hist.data() + h->hist.size() - rs, h->C, eps);
+    values[0] = eps[0];
+    values[1] = eps[h->C];
+    if (derivs)
+        for (int k = 0; k < h->P; ++k) {
+            derivs[k] = eps[1 + k];
+            derivs[h->P + k] = eps[h->C + 1 + k];
+        }
+    return AD_PIC_OK;
+}
+
+int ad_pic_history(const ad_pic* h, double* hist, int max_records, int* n_records) {
+    if (!h || !n_records || max_records < 0) return AD_PIC_ERR_INVALID_ARG;
+    const size_t rs = (size_t)15 * h->C;
+    const int n = (int)(h->hist.size() / rs);
+    *n_records = n;
+    if (hist) std::memcpy(hist, h->hist.data(), sizeof(double) * rs * (size_t)(n < max_records ? n : max_records));
+    return AD_PIC_OK;
+}
+
+int ad_pic_set_stream(ad_pic* h, void* stream) {
+    if (!h) return AD_PIC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) { cudaGetLastError(); return AD_PIC_ERR_CUDA; }
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    free_graphs(h);
+    return AD_PIC_OK;
+}
+
+int ad_pic_set_graphs(ad_pic* h, int enable) {
+    if (!h) return AD_PIC_ERR_INVALID_ARG;
+    h->use_graphs = enable != 0;
+    if (!h->use_graphs) free_graphs(h);
+    return AD_PIC_OK;
+}
+
+int ad_pic_set_timing(ad_pic* h, unsigned mask) {
+    if (!h) return AD_PIC_ERR_INVALID_ARG;
+    // graphs are keyed by the mask, so switching masks keeps the captured ones
+    h->tmask = mask & ((1u << kClasses) - 1u);
+    for (int c = 0; c < kClasses; ++c) { h->tms[c] = 0; h->tcount[c] = 0; }
+    return AD_PIC_OK;
+}
+
+int ad_pic_timing(const ad_pic* h, double* ms, int64_t* launches, int n) {
+    if (!h || n < 0) return AD_PIC_ERR_INVALID_ARG;
+    for (int c = 0; c < n && c < kClasses; ++c) {
+        if (ms) ms[c] = h->tms[c];
+        if (launches) launches[c] = h->tcount[c];
+    }
+    return AD_PIC_OK;
+}
+
+const char* ad_pic_kernel_name(int cls) { return (cls >= 0 && cls < kClasses) ? kClassNames[cls] : "?"; }
+int ad_pic_kernel_classes(void) { return kClasses; }
+
+int ad_pic_stage(ad_pic* h, int stage, int64_t kick, double* out) {
+    if (!h || stage < 0 || stage > 4 || (stage < 4 && !out) || kick < 0) return AD_PIC_ERR_INVALID_ARG;
+    if (!h->beam_set || !h->particles_set || (stage == 4 && !h->lattice_set)) return AD_PIC_ERR_STATE;
+    if (stage == 4 && h->coef_dirty && !h->lattice_set) return AD_PIC_ERR_STATE;
+    if (!h->lattice_set) {
+        // stages 0-3 need no lattice; use a placeholder period for the tables
+        ad_pic_lattice L{};
+        for (int e = 0; e < 5; ++e) { L.L[e] = 1.0; L.kicks[e] = 1; }
+        L.g[0] = 1.0; L.g[1] = -1.0;
+        for (int j = 0; j < 7; ++j) L.deriv_slot[j] = -1;
+        h->lat = L;
+        h->coef_dirty = true;
+    }
+    DISPATCH(h, I::stage(h, stage, kick, out));
+}
+
+int ad_pic_launches(const ad_pic* h, int64_t* n) {
+    if (!h || !n) return AD_PIC_ERR_INVALID_ARG;
+    *n = h->launches;
+    return AD_PIC_OK;
+}
+
+int ad_pic_constants(const ad_pic* h, double* out) {
+    if (!h || !out) return AD_PIC_ERR_INVALID_ARG;
+    if (!h->beam_set) return AD_PIC_ERR_STATE;
+    out[0] = h->gamma0; out[1] = h->beta0; out[2] = h->p0; out[3] = h->brho;
+    out[4] = h->kperp; out[5] = h->kz; out[6] = h->qm; out[7] = h->q;
+    return AD_PIC_OK;
+}
+
+void ad_pic_destroy(ad_pic* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_graphs(h);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    for (void* p : h->allocs)
+        if (p) cudaFree(p);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    cudaGetLastError();
+    delete h;
+}
+
+const char* ad_pic_strerror(int s) {
+    switch (s) {
+        case AD_PIC_OK: return "ok";
+        case AD_PIC_ERR_INVALID_ARG: return "invalid argument";
+        case AD_PIC_ERR_OOM: return "out of memory";
+        case AD_PIC_ERR_CUDA: return "CUDA runtime error";
+        case AD_PIC_ERR_STATE: return "call out of order";
+        case AD_PIC_ERR_NONFINITE: return "non-finite particle coordinate";
+        case AD_PIC_ERR_OUT_OF_GRID: return "particle outside the grid stencil";
+        case AD_PIC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case AD_PIC_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Shared device types and launcher declarations of the GB300 dual-number PIC library.
+//
+// Storage (device):
+//   state  T [6][N][CP]         coordinates (x, px, y, py, z, delta); channel 0 value,
+//                               channels 1..C-1 derivatives, C..CP-1 zero padding so a
+//                               particle's coordinate is 32 B (FP32, CP=8) / 64 B and
+//                               loads are 128-bit
+//   rho    T [nz][ny][nx][CP]   node charges, channel-minor (one 128-bit atomic per 4 channels)
+//   phi    T [nz][ny][nx][CP]   potential
+//   E      T [nz][ny][nx][3][CP] rest-frame field; boundary nodes stay zero
+//   X1     V2 [npair][nz][ny][Mx]   spectrum after the x pass (M = 2n, zero padded)
+//   X2     V2 [npair][nz][My][Mx]   after the y pass; the z pass works in place
+//   Ghat   T [nz+1][ny+1][nx+1] real, even spectrum of the Green's function
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adpic {
+
+constexpr int kErrOutOfGrid = 1;
+constexpr int kErrNonfinite = 2;
+
+template <typename T> struct V2T;
+template <> struct V2T<float> { using type = float2; };
+template <> struct V2T<double> { using type = double2; };
+template <typename T> using V2 = typename V2T<T>::type;
+
+// ordered-integer encoding of floating point for atomicMin/atomicMax
+template <typename T> struct OrdT;
+template <> struct OrdT<float> { using type = unsigned int; };
+template <> struct OrdT<double> { using type = unsigned long long; };
+template <typename T> using Ord = typename OrdT<T>::type;
+
+// Grid geometry of one kick, computed on the device from the value-part extrema.
+struct GeomDev {
+    double o[3];    // origin (lab, m)
+    double h[3];    // lab spacing (m)
+    double hr[3];   // rest-frame spacing (hx, hy, gamma0 hz)
+    float of[3], ihf[3];   // FP32 copies: origin and 1/h
+    double ihd[3];         // 1/h
+    int R[3];              // near-field box of the Green's function (cells per dimension)
+};
+
+// Dual 2x2 map per plane, entries (m11, m12, m21, m22).
+template <typename T, int CP> struct MapCoef { T m[3][4][CP]; };
+// Kick factors kappa_d * tau per field component (dual).
+template <typename T, int CP> struct KickCoef { T a[3][CP]; };
+
+struct FFTDims {
+    int nx, ny, nz;
+    int Mx, My, Mz;
+    int lx, ly, lz;     // log2 of M
+    int C, CP, npair;
+};
+
+// ---------------------------------------------------------------- launchers
+template <typename T, int C, int CP>
+void launch_init(const double* normals_dev, int64_t N, const double* coef_dev, T* state, cudaStream_t s);
+template <typename T, int CP>
+void launch_convert_in(const double* src, T* dst, int64_t N, int C, cudaStream_t s);
+template <typename T, int CP>
+void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_t s);
+
+template <typename T, int C, int CP>
+void launch_push(T* state, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
+                 const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
+                 cudaStream_t s);
+template <typename T, int C, int CP>
+void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
+                     int nblocks, Ord<T>* mm, cudaStream_t s);
+int boundary_blocks();
+template <typename T, int C, int CP>
+void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho,
+                    int* err, cudaStream_t s);
+void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s);
+
+template <typename T>
+void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geom, Ord<T>* chmax, int CP,
+                 cudaStream_t s);
+template <typename T>
+void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream_t s);
+template <typename T>
+void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, double* corner, T* G, T* Gtmp,
+                  T* Ghat, const T* dct_x, const T* dct_y, const T* dct_z, cudaStream_t s);
+template <typename T>
+void setup_fft_attrs();
+template <typename T>
+void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
+                     const V2<T>* twf_x, const V2<T>* twi_x, const V2<T>* twf_y, const V2<T>* twi_y,
+                     const V2<T>* twf_z, const V2<T>* twi_z, const Ord<T>* chmax, cudaStream_t s);
+template <typename T>
+void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int CP, T* E, cudaStream_t s);
+
+}  // namespace adpic

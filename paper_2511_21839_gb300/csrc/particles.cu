@@ -1,0 +1,527 @@
+// Particle kernels: initial distribution, state conversion, the fused
+// gather + kick + push (M2 then M1 maps), the period-boundary kernel (dual
+// moments in FP64 + half map), and cloud-in-cell deposition of every dual
+// channel.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace adpic {
+
+// ------------------------------------------------------------------ helpers
+
+template <typename T, int CP>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&v)[CP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q) {
+            float4 f = reinterpret_cast<const float4*>(p)[q];
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 2; ++q) {
+            double2 f = reinterpret_cast<const double2*>(p)[q];
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    }
+}
+
+template <typename T, int CP>
+__device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q) {
+            float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 2; ++q) {
+            double2 f = __ldg(reinterpret_cast<const double2*>(p) + q);
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    }
+}
+
+template <typename T, int CP>
+__device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[CP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+    }
+}
+
+__device__ __forceinline__ unsigned int ord_enc(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long ord_enc(double f) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(f);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+template <typename T>
+__device__ __forceinline__ T tmax() { return sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX; }
+
+// Block-wide min/max of three values, then one atomic per block and quantity.
+template <typename T>
+__device__ void block_minmax(T (&mn)[3], T (&mx)[3], Ord<T>* mm) {
+    __shared__ T smn[32][3], smx[32][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0)
+        for (int d = 0; d < 3; ++d) { smn[w][d] = mn[d]; smx[w][d] = mx[d]; }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            T a = l < nw ? smn[l][d] : tmax<T>();
+            T b = l < nw ? smx[l][d] : -tmax<T>();
+            for (int o = 16; o > 0; o >>= 1) {
+                a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+                b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            }
+            if (l == 0 && a <= b) {
+                atomicMin(&mm[d], ord_enc(a));
+                atomicMax(&mm[3 + d], ord_enc(b));
+            }
+        }
+    }
+}
+
+// Cell index and fractional offset of one coordinate; flags and clamps a
+// particle outside the stencil range [1, n-3] (the geometry guarantees it).
+template <typename T>
+__device__ __forceinline__ int cell_of(T x, T o, T ih, int n, T& f, int& bad) {
+    T u = (x - o) * ih;
+    T fl = floor(u);
+    int i = (int)fl;
+    if (!(fl >= (T)1 && fl <= (T)(n - 3))) {
+        bad |= isfinite(x) ? kErrOutOfGrid : kErrNonfinite;
+        i = i < 1 ? 1 : (i > n - 3 ? n - 3 : i);
+        if (!isfinite(x)) i = 1;
+        fl = (T)i;
+        u = fmin(fmax(u, fl), fl + (T)1);
+        if (!isfinite(x)) u = fl;
+    }
+    f = u - fl;
+    return i;
+}
+
+template <typename T> __device__ __forceinline__ T geom_o(const GeomDev& g, int d) {
+    return sizeof(T) == 4 ? (T)g.of[d] : (T)g.o[d];
+}
+template <typename T> __device__ __forceinline__ T geom_ih(const GeomDev& g, int d) {
+    return sizeof(T) == 4 ? (T)g.ihf[d] : (T)g.ihd[d];
+}
+
+// ------------------------------------------------------------------ init / convert
+
+// coef [3 planes][3 (a, b, alpha)][CP] duals then 6 means of the normals.
+// Per plane: u = a (n1 - mean n1), p = b ((n2 - mean n2) - alpha (n1 - mean n1)).
+template <typename T, int C, int CP>
+__global__ void init_kernel(const double* __restrict__ nrm, int64_t N, const double* __restrict__ coef,
+                            T* __restrict__ state) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double* means = coef + 3 * 3 * CP;
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+        const double* a = coef + (pl * 3 + 0) * CP;
+        const double* b = coef + (pl * 3 + 1) * CP;
+        const double* al = coef + (pl * 3 + 2) * CP;
+        double n1 = nrm[(2 * pl) * N + i] - means[2 * pl];
+        double n2 = nrm[(2 * pl + 1) * N + i] - means[2 * pl + 1];
+        double s0 = n2 - al[0] * n1;
+        T u[CP], p[CP];
+        u[0] = (T)(a[0] * n1);
+        p[0] = (T)(b[0] * s0);
+#pragma unroll
+        for (int k = 1; k < CP; ++k) {
+            u[k] = (T)(a[k] * n1);
+            p[k] = (T)(b[0] * (-al[k] * n1) + b[k] * s0);
+        }
+        stv<T, CP>(state + ((2 * pl) * N + i) * CP, u);
+        stv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
+    }
+}
+
+template <typename T, int C, int CP>
+void launch_init(const double* nrm, int64_t N, const double* coef, T* state, cudaStream_t s) {
+    if (N <= 0) return;
+    init_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(nrm, N, coef, state);
+}
+
+template <typename T, int CP>
+__global__ void convert_in_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t rows, int C) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= rows * CP) return;
+    int64_t r = t / CP;
+    int k = (int)(t % CP);
+    dst[t] = k < C ? (T)src[r * C + k] : (T)0;
+}
+
+template <typename T, int CP>
+__global__ void convert_out_kernel(const T* __restrict__ src, double* __restrict__ dst, int64_t rows, int C) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= rows * C) return;
+    int64_t r = t / C;
+    int k = (int)(t % C);
+    dst[t] = (double)src[r * CP + k];
+}
+
+template <typename T, int CP>
+void launch_convert_in(const double* src, T* dst, int64_t N, int C, cudaStream_t s) {
+    int64_t tot = 6 * N * CP;
+    if (tot > 0) convert_in_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, 6 * N, C);
+}
+template <typename T, int CP>
+void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_t s) {
+    int64_t tot = 6 * N * C;
+    if (tot > 0) convert_out_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, 6 * N, C);
+}
+
+// ------------------------------------------------------------------ gather + kick + push
+
+// One thread per particle: CIC gather of the dual rest-frame field (the weight
+// derivatives carry the particle's derivative channels), the kick M2(tau)
+// p += (kappa tau) E (dual product), then the dual map A (one half map, or
+// the composition of this kick's and the next kick's half maps), and the
+// value-part extrema of the new positions for the next grid geometry.
+template <typename T, int C, int CP, bool TRACK>
+__global__ void __launch_bounds__(256) push_kernel(T* __restrict__ state, int64_t N, const T* __restrict__ E,
+                                                   const GeomDev* __restrict__ geom, int nx, int ny, int nz,
+                                                   const MapCoef<T, CP> A, const KickCoef<T, CP> K,
+                                                   Ord<T>* __restrict__ mm, int* __restrict__ err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
+    T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
+    if (i < N) {
+        T u[6][CP];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ldv<T, CP>(state + (c * N + i) * CP, u[c]);
+        if (E != nullptr) {
+            const GeomDev& g = *geom;
+            const int n[3] = {nx, ny, nz};
+            T f[3], ih[3];
+            int idx[3];
+            int bad = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ih[d] = geom_ih<T>(g, d);
+                idx[d] = cell_of<T>(u[2 * d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
+            }
+            if (bad) atomicOr(err, bad);
+            T Ev[3][CP];
+            T Gr[3][3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+#pragma unroll
+                for (int k = 0; k < CP; ++k) Ev[q][k] = (T)0;
+                Gr[q][0] = Gr[q][1] = Gr[q][2] = (T)0;
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T wz = c ? f[2] : (T)1 - f[2];
+                const T sz = c ? (T)1 : (T)-1;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const T wy = b ? f[1] : (T)1 - f[1];
+                    const T sy = b ? (T)1 : (T)-1;
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        const T wx = a ? f[0] : (T)1 - f[0];
+                        const T sx = a ? (T)1 : (T)-1;
+                        const T W = wx * wy * wz;
+                        const T dWx = sx * wy * wz, dWy = wx * sy * wz, dWz = wx * wy * sz;
+                        const int64_t node = ((int64_t)(idx[2] + c) * ny + (idx[1] + b)) * nx + (idx[0] + a);
+                        const T* e = E + node * (3 * CP);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            T en[CP];
+                            ldg_v<T, CP>(e + q * CP, en);
+#pragma unroll
+                            for (int k = 0; k < CP; ++k) Ev[q][k] = fma(W, en[k], Ev[q][k]);
+                            Gr[q][0] = fma(dWx, en[0], Gr[q][0]);
+                            Gr[q][1] = fma(dWy, en[0], Gr[q][1]);
+                            Gr[q][2] = fma(dWz, en[0], Gr[q][2]);
+                        }
+                    }
+                }
+            }
+            // derivative of the weights: dW/dp_k = sum_d (x_d,k / h_d) dW/du_d
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const T gx = Gr[q][0] * ih[0], gy = Gr[q][1] * ih[1], gz = Gr[q][2] * ih[2];
+#pragma unroll
+                for (int k = 1; k < CP; ++k) Ev[q][k] = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[q][k])));
+            }
+            // kick: p += a E, a = kappa tau (dual)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                T* p = u[2 * q + 1];
+                const T a0 = K.a[q][0], e0 = Ev[q][0];
+#pragma unroll
+                for (int k = 1; k < CP; ++k) p[k] = fma(a0, Ev[q][k], fma(K.a[q][k], e0, p[k]));
+                p[0] = fma(a0, e0, p[0]);
+            }
+        }
+        // dual map
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            T* x = u[2 * pl];
+            T* p = u[2 * pl + 1];
+            const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
+            const T x0 = x[0], p0 = p[0];
+#pragma unroll
+            for (int k = 1; k < CP; ++k) {
+                const T xk = x[k], pk = p[k];
+                x[k] = fma(a0, xk, fma(b0, pk, fma(A.m[pl][0][k], x0, A.m[pl][1][k] * p0)));
+                p[k] = fma(c0, xk, fma(d0, pk, fma(A.m[pl][2][k], x0, A.m[pl][3][k] * p0)));
+            }
+            x[0] = fma(a0, x0, b0 * p0);
+            p[0] = fma(c0, x0, d0 * p0);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) stv<T, CP>(state + (c * N + i) * CP, u[c]);
+        if (TRACK) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) { mn[d] = u[2 * d][0]; mx[d] = u[2 * d][0]; }
+        }
+    }
+    if (TRACK) block_minmax<T>(mn, mx, mm);
+}
+
+template <typename T, int C, int CP>
+void launch_push(T* state, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
+                 const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
+                 cudaStream_t s) {
+    if (N <= 0) return;
+    unsigned blocks = (unsigned)((N + 255) / 256);
+    if (track)
+        push_kernel<T, C, CP, true><<<blocks, 256, 0, s>>>(state, N, E, geom, nx, ny, nz, A, K, mm, err);
+    else
+        push_kernel<T, C, CP, false><<<blocks, 256, 0, s>>>(state, N, E, geom, nx, ny, nz, A, K, mm, err);
+}
+
+// ------------------------------------------------------------------ period boundary: moments + half map
+
+// CP lanes per particle, lane k holds channel k of every coordinate. Each lane
+// accumulates, in FP64, channel k of the dual sums of u, p, u^2, u p, p^2
+// per plane (Eq. 2 for the products: d(u^2) = 2 u u_k, d(u p) = u p_k + p u_k),
+// and optionally applies the dual half map A to the state and tracks extrema.
+constexpr int kBoundaryBlocks = 152 * 8;
+int boundary_blocks() { return kBoundaryBlocks; }
+
+template <typename T, int C, int CP, bool MOM, bool APPLY>
+__global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ state, int64_t N, const MapCoef<T, CP> A,
+                                                       double* __restrict__ partial, Ord<T>* __restrict__ mm) {
+    constexpr int PPW = 32 / CP;
+    const int lane = threadIdx.x & 31;
+    const int k = lane & (CP - 1);
+    const int src = lane & ~(CP - 1);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc[3][5];
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[pl][q] = 0.0;
+    T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
+    T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
+    for (int64_t base = warp * PPW; base < N; base += nwarps * PPW) {
+        const int64_t i = base + lane / CP;
+        const bool valid = i < N;
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            T* pu = state + ((2 * pl) * N + i) * CP + k;
+            T* pp = state + ((2 * pl + 1) * N + i) * CP + k;
+            T u = valid ? *pu : (T)0;
+            T p = valid ? *pp : (T)0;
+            T u0 = __shfl_sync(0xffffffffu, u, src);
+            T p0 = __shfl_sync(0xffffffffu, p, src);
+            if (MOM && valid) {
+                double du = (double)u, dp = (double)p, du0 = (double)u0, dp0 = (double)p0;
+                acc[pl][0] += du;
+                acc[pl][1] += dp;
+                if (k == 0) {
+                    acc[pl][2] = fma(du, du, acc[pl][2]);
+                    acc[pl][3] = fma(du, dp, acc[pl][3]);
+                    acc[pl][4] = fma(dp, dp, acc[pl][4]);
+                } else {
+                    acc[pl][2] = fma(2.0 * du0, du, acc[pl][2]);
+                    acc[pl][3] = fma(du0, dp, fma(dp0, du, acc[pl][3]));
+                    acc[pl][4] = fma(2.0 * dp0, dp, acc[pl][4]);
+                }
+            }
+            if (APPLY && valid) {
+                const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
+                T un, pn;
+                if (k == 0) {
+                    un = fma(a0, u, b0 * p);
+                    pn = fma(c0, u, d0 * p);
+                    mn[pl] = fmin(mn[pl], un);
+                    mx[pl] = fmax(mx[pl], un);
+                } else {
+                    un = fma(a0, u, fma(b0, p, fma(A.m[pl][0][k], u0, A.m[pl][1][k] * p0)));
+                    pn = fma(c0, u, fma(d0, p, fma(A.m[pl][2][k], u0, A.m[pl][3][k] * p0)));
+                }
+                *pu = un;
+                *pp = pn;
+            }
+        }
+    }
+    if (APPLY) block_minmax<T>(mn, mx, mm);
+    if (MOM) {
+        // sum over the PPW particle groups of the warp (lanes with the same k)
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                for (int o = CP; o < 32; o <<= 1) acc[pl][q] += __shfl_xor_sync(0xffffffffu, acc[pl][q], o);
+        __shared__ double sm[8][15][CP];
+        const int w = threadIdx.x >> 5;
+        if (lane < CP)
+            for (int pl = 0; pl < 3; ++pl)
+                for (int q = 0; q < 5; ++q) sm[w][pl * 5 + q][lane] = acc[pl][q];
+        __syncthreads();
+        for (int t = threadIdx.x; t < 15 * CP; t += blockDim.x) {
+            double s = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += sm[ww][t / CP][t % CP];
+            partial[(int64_t)blockIdx.x * 15 * CP + t] = s;
+        }
+    }
+}
+
+template <typename T, int C, int CP>
+void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
+                     int nblocks, Ord<T>* mm, cudaStream_t s) {
+    if (apply && mom)
+        boundary_kernel<T, C, CP, true, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
+    else if (mom)
+        boundary_kernel<T, C, CP, true, false><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
+    else if (apply)
+        boundary_kernel<T, C, CP, false, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
+}
+
+// partial [nblocks][15][CP] -> out [15][CP] / N, summed in block order (reproducible)
+__global__ void moments_reduce_kernel(const double* __restrict__ partial, int nblocks, int CP, int64_t N,
+                                      double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 15 * CP) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * 15 * CP + t];
+    out[t] = N > 0 ? s / (double)N : 0.0;
+}
+
+void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s) {
+    moments_reduce_kernel<<<(15 * CP + 63) / 64, 64, 0, s>>>(partial, nblocks, CP, N, out);
+}
+
+// ------------------------------------------------------------------ deposition
+
+// One thread per particle: CIC weights of the value part and their
+// derivatives through the particle's derivative channels; node charge
+// q_m W for channel 0 and q_m dW/dp_k for channel k, accumulated with
+// 128-bit float atomics (FP32) or FP64 atomics.
+template <typename T, int C, int CP>
+__global__ void __launch_bounds__(256) deposit_kernel(const T* __restrict__ state, int64_t N,
+                                                      const GeomDev* __restrict__ geom, int nx, int ny, int nz,
+                                                      T qm, T* __restrict__ rho, int* __restrict__ err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const GeomDev& g = *geom;
+    const int n[3] = {nx, ny, nz};
+    T x[3][CP];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
+    T f[3], ih[3];
+    int idx[3];
+    int bad = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ih[d] = geom_ih<T>(g, d);
+        idx[d] = cell_of<T>(x[d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
+    }
+    if (bad) atomicOr(err, bad);
+    T dx[3][CP];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int k = 1; k < CP; ++k) dx[d][k] = qm * x[d][k] * ih[d];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const T wz = c ? f[2] : (T)1 - f[2];
+        const T sz = c ? (T)1 : (T)-1;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const T wy = b ? f[1] : (T)1 - f[1];
+            const T sy = b ? (T)1 : (T)-1;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const T wx = a ? f[0] : (T)1 - f[0];
+                const T sx = a ? (T)1 : (T)-1;
+                const T dWx = sx * wy * wz, dWy = wx * sy * wz, dWz = wx * wy * sz;
+                T q[CP];
+                q[0] = qm * (wx * wy * wz);
+#pragma unroll
+                for (int k = 1; k < CP; ++k) q[k] = fma(dx[0][k], dWx, fma(dx[1][k], dWy, dx[2][k] * dWz));
+                const int64_t node = ((int64_t)(idx[2] + c) * ny + (idx[1] + b)) * nx + (idx[0] + a);
+                T* dst = rho + node * CP;
+                if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                    for (int v = 0; v < CP / 4; ++v)
+                        atomicAdd(reinterpret_cast<float4*>(dst) + v,
+                                  make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < C; ++k) atomicAdd(dst + k, q[k]);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int C, int CP>
+void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho, int* err,
+                    cudaStream_t s) {
+    if (N <= 0) return;
+    deposit_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(state, N, geom, nx, ny, nz, qm, rho, err);
+}
+
+// ------------------------------------------------------------------ instantiations
+#define ADPIC_INST(T, C, CP)                                                                                       \
+    template void launch_init<T, C, CP>(const double*, int64_t, const double*, T*, cudaStream_t);                \
+    template void launch_push<T, C, CP>(T*, int64_t, const T*, const GeomDev*, int, int, int,                     \
+                                        const MapCoef<T, CP>&, const KickCoef<T, CP>&, bool, Ord<T>*, int*,      \
+                                        cudaStream_t);                                                           \
+    template void launch_boundary<T, C, CP>(T*, int64_t, const MapCoef<T, CP>&, bool, bool, double*, int,       \
+                                            Ord<T>*, cudaStream_t);                                              \
+    template void launch_deposit<T, C, CP>(const T*, int64_t, const GeomDev*, int, int, int, T, T*, int*,        \
+                                           cudaStream_t);
+ADPIC_INST(float, 8, 8)
+ADPIC_INST(float, 14, 16)
+ADPIC_INST(double, 8, 8)
+ADPIC_INST(double, 14, 16)
+template void launch_convert_in<float, 8>(const double*, float*, int64_t, int, cudaStream_t);
+template void launch_convert_in<float, 16>(const double*, float*, int64_t, int, cudaStream_t);
+template void launch_convert_in<double, 8>(const double*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_in<double, 16>(const double*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out<float, 8>(const float*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out<float, 16>(const float*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out<double, 8>(const double*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out<double, 16>(const double*, double*, int64_t, int, cudaStream_t);
+
+}  // namespace adpic

@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (stated per result):
+  FP64 path   emittances and derivatives 1e-10 relative; grid stages 1e-11 of the channel's max
+  FP32 path   emittances 1e-5, derivatives 1e-4 relative; grid stages 2e-5 of the channel's max
+Derivative relative errors use max(|d_k|, 1e-3 max_j |d_j|) per emittance as the denominator, so a
+derivative that is zero up to rounding is compared at the scale of the largest one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_21839_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: dict(eps=1e-10, der=1e-10, grid=1e-11, state=1e-9), 1: dict(eps=1e-5, der=1e-4, grid=2e-5, state=2e-4)}
+
+
+@pytest.fixture(scope="module")
+def adpic():
+    from paper_2511_21839_gb300 import build
+    from paper_2511_21839_gb300 import adpic as A
+
+    build.build()
+    A.lib()
+    return A
+
+
+def rel_eps(v, ref):
+    return np.abs(v - ref) / np.abs(ref)
+
+
+def rel_der(d, ref):
+    scale = np.abs(ref).max(axis=-1, keepdims=True)
+    return np.abs(d - ref) / np.maximum(np.abs(ref), 1e-3 * scale)
+
+
+def chan_close(gpu, ref, tol, axis_chan):
+    """Element-wise comparison relative to the max of each channel."""
+    g = np.moveaxis(gpu, axis_chan, 0).reshape(gpu.shape[axis_chan], -1)
+    r = np.moveaxis(ref, axis_chan, 0).reshape(ref.shape[axis_chan], -1)
+    scale = np.abs(r).max(axis=1, keepdims=True)
+    scale = np.where(scale > 0, scale, 1.0)
+    err = (np.abs(g - r) / scale).max()
+    assert err < tol, err
+    return err
+
+
+def make_pair(adpic, N, grid, P, prec, wname="fodo_10k_32", beam=None, q=None):
+    w = I.workload(wname)
+    b = beam or (w.beam if P == 7 else I.default_beam(13))
+    if q is not None:
+        b = I.Beam(**{**b.__dict__, "bunch_charge_C": q})
+    kw = I.orc_kwargs(w, n_particles=N, grid=grid, n_deriv=P, beam=b)
+    o = oracle.Oracle(**kw)
+    sim = adpic.ADPIC(grid, N, P, prec)
+    sim.set_beam(b)
+    sim.set_lattice(w.lattice)
+    return o, sim, w, b
+
+
+# ---------------------------------------------------------------- stages
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("P", [7, 13])
+def test_stage_parity(adpic, prec, P):
+    N, grid = 5003, (16, 32, 16)
+    o, sim, w, b = make_pair(adpic, N, grid, P, prec)
+    st = o.beam_init(I.normals(41, N))
+    o.apply_half_map(st, 0)
+    if prec == 1:
+        st32 = st.astype(np.float32).astype(np.float64)   # the FP32 state the GPU holds
+        st = st32
+    sim.set_particles(st)
+    tol = TOL[prec]["grid"]
+    geom = sim.stage(0)
+    gref = o.geometry(st)
+    np.testing.assert_allclose(geom, gref, rtol=1e-12 if prec == 0 else 1e-6)
+    rho = sim.stage(1)
+    rho_ref = o.deposit(st, geom)
+    chan_close(rho, rho_ref, tol, 0)
+    assert abs(rho[0].sum() - o.constants()["q_macro"] * N) < 1e-6 * o.constants()["q_macro"] * N
+    phi = sim.stage(2)
+    phi_ref = o.solve(geom, rho_ref)
+    chan_close(phi, phi_ref, tol, 0)
+    E = sim.stage(3)
+    E_ref = o.field(geom, phi_ref)
+    chan_close(E.reshape(3 * o.C, -1), E_ref.reshape(3 * o.C, -1), tol * 5, 0)
+    sim.stage(4, kick=5)
+    after = sim.get_particles()
+    ref = st.copy()
+    o.kick(ref, geom, E_ref, 5)
+    # the kick changes only the momenta: compare the change relative to its own scale
+    d_gpu = after - st
+    d_ref = ref - st
+    for c in (1, 3, 5):
+        chan_close(d_gpu[c], d_ref[c], TOL[prec]["grid"] * 10, 1)
+    for c in (0, 2, 4):
+        assert np.array_equal(after[c], st[c])
+    sim.close()
+
+
+# ---------------------------------------------------------------- whole runs
+
+@pytest.fixture(scope="module")
+def config1_ref():
+    w = I.workload("fodo_10k_32")
+    o = oracle.Oracle(**I.orc_kwargs(w))
+    nrm = I.normals(w.seed, w.n_particles)
+    st0 = o.beam_init(nrm)
+    st = st0.copy()
+    hist, _ = o.run(st, w.n_kicks)
+    return w, nrm, st0, st, hist, o
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config1_single_period(adpic, config1_ref, prec):
+    """10,000 particles, 32^3, one FODO period of 20 kicks, P = 7, GPU init from the same normals."""
+    w, nrm, st0, st, hist, o = config1_ref
+    sim = adpic.ADPIC(w.grid, w.n_particles, 7, prec)
+    sim.set_beam(w.beam, nrm)
+    sim.set_lattice(w.lattice)
+    init = sim.get_particles()
+    chan_close(init.reshape(6, -1, 8), st0, 1e-14 if prec == 0 else 1e-7, 2)
+    sim.run(w.n_kicks)
+    vals, der = sim.moments()
+    ref = o.emittance(hist[-1])[:2]
+    assert rel_eps(vals, ref[:, 0]).max() < TOL[prec]["eps"]
+    assert rel_der(der, ref[:, 1:]).max() < TOL[prec]["der"]
+    gh = sim.history()
+    assert gh.shape[0] == 2
+    np.testing.assert_allclose(gh[0], o.moments(st0), rtol=1e-12 if prec == 0 else 1e-5,
+                               atol=1e-30)
+    fin = sim.get_particles()
+    chan_close(fin, st, TOL[prec]["state"], 2)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_p13_twiss_derivatives(adpic, prec):
+    N, grid = 4096, (16, 16, 16)
+    o, sim, w, b = make_pair(adpic, N, grid, 13, prec)
+    nrm = I.normals(43, N)
+    st = o.beam_init(nrm)
+    hist, _ = o.run(st, 20)
+    sim.set_beam(b, nrm)
+    sim.run(20)
+    vals, der = sim.moments()
+    ref = o.emittance(hist[-1])[:2]
+    assert rel_eps(vals, ref[:, 0]).max() < TOL[prec]["eps"]
+    assert rel_der(der, ref[:, 1:]).max() < TOL[prec]["der"]
+    sim.close()
+
+
+def test_split_runs_and_graph_replay(adpic):
+    """run(20) equals run(7) + run(13) (period-end moments and the kick counter carry over);
+    graph capture and eager launches agree."""
+    N, grid = 3000, (16, 16, 16)
+    w = I.workload("fodo_10k_32")
+    nrm = I.normals(44, N)
+    res = []
+    for split, graphs in (((20,), True), ((7, 13), True), ((20,), False), ((20,), True)):
+        sim = adpic.ADPIC(grid, N, 7, 0)
+        sim.set_graphs(graphs)
+        sim.set_beam(w.beam, nrm)
+        sim.set_lattice(w.lattice)
+        for n in split:
+            sim.run(n)
+        res.append(np.concatenate([sim.moments()[0], sim.moments()[1].ravel()]))
+        sim.close()
+    for r in res[1:]:
+        np.testing.assert_allclose(r, res[0], rtol=1e-11, atol=1e-24)
+
+
+def test_multi_period_records(adpic):
+    N, grid = 2000, (16, 16, 16)
+    o, sim, w, b = make_pair(adpic, N, grid, 7, 0)
+    nrm = I.normals(45, N)
+    st = o.beam_init(nrm)
+    hist, _ = o.run(st, 50)              # records after kicks 20, 40, 50
+    sim.set_beam(b, nrm)
+    sim.run(50)
+    gh = sim.history()
+    assert gh.shape[0] == 4
+    for r in range(3):
+        e_g = o.emittance(gh[r + 1])
+        e_o = o.emittance(hist[r])
+        assert rel_eps(e_g[:2, 0], e_o[:2, 0]).max() < 1e-10
+        assert rel_der(e_g[:2, 1:], e_o[:2, 1:]).max() < 1e-10
+    sim.close()
+
+
+# ---------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_zero_current_conserves_emittance(adpic, prec):
+    N, grid = 3000, (16, 16, 16)
+    o, sim, w, b = make_pair(adpic, N, grid, 7, prec, q=0.0)
+    sim.set_beam(b, I.normals(46, N))
+    sim.run(20)
+    h = sim.history()
+    e0 = o.emittance(h[0])
+    e1 = o.emittance(h[-1])
+    tol = 1e-12 if prec == 0 else 2e-6
+    np.testing.assert_allclose(e1[:2, 0], e0[:2, 0], rtol=tol)
+    assert np.all(np.abs(e1[:2, 1:]) < tol * e0[:2, :1])
+    sim.close()
+
+
+def test_single_particle_and_tiny_grid(adpic):
+    o, sim, w, b = make_pair(adpic, 1, (8, 8, 8), 7, 0)
+    nrm = np.array([[0.3], [0.1], [-0.2], [0.4], [0.5], [-0.6]])
+    sim.set_beam(b, nrm)
+    sim.run(20)
+    st = o.beam_init(nrm)
+    o.run(st, 20)
+    fin = sim.get_particles()
+    np.testing.assert_allclose(fin, st, rtol=1e-12, atol=1e-20)
+    sim.close()
+
+
+def test_call_order_and_argument_errors(adpic):
+    sim = adpic.ADPIC((16, 16, 16), 100, 7, 0)
+    with pytest.raises(adpic.AdPicError) as e:
+        sim.run(1)
+    assert e.value.status == -4
+    bad = I.Lattice(kicks=(4, 0, 8, 2, 4))
+    with pytest.raises(adpic.AdPicError) as e:
+        sim.set_lattice(bad)
+    assert e.value.status == -1
+    sim.close()
+
+
+# ---------------------------------------------------------------- full size (1,048,576 particles, 64^3)
+
+@pytest.fixture(scope="module")
+def full_ref():
+    w = I.workload("fodo_1m_64")
+    o = oracle.Oracle(**I.orc_kwargs(w))
+    nrm = I.normals(w.seed, w.n_particles)
+    st = o.beam_init(nrm)
+    hist, _ = o.run(st, 20)
+    return w, nrm, hist, o
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_one_period_vs_oracle(adpic, full_ref, prec):
+    """The launch configuration bench.py times (1M particles, 64^3, P = 7), one period, vs the oracle."""
+    w, nrm, hist, o = full_ref
+    sim = adpic.ADPIC(w.grid, w.n_particles, 7, prec)
+    sim.set_beam(w.beam, nrm)
+    sim.set_lattice(w.lattice)
+    sim.run(20)
+    vals, der = sim.moments()
+    ref = o.emittance(hist[-1])[:2]
+    assert rel_eps(vals, ref[:, 0]).max() < TOL[prec]["eps"]
+    assert rel_der(der, ref[:, 1:]).max() < TOL[prec]["der"]
+    sim.close()
+
+
+def test_full_size_ten_periods_fp32_vs_fp64(adpic):
+    """The whole 10-period run: FP32 bulk arithmetic against the FP64 path (itself pinned to the
+    oracle above), emittance <= 1e-5 and derivatives <= 1e-4 relative at every period end."""
+    w = I.workload("fodo_1m_64")
+    nrm = I.normals(w.seed, w.n_particles)
+    hs = []
+    for prec in (0, 1):
+        sim = adpic.ADPIC(w.grid, w.n_particles, 7, prec)
+        sim.set_beam(w.beam, nrm)
+        sim.set_lattice(w.lattice)
+        sim.run(w.n_kicks)
+        hs.append(sim.history())
+        sim.close()
+    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=1))
+    for r in range(hs[0].shape[0]):
+        e64 = o.emittance(hs[0][r])[:2]
+        e32 = o.emittance(hs[1][r])[:2]
+        assert rel_eps(e32[:, 0], e64[:, 0]).max() < 1e-5, r
+        assert rel_der(e32[:, 1:], e64[:, 1:]).max() < 1e-4, r
