@@ -115,7 +115,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -182,6 +182,28 @@ def measure(sim, steps, warmup, kicks, torch, timing_mask=0):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps, sim.launches() - l0
+
+
+def e2e_measure(args, sim, w, kicks, ws, barrier, torch, np):
+    state = torch.empty((6, w.n_particles, w.n_deriv + 1), dtype=torch.float64, pin_memory=True)
+    state.numpy()[...] = sim.get_particles()
+    for _ in range(2):
+        sim.set_particles(state.numpy())
+        sim.run(kicks)
+        sim.moments()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_particles(state.numpy())
+        sim.run(kicks)
+        vals, der = sim.moments()
+    barrier()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
+    h2d = state.numel() * 8
+    d2h = 8 * (2 + 2 * w.n_deriv) + 15 * 8 * (w.n_deriv + 1) + 4
+    e2e_value = ws * w.n_particles * kicks / (e2e_ms / 1000.0)
+    fp32_eps = vals
+    return e2e_value, e2e_ms, h2d, d2h, fp32_eps
 
 
 def run_native(args):
@@ -251,24 +273,11 @@ def run_native(args):
 
     # ---- end to end through the public API with host buffers: upload the step's dual state
     # from pinned host memory, run the period, read the emittances back
-    state = torch.empty((6, w.n_particles, w.n_deriv + 1), dtype=torch.float64, pin_memory=True)
-    state.numpy()[...] = sim.get_particles()
-    for _ in range(2):
-        sim.set_particles(state.numpy())
-        sim.run(kicks)
-        sim.moments()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sim.set_particles(state.numpy())
-        sim.run(kicks)
-        vals, der = sim.moments()
-    barrier()
-    e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
-    h2d = state.numel() * 8
-    d2h = 8 * (2 + 2 * w.n_deriv) + 15 * 8 * (w.n_deriv + 1) + 4
-    e2e_value = ws * w.n_particles * kicks / (e2e_ms / 1000.0)
-    fp32_eps = vals
+    if args.no_e2e:
+        e2e_value = e2e_ms = h2d = d2h = None
+        fp32_eps = sim.moments()[0]
+    else:
+        e2e_value, e2e_ms, h2d, d2h, fp32_eps = e2e_measure(args, sim, w, kicks, ws, barrier, torch, np)
     sim.close()
 
     # ---- plain FP64 path on the same workload
@@ -314,8 +323,8 @@ def run_native(args):
                 "config": workload_config(w, {"precision": "FP32 particles/deposit/FFT/field/push, FP64 geometry, "
                                                            "Green's-function integrals and moment reductions"}),
                 "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": e2e_ms},
+                "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
                 "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64,
                 "final_eps_fp32": [float(v) for v in fp32_eps]}
         print(json.dumps(line))
@@ -327,12 +336,13 @@ def run_native(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-kicks", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

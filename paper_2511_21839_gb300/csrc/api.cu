@@ -117,7 +117,7 @@ struct ad_pic {
     void* Ghat = nullptr;
     double* corner = nullptr;
     void* dct[3] = {nullptr, nullptr, nullptr};
-    void* tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* tw[3] = {nullptr, nullptr, nullptr};
     GeomDev* geom = nullptr;
     void* mm = nullptr;
     void* chmax = nullptr;
@@ -301,7 +301,6 @@ struct Impl {
         FFTDims d = dims(h);
         launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
-                           (const V2<T>*)h->tw[3], (const V2<T>*)h->tw[4], (const V2<T>*)h->tw[5],
                            (const Ord<T>*)h->chmax, s);
         tend(h, K_FFT, cap);
         tbegin(h, K_FIELD, cap);
@@ -584,7 +583,6 @@ struct Impl {
         FFTDims d = dims(h);
         launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
-                           (const V2<T>*)h->tw[3], (const V2<T>*)h->tw[4], (const V2<T>*)h->tw[5],
                            (const Ord<T>*)h->chmax, s);
         if (which == 2) {
             buf.resize(nodes * CP);
@@ -635,10 +633,7 @@ struct Impl {
         const int ns[3] = {h->nx, h->ny, h->nz};
         for (int d = 0; d < 3; ++d) r |= dalloc(h, &h->dct[d], sizeof(T) * (ns[d] + 1) * (ns[d] + 1));
         const int Ms[3] = {Mx, My, Mz};
-        for (int d = 0; d < 3; ++d) {
-            r |= dalloc(h, &h->tw[2 * d], sizeof(V2<T>) * Ms[d] / 2);
-            r |= dalloc(h, &h->tw[2 * d + 1], sizeof(V2<T>) * Ms[d] / 2);
-        }
+        for (int d = 0; d < 3; ++d) r |= dalloc(h, &h->tw[d], sizeof(V2<T>) * Ms[d]);
         r |= dalloc(h, (void**)&h->geom, sizeof(GeomDev));
         r |= dalloc(h, &h->mm, sizeof(Ord<T>) * 6);
         r |= dalloc(h, &h->chmax, sizeof(Ord<T>) * CP);
@@ -661,16 +656,16 @@ struct Impl {
                 }
             CK(cudaMemcpy(h->dct[d], D.data(), sizeof(T) * D.size(), cudaMemcpyHostToDevice));
             const int M = Ms[d];
-            std::vector<V2<T>> f(M / 2), i(M / 2);
-            for (int j = 0; j < M / 2; ++j) {
+            std::vector<V2<T>> f(M);
+            for (int j = 0; j < M; ++j) {
                 const double a = 2.0 * M_PI * (double)j / (double)M;
-                f[j].x = (T)std::cos(a); f[j].y = (T)(-std::sin(a));
-                i[j].x = (T)std::cos(a); i[j].y = (T)std::sin(a);
+                f[j].x = (T)std::cos(a);
+                f[j].y = (T)(-std::sin(a));
             }
-            CK(cudaMemcpy(h->tw[2 * d], f.data(), sizeof(V2<T>) * f.size(), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(h->tw[2 * d + 1], i.data(), sizeof(V2<T>) * i.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->tw[d], f.data(), sizeof(V2<T>) * f.size(), cudaMemcpyHostToDevice));
         }
-        setup_fft_attrs<T>();
+        setup_green<T>();
+        setup_fft<T>();
         CK(cudaStreamSynchronize(h->stream));
         return AD_PIC_OK;
     }

@@ -38,6 +38,8 @@ struct GeomDev {
     double hr[3];   // rest-frame spacing (hx, hy, gamma0 hz)
     float of[3], ihf[3];   // FP32 copies: origin and 1/h
     double ihd[3];         // 1/h
+    float fdf[3];          // 1/(2 hr): central-difference factors (FP32 copy)
+    double fdd[3];         // 1/(2 hr)
     int R[3];              // near-field box of the Green's function (cells per dimension)
 };
 
@@ -83,11 +85,13 @@ template <typename T>
 void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, double* corner, T* G, T* Gtmp,
                   T* Ghat, const T* dct_x, const T* dct_y, const T* dct_z, cudaStream_t s);
 template <typename T>
-void setup_fft_attrs();
+void setup_green();
+template <typename T>
+void setup_fft();
+// twx/twy/twz: exp(-2 pi i j / M) for j < M of each axis (M = 2n)
 template <typename T>
 void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
-                     const V2<T>* twf_x, const V2<T>* twi_x, const V2<T>* twf_y, const V2<T>* twi_y,
-                     const V2<T>* twf_z, const V2<T>* twi_z, const Ord<T>* chmax, cudaStream_t s);
+                     const V2<T>* twx, const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s);
 template <typename T>
 void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int CP, T* E, cudaStream_t s);
 

@@ -200,11 +200,15 @@ void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_
 // p += (kappa tau) E (dual product), then the dual map A (one half map, or
 // the composition of this kick's and the next kick's half maps), and the
 // value-part extrema of the new positions for the next grid geometry.
+// The gather runs one field component at a time over the eight nodes, so
+// only that component's CP accumulators and its three interpolant gradients
+// are live: E_p,k = sum W E_k + sum_d (x_d,k / h_d) sum dW/du_d E_0 (Eq. 2 on
+// the weight product), then p_k += a0 E_p,k + a_k E_p,0 in one rounding.
 template <typename T, int C, int CP, bool TRACK>
-__global__ void __launch_bounds__(256) push_kernel(T* __restrict__ state, int64_t N, const T* __restrict__ E,
-                                                   const GeomDev* __restrict__ geom, int nx, int ny, int nz,
-                                                   const MapCoef<T, CP> A, const KickCoef<T, CP> K,
-                                                   Ord<T>* __restrict__ mm, int* __restrict__ err) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) push_kernel(T* __restrict__ state, int64_t N, const T* __restrict__ E,
+                                                      const GeomDev* __restrict__ geom, int nx, int ny, int nz,
+                                                      const MapCoef<T, CP> A, const KickCoef<T, CP> K,
+                                                      Ord<T>* __restrict__ mm, int* __restrict__ err) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
@@ -224,58 +228,48 @@ __global__ void __launch_bounds__(256) push_kernel(T* __restrict__ state, int64_
                 idx[d] = cell_of<T>(u[2 * d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
             }
             if (bad) atomicOr(err, bad);
-            T Ev[3][CP];
-            T Gr[3][3];
+            const T* e0 = E + (((int64_t)idx[2] * ny + idx[1]) * nx + idx[0]) * (3 * CP);
+            const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
+                T Ev[CP];
+                T gx = (T)0, gy = (T)0, gz = (T)0;
 #pragma unroll
-                for (int k = 0; k < CP; ++k) Ev[q][k] = (T)0;
-                Gr[q][0] = Gr[q][1] = Gr[q][2] = (T)0;
-            }
+                for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const T wz = c ? f[2] : (T)1 - f[2];
-                const T sz = c ? (T)1 : (T)-1;
+                for (int c = 0; c < 2; ++c) {
+                    const T wz = c ? f[2] : (T)1 - f[2];
+                    const T sz_ = c ? (T)1 : (T)-1;
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const T wy = b ? f[1] : (T)1 - f[1];
-                    const T sy = b ? (T)1 : (T)-1;
+                    for (int b = 0; b < 2; ++b) {
+                        const T wy = b ? f[1] : (T)1 - f[1];
+                        const T sy_ = b ? (T)1 : (T)-1;
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        const T wx = a ? f[0] : (T)1 - f[0];
-                        const T sx = a ? (T)1 : (T)-1;
-                        const T W = wx * wy * wz;
-                        const T dWx = sx * wy * wz, dWy = wx * sy * wz, dWz = wx * wy * sz;
-                        const int64_t node = ((int64_t)(idx[2] + c) * ny + (idx[1] + b)) * nx + (idx[0] + a);
-                        const T* e = E + node * (3 * CP);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
+                        for (int a = 0; a < 2; ++a) {
+                            const T wx = a ? f[0] : (T)1 - f[0];
+                            const T sx_ = a ? (T)1 : (T)-1;
+                            const T W = wx * wy * wz;
                             T en[CP];
-                            ldg_v<T, CP>(e + q * CP, en);
+                            ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en);
 #pragma unroll
-                            for (int k = 0; k < CP; ++k) Ev[q][k] = fma(W, en[k], Ev[q][k]);
-                            Gr[q][0] = fma(dWx, en[0], Gr[q][0]);
-                            Gr[q][1] = fma(dWy, en[0], Gr[q][1]);
-                            Gr[q][2] = fma(dWz, en[0], Gr[q][2]);
+                            for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[k], Ev[k]);
+                            gx = fma(sx_ * wy * wz, en[0], gx);
+                            gy = fma(wx * sy_ * wz, en[0], gy);
+                            gz = fma(wx * wy * sz_, en[0], gz);
                         }
                     }
                 }
-            }
-            // derivative of the weights: dW/dp_k = sum_d (x_d,k / h_d) dW/du_d
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const T gx = Gr[q][0] * ih[0], gy = Gr[q][1] * ih[1], gz = Gr[q][2] * ih[2];
-#pragma unroll
-                for (int k = 1; k < CP; ++k) Ev[q][k] = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[q][k])));
-            }
-            // kick: p += a E, a = kappa tau (dual)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
+                gx *= ih[0];
+                gy *= ih[1];
+                gz *= ih[2];
                 T* p = u[2 * q + 1];
-                const T a0 = K.a[q][0], e0 = Ev[q][0];
+                const T a0 = K.a[q][0], E0 = Ev[0];
 #pragma unroll
-                for (int k = 1; k < CP; ++k) p[k] = fma(a0, Ev[q][k], fma(K.a[q][k], e0, p[k]));
-                p[0] = fma(a0, e0, p[0]);
+                for (int k = 1; k < CP; ++k) {
+                    const T Ek = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[k])));
+                    p[k] = fma(a0, Ek, fma(K.a[q][k], E0, p[k]));
+                }
+                p[0] = fma(a0, E0, p[0]);
             }
         }
         // dual map
@@ -322,6 +316,22 @@ void launch_push(T* state, int64_t N, const T* E, const GeomDev* geom, int nx, i
 // accumulates, in FP64, channel k of the dual sums of u, p, u^2, u p, p^2
 // per plane (Eq. 2 for the products: d(u^2) = 2 u u_k, d(u p) = u p_k + p u_k),
 // and optionally applies the dual half map A to the state and tracks extrema.
+// error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) on a
+// double-float accumulator (hi, lo)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float a) {
+    const float s = hi + a;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (a - bb);
+    hi = s;
+    lo += e;
+}
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
+    const float ph = a * b;
+    const float pl = fmaf(a, b, -ph);
+    df_add(hi, lo, ph);
+    lo += pl;
+}
+
 constexpr int kBoundaryBlocks = 152 * 8;
 int boundary_blocks() { return kBoundaryBlocks; }
 
@@ -335,10 +345,11 @@ __global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ state, in
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double acc[3][5];
+    float ah[3][5], al[3][5];   // FP32 path: double-float partial sums
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) acc[pl][q] = 0.0;
+        for (int q = 0; q < 5; ++q) { acc[pl][q] = 0.0; ah[pl][q] = 0.f; al[pl][q] = 0.f; }
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
     for (int64_t base = warp * PPW; base < N; base += nwarps * PPW) {
@@ -353,17 +364,35 @@ __global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ state, in
             T u0 = __shfl_sync(0xffffffffu, u, src);
             T p0 = __shfl_sync(0xffffffffu, p, src);
             if (MOM && valid) {
-                double du = (double)u, dp = (double)p, du0 = (double)u0, dp0 = (double)p0;
-                acc[pl][0] += du;
-                acc[pl][1] += dp;
-                if (k == 0) {
-                    acc[pl][2] = fma(du, du, acc[pl][2]);
-                    acc[pl][3] = fma(du, dp, acc[pl][3]);
-                    acc[pl][4] = fma(dp, dp, acc[pl][4]);
+                if constexpr (sizeof(T) == 8) {
+                    acc[pl][0] += u;
+                    acc[pl][1] += p;
+                    if (k == 0) {
+                        acc[pl][2] = fma(u, u, acc[pl][2]);
+                        acc[pl][3] = fma(u, p, acc[pl][3]);
+                        acc[pl][4] = fma(p, p, acc[pl][4]);
+                    } else {
+                        acc[pl][2] = fma(2.0 * u0, u, acc[pl][2]);
+                        acc[pl][3] = fma(u0, p, fma(p0, u, acc[pl][3]));
+                        acc[pl][4] = fma(2.0 * p0, p, acc[pl][4]);
+                    }
                 } else {
-                    acc[pl][2] = fma(2.0 * du0, du, acc[pl][2]);
-                    acc[pl][3] = fma(du0, dp, fma(dp0, du, acc[pl][3]));
-                    acc[pl][4] = fma(2.0 * dp0, dp, acc[pl][4]);
+                    // FP32 state: every product of two FP32 values is formed exactly as an
+                    // unevaluated pair (hi, lo) and added with error-free sums, so the
+                    // per-lane partials carry ~48 significant bits before they go to FP64
+                    const float a = 2.0f * (float)u0;
+                    df_add(ah[pl][0], al[pl][0], (float)u);
+                    df_add(ah[pl][1], al[pl][1], (float)p);
+                    if (k == 0) {
+                        df_add_prod(ah[pl][2], al[pl][2], (float)u, (float)u);
+                        df_add_prod(ah[pl][3], al[pl][3], (float)u, (float)p);
+                        df_add_prod(ah[pl][4], al[pl][4], (float)p, (float)p);
+                    } else {
+                        df_add_prod(ah[pl][2], al[pl][2], a, (float)u);
+                        df_add_prod(ah[pl][3], al[pl][3], (float)u0, (float)p);
+                        df_add_prod(ah[pl][3], al[pl][3], (float)p0, (float)u);
+                        df_add_prod(ah[pl][4], al[pl][4], 2.0f * (float)p0, (float)p);
+                    }
                 }
             }
             if (APPLY && valid) {
@@ -385,6 +414,12 @@ __global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ state, in
     }
     if (APPLY) block_minmax<T>(mn, mx, mm);
     if (MOM) {
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[pl][q] = (double)ah[pl][q] + (double)al[pl][q];
+        }
         // sum over the PPW particle groups of the warp (lanes with the same k)
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl)
@@ -416,18 +451,25 @@ void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, b
         boundary_kernel<T, C, CP, false, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
 }
 
-// partial [nblocks][15][CP] -> out [15][CP] / N, summed in block order (reproducible)
+// partial [nblocks][15][CP] -> out [15][CP] / N: one block per output value,
+// a fixed strided split and a fixed shared-memory tree (reproducible)
 __global__ void moments_reduce_kernel(const double* __restrict__ partial, int nblocks, int CP, int64_t N,
                                       double* __restrict__ out) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 15 * CP) return;
+    __shared__ double sm[256];
+    const int t = blockIdx.x;            // output index in [0, 15 CP)
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * 15 * CP + t];
-    out[t] = N > 0 ? s / (double)N : 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)b * 15 * CP + t];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[t] = N > 0 ? sm[0] / (double)N : 0.0;
 }
 
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s) {
-    moments_reduce_kernel<<<(15 * CP + 63) / 64, 64, 0, s>>>(partial, nblocks, CP, N, out);
+    moments_reduce_kernel<<<15 * CP, 256, 0, s>>>(partial, nblocks, CP, N, out);
 }
 
 // ------------------------------------------------------------------ deposition
