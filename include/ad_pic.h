@@ -161,6 +161,27 @@ int ad_pic_launches(const ad_pic* h, int64_t* n);
    in place (out unused). Stages 1-4 use the geometry of the current state. */
 int ad_pic_stage(ad_pic* h, int stage, int64_t kick, double* out);
 
+/* Allocation-free dual moments of a caller-owned device state (the paper has
+   no counterpart: this exists for callers that cannot let the library call
+   cudaMalloc/cudaFree - code running inside another framework's device-memory
+   budget, or latency-critical loops that must not take the implicit
+   synchronisation those calls can bring).
+   state_dev: device pointer to the dual state [6][n_particles][CP] of the
+   precision's type (double for AD_PIC_FP64, float for AD_PIC_FP32_MIXED),
+   CP = 8 for n_deriv 7 and 16 for n_deriv 13 (channels beyond n_deriv+1 are
+   padding). mom_dev: device pointer to 15*CP doubles, written as
+   [3][5][CP] per plane (x, y, z) the means <u>, <p>, <u^2>, <u p>, <p^2>.
+   stream: cudaStream_t as void* (NULL = default stream); the call only
+   enqueues work and does not synchronise. The per-block partial sums live in
+   one static device array of 583,680 bytes (304 blocks x 15 x 16 doubles)
+   that every GPU loading the library holds until exit; n_deriv other than 7
+   or 13 exceeds it and returns AD_PIC_ERR_INVALID_ARG. The first call on a
+   device looks the array's address up (cudaGetSymbolAddress) with that
+   device current; make that first call before any stream capture. All calls
+   share the array, so calls that overlap on the GPU race. */
+int ad_pic_moments_device(const void* state_dev, int64_t n_particles, int n_deriv, int precision, double* mom_dev,
+                          void* stream);
+
 /* Derived constants: out[8] = gamma0, beta0, p0 (kg m/s), B rho (T m),
    kappa_perp, kappa_z (1/(V/m * m)), macroparticle charge (C), q (C). */
 int ad_pic_constants(const ad_pic* h, double* out);

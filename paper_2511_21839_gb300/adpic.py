@@ -71,6 +71,7 @@ def lib():
             "ad_pic_stage": (ct.c_int, [vp, ct.c_int, ct.c_int64, dp]),
             "ad_pic_constants": (ct.c_int, [vp, dp]),
             "ad_pic_launches": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
+            "ad_pic_moments_device": (ct.c_int, [vp, ct.c_int64, ct.c_int, ct.c_int, vp, vp]),
             "ad_pic_destroy": (None, [vp]),
             "ad_pic_strerror": (ct.c_char_p, [ct.c_int]),
         }
@@ -178,6 +179,13 @@ def ad_pic_kernel_name(cls):
 def ad_pic_stage(h, stage, kick, out=None):
     _ck("ad_pic_stage", lib().ad_pic_stage(h, int(stage), int(kick), None if out is None else _p(out)))
     return out
+
+
+def ad_pic_moments_device(state_ptr, n_particles, n_deriv, precision, mom_ptr, stream_ptr=None):
+    """Allocation-free dual moments of a device state (device pointers as integers); enqueues only."""
+    _ck("ad_pic_moments_device", lib().ad_pic_moments_device(ct.c_void_p(state_ptr), int(n_particles), int(n_deriv),
+                                                             int(precision), ct.c_void_p(mom_ptr),
+                                                             ct.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 def ad_pic_launches(h):
