@@ -107,6 +107,14 @@ struct ad_pic {
     cudaStream_t own_stream = nullptr, stream = nullptr;
     // device memory
     void* state = nullptr;
+    void* state2 = nullptr;      // the other buffer of the cell-sorting push
+    int cur = 0;                 // which buffer holds the particles (0: state, 1: state2)
+    int* ids[2] = {nullptr, nullptr};   // caller's particle index of each slot
+    int* key = nullptr;          // cell of each particle at the last deposit
+    int* rank = nullptr;         // rank among that cell's particles
+    int* cellcount = nullptr;    // particles per cell (zero between kicks)
+    int* offs = nullptr;         // exclusive cell offsets
+    int* bsum = nullptr;         // scan chunk totals
     void* rho = nullptr;
     void* phi = nullptr;
     void* E = nullptr;
@@ -127,14 +135,13 @@ struct ad_pic {
     int records_cap = 0;
     double* staging = nullptr;      // FP64 [6][N][C] staging buffer of set/get_particles
     int64_t launches = 0;           // kernels launched by ad_pic_run so far
-    std::map<std::tuple<int, int, int, unsigned>, int64_t> graph_launches;
     std::vector<void*> allocs;
     // per-kick coefficients of the handle's precision (raw MapCoef / KickCoef)
     std::vector<unsigned char> half, comp, kcoef;
     std::vector<double> hist;   // records [3][5][C]
     // graphs
     bool use_graphs = true;
-    std::map<std::tuple<int, int, int, unsigned>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int, unsigned, int>, cudaGraphExec_t> graphs;
     // timing
     unsigned tmask = 0;
     std::vector<cudaEvent_t> events;
@@ -204,7 +211,24 @@ struct Impl {
     using M = MapCoef<T, CP>;
     using K = KickCoef<T, CP>;
 
-    static T* st(ad_pic* h) { return (T*)h->state; }
+    static T* buf(ad_pic* h, int b) { return (T*)(b ? h->state2 : h->state); }
+    static T* st(ad_pic* h) { return buf(h, h->cur); }
+    static SortBuf sortbuf(ad_pic* h, int from) {
+        SortBuf sb;
+        sb.key = h->key;
+        sb.rank = h->rank;
+        sb.hist = h->cellcount;
+        sb.offs = h->offs;
+        sb.ids_in = h->ids[from];
+        sb.ids_out = h->ids[1 - from];
+        return sb;
+    }
+    // gather + kick + map A from buffer `from` into the other one, in cell-sorted order
+    static void push(ad_pic* h, int& from, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track) {
+        launch_push<T, C, CP>(buf(h, from), buf(h, 1 - from), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, A,
+                              K, track, (Ord<T>*)h->mm, h->err, sortbuf(h, from), h->stream);
+        from = 1 - from;
+    }
 
     static M to_map(const HMap& a) {
         M r;
@@ -278,7 +302,7 @@ struct Impl {
     }
 
     // geometry -> deposit -> Green -> convolution -> field for the current state
-    static void enqueue_field(ad_pic* h, bool cap) {
+    static void enqueue_field(ad_pic* h, int from, bool cap) {
         cudaStream_t s = h->stream;
         const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
         tbegin(h, K_GEOM, cap);
@@ -288,9 +312,11 @@ struct Impl {
         cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s);
         tend(h, K_MISC, cap);
         tbegin(h, K_DEPOSIT, cap);
-        launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err, s);
+        launch_deposit<T, C, CP>(buf(h, from), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
+                                 sortbuf(h, from), s);
         tend(h, K_DEPOSIT, cap);
         tbegin(h, K_MISC, cap);
+        launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, s);
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
         tend(h, K_MISC, cap);
         tbegin(h, K_GREEN, cap);
@@ -314,50 +340,50 @@ struct Impl {
         tend(h, K_MISC, cap);
     }
 
-    // kernels launched by one enqueue_field (geometry 1, deposit 1, chmax 1,
-    // Green's function 5, convolution 5, field 1; the memset is not a kernel)
-    static constexpr int kFieldLaunches = 14;
+    // kernels launched by one enqueue_field (geometry 1, deposit 1, scan 3,
+    // chmax 1, Green's function 5, convolution 5, field 1; the memset is not a kernel)
+    static constexpr int kFieldLaunches = 17;
 
     // the launch sequence of one run; returns the number of moment records
-    static int enqueue_run(ad_pic* h, int64_t g0, int n, bool first, bool cap) {
+    // `from` is the buffer holding the particles at the start; each push moves
+    // them to the other buffer in cell-sorted order
+    static int enqueue_run(ad_pic* h, int64_t g0, int n, bool first, bool cap, int from) {
         cudaStream_t s = h->stream;
         const int nb = boundary_blocks();
         int nrec = 0;
         cudaMemsetAsync(h->err, 0, sizeof(int), s);
         if (n == 0) {
             tbegin(h, K_BOUNDARY, cap);
-            launch_boundary<T, C, CP>(st(h), h->N, identity(), false, true, h->partial, nb, (Ord<T>*)h->mm, s);
+            launch_boundary<T, C, CP>(buf(h, from), h->N, identity(), false, true, h->partial, nb, (Ord<T>*)h->mm, s);
             tend(h, K_BOUNDARY, cap);
             record(h, nrec++, cap);
             return nrec;
         }
         // opening half map M1(tau/2) of the first kick (+ initial moments)
         tbegin(h, K_BOUNDARY, cap);
-        launch_boundary<T, C, CP>(st(h), h->N, half(h, g0), true, first, h->partial, nb, (Ord<T>*)h->mm, s);
+        launch_boundary<T, C, CP>(buf(h, from), h->N, half(h, g0), true, first, h->partial, nb, (Ord<T>*)h->mm, s);
         tend(h, K_BOUNDARY, cap);
         if (first) record(h, nrec++, cap);
         for (int i = 0; i < n; ++i) {
             const int64_t g = g0 + i;
-            enqueue_field(h, cap);
+            enqueue_field(h, from, cap);
             const bool last = i == n - 1;
             const bool pend = ((g + 1) % h->kpp) == 0;
             if (last || pend) {
                 // M2(tau) then the closing M1(tau/2); moments at the period end,
                 // then the next kick's opening M1(tau/2)
                 tbegin(h, K_PUSH, cap);
-                launch_push<T, C, CP>(st(h), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, half(h, g),
-                                      kick(h, g), false, (Ord<T>*)h->mm, h->err, s);
+                push(h, from, half(h, g), kick(h, g), false);
                 tend(h, K_PUSH, cap);
                 tbegin(h, K_BOUNDARY, cap);
-                launch_boundary<T, C, CP>(st(h), h->N, half(h, g + 1), !last, true, h->partial, nb, (Ord<T>*)h->mm,
-                                          s);
+                launch_boundary<T, C, CP>(buf(h, from), h->N, half(h, g + 1), !last, true, h->partial, nb,
+                                          (Ord<T>*)h->mm, s);
                 tend(h, K_BOUNDARY, cap);
                 record(h, nrec++, cap);
             } else {
                 // M2(tau) then M1(tau/2) of this kick composed with M1(tau/2) of the next
                 tbegin(h, K_PUSH, cap);
-                launch_push<T, C, CP>(st(h), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, comp(h, g),
-                                      kick(h, g), true, (Ord<T>*)h->mm, h->err, s);
+                push(h, from, comp(h, g), kick(h, g), true);
                 tend(h, K_PUSH, cap);
             }
         }
@@ -390,13 +416,14 @@ struct Impl {
             else l = 1 + (int64_t)n * (kFieldLaunches + 1) + 2 * (int64_t)nr - (first ? 1 : 0);
             h->launches += l;
         }
+        const int from = h->cur;
         if (h->use_graphs) {
-            auto key = std::make_tuple((int)(g0 % h->kpp), n, first ? 1 : 0, h->tmask);
+            auto key = std::make_tuple((int)(g0 % h->kpp), n, first ? 1 : 0, h->tmask, from);
             auto it = h->graphs.find(key);
             if (it == h->graphs.end()) {
                 cudaGraph_t graph;
                 CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-                nrec = enqueue_run(h, g0, n, first, true);
+                nrec = enqueue_run(h, g0, n, first, true, from);
                 CK(cudaStreamEndCapture(h->stream, &graph));
                 cudaGraphExec_t ex;
                 CK(cudaGraphInstantiate(&ex, graph, 0));
@@ -409,9 +436,10 @@ struct Impl {
             }
             CK(cudaGraphLaunch(it->second, h->stream));
         } else {
-            nrec = enqueue_run(h, g0, n, first, false);
+            nrec = enqueue_run(h, g0, n, first, false, from);
             CK(cudaGetLastError());
         }
+        h->cur = (n % 2) ? 1 - from : from;
         std::vector<double> rec((size_t)nrec * 15 * CP);
         int errw = 0;
         CK(cudaMemcpyAsync(rec.data(), h->records, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, h->stream));
@@ -443,6 +471,7 @@ struct Impl {
         int pend = nrec - (first ? 1 : 0);   // boundary+record pairs inside the loop
         int e = on(K_BOUNDARY) + (first ? on(K_MISC) : 0);
         e += n * (on(K_GEOM) + 2 * on(K_MISC) + on(K_DEPOSIT) + on(K_GREEN) + on(K_FFT) + on(K_FIELD) + on(K_PUSH));
+        // (the scan and chmax share one MISC event pair; the memset has its own)
         e += pend * (on(K_BOUNDARY) + on(K_MISC));
         return 2 * e;
     }
@@ -492,7 +521,10 @@ struct Impl {
         }
         cudaError_t e1 = cudaMemcpyAsync(nd, normals, sizeof(double) * 6 * h->N, cudaMemcpyHostToDevice, h->stream);
         cudaError_t e2 = cudaMemcpyAsync(cd, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, h->stream);
-        if (e1 == cudaSuccess && e2 == cudaSuccess) launch_init<T, C, CP>(nd, h->N, cd, st(h), h->stream);
+        if (e1 == cudaSuccess && e2 == cudaSuccess) {
+            launch_init<T, C, CP>(nd, h->N, cd, st(h), h->stream);
+            launch_iota(h->ids[h->cur], h->N, h->stream);
+        }
         cudaError_t e3 = cudaStreamSynchronize(h->stream);
         cudaFree(nd);
         cudaFree(cd);
@@ -520,7 +552,10 @@ struct Impl {
         int r = staging(h, &tmp);
         if (r) return r;
         cudaError_t e1 = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, h->stream);
-        if (e1 == cudaSuccess) launch_convert_in<T, CP>(tmp, st(h), h->N, C, h->stream);
+        if (e1 == cudaSuccess) {
+            launch_convert_in<T, CP>(tmp, st(h), h->N, C, h->stream);
+            launch_iota(h->ids[h->cur], h->N, h->stream);
+        }
         cudaError_t e2 = cudaStreamSynchronize(h->stream);
         if (e1 != cudaSuccess || e2 != cudaSuccess || cudaGetLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
         h->particles_set = true;
@@ -536,7 +571,7 @@ struct Impl {
         const size_t bytes = sizeof(double) * 6 * h->N * C;
         int r = staging(h, &tmp);
         if (r) return r;
-        launch_convert_out<T, CP>(st(h), tmp, h->N, C, h->stream);
+        launch_convert_out_perm<T, CP>(st(h), h->ids[h->cur], tmp, h->N, C, h->stream);
         cudaError_t e1 = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
         cudaError_t e2 = cudaStreamSynchronize(h->stream);
         if (e1 != cudaSuccess || e2 != cudaSuccess || cudaGetLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
@@ -568,7 +603,9 @@ struct Impl {
         }
         // the geometry kernel already ran: do not run it twice (it resets the extrema)
         CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s));
-        launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err, s);
+        launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
+                                 sortbuf(h, h->cur), s);
+        launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, s);
         std::vector<T> buf;
         if (which == 1) {
             buf.resize(nodes * CP);
@@ -599,8 +636,7 @@ struct Impl {
             grid_out(buf, 3, nodes, out);
             return check_err(h);
         }
-        launch_push<T, C, CP>(st(h), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, identity(), kick(h, kk),
-                              false, (Ord<T>*)h->mm, h->err, s);
+        push(h, h->cur, identity(), kick(h, kk), false);
         CK(cudaStreamSynchronize(s));
         return check_err(h);
     }
@@ -621,6 +657,14 @@ struct Impl {
         const int Mx = 2 * h->nx, My = 2 * h->ny, Mz = 2 * h->nz;
         int r = 0;
         r |= dalloc(h, &h->state, sizeof(T) * 6 * h->N * CP);
+        r |= dalloc(h, &h->state2, sizeof(T) * 6 * h->N * CP);
+        r |= dalloc(h, (void**)&h->ids[0], sizeof(int) * h->N);
+        r |= dalloc(h, (void**)&h->ids[1], sizeof(int) * h->N);
+        r |= dalloc(h, (void**)&h->key, sizeof(int) * h->N);
+        r |= dalloc(h, (void**)&h->rank, sizeof(int) * h->N);
+        r |= dalloc(h, (void**)&h->cellcount, sizeof(int) * nodes);
+        r |= dalloc(h, (void**)&h->offs, sizeof(int) * nodes);
+        r |= dalloc(h, (void**)&h->bsum, sizeof(int) * (scan_blocks((int)nodes) + 1));
         r |= dalloc(h, &h->rho, sizeof(T) * nodes * CP);
         r |= dalloc(h, &h->phi, sizeof(T) * nodes * CP);
         r |= dalloc(h, &h->E, sizeof(T) * nodes * 3 * CP);
@@ -641,6 +685,8 @@ struct Impl {
         r |= dalloc(h, (void**)&h->partial, sizeof(double) * boundary_blocks() * 15 * CP);
         if (r) return AD_PIC_ERR_OOM;
         CK(cudaMemsetAsync(h->state, 0, sizeof(T) * 6 * h->N * CP, h->stream));
+        CK(cudaMemsetAsync(h->cellcount, 0, sizeof(int) * nodes, h->stream));
+        launch_iota(h->ids[0], h->N, h->stream);
         CK(cudaMemsetAsync(h->E, 0, sizeof(T) * nodes * 3 * CP, h->stream));
         std::vector<Ord<T>> mm0 = {~(Ord<T>)0, ~(Ord<T>)0, ~(Ord<T>)0, 0, 0, 0};
         CK(cudaMemcpyAsync(h->mm, mm0.data(), sizeof(Ord<T>) * 6, cudaMemcpyHostToDevice, h->stream));

@@ -63,17 +63,36 @@ void launch_convert_in(const double* src, T* dst, int64_t N, int C, cudaStream_t
 template <typename T, int CP>
 void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_t s);
 
+// Cell sort carried by the particle kernels: the deposit records each
+// particle's cell (key) and its rank among the particles of that cell (hist
+// counts them); the scan turns hist into exclusive offsets (offs) and clears
+// hist; the push writes particle i to slot offs[key[i]] + rank[i] of the
+// other state buffer and carries its id along (ids_out[slot] = ids_in[i]).
+struct SortBuf {
+    int* key;
+    int* rank;
+    int* hist;
+    const int* offs;
+    const int* ids_in;
+    int* ids_out;
+};
+
 template <typename T, int C, int CP>
-void launch_push(T* state, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
+void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
-                 cudaStream_t s);
+                 const SortBuf& sb, cudaStream_t s);
+void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s);
+int scan_blocks(int ncells);
+void launch_iota(int* ids, int64_t N, cudaStream_t s);
+template <typename T, int CP>
+void launch_convert_out_perm(const T* src, const int* ids, double* dst, int64_t N, int C, cudaStream_t s);
 template <typename T, int C, int CP>
 void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
                      int nblocks, Ord<T>* mm, cudaStream_t s);
 int boundary_blocks();
 template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho,
-                    int* err, cudaStream_t s);
+                    int* err, const SortBuf& sb, cudaStream_t s);
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s);
 
 template <typename T>

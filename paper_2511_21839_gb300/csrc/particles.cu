@@ -205,10 +205,10 @@ void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_
 // are live: E_p,k = sum W E_k + sum_d (x_d,k / h_d) sum dW/du_d E_0 (Eq. 2 on
 // the weight product), then p_k += a0 E_p,k + a_k E_p,0 in one rounding.
 template <typename T, int C, int CP, bool TRACK>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) push_kernel(T* __restrict__ state, int64_t N, const T* __restrict__ E,
-                                                      const GeomDev* __restrict__ geom, int nx, int ny, int nz,
-                                                      const MapCoef<T, CP> A, const KickCoef<T, CP> K,
-                                                      Ord<T>* __restrict__ mm, int* __restrict__ err) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    push_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
+                const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
+                const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
@@ -288,8 +288,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) push_kernel(T* __
             x[0] = fma(a0, x0, b0 * p0);
             p[0] = fma(c0, x0, d0 * p0);
         }
+        // cell-sorted slot of this particle (cell and rank from this kick's deposit)
+        const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
+        if (sb.ids_out) sb.ids_out[dst] = sb.ids_in[i];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) stv<T, CP>(state + (c * N + i) * CP, u[c]);
+        for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
         if (TRACK) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) { mn[d] = u[2 * d][0]; mx[d] = u[2 * d][0]; }
@@ -299,15 +302,131 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) push_kernel(T* __
 }
 
 template <typename T, int C, int CP>
-void launch_push(T* state, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
+void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
-                 cudaStream_t s) {
+                 const SortBuf& sb, cudaStream_t s) {
     if (N <= 0) return;
     unsigned blocks = (unsigned)((N + 255) / 256);
     if (track)
-        push_kernel<T, C, CP, true><<<blocks, 256, 0, s>>>(state, N, E, geom, nx, ny, nz, A, K, mm, err);
+        push_kernel<T, C, CP, true><<<blocks, 256, 0, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err,
+                                                          sb);
     else
-        push_kernel<T, C, CP, false><<<blocks, 256, 0, s>>>(state, N, E, geom, nx, ny, nz, A, K, mm, err);
+        push_kernel<T, C, CP, false><<<blocks, 256, 0, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm,
+                                                           err, sb);
+}
+
+// ------------------------------------------------------------------ cell sort: scan, ids
+
+constexpr int kScanChunk = 2048;   // cells per block of the scan
+int scan_blocks(int ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
+
+__device__ __forceinline__ int block_excl_scan(int v, int* sm, int& total) {
+    // 256-thread exclusive scan of one int per thread
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sm[lane] = t;
+    }
+    __syncthreads();
+    total = sm[(blockDim.x >> 5) - 1];
+    const int before = w > 0 ? sm[w - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+// per-chunk totals of hist
+__global__ void scan_sum_kernel(const int* __restrict__ hist, int ncells, int* __restrict__ bsum) {
+    __shared__ int sm[32];
+    const int base = blockIdx.x * kScanChunk;
+    int v = 0;
+    for (int j = threadIdx.x; j < kScanChunk; j += blockDim.x)
+        if (base + j < ncells) v += hist[base + j];
+    int total;
+    block_excl_scan(v, sm, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// exclusive scan of the chunk totals (one block; at most 256 x 8 chunks)
+__global__ void scan_top_kernel(int* __restrict__ bsum, int nb) {
+    __shared__ int sm[32];
+    constexpr int PER = 8;
+    int v[PER], s = 0;
+    for (int q = 0; q < PER; ++q) {
+        const int j = threadIdx.x * PER + q;
+        v[q] = j < nb ? bsum[j] : 0;
+        s += v[q];
+    }
+    int total;
+    int run = block_excl_scan(s, sm, total);
+    for (int q = 0; q < PER; ++q) {
+        const int j = threadIdx.x * PER + q;
+        if (j < nb) bsum[j] = run;
+        run += v[q];
+    }
+}
+
+// exclusive offsets of every cell; clears hist for the next kick
+__global__ void scan_apply_kernel(int* __restrict__ hist, int ncells, const int* __restrict__ bsum,
+                                  int* __restrict__ offs) {
+    __shared__ int sm[32];
+    constexpr int PER = kScanChunk / 256;
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * PER;
+    int v[PER], s = 0;
+    for (int q = 0; q < PER; ++q) {
+        v[q] = base + q < ncells ? hist[base + q] : 0;
+        s += v[q];
+    }
+    int total;
+    int run = block_excl_scan(s, sm, total) + bsum[blockIdx.x];
+    for (int q = 0; q < PER; ++q) {
+        if (base + q < ncells) {
+            offs[base + q] = run;
+            hist[base + q] = 0;
+        }
+        run += v[q];
+    }
+}
+
+void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s) {
+    const int nb = scan_blocks(ncells);
+    scan_sum_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum);
+    scan_top_kernel<<<1, 256, 0, s>>>(bsum, nb);
+    scan_apply_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum, offs);
+}
+
+__global__ void iota_kernel(int* ids, int64_t N) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) ids[i] = (int)i;
+}
+void launch_iota(int* ids, int64_t N, cudaStream_t s) {
+    if (N > 0) iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ids, N);
+}
+
+// device state [6][N][CP] in sorted order -> host layout [6][N][C] in the caller's order
+template <typename T, int CP>
+__global__ void convert_out_perm_kernel(const T* __restrict__ src, const int* __restrict__ ids, double* __restrict__ dst,
+                                        int64_t N, int C) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 6 * N * C) return;
+    const int k = (int)(t % C);
+    const int64_t i = (t / C) % N, c = t / ((int64_t)N * C);
+    dst[(c * N + ids[i]) * C + k] = (double)src[(c * N + i) * CP + k];
+}
+template <typename T, int CP>
+void launch_convert_out_perm(const T* src, const int* ids, double* dst, int64_t N, int C, cudaStream_t s) {
+    const int64_t tot = 6 * N * C;
+    if (tot > 0) convert_out_perm_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, ids, dst, N, C);
 }
 
 // ------------------------------------------------------------------ period boundary: moments + half map
@@ -474,52 +593,77 @@ void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N
 
 // ------------------------------------------------------------------ deposition
 
-// One thread per particle: CIC weights of the value part and their
-// derivatives through the particle's derivative channels; node charge
-// q_m W for channel 0 and q_m dW/dp_k for channel k, accumulated with
-// 128-bit float atomics (FP32) or FP64 atomics.
-template <typename T, int C, int CP>
-__global__ void __launch_bounds__(256) deposit_kernel(const T* __restrict__ state, int64_t N,
+// CIC weights of the value part and their derivatives through the particle's
+// derivative channels; node charge q_m W for channel 0 and q_m dW/dp_k for
+// channel k. Each thread takes RUN consecutive particles (the push keeps them
+// cell-sorted), accumulates the eight node records in registers while the
+// cell does not change, and flushes them with 128-bit float atomics (FP32) or
+// FP64 atomics when it does. Records every particle's cell and its rank among
+// that cell's particles for the sort.
+template <typename T, int C, int CP, int RUN>
+__global__ void __launch_bounds__(RUN > 1 ? 128 : 256, RUN > 1 ? 3 : 1) deposit_kernel(const T* __restrict__ state, int64_t N,
                                                       const GeomDev* __restrict__ geom, int nx, int ny, int nz,
-                                                      T qm, T* __restrict__ rho, int* __restrict__ err) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
+                                                      T qm, T* __restrict__ rho, int* __restrict__ err,
+                                                      const SortBuf sb) {
+    const int64_t first = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * RUN;
+    if (first >= N) return;
     const GeomDev& g = *geom;
     const int n[3] = {nx, ny, nz};
-    T x[3][CP];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
-    T f[3], ih[3];
-    int idx[3];
-    int bad = 0;
+    T ih[3], o[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         ih[d] = geom_ih<T>(g, d);
-        idx[d] = cell_of<T>(x[d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
+        o[d] = geom_o<T>(g, d);
     }
-    if (bad) atomicOr(err, bad);
-    T dx[3][CP];
+    T acc[RUN > 1 ? 8 : 1][RUN > 1 ? CP : 1];
+    int cur = -1;
+    int bad = 0;
+    auto flush = [&](int cell) {
+        const int i0 = cell % nx, j0 = (cell / nx) % ny, k0 = cell / (nx * ny);
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+        for (int nd = 0; nd < 8; ++nd) {
+            const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+            const int64_t node = ((int64_t)(k0 + c) * ny + (j0 + b)) * nx + (i0 + a);
+            T* dst = rho + node * CP;
+            if constexpr (RUN > 1 && sizeof(T) == 4) {
 #pragma unroll
-        for (int k = 1; k < CP; ++k) dx[d][k] = qm * x[d][k] * ih[d];
+                for (int v = 0; v < CP / 4; ++v)
+                    atomicAdd(reinterpret_cast<float4*>(dst) + v,
+                              make_float4(acc[nd][4 * v], acc[nd][4 * v + 1], acc[nd][4 * v + 2], acc[nd][4 * v + 3]));
+            } else if constexpr (RUN > 1) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const T wz = c ? f[2] : (T)1 - f[2];
-        const T sz = c ? (T)1 : (T)-1;
+                for (int k = 0; k < C; ++k) atomicAdd(dst + k, acc[nd][k]);
+            }
+        }
+    };
+    for (int r = 0; r < RUN; ++r) {
+        const int64_t i = first + r;
+        if (i >= N) break;
+        T x[3][CP];
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const T wy = b ? f[1] : (T)1 - f[1];
-            const T sy = b ? (T)1 : (T)-1;
+        for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
+        T f[3];
+        int idx[3];
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const T wx = a ? f[0] : (T)1 - f[0];
-                const T sx = a ? (T)1 : (T)-1;
-                const T dWx = sx * wy * wz, dWy = wx * sy * wz, dWz = wx * wy * sz;
+        for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(x[d][0], o[d], ih[d], n[d], f[d], bad);
+        const int cell = (idx[2] * ny + idx[1]) * nx + idx[0];
+        if (sb.key) {
+            sb.key[i] = cell;
+            sb.rank[i] = atomicAdd(&sb.hist[cell], 1);
+        }
+        if constexpr (RUN == 1) {
+            // one particle per thread: add each node record at once
+#pragma unroll
+            for (int nd = 0; nd < 8; ++nd) {
+                const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
+                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
+                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
+                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
                 T q[CP];
                 q[0] = qm * (wx * wy * wz);
 #pragma unroll
-                for (int k = 1; k < CP; ++k) q[k] = fma(dx[0][k], dWx, fma(dx[1][k], dWy, dx[2][k] * dWz));
+                for (int k = 1; k < CP; ++k) q[k] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
                 const int64_t node = ((int64_t)(idx[2] + c) * ny + (idx[1] + b)) * nx + (idx[0] + a);
                 T* dst = rho + node * CP;
                 if constexpr (sizeof(T) == 4) {
@@ -532,27 +676,55 @@ __global__ void __launch_bounds__(256) deposit_kernel(const T* __restrict__ stat
                     for (int k = 0; k < C; ++k) atomicAdd(dst + k, q[k]);
                 }
             }
+        } else {
+            if (cell != cur) {
+                if (cur >= 0) flush(cur);
+                cur = cell;
+#pragma unroll
+                for (int nd = 0; nd < 8; ++nd)
+#pragma unroll
+                    for (int k = 0; k < CP; ++k) acc[nd][k] = (T)0;
+            }
+#pragma unroll
+            for (int nd = 0; nd < 8; ++nd) {
+                const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
+                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
+                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
+                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
+                acc[nd][0] = fma(qm, wx * wy * wz, acc[nd][0]);
+#pragma unroll
+                for (int k = 1; k < CP; ++k) acc[nd][k] = fma(x[0][k], gx, fma(x[1][k], gy, fma(x[2][k], gz, acc[nd][k])));
+            }
         }
     }
+    if (RUN > 1 && cur >= 0) flush(cur);
+    if (bad) atomicOr(err, bad);
 }
 
 template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho, int* err,
-                    cudaStream_t s) {
+                    const SortBuf& sb, cudaStream_t s) {
     if (N <= 0) return;
-    deposit_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(state, N, geom, nx, ny, nz, qm, rho, err);
+    // register-resident runs for the FP32 8-channel dual; the other variants take one particle per
+    // thread (their eight node records would not fit in registers)
+    constexpr int RUN = (CP == 8 && sizeof(T) == 4) ? 8 : 1;
+    const int64_t threads = (N + RUN - 1) / RUN;
+    constexpr int BS = RUN > 1 ? 128 : 256;
+    deposit_kernel<T, C, CP, RUN><<<(unsigned)((threads + BS - 1) / BS), BS, 0, s>>>(state, N, geom, nx, ny, nz, qm,
+                                                                                    rho, err, sb);
 }
 
 // ------------------------------------------------------------------ instantiations
 #define ADPIC_INST(T, C, CP)                                                                                       \
     template void launch_init<T, C, CP>(const double*, int64_t, const double*, T*, cudaStream_t);                \
-    template void launch_push<T, C, CP>(T*, int64_t, const T*, const GeomDev*, int, int, int,                     \
+    template void launch_push<T, C, CP>(const T*, T*, int64_t, const T*, const GeomDev*, int, int, int,         \
                                         const MapCoef<T, CP>&, const KickCoef<T, CP>&, bool, Ord<T>*, int*,      \
-                                        cudaStream_t);                                                           \
+                                        const SortBuf&, cudaStream_t);                                           \
     template void launch_boundary<T, C, CP>(T*, int64_t, const MapCoef<T, CP>&, bool, bool, double*, int,       \
                                             Ord<T>*, cudaStream_t);                                              \
     template void launch_deposit<T, C, CP>(const T*, int64_t, const GeomDev*, int, int, int, T, T*, int*,        \
-                                           cudaStream_t);
+                                           const SortBuf&, cudaStream_t);
 ADPIC_INST(float, 8, 8)
 ADPIC_INST(float, 14, 16)
 ADPIC_INST(double, 8, 8)
@@ -565,5 +737,9 @@ template void launch_convert_out<float, 8>(const float*, double*, int64_t, int, 
 template void launch_convert_out<float, 16>(const float*, double*, int64_t, int, cudaStream_t);
 template void launch_convert_out<double, 8>(const double*, double*, int64_t, int, cudaStream_t);
 template void launch_convert_out<double, 16>(const double*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out_perm<float, 8>(const float*, const int*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out_perm<float, 16>(const float*, const int*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out_perm<double, 8>(const double*, const int*, double*, int64_t, int, cudaStream_t);
+template void launch_convert_out_perm<double, 16>(const double*, const int*, double*, int64_t, int, cudaStream_t);
 
 }  // namespace adpic
