@@ -161,6 +161,43 @@ int ad_pic_launches(const ad_pic* h, int64_t* n);
    in place (out unused). Stages 1-4 use the geometry of the current state. */
 int ad_pic_stage(ad_pic* h, int stage, int64_t kick, double* out);
 
+/* ---------------------------------------------------------------------
+   Batched runs: many instances (own lattice, beam, particle count and cubic
+   grid each; n_deriv 7) advanced together, as sensitivity scans and line
+   searches need. Each kick of every instance is the same split step as
+   ad_pic_run; the batch walks it phase by phase for all instances at once in
+   one persistent cooperative kernel (or one launch per phase), captured in a
+   CUDA graph. All instances must share the kicks per element and be set up
+   (beam, lattice) before ad_pic_batch_run; they advance in lockstep.
+   --------------------------------------------------------------------- */
+typedef struct ad_pic_batch ad_pic_batch;
+
+/* grids[i]: cubic, nx = ny = nz = 32 or 64; n_particles[i] in [1, 2^31 - 1];
+   n_deriv must be 7 and precision AD_PIC_FP32_MIXED (else
+   AD_PIC_ERR_UNSUPPORTED). Allocates every instance. */
+int ad_pic_batch_create(int n_inst, const ad_pic_grid* grids, const int64_t* n_particles, int n_deriv,
+                        int precision, ad_pic_batch** out);
+/* Per-instance set-up and read-back; same arguments and semantics as the
+   single-instance calls (inst in [0, n_inst)). */
+int ad_pic_batch_set_beam(ad_pic_batch* b, int inst, const ad_pic_beam* beam, const double* normals);
+int ad_pic_batch_set_particles(ad_pic_batch* b, int inst, const double* state);
+int ad_pic_batch_set_lattice(ad_pic_batch* b, int inst, const ad_pic_lattice* lattice);
+int ad_pic_batch_moments(const ad_pic_batch* b, int inst, double* values, double* derivs);
+int ad_pic_batch_history(const ad_pic_batch* b, int inst, double* hist, int max_records, int* n_records);
+int ad_pic_batch_get_particles(const ad_pic_batch* b, int inst, double* state);
+/* Advance every instance n_steps kicks (synchronises). Returns
+   AD_PIC_ERR_STATE if the instances are not in lockstep or not set up. */
+int ad_pic_batch_run(ad_pic_batch* b, int n_steps);
+/* Execution mode: 0 autotune (default; times one kick of the batch in each
+   mode on the first run and keeps the fastest), 1 persistent kernel with one
+   block per SM, 2 persistent with two, 3 one launch per phase. */
+int ad_pic_batch_set_mode(ad_pic_batch* b, int mode);
+/* Mode in use and the tuner's per-kick times ms[3] for modes 1..3 (ms; -1 =
+   not possible on this device, 0 = not tuned). */
+int ad_pic_batch_tuning(const ad_pic_batch* b, int* mode, double* ms);
+int ad_pic_batch_set_stream(ad_pic_batch* b, void* stream);
+void ad_pic_batch_destroy(ad_pic_batch* b);
+
 /* Allocation-free dual moments of a caller-owned device state (the paper has
    no counterpart: this exists for callers that cannot let the library call
    cudaMalloc/cudaFree - code running inside another framework's device-memory

@@ -72,6 +72,19 @@ def lib():
             "ad_pic_constants": (ct.c_int, [vp, dp]),
             "ad_pic_launches": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
             "ad_pic_moments_device": (ct.c_int, [vp, ct.c_int64, ct.c_int, ct.c_int, vp, vp]),
+            "ad_pic_batch_create": (ct.c_int, [ct.c_int, ct.POINTER(ad_pic_grid), ct.POINTER(ct.c_int64), ct.c_int,
+                                               ct.c_int, ct.POINTER(vp)]),
+            "ad_pic_batch_set_beam": (ct.c_int, [vp, ct.c_int, ct.POINTER(ad_pic_beam), dp]),
+            "ad_pic_batch_set_particles": (ct.c_int, [vp, ct.c_int, dp]),
+            "ad_pic_batch_set_lattice": (ct.c_int, [vp, ct.c_int, ct.POINTER(ad_pic_lattice)]),
+            "ad_pic_batch_moments": (ct.c_int, [vp, ct.c_int, dp, dp]),
+            "ad_pic_batch_history": (ct.c_int, [vp, ct.c_int, dp, ct.c_int, ct.POINTER(ct.c_int)]),
+            "ad_pic_batch_get_particles": (ct.c_int, [vp, ct.c_int, dp]),
+            "ad_pic_batch_run": (ct.c_int, [vp, ct.c_int]),
+            "ad_pic_batch_set_mode": (ct.c_int, [vp, ct.c_int]),
+            "ad_pic_batch_tuning": (ct.c_int, [vp, ct.POINTER(ct.c_int), dp]),
+            "ad_pic_batch_set_stream": (ct.c_int, [vp, vp]),
+            "ad_pic_batch_destroy": (None, [vp]),
             "ad_pic_destroy": (None, [vp]),
             "ad_pic_strerror": (ct.c_char_p, [ct.c_int]),
         }
@@ -210,6 +223,75 @@ def ad_pic_strerror(status):
     return lib().ad_pic_strerror(int(status)).decode()
 
 
+def ad_pic_batch_create(grids, n_particles, n_deriv, precision):
+    n = len(grids)
+    g = (ad_pic_grid * n)(*[ad_pic_grid(*gr) for gr in grids])
+    npart = (ct.c_int64 * n)(*[int(v) for v in n_particles])
+    b = ct.c_void_p()
+    _ck("ad_pic_batch_create", lib().ad_pic_batch_create(n, g, npart, int(n_deriv), int(precision), ct.byref(b)))
+    return b
+
+
+def ad_pic_batch_set_beam(b, inst, beam: ad_pic_beam, normals=None):
+    nrm = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64)
+    _ck("ad_pic_batch_set_beam", lib().ad_pic_batch_set_beam(b, int(inst), ct.byref(beam),
+                                                             None if nrm is None else _p(nrm)))
+
+
+def ad_pic_batch_set_particles(b, inst, state):
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    _ck("ad_pic_batch_set_particles", lib().ad_pic_batch_set_particles(b, int(inst), _p(s)))
+
+
+def ad_pic_batch_set_lattice(b, inst, lat: ad_pic_lattice):
+    _ck("ad_pic_batch_set_lattice", lib().ad_pic_batch_set_lattice(b, int(inst), ct.byref(lat)))
+
+
+def ad_pic_batch_run(b, n_steps):
+    _ck("ad_pic_batch_run", lib().ad_pic_batch_run(b, int(n_steps)))
+
+
+def ad_pic_batch_moments(b, inst, P):
+    v = np.zeros(2)
+    d = np.zeros(2 * P)
+    _ck("ad_pic_batch_moments", lib().ad_pic_batch_moments(b, int(inst), _p(v), _p(d)))
+    return v, d.reshape(2, P)
+
+
+def ad_pic_batch_history(b, inst, C):
+    n = ct.c_int()
+    _ck("ad_pic_batch_history", lib().ad_pic_batch_history(b, int(inst), None, 0, ct.byref(n)))
+    out = np.zeros((n.value, 3, 5, C))
+    if n.value:
+        _ck("ad_pic_batch_history", lib().ad_pic_batch_history(b, int(inst), _p(out), n.value, ct.byref(n)))
+    return out
+
+
+def ad_pic_batch_get_particles(b, inst, out):
+    _ck("ad_pic_batch_get_particles", lib().ad_pic_batch_get_particles(b, int(inst), _p(out)))
+    return out
+
+
+def ad_pic_batch_set_mode(b, mode):
+    _ck("ad_pic_batch_set_mode", lib().ad_pic_batch_set_mode(b, int(mode)))
+
+
+def ad_pic_batch_tuning(b):
+    m = ct.c_int()
+    ms = np.zeros(3)
+    _ck("ad_pic_batch_tuning", lib().ad_pic_batch_tuning(b, ct.byref(m), _p(ms)))
+    return m.value, ms
+
+
+def ad_pic_batch_set_stream(b, stream_ptr):
+    _ck("ad_pic_batch_set_stream", lib().ad_pic_batch_set_stream(b, ct.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def ad_pic_batch_destroy(b):
+    if b:
+        lib().ad_pic_batch_destroy(b)
+
+
 # ------------------------------------------------------------------ convenience wrapper
 
 def make_beam(b) -> ad_pic_beam:
@@ -293,3 +375,49 @@ class ADPIC:
 
     def timing(self):
         return ad_pic_timing(self.h)
+
+
+class Batch:
+    """Many instances advanced together (the batched scan)."""
+
+    def __init__(self, grids, n_particles, precision=AD_PIC_FP32_MIXED, n_deriv=7):
+        self.n = len(grids)
+        self.P = n_deriv
+        self.C = n_deriv + 1
+        self.N = [int(v) for v in n_particles]
+        self.b = ad_pic_batch_create([tuple(g) for g in grids], self.N, n_deriv, precision)
+
+    def close(self):
+        if self.b:
+            ad_pic_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_beam(self, i, beam, normals=None):
+        ad_pic_batch_set_beam(self.b, i, make_beam(beam), normals)
+
+    def set_lattice(self, i, lat):
+        ad_pic_batch_set_lattice(self.b, i, make_lattice(lat))
+
+    def run(self, n_steps):
+        ad_pic_batch_run(self.b, n_steps)
+
+    def moments(self, i):
+        return ad_pic_batch_moments(self.b, i, self.P)
+
+    def history(self, i):
+        return ad_pic_batch_history(self.b, i, self.C)
+
+    def get_particles(self, i):
+        return ad_pic_batch_get_particles(self.b, i, np.zeros((6, self.N[i], self.C)))
+
+    def set_mode(self, mode):
+        ad_pic_batch_set_mode(self.b, mode)
+
+    def tuning(self):
+        return ad_pic_batch_tuning(self.b)

@@ -13,6 +13,7 @@
 
 #include "ad_pic.h"
 #include "common.cuh"
+#include "handle.h"
 
 using namespace adpic;
 
@@ -23,7 +24,6 @@ constexpr double kC = 299792458.0;
 constexpr double kQE = 1.602176634e-19;
 
 constexpr int kMaxCP = 16;
-constexpr int kClasses = 8;
 const char* kClassNames[kClasses] = {"push", "boundary", "deposit", "green", "fft", "field", "geometry", "misc"};
 enum { K_PUSH = 0, K_BOUNDARY, K_DEPOSIT, K_GREEN, K_FFT, K_FIELD, K_GEOM, K_MISC };
 
@@ -94,62 +94,7 @@ int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 }  // namespace
 
-struct ad_pic {
-    int prec = 0, P = 7, C = 8, CP = 8;
-    int nx = 0, ny = 0, nz = 0;
-    int64_t N = 0;
-    bool beam_set = false, particles_set = false, lattice_set = false, coef_dirty = true;
-    double gamma0 = 0, beta0 = 0, p0 = 0, brho = 0, kperp = 0, kz = 0, qm = 0, q = 0;
-    ad_pic_lattice lat{};
-    int kpp = 0;
-    int64_t kick = 0;
-    bool first_record = true;
-    cudaStream_t own_stream = nullptr, stream = nullptr;
-    // device memory
-    void* state = nullptr;
-    void* state2 = nullptr;      // the other buffer of the cell-sorting push
-    int cur = 0;                 // which buffer holds the particles (0: state, 1: state2)
-    int* ids[2] = {nullptr, nullptr};   // caller's particle index of each slot
-    int* key = nullptr;          // cell of each particle at the last deposit
-    int* rank = nullptr;         // rank among that cell's particles
-    int* cellcount = nullptr;    // particles per cell (zero between kicks)
-    int* offs = nullptr;         // exclusive cell offsets
-    int* bsum = nullptr;         // scan chunk totals
-    void* rho = nullptr;
-    void* phi = nullptr;
-    void* E = nullptr;
-    void* X1 = nullptr;
-    void* X2 = nullptr;
-    void* G = nullptr;
-    void* Gtmp = nullptr;
-    void* Ghat = nullptr;
-    double* corner = nullptr;
-    void* dct[3] = {nullptr, nullptr, nullptr};
-    void* tw[3] = {nullptr, nullptr, nullptr};
-    GeomDev* geom = nullptr;
-    void* mm = nullptr;
-    void* chmax = nullptr;
-    int* err = nullptr;
-    double* partial = nullptr;
-    double* records = nullptr;
-    int records_cap = 0;
-    double* staging = nullptr;      // FP64 [6][N][C] staging buffer of set/get_particles
-    int64_t launches = 0;           // kernels launched by ad_pic_run so far
-    std::vector<void*> allocs;
-    // per-kick coefficients of the handle's precision (raw MapCoef / KickCoef)
-    std::vector<unsigned char> half, comp, kcoef;
-    std::vector<double> hist;   // records [3][5][C]
-    // graphs
-    bool use_graphs = true;
-    std::map<std::tuple<int, int, int, unsigned, int>, cudaGraphExec_t> graphs;
-    // timing
-    unsigned tmask = 0;
-    std::vector<cudaEvent_t> events;
-    std::vector<int> ev_class;
-    int ev_used = 0;
-    double tms[kClasses] = {0};
-    int64_t tcount[kClasses] = {0};
-};
+
 
 namespace {
 
@@ -390,12 +335,8 @@ struct Impl {
         return nrec;
     }
 
-    static int run(ad_pic* h, int n) {
-        if (h->coef_dirty) build_coef(h);
-        const int64_t g0 = h->kick;
-        const bool first = h->first_record;
-        // records needed
-        int need = (first ? 1 : 0) + 1 + (int)(n / (h->kpp > 0 ? h->kpp : 1)) + 1;
+    static int ensure_records(ad_pic* h, int n) {
+        const int need = (h->first_record ? 1 : 0) + 1 + (int)(n / (h->kpp > 0 ? h->kpp : 1)) + 1;
         if (need > h->records_cap) {
             if (h->records) cudaFree(h->records);
             for (auto& p : h->allocs) if (p == h->records) p = nullptr;
@@ -404,6 +345,35 @@ struct Impl {
             if (st_) return st_;
             h->records_cap = need;
             free_graphs(h);
+        }
+        return AD_PIC_OK;
+    }
+
+    // append moment records [nrec][15][CP] to the history; advance counter and buffer parity
+    static void finish(ad_pic* h, const double* rec, int nrec, int n) {
+        for (int r = 0; r < nrec; ++r)
+            for (int q = 0; q < 15; ++q)
+                for (int k = 0; k < C; ++k) h->hist.push_back(rec[((size_t)r * 15 + q) * CP + k]);
+        h->kick += n;
+        h->first_record = false;
+        if (n % 2) h->cur = 1 - h->cur;
+    }
+
+    static int prepare(ad_pic* h, int n, int* nrec) {
+        if (h->coef_dirty) build_coef(h);
+        int st_ = ensure_records(h, n);
+        if (st_) return st_;
+        *nrec = count_records(h, h->kick, n, h->first_record);
+        return AD_PIC_OK;
+    }
+
+    static int run(ad_pic* h, int n) {
+        if (h->coef_dirty) build_coef(h);
+        const int64_t g0 = h->kick;
+        const bool first = h->first_record;
+        {
+            int st_ = ensure_records(h, n);
+            if (st_) return st_;
         }
         h->ev_used = 0;
         int nrec = 0;
@@ -439,18 +409,13 @@ struct Impl {
             nrec = enqueue_run(h, g0, n, first, false, from);
             CK(cudaGetLastError());
         }
-        h->cur = (n % 2) ? 1 - from : from;
         std::vector<double> rec((size_t)nrec * 15 * CP);
         int errw = 0;
         CK(cudaMemcpyAsync(rec.data(), h->records, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaMemcpyAsync(&errw, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         if (h->tmask) tcollect(h, h->ev_used / 2);
-        for (int r = 0; r < nrec; ++r)
-            for (int q = 0; q < 15; ++q)
-                for (int k = 0; k < C; ++k) h->hist.push_back(rec[((size_t)r * 15 + q) * CP + k]);
-        h->kick += n;
-        h->first_record = false;
+        finish(h, rec.data(), nrec, n);
         if (errw & kErrNonfinite) return AD_PIC_ERR_NONFINITE;
         if (errw & kErrOutOfGrid) return AD_PIC_ERR_OUT_OF_GRID;
         return AD_PIC_OK;
@@ -726,6 +691,17 @@ struct Impl {
         if ((h)->prec == AD_PIC_FP32_MIXED && (h)->P == 13) { using I = Impl<float, 14, 16>; return expr; } \
         return AD_PIC_ERR_INVALID_ARG;                                         \
     } while (0)
+
+}  // namespace
+
+int adpic_prepare_run(ad_pic* h, int n_steps, int* n_records) { DISPATCH(h, I::prepare(h, n_steps, n_records)); }
+
+void adpic_finish_run(ad_pic* h, const double* rec, int nrec, int n_steps) {
+    auto f = [&]() -> int { DISPATCH(h, (I::finish(h, rec, nrec, n_steps), 0)); };
+    f();
+}
+
+namespace {
 
 // host dual emittance from one record [3][5][C]: centred moments, Eqs. for D eps
 void emittance(const double* rec, int C, double* eps /*[3][C]*/) {

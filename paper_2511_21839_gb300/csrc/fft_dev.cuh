@@ -1,0 +1,378 @@
+// Device code of fft.cu (helpers, kernel bodies taking an explicit block index,
+// and their kernel wrappers), shared by fft.cu and the batched persistent kernel.
+#pragma once
+// Zero-padded (Hockney) FFT convolution of all dual channels with the real,
+// even spectrum of the Green's function.
+//
+// Each 1D transform of length M = 2n is a two-step Cooley-Tukey split
+// M = R1 R2: with n = R2 n1 + n2 and k = k1 + R1 k2,
+//   X[k1 + R1 k2] = sum_n2 W_R2^(n2 k2) [ W_M^(n2 k1) sum_n1 x[R2 n1 + n2] W_R1^(n1 k1) ].
+// Step 1: one thread per (line, n2) does the R1-point DFT over n1 in registers
+// and applies W_M^(n2 k1); step 2: one thread per (line, k1) does the
+// R2-point DFT over n2 in registers. A line lives in shared memory in the
+// padded layout pos(n) = (n / R2) (R2 + 1) + n % R2, so both steps are free of
+// bank conflicts and step 1 works in place. In forward transforms of
+// zero-padded data the upper half of the inputs (n1 >= R1/2) is known to be
+// zero and is never loaded.
+//
+// Passes (npair = C/2 channel pairs packed as complex, see the x passes):
+//   fftx_fwd   rho rows (x < nx)        -> X1 [p][z][y][kx]     (all Mx)
+//   ffty<fwd>  X1 columns (y < ny)      -> X2 [p][z][ky][kx]    (all My)
+//   fftz       X2 columns (z < nz): forward, times Ghat, inverse, keep z < nz, in place
+//   ffty<inv>  X2 columns (all My)      -> X1 (y < ny)
+//   fftx_inv   X1 rows (all Mx)         -> phi rows (x < nx), scaled back
+#include <cmath>
+
+#include "common.cuh"
+
+namespace adpic {
+
+static __constant__ float2 c_tw16f[16];    // exp(-2 pi i j / 16)
+static __constant__ double2 c_tw16d[16];
+
+template <typename T>
+__device__ __forceinline__ V2<T> tw16(int j) {
+    if constexpr (sizeof(T) == 4) return c_tw16f[j];
+    else return c_tw16d[j];
+}
+
+template <typename T>
+__device__ __forceinline__ V2<T> cmul(V2<T> a, V2<T> b) {
+    V2<T> r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+__host__ __device__ constexpr int brev_c(int k, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((k >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int log2_c(int n) { return n <= 1 ? 0 : 1 + log2_c(n / 2); }
+
+// R-point DFT in registers (R <= 16): radix-2 decimation in frequency, natural
+// input order, output X[k] in v[brev(k)]. INV uses the conjugate twiddles.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
+#pragma unroll
+    for (int len = R; len >= 2; len >>= 1) {
+        const int half = len >> 1;
+#pragma unroll
+        for (int g = 0; g < R; g += len) {
+#pragma unroll
+            for (int j = 0; j < half; ++j) {
+                const V2<T> a = v[g + j], b = v[g + j + half];
+                v[g + j].x = a.x + b.x;
+                v[g + j].y = a.y + b.y;
+                V2<T> d;
+                d.x = a.x - b.x;
+                d.y = a.y - b.y;
+                if (j == 0) {
+                    v[g + j + half] = d;
+                } else {
+                    V2<T> w = tw16<T>(j * (16 / len));
+                    if (INV) w.y = -w.y;
+                    v[g + j + half] = cmul<T>(d, w);
+                }
+            }
+        }
+    }
+}
+
+template <int M> struct Split;
+template <> struct Split<16> { static constexpr int R1 = 4, R2 = 4; };
+template <> struct Split<32> { static constexpr int R1 = 8, R2 = 4; };
+template <> struct Split<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct Split<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct Split<256> { static constexpr int R1 = 16, R2 = 16; };
+
+template <int M>
+struct Lay {
+    static constexpr int R1 = Split<M>::R1, R2 = Split<M>::R2;
+    static constexpr int LS = R1 * (R2 + 1) + 1;   // line stride in complex words (odd)
+    __device__ static __forceinline__ int pos(int n) { return (n / R2) * (R2 + 1) + n % R2; }
+};
+
+// Step 1 for work item w of nlines * R2 (line = w % nlines, n2 = w / nlines):
+// R1-point DFT over n1 in place, times W_M^(n2 k1). `half_zero`: inputs with
+// n >= M/2 are zero (zero padding) and not read.
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void step1(V2<T>* buf, int nlines, const V2<T>* twM, bool half_zero) {
+    using L = Lay<M>;
+    constexpr int R1 = L::R1, R2 = L::R2;
+    for (int w = threadIdx.x; w < nlines * R2; w += blockDim.x) {
+        const int line = w % nlines, n2 = w / nlines;
+        V2<T>* b = buf + line * L::LS + n2;
+        V2<T> v[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            if (half_zero && n1 >= R1 / 2) { v[n1].x = (T)0; v[n1].y = (T)0; }
+            else v[n1] = b[n1 * (R2 + 1)];
+        }
+        dft_reg<T, R1, INV>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            V2<T> y = v[brev_c(k1, log2_c(R1))];
+            if (k1 != 0 && n2 != 0) {
+                V2<T> t = twM[(n2 * k1) & (M - 1)];
+                if (INV) t.y = -t.y;
+                y = cmul<T>(y, t);
+            }
+            b[k1 * (R2 + 1)] = y;
+        }
+    }
+}
+
+// Step 2 loads for work item w of nlines * R1 (line = w % nlines, k1 = w / nlines)
+// the R2 values of row k1 and transforms them; X[k1 + R1 k2] = v[brev(k2)].
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void step2(const V2<T>* buf, int line, int k1, V2<T> (&v)[Lay<M>::R2]) {
+    using L = Lay<M>;
+    constexpr int R2 = L::R2;
+    const V2<T>* b = buf + line * L::LS + k1 * (R2 + 1);
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = b[n2];
+    dft_reg<T, R2, INV>(v);
+}
+
+template <typename T>
+__device__ __forceinline__ T chan_scale(const Ord<T>* chmax, int c, bool inverse) {
+    T m;
+    if constexpr (sizeof(T) == 4) m = __uint_as_float(chmax[c]);
+    else m = __longlong_as_double((long long)chmax[c]);
+    // an identically zero channel (a derivative the beam has not yet picked
+    // up) must stay exactly zero: its partner's rounding is not let through
+    if (m == (T)0) return inverse ? (T)0 : (T)1;
+    if (!isfinite(m)) return (T)1;
+    int e;
+    frexp(m, &e);                         // m = f 2^e, f in [0.5, 1)
+    return inverse ? ldexp((T)1, e) : ldexp((T)1, -e);
+}
+
+constexpr int kRowsX = 2;   // grid rows per CTA in the x passes
+constexpr int kTile = 16;   // columns per CTA in the y and z passes
+
+// x pass, forward: rows (y < ny, z < nz) of every channel pair. Channel pair
+// (2p, 2p+1) becomes one complex line (the spectrum of G is real and even, so
+// the two real convolutions separate again at the end); each channel is
+// scaled by a power of two so both halves of a pair have comparable magnitude.
+template <typename T, int M>
+__device__ __forceinline__ void fftx_fwd_kernel_body(const T* __restrict__ rho, V2<T>* __restrict__ X1, FFTDims d,
+                                                       const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax,
+    const int bx_, const int by_, const int bz_, const int nbx_) {
+    using L = Lay<M>;
+    extern __shared__ unsigned char smraw[];
+    V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* buf = twM + M;
+    const int nl = kRowsX * d.npair;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
+    const int64_t row0 = (int64_t)bx_ * kRowsX;
+    const int nrows = d.ny * d.nz;
+    for (int t = threadIdx.x; t < kRowsX * d.nx * d.CP; t += blockDim.x) {
+        const int r = t / (d.nx * d.CP);
+        const int rem = t % (d.nx * d.CP);
+        const int x = rem / d.CP, c = rem % d.CP;
+        if (row0 + r >= nrows || c >= d.C) continue;
+        const T v = rho[((row0 + r) * d.nx + x) * d.CP + c] * chan_scale<T>(chmax, c, false);
+        V2<T>& dst = buf[(r * d.npair + (c >> 1)) * L::LS + L::pos(x)];
+        if (c & 1) dst.y = v; else dst.x = v;
+    }
+    __syncthreads();
+    step1<T, M, false>(buf, nl, twM, true);
+    __syncthreads();
+    for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
+        const int line = w % nl, k1 = w / nl;
+        V2<T> v[L::R2];
+        step2<T, M, false>(buf, line, k1, v);
+        const int r = line / d.npair, p = line % d.npair;
+        if (row0 + r >= nrows) continue;
+        const int64_t z = (row0 + r) / d.ny, y = (row0 + r) % d.ny;
+        V2<T>* out = X1 + (((int64_t)p * d.nz + z) * d.ny + y) * M;
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) out[k1 + L::R1 * k2] = v[brev_c(k2, log2_c(L::R2))];
+    }
+}
+
+template <typename T, int M>
+static __global__ void __launch_bounds__(256) fftx_fwd_kernel(const T* __restrict__ rho, V2<T>* __restrict__ X1, FFTDims d,
+                                                       const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax) {
+    fftx_fwd_kernel_body<T, M>(rho, X1, d, tw, chmax, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// y pass over a tile of kTile consecutive kx for one (z, pair).
+// forward: X1 (y < ny) -> X2 (all My); inverse: X2 (all My) -> X1 (y < ny).
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void ffty_kernel_body(const V2<T>* __restrict__ in, V2<T>* __restrict__ out, FFTDims d,
+                                                   const V2<T>* __restrict__ tw,
+    const int bx_, const int by_, const int bz_, const int nbx_) {
+    using L = Lay<M>;
+    extern __shared__ unsigned char smraw[];
+    V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* buf = twM + M;
+    const int kx0 = bx_ * kTile, z = by_, p = bz_;
+    const int yin = INV ? M : d.ny, yout = INV ? d.ny : M;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
+    const int64_t plane_in = ((int64_t)p * d.nz + z) * yin;
+    for (int t = threadIdx.x; t < yin * kTile; t += blockDim.x) {
+        const int y = t / kTile, j = t % kTile;
+        buf[j * L::LS + L::pos(y)] = in[(plane_in + y) * d.Mx + kx0 + j];
+    }
+    __syncthreads();
+    step1<T, M, INV>(buf, kTile, twM, !INV);
+    __syncthreads();
+    const int64_t plane_out = ((int64_t)p * d.nz + z) * yout;
+    for (int w = threadIdx.x; w < kTile * L::R1; w += blockDim.x) {
+        const int j = w % kTile, k1 = w / kTile;
+        V2<T> v[L::R2];
+        step2<T, M, INV>(buf, j, k1, v);
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) {
+            const int y = k1 + L::R1 * k2;
+            if (y < yout) out[(plane_out + y) * d.Mx + kx0 + j] = v[brev_c(k2, log2_c(L::R2))];
+        }
+    }
+}
+
+template <typename T, int M, bool INV>
+static __global__ void __launch_bounds__(256) ffty_kernel(const V2<T>* __restrict__ in, V2<T>* __restrict__ out, FFTDims d,
+                                                   const V2<T>* __restrict__ tw) {
+    ffty_kernel_body<T, M, INV>(in, out, d, tw, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// z pass over a tile of kx at one (ky, pair), in place on X2: forward
+// transform of the zero-padded column, multiply by Ghat, inverse, keep z < nz.
+template <typename T, int M>
+__device__ __forceinline__ void fftz_kernel_body(V2<T>* __restrict__ X2, const T* __restrict__ Ghat, FFTDims d,
+                                                   const V2<T>* __restrict__ tw,
+    const int bx_, const int by_, const int bz_, const int nbx_) {
+    using L = Lay<M>;
+    extern __shared__ unsigned char smraw[];
+    V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* buf = twM + M;
+    const int kx0 = bx_ * kTile, ky = by_, p = bz_;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
+    const int64_t zstride = (int64_t)d.My * d.Mx;
+    V2<T>* base = X2 + (int64_t)p * d.nz * zstride + (int64_t)ky * d.Mx + kx0;
+    for (int t = threadIdx.x; t < d.nz * kTile; t += blockDim.x) {
+        const int z = t / kTile, j = t % kTile;
+        buf[j * L::LS + L::pos(z)] = base[z * zstride + j];
+    }
+    __syncthreads();
+    step1<T, M, false>(buf, kTile, twM, true);
+    __syncthreads();
+    // forward step 2 into registers, times Ghat, back in the input layout
+    constexpr int NW = (kTile * L::R1 + 255) / 256;
+    V2<T> keep[NW][L::R2];
+    const int kyr = ky <= d.ny ? ky : d.My - ky;
+#pragma unroll
+    for (int s = 0; s < NW; ++s) {
+        const int w = threadIdx.x + s * blockDim.x;
+        if (w < kTile * L::R1) step2<T, M, false>(buf, w % kTile, w / kTile, keep[s]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NW; ++s) {
+        const int w = threadIdx.x + s * blockDim.x;
+        if (w >= kTile * L::R1) continue;
+        const int j = w % kTile, k1 = w / kTile;
+        const int kx = kx0 + j;
+        const int kxr = kx <= d.nx ? kx : d.Mx - kx;
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) {
+            const int kz = k1 + L::R1 * k2;
+            const int kzr = kz <= d.nz ? kz : M - kz;
+            const T gh = Ghat[((int64_t)kzr * (d.ny + 1) + kyr) * (d.nx + 1) + kxr];
+            V2<T> v = keep[s][brev_c(k2, log2_c(L::R2))];
+            v.x *= gh;
+            v.y *= gh;
+            buf[j * L::LS + L::pos(kz)] = v;
+        }
+    }
+    __syncthreads();
+    step1<T, M, true>(buf, kTile, twM, false);
+    __syncthreads();
+    for (int w = threadIdx.x; w < kTile * L::R1; w += blockDim.x) {
+        const int j = w % kTile, k1 = w / kTile;
+        V2<T> v[L::R2];
+        step2<T, M, true>(buf, j, k1, v);
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) {
+            const int z = k1 + L::R1 * k2;
+            if (z < d.nz) base[z * zstride + j] = v[brev_c(k2, log2_c(L::R2))];
+        }
+    }
+}
+
+template <typename T, int M>
+static __global__ void __launch_bounds__(256) fftz_kernel(V2<T>* __restrict__ X2, const T* __restrict__ Ghat, FFTDims d,
+                                                   const V2<T>* __restrict__ tw) {
+    fftz_kernel_body<T, M>(X2, Ghat, d, tw, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// x pass, inverse: rows (y < ny, z < nz) of every pair, keep x < nx, undo the
+// channel scaling and the 1/(Mx My Mz) normalisation, write phi [node][CP]
+// through shared memory so the row is stored contiguously.
+template <typename T, int M>
+__device__ __forceinline__ void fftx_inv_kernel_body(const V2<T>* __restrict__ X1, T* __restrict__ phi, FFTDims d,
+                                                       const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax,
+    const int bx_, const int by_, const int bz_, const int nbx_) {
+    using L = Lay<M>;
+    extern __shared__ unsigned char smraw[];
+    V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* buf = twM + M;
+    const int nl = kRowsX * d.npair;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
+    const int64_t row0 = (int64_t)bx_ * kRowsX;
+    const int nrows = d.ny * d.nz;
+    for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
+        const int line = t / M, kx = t % M;
+        const int r = line / d.npair, p = line % d.npair;
+        V2<T> v;
+        v.x = (T)0;
+        v.y = (T)0;
+        if (row0 + r < nrows) {
+            const int64_t z = (row0 + r) / d.ny, y = (row0 + r) % d.ny;
+            v = X1[(((int64_t)p * d.nz + z) * d.ny + y) * M + kx];
+        }
+        buf[line * L::LS + L::pos(kx)] = v;
+    }
+    __syncthreads();
+    step1<T, M, true>(buf, nl, twM, false);
+    __syncthreads();
+    // outputs x < nx of every line into a row-major staging area [r][x][CP]
+    T* stage = reinterpret_cast<T*>(buf + nl * L::LS);
+    const T norm = (T)(1.0 / ((double)d.Mx * d.My * d.Mz));
+    for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
+        const int line = w % nl, k1 = w / nl;
+        V2<T> v[L::R2];
+        step2<T, M, true>(buf, line, k1, v);
+        const int r = line / d.npair, p = line % d.npair;
+        const T sa = norm * chan_scale<T>(chmax, 2 * p, true);
+        const T sb = norm * chan_scale<T>(chmax, 2 * p + 1, true);
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) {
+            const int x = k1 + L::R1 * k2;
+            if (x < d.nx) {
+                const V2<T> q = v[brev_c(k2, log2_c(L::R2))];
+                stage[(r * d.nx + x) * d.CP + 2 * p] = q.x * sa;
+                stage[(r * d.nx + x) * d.CP + 2 * p + 1] = q.y * sb;
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kRowsX * d.nx * d.CP; t += blockDim.x) {
+        const int r = t / (d.nx * d.CP);
+        const int c = t % d.CP;
+        if (row0 + r >= nrows) continue;
+        phi[row0 * d.nx * d.CP + t] = c < d.C ? stage[t] : (T)0;
+    }
+}
+
+template <typename T, int M>
+static __global__ void __launch_bounds__(256) fftx_inv_kernel(const V2<T>* __restrict__ X1, T* __restrict__ phi, FFTDims d,
+                                                       const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax) {
+    fftx_inv_kernel_body<T, M>(X1, phi, d, tw, chmax, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+}  // namespace adpic

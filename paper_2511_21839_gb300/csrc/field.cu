@@ -1,65 +1,9 @@
 // Grid-side kernels: per-kick geometry, the integrated Green's function and
 // its real even spectrum, the zero-padded (Hockney) FFT convolution of all
 // dual channels, and the central finite-difference field.
-#include <cfloat>
-#include <cmath>
-
-#include "common.cuh"
+#include "field_dev.cuh"
 
 namespace adpic {
-
-__device__ __forceinline__ float ord_dec(unsigned int u) {
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-__device__ __forceinline__ double ord_dec(unsigned long long u) {
-    return __longlong_as_double((long long)((u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u));
-}
-
-// ------------------------------------------------------------------ geometry
-
-// Value-part extrema -> nodes x_j = origin + j h with h = (max - min) / (n - 4)
-// and origin = min - 1.5 h, so every particle has u = (x - origin)/h in
-// [1.5, n - 2.5]: its CIC nodes lie in [1, n-2] and the FD stencil in [0, n-1].
-// The geometry is a constant of the kick, not differentiated. Resets the
-// extrema and the channel maxima for the next kick.
-template <typename T>
-__global__ void geom_kernel(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* g, Ord<T>* chmax, int CP) {
-    const int d = threadIdx.x;
-    if (d < 3) {
-        const int n = d == 0 ? nx : (d == 1 ? ny : nz);
-        double lo = (double)ord_dec(mm[d]), hi = (double)ord_dec(mm[3 + d]);
-        if (!(lo <= hi)) { lo = 0.0; hi = 0.0; }
-        double w = hi - lo;
-        if (!(w > 0.0)) w = 1e-6;
-        double h = w / (double)(n - 4);
-        double o = lo - 1.5 * h;
-        g->o[d] = o;
-        g->h[d] = h;
-        g->hr[d] = d == 2 ? h * gamma0 : h;
-        g->of[d] = (float)o;
-        g->ihf[d] = (float)(1.0 / h);
-        g->ihd[d] = 1.0 / h;
-        const double hr = d == 2 ? h * gamma0 : h;
-        g->fdd[d] = 0.5 / hr;
-        g->fdf[d] = (float)(0.5 / hr);
-    }
-    __syncthreads();
-    if (d < 3) {
-        // exact integrals (FP64) for every cell of the FP64 path; in FP32 for
-        // the cells whose centre is within 10 h_max, beyond which the
-        // fourth-order expansion is below FP32 rounding
-        const int n = d == 0 ? nx : (d == 1 ? ny : nz);
-        double hmax = fmax(g->hr[0], fmax(g->hr[1], g->hr[2]));
-        int R = (int)ceil(10.0 * hmax / g->hr[d]);
-        g->R[d] = (sizeof(T) == 8 || R > n) ? n : R;
-    }
-    __syncthreads();
-    if (d < 3) {
-        mm[d] = ~(Ord<T>)0;
-        mm[3 + d] = (Ord<T>)0;
-    }
-    for (int c = d; c < CP; c += blockDim.x) chmax[c] = (Ord<T>)0;
-}
 
 template <typename T>
 void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geom, Ord<T>* chmax, int CP,
@@ -67,122 +11,9 @@ void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geo
     geom_kernel<T><<<1, 32, 0, s>>>(mm, nx, ny, nz, gamma0, geom, chmax, CP);
 }
 
-// per-channel max |rho| (ordered bits of a non-negative value are its bits)
-template <typename T>
-__global__ void chmax_kernel(const T* __restrict__ rho, int64_t nodes, int CP, Ord<T>* chmax) {
-    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // multiple of CP
-    T m = (T)0;
-    for (int64_t t = t0; t < nodes * CP; t += stride) m = fmax(m, fabs(rho[t]));
-    for (int o = CP; o < 32; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) < CP) {
-        if constexpr (sizeof(T) == 4)
-            atomicMax(&chmax[threadIdx.x & 31], __float_as_uint(m));
-        else
-            atomicMax(&chmax[threadIdx.x & 31], (unsigned long long)__double_as_longlong(m));
-    }
-}
-
 template <typename T>
 void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream_t s) {
     chmax_kernel<T><<<152 * 2, 256, 0, s>>>(rho, nodes, CP, chmax);
-}
-
-// ------------------------------------------------------------------ Green's function
-
-// An antiderivative of 1/r: d^3 F / dx dy dz = 1/sqrt(x^2 + y^2 + z^2).
-__device__ double igf_F(double x, double y, double z) {
-    const double r = sqrt(x * x + y * y + z * z);
-    return y * z * log(x + r) + x * z * log(y + r) + x * y * log(z + r) - 0.5 * x * x * atan(y * z / (x * r)) -
-           0.5 * y * y * atan(x * z / (y * r)) - 0.5 * z * z * atan(x * y / (z * r));
-}
-
-// F at the cell corners ((i - 1/2) hx, (j - 1/2) hy, (k - 1/2) hzr), i in [0, Rx+1] etc. (FP64)
-// Launched over the full (nx+2)(ny+2)(nz+2) corner lattice; corners outside
-// the near box of this kick return at once.
-__global__ void green_corner_kernel(const GeomDev* __restrict__ g, int nx, int ny, int nz, double* __restrict__ F) {
-    const int cx = nx + 2, cy = ny + 2, cz = nz + 2;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;     // < 130^3
-    if (t >= cx * cy * cz) return;
-    const int i = t % cx, j = (t / cx) % cy, k = t / (cx * cy);
-    if (i > g->R[0] + 1 || j > g->R[1] + 1 || k > g->R[2] + 1) return;
-    F[t] = igf_F((i - 0.5) * g->hr[0], (j - 0.5) * g->hr[1], (k - 0.5) * g->hr[2]);
-}
-
-// Cell average of 1/(4 pi eps0 r) over the cell centred at offset (i, j, k):
-// the 8-corner difference of F in FP64 inside the near box (every cell on
-// the FP64 path), else the Taylor expansion of the box average of a smooth
-// function, f + (1/24) sum_d h_d^2 f_dd + (1/1920) sum_d h_d^4 f_dddd
-// + (1/576) sum_{d<e} h_d^2 h_e^2 f_ddee, with the derivatives of 1/r
-// f_dd = (3 d^2 - r^2)/r^5, f_dddd = 3 (35 d^4 - 30 d^2 r^2 + 3 r^4)/r^9,
-// f_ddee = 3 (35 d^2 e^2 - 5 r^2 (d^2 + e^2) + r^4)/r^9; its O(h^6) remainder
-// is below FP32 rounding beyond 10 h_max.
-template <typename T>
-__global__ void green_cell_kernel(const GeomDev* __restrict__ g, int nx, int ny, int nz,
-                                  const double* __restrict__ F, T* __restrict__ G) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;     // < 129^3
-    const int gx = nx + 1, gy = ny + 1, gz = nz + 1;
-    if (t >= gx * gy * gz) return;
-    const int i = t % gx, j = (t / gx) % gy, k = t / (gx * gy);
-    const double hx = g->hr[0], hy = g->hr[1], hz = g->hr[2];
-    const double k4 = 1.0 / (4.0 * 3.14159265358979323846 * 8.8541878128e-12);
-    if (i <= g->R[0] && j <= g->R[1] && k <= g->R[2]) {
-        const int cx = nx + 2, cy = ny + 2;
-        auto at = [&](int a, int b, int c) { return F[((int64_t)c * cy + b) * cx + a]; };
-        double s = at(i + 1, j + 1, k + 1) - at(i, j + 1, k + 1) - at(i + 1, j, k + 1) - at(i + 1, j + 1, k) +
-                   at(i, j, k + 1) + at(i, j + 1, k) + at(i + 1, j, k) - at(i, j, k);
-        G[t] = (T)(k4 * s / (hx * hy * hz));
-    } else {
-        // in units of r: direction cosines c_d = d / r and ratios t_d = h_d / r
-        const T x = (T)i * (T)hx, y = (T)j * (T)hy, z = (T)k * (T)hz;
-        const T ir = rsqrt(x * x + y * y + z * z);
-        const T c2[3] = {x * x * ir * ir, y * y * ir * ir, z * z * ir * ir};
-        const T t2[3] = {(T)hx * (T)hx * ir * ir, (T)hy * (T)hy * ir * ir, (T)hz * (T)hz * ir * ir};
-        T s2 = (T)0, s4 = (T)0, s22 = (T)0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            s2 += t2[d] * ((T)3 * c2[d] - (T)1);
-            s4 += t2[d] * t2[d] * (T)3 * ((T)35 * c2[d] * c2[d] - (T)30 * c2[d] + (T)3);
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int e = (d + 1) % 3;
-            s22 += t2[d] * t2[e] * (T)3 * ((T)35 * c2[d] * c2[e] - (T)5 * (c2[d] + c2[e]) + (T)1);
-        }
-        G[t] = (T)k4 * ir * ((T)1 + s2 / (T)24 + s4 / (T)1920 + s22 / (T)576);
-    }
-}
-
-// One DCT-I pass over the contiguous axis of in [BA][L] (L = n+1) into
-// out [L][BA]: out[k][ba] = sum_l D[k][l] in[ba][l], D[k][l] = w_l cos(pi l k / n),
-// w_0 = w_n = 1, else 2. Three passes (rotating the axes) give the real
-// spectrum of the even extension of G to the 2n-periodic grid. A block
-// stages kDctLines input lines and the matrix D in shared memory.
-constexpr int kDctLines = 8;
-
-template <typename T>
-__global__ void dct_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA) {
-    extern __shared__ unsigned char smraw[];
-    T* Ds = reinterpret_cast<T*>(smraw);            // [L][L]
-    T* xs = Ds + L * L;                             // [kDctLines][L + 1]
-    const int64_t ba0 = (int64_t)blockIdx.x * kDctLines;
-    const int nl = (int)min((int64_t)kDctLines, BA - ba0);
-    for (int t = threadIdx.x; t < L * L; t += blockDim.x) Ds[t] = D[t];
-    for (int t = threadIdx.x; t < nl * L; t += blockDim.x) {
-        const int l = t / L, c = t % L;
-        xs[l * (L + 1) + c] = in[(ba0 + l) * L + c];
-    }
-    __syncthreads();
-    // thread -> (k, line) with the line fastest so the writes of one k are contiguous
-    for (int t = threadIdx.x; t < L * kDctLines; t += blockDim.x) {
-        const int k = t / kDctLines, l = t % kDctLines;
-        if (l >= nl) continue;
-        const T* row = Ds + k * L;
-        const T* x = xs + l * (L + 1);
-        T s = (T)0;
-        for (int c = 0; c < L; ++c) s = fma(row[c], x[c], s);
-        out[(int64_t)k * BA + ba0 + l] = s;
-    }
 }
 
 template <typename T>
@@ -201,31 +32,6 @@ void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, doubl
     pass(G, Gtmp, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));
     pass(Gtmp, G, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1));
     pass(G, Ghat, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1));
-}
-
-// ------------------------------------------------------------------ field
-
-// E = -grad(phi) by central differences on interior nodes, rest-frame
-// spacings (hx, hy, gamma0 hz); E layout [node][3][CP].
-template <typename T>
-__global__ void field_kernel(const T* __restrict__ phi, const GeomDev* __restrict__ g, int nx, int ny, int nz, int CP,
-                             T* __restrict__ E) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nodes = (int64_t)nx * ny * nz;
-    if (t >= nodes * CP) return;
-    const int c = (int)(t % CP);
-    const int64_t node = t / CP;
-    const int i = (int)(node % nx), j = (int)((node / nx) % ny), k = (int)(node / ((int64_t)nx * ny));
-    if (i < 1 || i > nx - 2 || j < 1 || j > ny - 2 || k < 1 || k > nz - 2) return;
-    const T ax = sizeof(T) == 4 ? (T)g->fdf[0] : (T)g->fdd[0];
-    const T ay = sizeof(T) == 4 ? (T)g->fdf[1] : (T)g->fdd[1];
-    const T az = sizeof(T) == 4 ? (T)g->fdf[2] : (T)g->fdd[2];
-    const int64_t sx = CP, sy = (int64_t)nx * CP, sz = (int64_t)nx * ny * CP;
-    const int64_t a = node * CP + c;
-    T* e = E + node * 3 * CP + c;
-    e[0] = -(phi[a + sx] - phi[a - sx]) * ax;
-    e[CP] = -(phi[a + sy] - phi[a - sy]) * ay;
-    e[2 * CP] = -(phi[a + sz] - phi[a - sz]) * az;
 }
 
 template <typename T>
@@ -248,5 +54,6 @@ void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int
     template void setup_green<T>();
 ADPIC_FIELD_INST(float)
 ADPIC_FIELD_INST(double)
+
 
 }  // namespace adpic

@@ -2,184 +2,14 @@
 // gather + kick + push (M2 then M1 maps), the period-boundary kernel (dual
 // moments in FP64 + half map), and cloud-in-cell deposition of every dual
 // channel.
-#include <cfloat>
-#include <cmath>
-
-#include "common.cuh"
+#include "particles_dev.cuh"
 
 namespace adpic {
-
-// ------------------------------------------------------------------ helpers
-
-template <typename T, int CP>
-__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&v)[CP]) {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int q = 0; q < CP / 4; ++q) {
-            float4 f = reinterpret_cast<const float4*>(p)[q];
-            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < CP / 2; ++q) {
-            double2 f = reinterpret_cast<const double2*>(p)[q];
-            v[2 * q] = f.x; v[2 * q + 1] = f.y;
-        }
-    }
-}
-
-template <typename T, int CP>
-__device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int q = 0; q < CP / 4; ++q) {
-            float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
-            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < CP / 2; ++q) {
-            double2 f = __ldg(reinterpret_cast<const double2*>(p) + q);
-            v[2 * q] = f.x; v[2 * q + 1] = f.y;
-        }
-    }
-}
-
-template <typename T, int CP>
-__device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[CP]) {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int q = 0; q < CP / 4; ++q)
-            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < CP / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
-    }
-}
-
-__device__ __forceinline__ unsigned int ord_enc(float f) {
-    unsigned int u = __float_as_uint(f);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ unsigned long long ord_enc(double f) {
-    unsigned long long u = (unsigned long long)__double_as_longlong(f);
-    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
-}
-
-template <typename T>
-__device__ __forceinline__ T tmax() { return sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX; }
-
-// Block-wide min/max of three values, then one atomic per block and quantity.
-template <typename T>
-__device__ void block_minmax(T (&mn)[3], T (&mx)[3], Ord<T>* mm) {
-    __shared__ T smn[32][3], smx[32][3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
-        }
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0)
-        for (int d = 0; d < 3; ++d) { smn[w][d] = mn[d]; smx[w][d] = mx[d]; }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            T a = l < nw ? smn[l][d] : tmax<T>();
-            T b = l < nw ? smx[l][d] : -tmax<T>();
-            for (int o = 16; o > 0; o >>= 1) {
-                a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-                b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-            }
-            if (l == 0 && a <= b) {
-                atomicMin(&mm[d], ord_enc(a));
-                atomicMax(&mm[3 + d], ord_enc(b));
-            }
-        }
-    }
-}
-
-// Cell index and fractional offset of one coordinate; flags and clamps a
-// particle outside the stencil range [1, n-3] (the geometry guarantees it).
-template <typename T>
-__device__ __forceinline__ int cell_of(T x, T o, T ih, int n, T& f, int& bad) {
-    T u = (x - o) * ih;
-    T fl = floor(u);
-    int i = (int)fl;
-    if (!(fl >= (T)1 && fl <= (T)(n - 3))) {
-        bad |= isfinite(x) ? kErrOutOfGrid : kErrNonfinite;
-        i = i < 1 ? 1 : (i > n - 3 ? n - 3 : i);
-        if (!isfinite(x)) i = 1;
-        fl = (T)i;
-        u = fmin(fmax(u, fl), fl + (T)1);
-        if (!isfinite(x)) u = fl;
-    }
-    f = u - fl;
-    return i;
-}
-
-template <typename T> __device__ __forceinline__ T geom_o(const GeomDev& g, int d) {
-    return sizeof(T) == 4 ? (T)g.of[d] : (T)g.o[d];
-}
-template <typename T> __device__ __forceinline__ T geom_ih(const GeomDev& g, int d) {
-    return sizeof(T) == 4 ? (T)g.ihf[d] : (T)g.ihd[d];
-}
-
-// ------------------------------------------------------------------ init / convert
-
-// coef [3 planes][3 (a, b, alpha)][CP] duals then 6 means of the normals.
-// Per plane: u = a (n1 - mean n1), p = b ((n2 - mean n2) - alpha (n1 - mean n1)).
-template <typename T, int C, int CP>
-__global__ void init_kernel(const double* __restrict__ nrm, int64_t N, const double* __restrict__ coef,
-                            T* __restrict__ state) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double* means = coef + 3 * 3 * CP;
-#pragma unroll
-    for (int pl = 0; pl < 3; ++pl) {
-        const double* a = coef + (pl * 3 + 0) * CP;
-        const double* b = coef + (pl * 3 + 1) * CP;
-        const double* al = coef + (pl * 3 + 2) * CP;
-        double n1 = nrm[(2 * pl) * N + i] - means[2 * pl];
-        double n2 = nrm[(2 * pl + 1) * N + i] - means[2 * pl + 1];
-        double s0 = n2 - al[0] * n1;
-        T u[CP], p[CP];
-        u[0] = (T)(a[0] * n1);
-        p[0] = (T)(b[0] * s0);
-#pragma unroll
-        for (int k = 1; k < CP; ++k) {
-            u[k] = (T)(a[k] * n1);
-            p[k] = (T)(b[0] * (-al[k] * n1) + b[k] * s0);
-        }
-        stv<T, CP>(state + ((2 * pl) * N + i) * CP, u);
-        stv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
-    }
-}
 
 template <typename T, int C, int CP>
 void launch_init(const double* nrm, int64_t N, const double* coef, T* state, cudaStream_t s) {
     if (N <= 0) return;
     init_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(nrm, N, coef, state);
-}
-
-template <typename T, int CP>
-__global__ void convert_in_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t rows, int C) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= rows * CP) return;
-    int64_t r = t / CP;
-    int k = (int)(t % CP);
-    dst[t] = k < C ? (T)src[r * C + k] : (T)0;
-}
-
-template <typename T, int CP>
-__global__ void convert_out_kernel(const T* __restrict__ src, double* __restrict__ dst, int64_t rows, int C) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= rows * C) return;
-    int64_t r = t / C;
-    int k = (int)(t % C);
-    dst[t] = (double)src[r * CP + k];
 }
 
 template <typename T, int CP>
@@ -191,114 +21,6 @@ template <typename T, int CP>
 void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_t s) {
     int64_t tot = 6 * N * C;
     if (tot > 0) convert_out_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, 6 * N, C);
-}
-
-// ------------------------------------------------------------------ gather + kick + push
-
-// One thread per particle: CIC gather of the dual rest-frame field (the weight
-// derivatives carry the particle's derivative channels), the kick M2(tau)
-// p += (kappa tau) E (dual product), then the dual map A (one half map, or
-// the composition of this kick's and the next kick's half maps), and the
-// value-part extrema of the new positions for the next grid geometry.
-// The gather runs one field component at a time over the eight nodes, so
-// only that component's CP accumulators and its three interpolant gradients
-// are live: E_p,k = sum W E_k + sum_d (x_d,k / h_d) sum dW/du_d E_0 (Eq. 2 on
-// the weight product), then p_k += a0 E_p,k + a_k E_p,0 in one rounding.
-template <typename T, int C, int CP, bool TRACK>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
-    push_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
-                const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
-                const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
-    T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
-    if (i < N) {
-        T u[6][CP];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) ldv<T, CP>(state + (c * N + i) * CP, u[c]);
-        if (E != nullptr) {
-            const GeomDev& g = *geom;
-            const int n[3] = {nx, ny, nz};
-            T f[3], ih[3];
-            int idx[3];
-            int bad = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                ih[d] = geom_ih<T>(g, d);
-                idx[d] = cell_of<T>(u[2 * d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
-            }
-            if (bad) atomicOr(err, bad);
-            const T* e0 = E + (((int64_t)idx[2] * ny + idx[1]) * nx + idx[0]) * (3 * CP);
-            const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                T Ev[CP];
-                T gx = (T)0, gy = (T)0, gz = (T)0;
-#pragma unroll
-                for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const T wz = c ? f[2] : (T)1 - f[2];
-                    const T sz_ = c ? (T)1 : (T)-1;
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const T wy = b ? f[1] : (T)1 - f[1];
-                        const T sy_ = b ? (T)1 : (T)-1;
-#pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            const T wx = a ? f[0] : (T)1 - f[0];
-                            const T sx_ = a ? (T)1 : (T)-1;
-                            const T W = wx * wy * wz;
-                            T en[CP];
-                            ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en);
-#pragma unroll
-                            for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[k], Ev[k]);
-                            gx = fma(sx_ * wy * wz, en[0], gx);
-                            gy = fma(wx * sy_ * wz, en[0], gy);
-                            gz = fma(wx * wy * sz_, en[0], gz);
-                        }
-                    }
-                }
-                gx *= ih[0];
-                gy *= ih[1];
-                gz *= ih[2];
-                T* p = u[2 * q + 1];
-                const T a0 = K.a[q][0], E0 = Ev[0];
-#pragma unroll
-                for (int k = 1; k < CP; ++k) {
-                    const T Ek = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[k])));
-                    p[k] = fma(a0, Ek, fma(K.a[q][k], E0, p[k]));
-                }
-                p[0] = fma(a0, E0, p[0]);
-            }
-        }
-        // dual map
-#pragma unroll
-        for (int pl = 0; pl < 3; ++pl) {
-            T* x = u[2 * pl];
-            T* p = u[2 * pl + 1];
-            const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
-            const T x0 = x[0], p0 = p[0];
-#pragma unroll
-            for (int k = 1; k < CP; ++k) {
-                const T xk = x[k], pk = p[k];
-                x[k] = fma(a0, xk, fma(b0, pk, fma(A.m[pl][0][k], x0, A.m[pl][1][k] * p0)));
-                p[k] = fma(c0, xk, fma(d0, pk, fma(A.m[pl][2][k], x0, A.m[pl][3][k] * p0)));
-            }
-            x[0] = fma(a0, x0, b0 * p0);
-            p[0] = fma(c0, x0, d0 * p0);
-        }
-        // cell-sorted slot of this particle (cell and rank from this kick's deposit)
-        const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
-        if (sb.ids_out) sb.ids_out[dst] = sb.ids_in[i];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
-        if (TRACK) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) { mn[d] = u[2 * d][0]; mx[d] = u[2 * d][0]; }
-        }
-    }
-    if (TRACK) block_minmax<T>(mn, mx, mm);
 }
 
 template <typename T, int C, int CP>
@@ -313,90 +35,8 @@ void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const G
     else
         push_kernel<T, C, CP, false><<<blocks, 256, 0, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm,
                                                            err, sb);
-}
-
-// ------------------------------------------------------------------ cell sort: scan, ids
-
-constexpr int kScanChunk = 2048;   // cells per block of the scan
+}   // cells per block of the scan
 int scan_blocks(int ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
-
-__device__ __forceinline__ int block_excl_scan(int v, int* sm, int& total) {
-    // 256-thread exclusive scan of one int per thread
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sm[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        sm[lane] = t;
-    }
-    __syncthreads();
-    total = sm[(blockDim.x >> 5) - 1];
-    const int before = w > 0 ? sm[w - 1] : 0;
-    __syncthreads();
-    return before + x - v;
-}
-
-// per-chunk totals of hist
-__global__ void scan_sum_kernel(const int* __restrict__ hist, int ncells, int* __restrict__ bsum) {
-    __shared__ int sm[32];
-    const int base = blockIdx.x * kScanChunk;
-    int v = 0;
-    for (int j = threadIdx.x; j < kScanChunk; j += blockDim.x)
-        if (base + j < ncells) v += hist[base + j];
-    int total;
-    block_excl_scan(v, sm, total);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-}
-
-// exclusive scan of the chunk totals (one block; at most 256 x 8 chunks)
-__global__ void scan_top_kernel(int* __restrict__ bsum, int nb) {
-    __shared__ int sm[32];
-    constexpr int PER = 8;
-    int v[PER], s = 0;
-    for (int q = 0; q < PER; ++q) {
-        const int j = threadIdx.x * PER + q;
-        v[q] = j < nb ? bsum[j] : 0;
-        s += v[q];
-    }
-    int total;
-    int run = block_excl_scan(s, sm, total);
-    for (int q = 0; q < PER; ++q) {
-        const int j = threadIdx.x * PER + q;
-        if (j < nb) bsum[j] = run;
-        run += v[q];
-    }
-}
-
-// exclusive offsets of every cell; clears hist for the next kick
-__global__ void scan_apply_kernel(int* __restrict__ hist, int ncells, const int* __restrict__ bsum,
-                                  int* __restrict__ offs) {
-    __shared__ int sm[32];
-    constexpr int PER = kScanChunk / 256;
-    const int base = blockIdx.x * kScanChunk + threadIdx.x * PER;
-    int v[PER], s = 0;
-    for (int q = 0; q < PER; ++q) {
-        v[q] = base + q < ncells ? hist[base + q] : 0;
-        s += v[q];
-    }
-    int total;
-    int run = block_excl_scan(s, sm, total) + bsum[blockIdx.x];
-    for (int q = 0; q < PER; ++q) {
-        if (base + q < ncells) {
-            offs[base + q] = run;
-            hist[base + q] = 0;
-        }
-        run += v[q];
-    }
-}
 
 void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s) {
     const int nb = scan_blocks(ncells);
@@ -404,160 +44,15 @@ void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s) {
     scan_top_kernel<<<1, 256, 0, s>>>(bsum, nb);
     scan_apply_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum, offs);
 }
-
-__global__ void iota_kernel(int* ids, int64_t N) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < N) ids[i] = (int)i;
-}
 void launch_iota(int* ids, int64_t N, cudaStream_t s) {
     if (N > 0) iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ids, N);
-}
-
-// device state [6][N][CP] in sorted order -> host layout [6][N][C] in the caller's order
-template <typename T, int CP>
-__global__ void convert_out_perm_kernel(const T* __restrict__ src, const int* __restrict__ ids, double* __restrict__ dst,
-                                        int64_t N, int C) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= 6 * N * C) return;
-    const int k = (int)(t % C);
-    const int64_t i = (t / C) % N, c = t / ((int64_t)N * C);
-    dst[(c * N + ids[i]) * C + k] = (double)src[(c * N + i) * CP + k];
 }
 template <typename T, int CP>
 void launch_convert_out_perm(const T* src, const int* ids, double* dst, int64_t N, int C, cudaStream_t s) {
     const int64_t tot = 6 * N * C;
     if (tot > 0) convert_out_perm_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, ids, dst, N, C);
 }
-
-// ------------------------------------------------------------------ period boundary: moments + half map
-
-// CP lanes per particle, lane k holds channel k of every coordinate. Each lane
-// accumulates, in FP64, channel k of the dual sums of u, p, u^2, u p, p^2
-// per plane (Eq. 2 for the products: d(u^2) = 2 u u_k, d(u p) = u p_k + p u_k),
-// and optionally applies the dual half map A to the state and tracks extrema.
-// error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) on a
-// double-float accumulator (hi, lo)
-__device__ __forceinline__ void df_add(float& hi, float& lo, float a) {
-    const float s = hi + a;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (a - bb);
-    hi = s;
-    lo += e;
-}
-__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
-    const float ph = a * b;
-    const float pl = fmaf(a, b, -ph);
-    df_add(hi, lo, ph);
-    lo += pl;
-}
-
-constexpr int kBoundaryBlocks = 152 * 8;
 int boundary_blocks() { return kBoundaryBlocks; }
-
-template <typename T, int C, int CP, bool MOM, bool APPLY>
-__global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ state, int64_t N, const MapCoef<T, CP> A,
-                                                       double* __restrict__ partial, Ord<T>* __restrict__ mm) {
-    constexpr int PPW = 32 / CP;
-    const int lane = threadIdx.x & 31;
-    const int k = lane & (CP - 1);
-    const int src = lane & ~(CP - 1);
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double acc[3][5];
-    float ah[3][5], al[3][5];   // FP32 path: double-float partial sums
-#pragma unroll
-    for (int pl = 0; pl < 3; ++pl)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) { acc[pl][q] = 0.0; ah[pl][q] = 0.f; al[pl][q] = 0.f; }
-    T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
-    T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
-    for (int64_t base = warp * PPW; base < N; base += nwarps * PPW) {
-        const int64_t i = base + lane / CP;
-        const bool valid = i < N;
-#pragma unroll
-        for (int pl = 0; pl < 3; ++pl) {
-            T* pu = state + ((2 * pl) * N + i) * CP + k;
-            T* pp = state + ((2 * pl + 1) * N + i) * CP + k;
-            T u = valid ? *pu : (T)0;
-            T p = valid ? *pp : (T)0;
-            T u0 = __shfl_sync(0xffffffffu, u, src);
-            T p0 = __shfl_sync(0xffffffffu, p, src);
-            if (MOM && valid) {
-                if constexpr (sizeof(T) == 8) {
-                    acc[pl][0] += u;
-                    acc[pl][1] += p;
-                    if (k == 0) {
-                        acc[pl][2] = fma(u, u, acc[pl][2]);
-                        acc[pl][3] = fma(u, p, acc[pl][3]);
-                        acc[pl][4] = fma(p, p, acc[pl][4]);
-                    } else {
-                        acc[pl][2] = fma(2.0 * u0, u, acc[pl][2]);
-                        acc[pl][3] = fma(u0, p, fma(p0, u, acc[pl][3]));
-                        acc[pl][4] = fma(2.0 * p0, p, acc[pl][4]);
-                    }
-                } else {
-                    // FP32 state: every product of two FP32 values is formed exactly as an
-                    // unevaluated pair (hi, lo) and added with error-free sums, so the
-                    // per-lane partials carry ~48 significant bits before they go to FP64
-                    const float a = 2.0f * (float)u0;
-                    df_add(ah[pl][0], al[pl][0], (float)u);
-                    df_add(ah[pl][1], al[pl][1], (float)p);
-                    if (k == 0) {
-                        df_add_prod(ah[pl][2], al[pl][2], (float)u, (float)u);
-                        df_add_prod(ah[pl][3], al[pl][3], (float)u, (float)p);
-                        df_add_prod(ah[pl][4], al[pl][4], (float)p, (float)p);
-                    } else {
-                        df_add_prod(ah[pl][2], al[pl][2], a, (float)u);
-                        df_add_prod(ah[pl][3], al[pl][3], (float)u0, (float)p);
-                        df_add_prod(ah[pl][3], al[pl][3], (float)p0, (float)u);
-                        df_add_prod(ah[pl][4], al[pl][4], 2.0f * (float)p0, (float)p);
-                    }
-                }
-            }
-            if (APPLY && valid) {
-                const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
-                T un, pn;
-                if (k == 0) {
-                    un = fma(a0, u, b0 * p);
-                    pn = fma(c0, u, d0 * p);
-                    mn[pl] = fmin(mn[pl], un);
-                    mx[pl] = fmax(mx[pl], un);
-                } else {
-                    un = fma(a0, u, fma(b0, p, fma(A.m[pl][0][k], u0, A.m[pl][1][k] * p0)));
-                    pn = fma(c0, u, fma(d0, p, fma(A.m[pl][2][k], u0, A.m[pl][3][k] * p0)));
-                }
-                *pu = un;
-                *pp = pn;
-            }
-        }
-    }
-    if (APPLY) block_minmax<T>(mn, mx, mm);
-    if (MOM) {
-        if constexpr (sizeof(T) == 4) {
-#pragma unroll
-            for (int pl = 0; pl < 3; ++pl)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) acc[pl][q] = (double)ah[pl][q] + (double)al[pl][q];
-        }
-        // sum over the PPW particle groups of the warp (lanes with the same k)
-#pragma unroll
-        for (int pl = 0; pl < 3; ++pl)
-#pragma unroll
-            for (int q = 0; q < 5; ++q)
-                for (int o = CP; o < 32; o <<= 1) acc[pl][q] += __shfl_xor_sync(0xffffffffu, acc[pl][q], o);
-        __shared__ double sm[8][15][CP];
-        const int w = threadIdx.x >> 5;
-        if (lane < CP)
-            for (int pl = 0; pl < 3; ++pl)
-                for (int q = 0; q < 5; ++q) sm[w][pl * 5 + q][lane] = acc[pl][q];
-        __syncthreads();
-        for (int t = threadIdx.x; t < 15 * CP; t += blockDim.x) {
-            double s = 0.0;
-            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += sm[ww][t / CP][t % CP];
-            partial[(int64_t)blockIdx.x * 15 * CP + t] = s;
-        }
-    }
-}
 
 template <typename T, int C, int CP>
 void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
@@ -570,136 +65,8 @@ void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, b
         boundary_kernel<T, C, CP, false, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
 }
 
-// partial [nblocks][15][CP] -> out [15][CP] / N: one block per output value,
-// a fixed strided split and a fixed shared-memory tree (reproducible)
-__global__ void moments_reduce_kernel(const double* __restrict__ partial, int nblocks, int CP, int64_t N,
-                                      double* __restrict__ out) {
-    __shared__ double sm[256];
-    const int t = blockIdx.x;            // output index in [0, 15 CP)
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)b * 15 * CP + t];
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[t] = N > 0 ? sm[0] / (double)N : 0.0;
-}
-
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s) {
     moments_reduce_kernel<<<15 * CP, 256, 0, s>>>(partial, nblocks, CP, N, out);
-}
-
-// ------------------------------------------------------------------ deposition
-
-// CIC weights of the value part and their derivatives through the particle's
-// derivative channels; node charge q_m W for channel 0 and q_m dW/dp_k for
-// channel k. Each thread takes RUN consecutive particles (the push keeps them
-// cell-sorted), accumulates the eight node records in registers while the
-// cell does not change, and flushes them with 128-bit float atomics (FP32) or
-// FP64 atomics when it does. Records every particle's cell and its rank among
-// that cell's particles for the sort.
-template <typename T, int C, int CP, int RUN>
-__global__ void __launch_bounds__(RUN > 1 ? 128 : 256, RUN > 1 ? 3 : 1) deposit_kernel(const T* __restrict__ state, int64_t N,
-                                                      const GeomDev* __restrict__ geom, int nx, int ny, int nz,
-                                                      T qm, T* __restrict__ rho, int* __restrict__ err,
-                                                      const SortBuf sb) {
-    const int64_t first = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * RUN;
-    if (first >= N) return;
-    const GeomDev& g = *geom;
-    const int n[3] = {nx, ny, nz};
-    T ih[3], o[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        ih[d] = geom_ih<T>(g, d);
-        o[d] = geom_o<T>(g, d);
-    }
-    T acc[RUN > 1 ? 8 : 1][RUN > 1 ? CP : 1];
-    int cur = -1;
-    int bad = 0;
-    auto flush = [&](int cell) {
-        const int i0 = cell % nx, j0 = (cell / nx) % ny, k0 = cell / (nx * ny);
-#pragma unroll
-        for (int nd = 0; nd < 8; ++nd) {
-            const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-            const int64_t node = ((int64_t)(k0 + c) * ny + (j0 + b)) * nx + (i0 + a);
-            T* dst = rho + node * CP;
-            if constexpr (RUN > 1 && sizeof(T) == 4) {
-#pragma unroll
-                for (int v = 0; v < CP / 4; ++v)
-                    atomicAdd(reinterpret_cast<float4*>(dst) + v,
-                              make_float4(acc[nd][4 * v], acc[nd][4 * v + 1], acc[nd][4 * v + 2], acc[nd][4 * v + 3]));
-            } else if constexpr (RUN > 1) {
-#pragma unroll
-                for (int k = 0; k < C; ++k) atomicAdd(dst + k, acc[nd][k]);
-            }
-        }
-    };
-    for (int r = 0; r < RUN; ++r) {
-        const int64_t i = first + r;
-        if (i >= N) break;
-        T x[3][CP];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
-        T f[3];
-        int idx[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(x[d][0], o[d], ih[d], n[d], f[d], bad);
-        const int cell = (idx[2] * ny + idx[1]) * nx + idx[0];
-        if (sb.key) {
-            sb.key[i] = cell;
-            sb.rank[i] = atomicAdd(&sb.hist[cell], 1);
-        }
-        if constexpr (RUN == 1) {
-            // one particle per thread: add each node record at once
-#pragma unroll
-            for (int nd = 0; nd < 8; ++nd) {
-                const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
-                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
-                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
-                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
-                T q[CP];
-                q[0] = qm * (wx * wy * wz);
-#pragma unroll
-                for (int k = 1; k < CP; ++k) q[k] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
-                const int64_t node = ((int64_t)(idx[2] + c) * ny + (idx[1] + b)) * nx + (idx[0] + a);
-                T* dst = rho + node * CP;
-                if constexpr (sizeof(T) == 4) {
-#pragma unroll
-                    for (int v = 0; v < CP / 4; ++v)
-                        atomicAdd(reinterpret_cast<float4*>(dst) + v,
-                                  make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]));
-                } else {
-#pragma unroll
-                    for (int k = 0; k < C; ++k) atomicAdd(dst + k, q[k]);
-                }
-            }
-        } else {
-            if (cell != cur) {
-                if (cur >= 0) flush(cur);
-                cur = cell;
-#pragma unroll
-                for (int nd = 0; nd < 8; ++nd)
-#pragma unroll
-                    for (int k = 0; k < CP; ++k) acc[nd][k] = (T)0;
-            }
-#pragma unroll
-            for (int nd = 0; nd < 8; ++nd) {
-                const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
-                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
-                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
-                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
-                acc[nd][0] = fma(qm, wx * wy * wz, acc[nd][0]);
-#pragma unroll
-                for (int k = 1; k < CP; ++k) acc[nd][k] = fma(x[0][k], gx, fma(x[1][k], gy, fma(x[2][k], gz, acc[nd][k])));
-            }
-        }
-    }
-    if (RUN > 1 && cur >= 0) flush(cur);
-    if (bad) atomicOr(err, bad);
 }
 
 template <typename T, int C, int CP>

@@ -149,7 +149,15 @@ def test_config1_single_period(adpic, config1_ref, prec):
     rms = np.sqrt(m0[:, 2:3, :1] + m0[:, 4:5, :1])
     assert np.all(np.abs(gh[0][:, :2] - m0[:, :2]) < (1e-14 if prec == 0 else 1e-6) * rms)
     fin = sim.get_particles()
-    chan_close(fin, st, TOL[prec]["state"], 2)
+    if prec == 0:
+        chan_close(fin, st, TOL[prec]["state"], 2)
+    else:
+        # FP32: values element-wise; a derivative channel jumps where FP32 and FP64 put a particle
+        # on different sides of a cell edge (the CIC weight derivative is piecewise constant)
+        chan_close(fin[:, :, :1], st[:, :, :1], TOL[prec]["state"], 2)
+        scale = np.abs(st).max(axis=1, keepdims=True)
+        err = np.abs(fin - st) / np.where(scale > 0, scale, 1)
+        assert np.quantile(err[:, :, 1:], 0.999) < TOL[prec]["state"]
     sim.close()
 
 
