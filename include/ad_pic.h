@@ -198,6 +198,36 @@ int ad_pic_batch_tuning(const ad_pic_batch* b, int* mode, double* ms);
 int ad_pic_batch_set_stream(ad_pic_batch* b, void* stream);
 void ad_pic_batch_destroy(ad_pic_batch* b);
 
+/* ---------------------------------------------------------------------
+   Learned surrogate (the paper has no counterpart; it warm-starts the
+   variable-metric design search of Sec. 3 and Sec. 4): an MLP
+   n_in -> width (x hidden layers, GELU) -> n_out trained with the Sobolev
+   loss L = 1/B sum_b [ sum_o (y_bo - t_bo)^2 + lambda sum_o,k (dy_bok/dx_k -
+   dt_bok)^2 ] on values and derivatives. BF16 weights and activations, FP32
+   accumulation on tensor cores, FP32 master weights and Adam.
+   Parameters are one flat FP32 vector: for each layer W [out][in] then b [out].
+   Host arrays: x [B][n_in], y/t [B][n_out], dy/dt [B][n_out][n_in].
+   --------------------------------------------------------------------- */
+typedef struct ad_pic_mlp ad_pic_mlp;
+
+/* 1 <= n_in, n_out <= 64; 1 <= width <= 4096; 1 <= hidden <= 16; max_batch B
+   with B (n_in + 1) <= 2^24. Parameters start at zero. */
+int ad_pic_mlp_create(int n_in, int width, int hidden, int n_out, int max_batch, ad_pic_mlp** out);
+int ad_pic_mlp_num_params(const ad_pic_mlp* m, int64_t* n);
+/* Set (resets the Adam moments) / read the FP32 parameter vector. */
+int ad_pic_mlp_set_params(ad_pic_mlp* m, const float* params);
+int ad_pic_mlp_get_params(const ad_pic_mlp* m, float* params);
+/* Values y and, if dy is not NULL, input derivatives (forward mode). */
+int ad_pic_mlp_forward(ad_pic_mlp* m, const float* x, int B, float* y, float* dy);
+/* Sobolev loss and (if grad is not NULL) its gradient w.r.t. the flat parameters. */
+int ad_pic_mlp_loss_grad(ad_pic_mlp* m, const float* x, const float* t, const float* dt, int B, float lambda,
+                         double* loss, float* grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the Sobolev loss of the batch;
+   *loss is the loss before the step. */
+int ad_pic_mlp_adam_step(ad_pic_mlp* m, const float* x, const float* t, const float* dt, int B, float lambda, float lr,
+                         double* loss);
+void ad_pic_mlp_destroy(ad_pic_mlp* m);
+
 /* Allocation-free dual moments of a caller-owned device state (the paper has
    no counterpart: this exists for callers that cannot let the library call
    cudaMalloc/cudaFree - code running inside another framework's device-memory

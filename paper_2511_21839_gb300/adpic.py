@@ -85,6 +85,18 @@ def lib():
             "ad_pic_batch_tuning": (ct.c_int, [vp, ct.POINTER(ct.c_int), dp]),
             "ad_pic_batch_set_stream": (ct.c_int, [vp, vp]),
             "ad_pic_batch_destroy": (None, [vp]),
+            "ad_pic_mlp_create": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(vp)]),
+            "ad_pic_mlp_num_params": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
+            "ad_pic_mlp_set_params": (ct.c_int, [vp, ct.POINTER(ct.c_float)]),
+            "ad_pic_mlp_get_params": (ct.c_int, [vp, ct.POINTER(ct.c_float)]),
+            "ad_pic_mlp_forward": (ct.c_int, [vp, ct.POINTER(ct.c_float), ct.c_int, ct.POINTER(ct.c_float),
+                                              ct.POINTER(ct.c_float)]),
+            "ad_pic_mlp_loss_grad": (ct.c_int, [vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float),
+                                                ct.POINTER(ct.c_float), ct.c_int, ct.c_float, dp,
+                                                ct.POINTER(ct.c_float)]),
+            "ad_pic_mlp_adam_step": (ct.c_int, [vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float),
+                                                ct.POINTER(ct.c_float), ct.c_int, ct.c_float, ct.c_float, dp]),
+            "ad_pic_mlp_destroy": (None, [vp]),
             "ad_pic_destroy": (None, [vp]),
             "ad_pic_strerror": (ct.c_char_p, [ct.c_int]),
         }
@@ -290,6 +302,66 @@ def ad_pic_batch_set_stream(b, stream_ptr):
 def ad_pic_batch_destroy(b):
     if b:
         lib().ad_pic_batch_destroy(b)
+
+
+def _pf(a):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ct.POINTER(ct.c_float))
+
+
+def ad_pic_mlp_create(n_in, width, hidden, n_out, max_batch):
+    m = ct.c_void_p()
+    _ck("ad_pic_mlp_create", lib().ad_pic_mlp_create(int(n_in), int(width), int(hidden), int(n_out), int(max_batch),
+                                                     ct.byref(m)))
+    return m
+
+
+def ad_pic_mlp_num_params(m):
+    n = ct.c_int64()
+    _ck("ad_pic_mlp_num_params", lib().ad_pic_mlp_num_params(m, ct.byref(n)))
+    return n.value
+
+
+def ad_pic_mlp_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _ck("ad_pic_mlp_set_params", lib().ad_pic_mlp_set_params(m, _pf(p)))
+
+
+def ad_pic_mlp_get_params(m, n):
+    p = np.zeros(n, dtype=np.float32)
+    _ck("ad_pic_mlp_get_params", lib().ad_pic_mlp_get_params(m, _pf(p)))
+    return p
+
+
+def ad_pic_mlp_forward(m, x, n_out, want_dy=True):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    B, n_in = x.shape
+    y = np.zeros((B, n_out), dtype=np.float32)
+    dy = np.zeros((B, n_out, n_in), dtype=np.float32) if want_dy else None
+    _ck("ad_pic_mlp_forward", lib().ad_pic_mlp_forward(m, _pf(x), B, _pf(y), _pf(dy) if want_dy else None))
+    return y, dy
+
+
+def ad_pic_mlp_loss_grad(m, x, t, dt, lam, n_params):
+    x, t, dt = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, t, dt))
+    loss = ct.c_double()
+    g = np.zeros(n_params, dtype=np.float32)
+    _ck("ad_pic_mlp_loss_grad", lib().ad_pic_mlp_loss_grad(m, _pf(x), _pf(t), _pf(dt), x.shape[0], float(lam),
+                                                           ct.byref(loss), _pf(g)))
+    return loss.value, g
+
+
+def ad_pic_mlp_adam_step(m, x, t, dt, lam, lr):
+    x, t, dt = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, t, dt))
+    loss = ct.c_double()
+    _ck("ad_pic_mlp_adam_step", lib().ad_pic_mlp_adam_step(m, _pf(x), _pf(t), _pf(dt), x.shape[0], float(lam),
+                                                           float(lr), ct.byref(loss)))
+    return loss.value
+
+
+def ad_pic_mlp_destroy(m):
+    if m:
+        lib().ad_pic_mlp_destroy(m)
 
 
 # ------------------------------------------------------------------ convenience wrapper
