@@ -10,6 +10,9 @@ particles x kicks / time, whole job.
   python bench.py [--gpus N --steps K --warmup W]         CUDA path (FP32 bulk + FP64 reductions;
                                                            the plain FP64 path is measured beside it)
   python bench.py --impl reference [...]                   the FP64 CPU oracle on the host cores
+  python bench.py --workload fodo_16m_128 [...]            the large instance: 16,777,216 particles,
+                                                           128^3, P = 13 (7 lattice + 6 Twiss derivatives)
+  python bench.py --workload batch [...]                   the batched scan of 256 instances
 Multi-GPU (torchrun): independent replicas, one instance per rank (weak scaling).
 """
 import argparse
@@ -31,6 +34,9 @@ sys.path.insert(0, ROOT)
 METRIC = "dual particle-steps/s (1M p, 64³, P=7), FP32/batched vs plain FP64 at fixed error"
 UNIT = "dual particle-steps/s"
 WORKLOAD = "fodo_1m_64"
+METRICS = {"fodo_1m_64": METRIC,
+           "fodo_16m_128": "dual particle-steps/s (16.8M p, 128³, P=13), FP32 dual arithmetic with FP64 reductions"}
+CPU_KICKS = {"fodo_1m_64": 8, "fodo_16m_128": 1}
 
 
 def workload_config(w, extra=None):
@@ -39,7 +45,9 @@ def workload_config(w, extra=None):
                        f"P={w.n_deriv}, step = one period of {w.kicks_per_period} kicks + FP64 moments",
            "particles": w.n_particles, "grid": list(w.grid), "n_deriv": w.n_deriv,
            "kicks_per_step": w.kicks_per_period,
-           "l2": "inputs larger than L2: the dual particle state is 403 MB (FP32) / 805 MB (FP64)",
+           "l2": f"inputs larger than L2: the dual particle state is "
+                 f"{w.n_particles * 6 * (w.n_deriv + 1) * 4 / 1e6:.0f} MB (FP32) / "
+                 f"{w.n_particles * 6 * (w.n_deriv + 1) * 8 / 1e6:.0f} MB (FP64)",
            "parallelism": "replicas (one independent instance per GPU, no collective)"}
     if extra:
         cfg.update(extra)
@@ -79,7 +87,7 @@ def run_reference(args):
         return 0
     from paper_2511_21839_gb300 import inputs as I
 
-    w = I.workload(WORKLOAD)
+    w = I.workload(args.workload)
     kicks_per_step = 1
     for _ in range(args.warmup):
         oracle_rate(w, kicks_per_step)
@@ -89,9 +97,9 @@ def run_reference(args):
         times.append(dt)
     ms = 1000.0 * sum(times) / len(times)
     value = w.n_particles * kicks_per_step / (ms / 1000.0)
-    sample = (f"each step: {kicks_per_step} kick of the {w.name} workload ({w.n_particles} particles, 64^3, P=7), "
-              f"FP64 oracle, OpenMP over particles")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    sample = (f"each step: {kicks_per_step} kick of the {w.name} workload ({w.n_particles} particles, "
+              f"{w.grid[0]}^3, P={w.n_deriv}), FP64 oracle, OpenMP over particles")
+    line = {"impl": "reference", "metric": METRICS[w.name], "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, {"kicks_per_step": kicks_per_step}),
@@ -225,7 +233,7 @@ def run_native(args):
         dist = None
     build.build()
     dev = torch.cuda.current_device()
-    w = I.workload(WORKLOAD)
+    w = I.workload(args.workload)
     kicks = w.kicks_per_period
     nrm = I.normals(w.seed + 1000 * rank, w.n_particles)
     stream = torch.cuda.Stream()        # one non-default stream shared by the library and the events
@@ -313,13 +321,13 @@ def run_native(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        kicks_cpu = args.cpu_kicks
+        kicks_cpu = args.cpu_kicks or CPU_KICKS[w.name]
         rate, dt = oracle_rate(w, kicks_cpu)
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{kicks_cpu} kicks of the {w.name} workload on the host cores ({dt:.1f} s)"}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        line = {"metric": METRICS[w.name], "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(w, {"precision": "FP32 particles/deposit/FFT/field/push, FP64 geometry, "
@@ -396,9 +404,9 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-kicks", type=int, default=8)
+    ap.add_argument("--cpu-kicks", type=int, default=0, help="oracle kicks of the CPU baseline (0: per workload)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["fodo_1m_64", "batch"], default="fodo_1m_64")
+    ap.add_argument("--workload", choices=["fodo_1m_64", "fodo_16m_128", "batch"], default="fodo_1m_64")
     ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -90,11 +90,13 @@ typedef struct {
     int twiss_deriv_slot[6];
 } ad_pic_beam;
 
-/* Create a handle for n_particles >= 1 macroparticles on the given grid with
-   n_deriv in {7, 13} derivative slots and precision AD_PIC_FP64 (every step
+/* Create a handle for n_particles in [1, 2^31 - 1] macroparticles (particle
+   indices and cell offsets are 32-bit) on the given grid (nx, ny, nz powers
+   of two in [8, 128]) with n_deriv in {7, 13} derivative slots and precision AD_PIC_FP64 (every step
    in FP64) or AD_PIC_FP32_MIXED (particles, deposit, FFT, field and push in
    FP32; grid geometry, Green's-function integrals and all moment reductions
-   in FP64). Allocates every device buffer; *out is NULL on failure. */
+   in FP64). Allocates every device buffer; *out is NULL on failure.
+   AD_PIC_ERR_INVALID_ARG for sizes outside these ranges. */
 int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int precision, ad_pic** out);
 
 /* Set the reference particle and bunch charge. If normals is not NULL it is

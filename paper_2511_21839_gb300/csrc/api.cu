@@ -728,7 +728,7 @@ extern "C" {
 int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int precision, ad_pic** out) {
     if (!out) return AD_PIC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!grid || n_particles < 1 || n_particles > ((int64_t)1 << 34)) return AD_PIC_ERR_INVALID_ARG;
+    if (!grid || n_particles < 1 || n_particles > (int64_t)0x7fffffff) return AD_PIC_ERR_INVALID_ARG;
     if (n_deriv != 7 && n_deriv != 13) return AD_PIC_ERR_INVALID_ARG;
     if (precision != AD_PIC_FP64 && precision != AD_PIC_FP32_MIXED) return AD_PIC_ERR_INVALID_ARG;
     if (!pow2_in(grid->nx, 8, 128) || !pow2_in(grid->ny, 8, 128) || !pow2_in(grid->nz, 8, 128))

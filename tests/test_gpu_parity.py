@@ -307,3 +307,54 @@ def test_full_size_ten_periods_fp32_vs_fp64(adpic):
         e32 = o.emittance(hs[1][r])[:2]
         ev, ed = report(f"period {r} fp32 vs fp64", e32[:, 0], e32[:, 1:], e64)
         assert ev < 1e-5 and ed < 1e-4, r
+
+
+@pytest.fixture(scope="module")
+def large_grid_ref():
+    """The large instance's launch configuration (128^3 grid, P = 13) with 20,000 particles, 2 kicks."""
+    w = I.workload("fodo_16m_128")
+    N = 20_000
+    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=N))
+    nrm = I.normals(11, N)
+    st = o.beam_init(nrm)
+    hist, _ = o.run(st, 2)
+    return w, N, nrm, st, hist, o
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_large_grid_p13_vs_oracle(adpic, large_grid_ref, prec):
+    """128^3 (256-point FFT lines, 129-point DCTs) with the 13 lattice and Twiss derivatives."""
+    w, N, nrm, st, hist, o = large_grid_ref
+    sim = adpic.ADPIC(w.grid, N, 13, prec)
+    sim.set_beam(w.beam, nrm)
+    sim.set_lattice(w.lattice)
+    sim.run(2)
+    vals, der = sim.moments()
+    ref = o.emittance(hist[-1])[:2]
+    ev, ed = report(f"128^3 P=13 prec={prec}", vals, der, ref)
+    assert ev < TOL[prec]["eps"] and ed < TOL[prec]["der"]
+    fin = sim.get_particles()
+    chan_close(fin[:, :, :1], st[:, :, :1], TOL[prec]["state"], 2)
+    sim.close()
+
+
+def test_large_instance_fp32_vs_fp64(adpic):
+    """The large instance at full size (16,777,216 particles, 128^3, P = 13), two periods: FP32 bulk
+    arithmetic against the FP64 path (pinned to the oracle at this grid above) at each period end."""
+    w = I.workload("fodo_16m_128")
+    nrm = I.normals(w.seed, w.n_particles)
+    hs = []
+    for prec in (0, 1):
+        sim = adpic.ADPIC(w.grid, w.n_particles, 13, prec)
+        sim.set_beam(w.beam, nrm)
+        sim.set_lattice(w.lattice)
+        sim.run(2 * w.kicks_per_period)
+        hs.append(sim.history())
+        sim.close()
+    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=1))
+    assert hs[0].shape[0] == 3
+    for r in range(1, 3):
+        e64 = o.emittance(hs[0][r])[:2]
+        e32 = o.emittance(hs[1][r])[:2]
+        ev, ed = report(f"large instance period {r} fp32 vs fp64", e32[:, 0], e32[:, 1:], e64)
+        assert ev < 1e-5 and ed < 1e-4, r
