@@ -243,6 +243,7 @@ struct Impl {
         d.Mx = 2 * h->nx; d.My = 2 * h->ny; d.Mz = 2 * h->nz;
         d.lx = ilog2(d.Mx); d.ly = ilog2(d.My); d.lz = ilog2(d.Mz);
         d.C = C; d.CP = CP; d.npair = C / 2;
+        d.norm = 1.0 / ((double)d.Mx * d.My * d.Mz);
         return d;
     }
 

@@ -524,6 +524,7 @@ int upload_instances(ad_pic_batch* b, int nrec) {
         in.d.C = kCP;
         in.d.CP = kCP;
         in.d.npair = kCP / 2;
+        in.d.norm = 1.0 / ((double)in.M * in.M * in.M);
         in.state[0] = (T*)h->state;
         in.state[1] = (T*)h->state2;
         in.ids[0] = h->ids[0];

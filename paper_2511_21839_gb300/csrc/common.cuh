@@ -53,6 +53,7 @@ struct FFTDims {
     int Mx, My, Mz;
     int lx, ly, lz;     // log2 of M
     int C, CP, npair;
+    double norm;        // 1 / (Mx My Mz), set on the host (FP64 is slow on this part)
 };
 
 // ---------------------------------------------------------------- launchers

@@ -342,7 +342,7 @@ __device__ __forceinline__ void fftx_inv_kernel_body(const V2<T>* __restrict__ X
     __syncthreads();
     // outputs x < nx of every line into a row-major staging area [r][x][CP]
     T* stage = reinterpret_cast<T*>(buf + nl * L::LS);
-    const T norm = (T)(1.0 / ((double)d.Mx * d.My * d.Mz));
+    const T norm = (T)d.norm;
     for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
         const int line = w % nl, k1 = w / nl;
         V2<T> v[L::R2];

@@ -21,12 +21,12 @@ void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, doubl
                   const T* dct_x, const T* dct_y, const T* dct_z, cudaStream_t s) {
     (void)exact;
     const int64_t nc = (int64_t)(nx + 2) * (ny + 2) * (nz + 2);
-    green_corner_kernel<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(geom, nx, ny, nz, corner);
+    green_corner_kernel<<<(unsigned)((nc + 63) / 64), 64, 0, s>>>(geom, nx, ny, nz, corner);
     const int64_t ng = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
     green_cell_kernel<T><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(geom, nx, ny, nz, corner, G);
     // G [z][y][x] -> pass x -> [x'][z][y] -> pass y -> [y'][x'][z] -> pass z -> [z'][y'][x']
     auto pass = [&](const T* in, T* out, const T* D, int L, int64_t BA) {
-        const size_t sm = sizeof(T) * ((size_t)L * L + (size_t)kDctLines * (L + 1));
+        const size_t sm = sizeof(T) * ((size_t)L * L + (size_t)kDctLines * L);
         dct_kernel<T><<<(unsigned)((BA + kDctLines - 1) / kDctLines), 256, sm, s>>>(in, out, D, L, BA);
     };
     pass(G, Gtmp, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));

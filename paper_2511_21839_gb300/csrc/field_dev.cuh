@@ -101,17 +101,19 @@ __device__ __forceinline__ double igf_F(double x, double y, double z) {
            0.5 * y * y * atan(x * z / (y * r)) - 0.5 * z * z * atan(x * y / (z * r));
 }
 
-// F at the cell corners ((i - 1/2) hx, (j - 1/2) hy, (k - 1/2) hzr), i in [0, Rx+1] etc. (FP64)
-// Launched over the full (nx+2)(ny+2)(nz+2) corner lattice; corners outside
-// the near box of this kick return at once.
+// F at the cell corners ((i - 1/2) hx, (j - 1/2) hy, (k - 1/2) hzr) of the near
+// box i in [0, Rx+1], j in [0, Ry+1], k in [0, Rz+1] (FP64), stored in the
+// (nx+2)(ny+2)(nz+2) corner lattice. The box is mapped onto the first threads
+// so its FP64 work spreads over consecutive small blocks; callers launch at
+// least (nx+2)(ny+2)(nz+2) threads (R <= n), the rest return at once.
 __device__ __forceinline__ void green_corner_kernel_body(const GeomDev* __restrict__ g, int nx, int ny, int nz, double* __restrict__ F,
     const int bx_, const int by_, const int bz_, const int nbx_) {
-    const int cx = nx + 2, cy = ny + 2, cz = nz + 2;
-    const int t = bx_ * blockDim.x + threadIdx.x;     // < 130^3
-    if (t >= cx * cy * cz) return;
-    const int i = t % cx, j = (t / cx) % cy, k = t / (cx * cy);
-    if (i > g->R[0] + 1 || j > g->R[1] + 1 || k > g->R[2] + 1) return;
-    F[t] = igf_F((i - 0.5) * g->hr[0], (j - 0.5) * g->hr[1], (k - 0.5) * g->hr[2]);
+    const int cx = nx + 2, cy = ny + 2;
+    const int t = bx_ * blockDim.x + threadIdx.x;
+    const int ex = g->R[0] + 2, ey = g->R[1] + 2, ez = g->R[2] + 2;
+    if (t >= ex * ey * ez) return;
+    const int i = t % ex, j = (t / ex) % ey, k = t / (ex * ey);
+    F[((int64_t)k * cy + j) * cx + i] = igf_F((i - 0.5) * g->hr[0], (j - 0.5) * g->hr[1], (k - 0.5) * g->hr[2]);
 }
 
 static __global__ void green_corner_kernel(const GeomDev* __restrict__ g, int nx, int ny, int nz, double* __restrict__ F) {
@@ -172,33 +174,64 @@ static __global__ void green_cell_kernel(const GeomDev* __restrict__ g, int nx, 
 // One DCT-I pass over the contiguous axis of in [BA][L] (L = n+1) into
 // out [L][BA]: out[k][ba] = sum_l D[k][l] in[ba][l], D[k][l] = w_l cos(pi l k / n),
 // w_0 = w_n = 1, else 2. Three passes (rotating the axes) give the real
-// spectrum of the even extension of G to the 2n-periodic grid. A block
-// stages kDctLines input lines and the matrix D in shared memory.
-constexpr int kDctLines = 8;
+// spectrum of the even extension of G to the 2n-periodic grid. A block of
+// 256 threads stages kDctLines = 32 input lines and the matrix D in shared
+// memory; lane l of warp w accumulates out[k][line l] for k = w, w + 8, ...
+// in registers (the D reads are warp-wide broadcasts, the line stride L is
+// odd so the line reads are conflict-free, and the stores of one k are 32
+// consecutive words).
+constexpr int kDctLines = 32;
+constexpr int kDctAcc = 8;
 
 template <typename T>
 __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
     const int bx_, const int by_, const int bz_, const int nbx_) {
     extern __shared__ unsigned char smraw[];
     T* Ds = reinterpret_cast<T*>(smraw);            // [L][L]
-    T* xs = Ds + L * L;                             // [kDctLines][L + 1]
+    T* xs = Ds + L * L;                             // [kDctLines][L] (room for [kDctLines][L + 1])
     const int64_t ba0 = (int64_t)bx_ * kDctLines;
     const int nl = (int)min((int64_t)kDctLines, BA - ba0);
-    for (int t = threadIdx.x; t < L * L; t += blockDim.x) Ds[t] = D[t];
-    for (int t = threadIdx.x; t < nl * L; t += blockDim.x) {
-        const int l = t / L, c = t % L;
-        xs[l * (L + 1) + c] = in[(ba0 + l) * L + c];
-    }
+    // global -> shared in batches of 8 independent loads per thread (one latency per batch)
+    auto stage = [&](const T* __restrict__ src, T* dst, int count, int total) {
+        for (int t0 = threadIdx.x; t0 < total; t0 += 8 * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int t = t0 + q * blockDim.x;
+                v[q] = t < count ? src[t] : (T)0;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int t = t0 + q * blockDim.x;
+                if (t < total) dst[t] = v[q];
+            }
+        }
+    };
+    stage(D, Ds, L * L, L * L);
+    stage(in + ba0 * L, xs, nl * L, kDctLines * L);
     __syncthreads();
-    // thread -> (k, line) with the line fastest so the writes of one k are contiguous
-    for (int t = threadIdx.x; t < L * kDctLines; t += blockDim.x) {
-        const int k = t / kDctLines, l = t % kDctLines;
-        if (l >= nl) continue;
-        const T* row = Ds + k * L;
-        const T* x = xs + l * (L + 1);
-        T s = (T)0;
-        for (int c = 0; c < L; ++c) s = fma(row[c], x[c], s);
-        out[(int64_t)k * BA + ba0 + l] = s;
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const T* x = xs + l * L;
+    for (int k0 = w; k0 < L; k0 += nw * kDctAcc) {
+        T acc[kDctAcc];
+        const T* row[kDctAcc];
+#pragma unroll
+        for (int q = 0; q < kDctAcc; ++q) {
+            acc[q] = (T)0;
+            row[q] = Ds + min(k0 + q * nw, L - 1) * L;
+        }
+        for (int c = 0; c < L; ++c) {
+            const T xv = x[c];
+#pragma unroll
+            for (int q = 0; q < kDctAcc; ++q) acc[q] = fma(row[q][c], xv, acc[q]);
+        }
+        if (l < nl) {
+#pragma unroll
+            for (int q = 0; q < kDctAcc; ++q) {
+                const int k = k0 + q * nw;
+                if (k < L) out[(int64_t)k * BA + ba0 + l] = acc[q];
+            }
+        }
     }
 }
 

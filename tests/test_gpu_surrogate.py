@@ -106,3 +106,75 @@ def test_adam_fits_a_smooth_map_with_derivatives(lib):
     assert np.sqrt(np.mean((y - t) ** 2)) < 0.1 * np.sqrt(np.mean(t ** 2))
     assert np.sqrt(np.mean((dy - dt) ** 2)) < 0.2 * np.sqrt(np.mean(dt ** 2))
     lib.ad_pic_mlp_destroy(m)
+
+
+# ---------------------------------------------------------------- the surrogate workflow
+
+@pytest.fixture(scope="module")
+def workflow(lib):
+    """4,096 single-period dual-PIC runs of the 10,000-particle, 32^3, P = 7 FODO problem at
+    lattice parameters drawn uniformly within +-20 % (seed 5) on the batched runtime; 90 % train
+    the network with the Sobolev loss, 10 % are held out."""
+    from paper_2511_21839_gb300 import surrogate as S
+
+    prob = S.Problem()
+    X, Y, dY = S.generate_dataset(prob, 4096, seed=5)
+    ntr = int(0.9 * len(X))
+    sur = S.Surrogate()
+    sur.fit(X[:ntr], Y[:ntr], dY[:ntr], steps=3000, lam=1.0)
+    yield S, prob, (X, Y, dY, ntr), sur
+    sur.close()
+    prob.close()
+
+
+def test_dataset_matches_single_runs(workflow):
+    """Batched dataset runs reproduce the single-instance dual PIC at the same parameters."""
+    S, prob, (X, Y, dY, ntr), sur = workflow
+    for i in (0, 1, 4095):
+        y, dy = prob.evaluate(X[i])
+        assert np.abs(y - Y[i]).max() < 1e-7
+        assert np.abs(dy - dY[i]).max() < 1e-4 * np.abs(dY[i]).max()
+
+
+def test_surrogate_generalises_and_sobolev_loss_helps_derivatives(workflow):
+    """Held-out relative rms errors of values and derivatives; training on values alone (lam = 0)
+    leaves the derivatives markedly worse."""
+    S, prob, (X, Y, dY, ntr), sur = workflow
+    ev, ed = sur.errors(X[ntr:], Y[ntr:], dY[ntr:])
+    plain = S.Surrogate()
+    plain.fit(X[:ntr], Y[:ntr], dY[:ntr], steps=3000, lam=0.0)
+    pv, pd = plain.errors(X[ntr:], Y[ntr:], dY[ntr:])
+    plain.close()
+    print(f"held-out: Sobolev value {ev:.3f} derivative {ed:.3f}; values only: value {pv:.3f} derivative {pd:.3f}")
+    assert ev < 0.1 and ed < 0.06
+    assert ed < 0.6 * pd
+
+
+def test_warm_start_needs_fewer_dual_pic_runs(workflow):
+    """Target emittances of hidden lattices: the surrogate-warm-started search reaches each target
+    (judged by the dual PIC) with fewer dual-PIC evaluations than BFGS on dual-PIC gradients alone,
+    and the surrogate's own optimum, before any correction, is already verified close by the PIC."""
+    S, prob, (X, Y, dY, ntr), sur = workflow
+    scale = sur.y_scale
+    rng = np.random.default_rng(9)
+    ftol = 1e-4                                   # residual 1 % of the spread of each emittance
+    cold = warm = 0
+    for k in range(8):
+        target = prob.evaluate(rng.uniform(-0.8, 0.8, size=7))[0]
+        x0 = np.zeros(7)
+        f0 = S.objective(*prob.evaluate(x0), target, scale)[0]
+        xs, _, _ = S.bfgs(lambda x: S.objective(*(a[0] for a in sur.predict(x)), target, scale), x0,
+                          -np.ones(7), np.ones(7), max_iter=200)
+        fs = S.objective(*prob.evaluate(xs), target, scale)[0]
+        xc, fc, nc = S.search_cold(prob, target, x0, ftol, max_evals=80, scale=scale)
+        xw, fw, nw = S.search_warm(prob, sur, target, x0, ftol, max_evals=80, scale=scale)
+        print(f"target {k}: f(x0) {f0:.2e}, f(surrogate optimum) {fs:.2e}; cold {nc} runs -> {fc:.1e}, "
+              f"warm {nw} runs -> {fw:.1e}")
+        assert fs < 0.05 * f0
+        # the final points are judged by a fresh dual-PIC run
+        assert S.objective(*prob.evaluate(xw), target, scale)[0] < ftol
+        assert fc < ftol
+        cold += nc
+        warm += nw
+    print(f"dual-PIC runs over 8 targets: cold {cold}, warm {warm}")
+    assert warm < 0.7 * cold
