@@ -156,22 +156,28 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- native arm
 
-def traffic_from_profile(kernel_src_hash):
-    """Per-launch DRAM traffic of the push kernel from the committed ncu summary, if it was taken
-    on the current kernel source (else null)."""
-    path = os.path.join(ROOT, "profiles", "push_fodo_1m_64.json")
+def traffic_from_profile(workload, src_hash):
+    """Per-launch DRAM traffic of the push kernel from the committed ncu summary of this workload
+    (lines `dram_bytes_per_launch: B` and `kernel_src_sha256: H`), if it was taken on the current
+    kernel source (else null)."""
+    import re
+
+    path = os.path.join(ROOT, "profiles", f"push_{workload}.md")
     try:
-        d = json.load(open(path))
-    except (OSError, ValueError):
+        text = open(path).read()
+    except OSError:
         return None
-    if d.get("kernel_src_sha256") != kernel_src_hash:
+    h = re.search(r"kernel_src_sha256:\s*([0-9a-f]{64})", text)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not h or not b or h.group(1) != src_hash:
         return None
-    return d.get("dram_bytes_per_launch")
+    return int(b.group(1))
 
 
 def kernel_src_hash():
+    """SHA-256 over the sources that make up the push kernel."""
     h = hashlib.sha256()
-    for f in ("particles.cu", "common.cuh"):
+    for f in ("particles.cu", "particles_dev.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2511_21839_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -317,7 +323,7 @@ def run_native(args):
             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": push_ms,
-            "traffic": traffic_from_profile(kernel_src_hash())}
+            "traffic": traffic_from_profile(w.name, kernel_src_hash())}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -120,8 +120,9 @@ void free_graphs(ad_pic* h) {
 }
 
 // event timing around the launches of the selected kernel classes
-void tbegin(ad_pic* h, int cls, bool capturing) {
+void tbegin(ad_pic* h, int cls, bool capturing, cudaStream_t st = nullptr) {
     if (!((h->tmask >> cls) & 1u)) return;
+    if (!st) st = h->stream;
     while ((int)h->events.size() < h->ev_used + 2) {
         cudaEvent_t e;
         cudaEventCreate(&e);
@@ -129,13 +130,14 @@ void tbegin(ad_pic* h, int cls, bool capturing) {
     }
     if ((int)h->ev_class.size() < (h->ev_used + 2) / 2) h->ev_class.resize((h->ev_used + 2) / 2);
     h->ev_class[h->ev_used / 2] = cls;
-    if (capturing) cudaEventRecordWithFlags(h->events[h->ev_used], h->stream, cudaEventRecordExternal);
-    else cudaEventRecord(h->events[h->ev_used], h->stream);
+    if (capturing) cudaEventRecordWithFlags(h->events[h->ev_used], st, cudaEventRecordExternal);
+    else cudaEventRecord(h->events[h->ev_used], st);
 }
-void tend(ad_pic* h, int cls, bool capturing) {
+void tend(ad_pic* h, int cls, bool capturing, cudaStream_t st = nullptr) {
     if (!((h->tmask >> cls) & 1u)) return;
-    if (capturing) cudaEventRecordWithFlags(h->events[h->ev_used + 1], h->stream, cudaEventRecordExternal);
-    else cudaEventRecord(h->events[h->ev_used + 1], h->stream);
+    if (!st) st = h->stream;
+    if (capturing) cudaEventRecordWithFlags(h->events[h->ev_used + 1], st, cudaEventRecordExternal);
+    else cudaEventRecord(h->events[h->ev_used + 1], st);
     h->ev_used += 2;
 }
 void tcollect(ad_pic* h, int pairs) {
@@ -254,6 +256,15 @@ struct Impl {
         tbegin(h, K_GEOM, cap);
         launch_geom<T>((Ord<T>*)h->mm, h->nx, h->ny, h->nz, h->gamma0, h->geom, (Ord<T>*)h->chmax, CP, s);
         tend(h, K_GEOM, cap);
+        // Green's function on the side stream (it needs only the geometry)
+        cudaEventRecord(h->ev_fork, s);
+        cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+        tbegin(h, K_GREEN, cap, h->side);
+        launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
+                        (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2],
+                        fft_slab_path<T>(dims(h)) ? 1 : 0, h->side);
+        tend(h, K_GREEN, cap, h->side);
+        cudaEventRecord(h->ev_join, h->side);
         tbegin(h, K_MISC, cap);
         cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s);
         tend(h, K_MISC, cap);
@@ -265,10 +276,7 @@ struct Impl {
         launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, s);
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
         tend(h, K_MISC, cap);
-        tbegin(h, K_GREEN, cap);
-        launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
-                        (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2], s);
-        tend(h, K_GREEN, cap);
+        cudaStreamWaitEvent(s, h->ev_join, 0);
         tbegin(h, K_FFT, cap);
         FFTDims d = dims(h);
         launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
@@ -287,8 +295,8 @@ struct Impl {
     }
 
     // kernels launched by one enqueue_field (geometry 1, deposit 1, scan 3,
-    // chmax 1, Green's function 5, convolution 5, field 1; the memset is not a kernel)
-    static constexpr int kFieldLaunches = 17;
+    // chmax 1, Green's function 5, convolution 3 or 5, field 1; the memset is not a kernel)
+    static int field_launches(ad_pic* h) { return 12 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
 
     // the launch sequence of one run; returns the number of moment records
     // `from` is the buffer holding the particles at the start; each push moves
@@ -384,7 +392,7 @@ struct Impl {
             const int nr = count_records(h, g0, n, first);
             int64_t l = 0;
             if (n == 0) l = 2;
-            else l = 1 + (int64_t)n * (kFieldLaunches + 1) + 2 * (int64_t)nr - (first ? 1 : 0);
+            else l = 1 + (int64_t)n * (field_launches(h) + 1) + 2 * (int64_t)nr - (first ? 1 : 0);
             h->launches += l;
         }
         const int from = h->cur;
@@ -582,7 +590,8 @@ struct Impl {
         }
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
         launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
-                        (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2], s);
+                        (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2],
+                        fft_slab_path<T>(dims(h)) ? 1 : 0, s);
         FFTDims d = dims(h);
         launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
@@ -678,6 +687,8 @@ struct Impl {
         }
         setup_green<T>();
         setup_fft<T>();
+        setup_deposit<T, C, CP>();
+        setup_push<T, C, CP>();
         CK(cudaStreamSynchronize(h->stream));
         return AD_PIC_OK;
     }
@@ -748,6 +759,13 @@ int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int
         return AD_PIC_ERR_CUDA;
     }
     h->stream = h->own_stream;
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ad_pic_destroy(h);
+        return AD_PIC_ERR_CUDA;
+    }
     int st;
     auto alloc = [&]() -> int { DISPATCH(h, I::allocate(h)); };
     st = alloc();
@@ -899,11 +917,15 @@ int ad_pic_constants(const ad_pic* h, double* out) {
 void ad_pic_destroy(ad_pic* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);
     free_graphs(h);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (void* p : h->allocs)
         if (p) cudaFree(p);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     cudaGetLastError();
     delete h;
 }

@@ -464,18 +464,6 @@ int build_tables(ad_pic_batch* b) {
     cudaFuncSetAttribute(batch_persistent_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(batch_persistent_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(batch_phase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    // this translation unit's copy of the small-DFT twiddles
-    float2 f[16];
-    double2 dd[16];
-    for (int j = 0; j < 16; ++j) {
-        const double a = 2.0 * M_PI * (double)j / 16.0;
-        dd[j].x = std::cos(a);
-        dd[j].y = -std::sin(a);
-        f[j].x = (float)dd[j].x;
-        f[j].y = (float)dd[j].y;
-    }
-    if (cudaMemcpyToSymbol(c_tw16f, f, sizeof(f)) != cudaSuccess) return AD_PIC_ERR_CUDA;
-    if (cudaMemcpyToSymbol(c_tw16d, dd, sizeof(dd)) != cudaSuccess) return AD_PIC_ERR_CUDA;
     return AD_PIC_OK;
 }
 

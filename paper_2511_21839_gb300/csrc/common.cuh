@@ -19,6 +19,7 @@ namespace adpic {
 
 constexpr int kErrOutOfGrid = 1;
 constexpr int kErrNonfinite = 2;
+constexpr int kErrTimeout = 4;      // a bounded wait on a bulk copy gave up
 
 template <typename T> struct V2T;
 template <> struct V2T<float> { using type = float2; };
@@ -94,6 +95,10 @@ int boundary_blocks();
 template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho,
                     int* err, const SortBuf& sb, cudaStream_t s);
+template <typename T, int C, int CP>
+void setup_deposit();
+template <typename T, int C, int CP>
+void setup_push();
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s);
 
 template <typename T>
@@ -101,14 +106,20 @@ void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geo
                  cudaStream_t s);
 template <typename T>
 void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream_t s);
+// Ghat order 0: [kz'][ky'][kx'] (x fastest); order 1: [kx'][kz'][ky'] (y fastest)
 template <typename T>
 void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, double* corner, T* G, T* Gtmp,
-                  T* Ghat, const T* dct_x, const T* dct_y, const T* dct_z, cudaStream_t s);
+                  T* Ghat, const T* dct_x, const T* dct_y, const T* dct_z, int order, cudaStream_t s);
 template <typename T>
 void setup_green();
 template <typename T>
 void setup_fft();
 // twx/twy/twz: exp(-2 pi i j / M) for j < M of each axis (M = 2n)
+// true when launch_fft_conv takes the three-launch slab path for these
+// dimensions (it then expects Ghat in the [kx'][kz'][ky'] order, see launch_green)
+template <typename T>
+bool fft_slab_path(const FFTDims& d);
+int fft_conv_launches(bool slab);
 template <typename T>
 void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
                      const V2<T>* twx, const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s);

@@ -18,6 +18,8 @@
 //   fftz       X2 columns (z < nz): forward, times Ghat, inverse, keep z < nz, in place
 //   ffty<inv>  X2 columns (all My)      -> X1 (y < ny)
 //   fftx_inv   X1 rows (all Mx)         -> phi rows (x < nx), scaled back
+// Grids with nz <= 64 take the three-launch slab path instead (fftx_fwd_t,
+// fftyz, fftx_inv_t in fft_dev.cuh), with Ghat stored [kx'][kz'][ky'].
 #include "fft_dev.cuh"
 
 namespace adpic {
@@ -74,9 +76,91 @@ void conv_y(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFT
     }
 }
 
+// ---------------------------------------------------------------- slab path
+
+static int lay_ls(int M) {
+    switch (M) {
+        case 16: return Lay<16>::LS;
+        case 32: return Lay<32>::LS;
+        case 64: return Lay<64>::LS;
+        case 128: return Lay<128>::LS;
+        default: return Lay<256>::LS;
+    }
+}
+
+template <typename T>
+static size_t sm_fwd_t(const FFTDims& d, int yt) {
+    return sizeof(V2<T>) * ((size_t)d.Mx + (size_t)yt * d.npair * lay_ls(d.Mx)) + sizeof(T) * 16;
+}
+template <typename T>
+static size_t sm_inv_t(const FFTDims& d, int yt) {
+    return sm_fwd_t<T>(d, yt) + sizeof(T) * (size_t)yt * ((size_t)d.nx * d.CP + 1);
+}
+template <typename T>
+static size_t sm_yz(const FFTDims& d) {
+    return sizeof(V2<T>) * ((size_t)d.My + d.Mz + (size_t)d.nz * lay_ls(d.My) + (size_t)slab_kc<T>() * lay_ls(d.Mz));
+}
+constexpr size_t kSmemCap = 200 * 1024;
+
+// rows per CTA of the x passes: up to 16 while both x kernels stay within 96 KB
+template <typename T>
+static int slab_yt(const FFTDims& d) {
+    int yt = d.ny < 16 ? d.ny : 16;
+    while (yt > 1 && sm_inv_t<T>(d, yt) > 96 * 1024) yt >>= 1;
+    return yt;
+}
+
+template <typename T>
+bool fft_slab_path(const FFTDims& d) {
+    return d.nz <= 64 && d.My <= 128 && d.Mz <= 128 && sm_yz<T>(d) <= kSmemCap &&
+           sm_inv_t<T>(d, slab_yt<T>(d)) <= kSmemCap;
+}
+
+int fft_conv_launches(bool slab) { return slab ? 3 : 5; }
+
+template <typename T, int MX, int MY, int MZ>
+void conv_slab(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
+               const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+    const int yt = slab_yt<T>(d);
+    const dim3 gx((unsigned)(d.ny / yt), (unsigned)d.nz);
+    fftx_fwd_t_kernel<T, MX><<<gx, 256, sm_fwd_t<T>(d, yt), s>>>(rho, X1, d, twx, chmax, yt);
+    fftyz_kernel<T, MY, MZ><<<dim3((unsigned)d.Mx, (unsigned)d.npair), 256, sm_yz<T>(d), s>>>(X1, Ghat, d, twy, twz);
+    fftx_inv_t_kernel<T, MX><<<gx, 256, sm_inv_t<T>(d, yt), s>>>(X1, phi, d, twx, chmax, yt);
+}
+template <typename T, int MX, int MY>
+void conv_slab_z(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
+                 const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+    switch (d.Mz) {
+        case 16: conv_slab<T, MX, MY, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 32: conv_slab<T, MX, MY, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 64: conv_slab<T, MX, MY, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        default: conv_slab<T, MX, MY, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+    }
+}
+template <typename T, int MX>
+void conv_slab_y(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
+                 const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+    switch (d.My) {
+        case 16: conv_slab_z<T, MX, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 32: conv_slab_z<T, MX, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 64: conv_slab_z<T, MX, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        default: conv_slab_z<T, MX, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+    }
+}
+
 template <typename T>
 void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
                      const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+    if (fft_slab_path<T>(d)) {
+        switch (d.Mx) {
+            case 16: conv_slab_y<T, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+            case 32: conv_slab_y<T, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+            case 64: conv_slab_y<T, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+            case 128: conv_slab_y<T, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+            default: conv_slab_y<T, 256>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        }
+        return;
+    }
     switch (d.Mx) {
         case 16: conv_y<T, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
         case 32: conv_y<T, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
@@ -86,6 +170,19 @@ void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, 
     }
 }
 
+template <typename T, int M>
+static void slab_x_attrs() {
+    cudaFuncSetAttribute(fftx_fwd_t_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(fftx_inv_t_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+}
+template <typename T, int MY>
+static void slab_yz_attrs() {
+    cudaFuncSetAttribute(fftyz_kernel<T, MY, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(fftyz_kernel<T, MY, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(fftyz_kernel<T, MY, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(fftyz_kernel<T, MY, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+}
+
 template <typename T>
 void setup_fft() {
     Conv<T, 16>::attrs();
@@ -93,17 +190,15 @@ void setup_fft() {
     Conv<T, 64>::attrs();
     Conv<T, 128>::attrs();
     Conv<T, 256>::attrs();
-    float2 f[16];
-    double2 dd[16];
-    for (int j = 0; j < 16; ++j) {
-        const double a = 2.0 * M_PI * (double)j / 16.0;
-        dd[j].x = std::cos(a);
-        dd[j].y = -std::sin(a);
-        f[j].x = (float)dd[j].x;
-        f[j].y = (float)dd[j].y;
-    }
-    cudaMemcpyToSymbol(c_tw16f, f, sizeof(f));
-    cudaMemcpyToSymbol(c_tw16d, dd, sizeof(dd));
+    slab_x_attrs<T, 16>();
+    slab_x_attrs<T, 32>();
+    slab_x_attrs<T, 64>();
+    slab_x_attrs<T, 128>();
+    slab_x_attrs<T, 256>();
+    slab_yz_attrs<T, 16>();
+    slab_yz_attrs<T, 32>();
+    slab_yz_attrs<T, 64>();
+    slab_yz_attrs<T, 128>();
 }
 
 template void launch_fft_conv<float>(const float*, float2*, float2*, const float*, float*, const FFTDims&,
@@ -111,6 +206,8 @@ template void launch_fft_conv<float>(const float*, float2*, float2*, const float
 template void launch_fft_conv<double>(const double*, double2*, double2*, const double*, double*, const FFTDims&,
                                       const double2*, const double2*, const double2*, const unsigned long long*,
                                       cudaStream_t);
+template bool fft_slab_path<float>(const FFTDims&);
+template bool fft_slab_path<double>(const FFTDims&);
 template void setup_fft<float>();
 template void setup_fft<double>();
 

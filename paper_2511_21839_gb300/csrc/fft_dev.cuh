@@ -27,13 +27,30 @@
 
 namespace adpic {
 
-static __constant__ float2 c_tw16f[16];    // exp(-2 pi i j / 16)
-static __constant__ double2 c_tw16d[16];
-
-template <typename T>
-__device__ __forceinline__ V2<T> tw16(int j) {
-    if constexpr (sizeof(T) == 4) return c_tw16f[j];
-    else return c_tw16d[j];
+// d * exp(-+ 2 pi i e / 16) for e in [0, 8) (the sign is + for INV). Inside
+// unrolled loops e is a compile-time constant, so the switch folds away:
+// multiplications by -i cost nothing and the 45-degree ones two adds.
+template <typename T, bool INV>
+__device__ __forceinline__ V2<T> mul_w16(V2<T> d, int e) {
+    constexpr T c1 = (T)0.92387953251128675613;   // cos(pi / 8)
+    constexpr T s1 = (T)0.38268343236508977173;   // sin(pi / 8)
+    constexpr T h = (T)0.70710678118654752440;    // cos(pi / 4)
+    const T sg = INV ? (T)-1 : (T)1;              // exp(-i a) forward, exp(+i a) inverse
+    V2<T> r;
+    switch (e) {
+        case 0: r = d; break;
+        case 2: r.x = h * (d.x + sg * d.y); r.y = h * (d.y - sg * d.x); break;
+        case 4: r.x = sg * d.y; r.y = -sg * d.x; break;
+        case 6: r.x = h * (sg * d.y - d.x); r.y = -h * (d.y + sg * d.x); break;
+        default: {
+            // exp(-+ i a) with (cos a, sin a) = (c1, s1), (s1, c1), (-s1, c1), (-c1, s1) for e = 1, 3, 5, 7
+            const T ca = e == 1 ? c1 : (e == 3 ? s1 : (e == 5 ? -s1 : -c1));
+            const T sa = e == 1 ? s1 : (e == 3 ? c1 : (e == 5 ? c1 : s1));
+            r.x = fma(d.x, ca, sg * d.y * sa);
+            r.y = fma(d.y, ca, -sg * d.x * sa);
+        }
+    }
+    return r;
 }
 
 template <typename T>
@@ -68,13 +85,7 @@ __device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
                 V2<T> d;
                 d.x = a.x - b.x;
                 d.y = a.y - b.y;
-                if (j == 0) {
-                    v[g + j + half] = d;
-                } else {
-                    V2<T> w = tw16<T>(j * (16 / len));
-                    if (INV) w.y = -w.y;
-                    v[g + j + half] = cmul<T>(d, w);
-                }
+                v[g + j + half] = mul_w16<T, INV>(d, j * (16 / len));
             }
         }
     }
@@ -373,6 +384,288 @@ template <typename T, int M>
 static __global__ void __launch_bounds__(256) fftx_inv_kernel(const V2<T>* __restrict__ X1, T* __restrict__ phi, FFTDims d,
                                                        const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax) {
     fftx_inv_kernel_body<T, M>(X1, phi, d, tw, chmax, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// ------------------------------------------------------------------ slab path
+// For grids whose (z, 2ny) slab of one channel pair fits in shared memory
+// (n <= 64): the x passes exchange data with X1 in the layout
+// [pair][kx][z][y] (y fastest), and one CTA per (kx, pair) runs the y and z
+// transforms, the multiplication by Ghat and both inverses on its slab
+// without leaving shared memory. Ghat is then stored [kx'][kz'][ky'] so a
+// CTA reads one contiguous plane. Three launches instead of five, and the
+// (2ny)(2nx) nz intermediate never exists.
+
+// x pass, forward: rows (z, y0 .. y0 + yt - 1) of every pair -> X1 [p][kx][z][y]
+template <typename T, int M>
+__device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho, V2<T>* __restrict__ X1, FFTDims d,
+                                                         const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax,
+                                                         int yt, const int bx_, const int by_) {
+    using L = Lay<M>;
+    extern __shared__ unsigned char smraw[];
+    V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
+    T* sc = reinterpret_cast<T*>(twM + M);            // channel scales [16]
+    V2<T>* buf = reinterpret_cast<V2<T>*>(sc + 16);   // [npair * yt][LS], line = p * yt + r
+    const int nl = yt * d.npair;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
+    if (threadIdx.x < d.CP) sc[threadIdx.x] = chan_scale<T>(chmax, threadIdx.x, false);
+    __syncthreads();
+    const int y0 = bx_ * yt, z = by_;
+    const T* src = rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP;
+    for (int t = threadIdx.x; t < yt * d.nx * d.CP; t += blockDim.x) {
+        const int c = t % d.CP, x = (t / d.CP) % d.nx, r = t / (d.CP * d.nx);
+        if (c >= d.C) continue;
+        const T v = src[t] * sc[c];
+        V2<T>& dst = buf[((c >> 1) * yt + r) * L::LS + L::pos(x)];
+        if (c & 1) dst.y = v; else dst.x = v;
+    }
+    __syncthreads();
+    step1<T, M, false>(buf, nl, twM, true);
+    __syncthreads();
+    const int64_t kstride = (int64_t)d.nz * d.ny;
+    V2<T>* dst0 = X1 + (int64_t)z * d.ny + y0;
+    for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
+        const int line = w % nl, k1 = w / nl;
+        const int r = line % yt, p = line / yt;
+        V2<T> v[L::R2];
+        step2<T, M, false>(buf, line, k1, v);
+        V2<T>* o = dst0 + (int64_t)p * M * kstride + r;
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) o[(int64_t)(k1 + L::R1 * k2) * kstride] = v[brev_c(k2, log2_c(L::R2))];
+    }
+}
+
+template <typename T, int M>
+static __global__ void __launch_bounds__(256) fftx_fwd_t_kernel(const T* __restrict__ rho, V2<T>* __restrict__ X1,
+                                                                  FFTDims d, const V2<T>* __restrict__ tw,
+                                                                  const Ord<T>* __restrict__ chmax, int yt) {
+    fftx_fwd_t_kernel_body<T, M>(rho, X1, d, tw, chmax, yt, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// Pieces of the two-step transform used by the slab kernel (M = R1 R2, see
+// the file comment). With k = k1 + R1 k2 and n = R2 n1 + n2 the inverse
+// splits the same way,
+//   y[R2 n1 + n2] = sum_k1 W_R1^(-n1 k1) W_M^(-n2 k1) [ sum_k2 Y[k1 + R1 k2] W_R2^(-n2 k2) ],
+// so the thread that ends the forward transform for one k1 (holding every
+// k2) can begin the inverse in registers. Spectra stay in the "k1-major"
+// layout of the forward step 2: position k1 (R2 + 1) + m of a line holds the
+// bin k1 + R1 brev(m).
+
+// forward step 2 in place: line data at k1 (R2+1) + n2 -> bins k1 + R1 brev(m) at k1 (R2+1) + m
+template <typename T, int M>
+__device__ __forceinline__ void step2_fwd_inplace(V2<T>* line, int k1) {
+    using L = Lay<M>;
+    V2<T>* b = line + k1 * (L::R2 + 1);
+    V2<T> v[L::R2];
+#pragma unroll
+    for (int n2 = 0; n2 < L::R2; ++n2) v[n2] = b[n2];
+    dft_reg<T, L::R2, false>(v);
+#pragma unroll
+    for (int m = 0; m < L::R2; ++m) b[m] = v[m];
+}
+
+// first half of the inverse for one k1: spectrum bins u[k2] = Y[k1 + R1 k2]
+// -> Z[n2] W_M^(-n2 k1) stored at k1 (R2+1) + n2
+template <typename T, int M>
+__device__ __forceinline__ void inv_half1_store(V2<T>* line, int k1, V2<T> (&u)[Lay<M>::R2], const V2<T>* twM) {
+    using L = Lay<M>;
+    dft_reg<T, L::R2, true>(u);
+    V2<T>* b = line + k1 * (L::R2 + 1);
+#pragma unroll
+    for (int n2 = 0; n2 < L::R2; ++n2) {
+        V2<T> z = u[brev_c(n2, log2_c(L::R2))];
+        if (n2 != 0 && k1 != 0) {
+            V2<T> t = twM[(n2 * k1) & (M - 1)];
+            t.y = -t.y;
+            z = cmul<T>(z, t);
+        }
+        b[n2] = z;
+    }
+}
+
+// second half of the inverse for one n2: R1-point inverse DFT over k1 of
+// line[k1 (R2+1) + n2]; out[n1] = y[R2 n1 + n2]
+template <typename T, int M>
+__device__ __forceinline__ void inv_half2(const V2<T>* line, int n2, V2<T> (&out)[Lay<M>::R1]) {
+    using L = Lay<M>;
+    V2<T> v[L::R1];
+#pragma unroll
+    for (int k1 = 0; k1 < L::R1; ++k1) v[k1] = line[k1 * (L::R2 + 1) + n2];
+    dft_reg<T, L::R1, true>(v);
+#pragma unroll
+    for (int n1 = 0; n1 < L::R1; ++n1) out[n1] = v[brev_c(n1, log2_c(L::R1))];
+}
+
+template <int M>
+__device__ __forceinline__ int kmajor_pos(int k) {
+    using L = Lay<M>;
+    return (k % L::R1) * (L::R2 + 1) + brev_c(k / L::R1, log2_c(L::R2));
+}
+
+template <typename T>
+__host__ __device__ constexpr int slab_kc() { return sizeof(T) == 4 ? 32 : 16; }   // z columns per chunk
+
+// y and z transforms of the slab of one (kx, pair), in place on X1: forward
+// y (inputs y < ny); for slab_kc columns ky at a time: forward z (inputs
+// z < nz), times Ghat, inverse z (outputs z < nz); inverse y (outputs
+// y < ny). The slab lives in A as nz lines of 2ny; a chunk of columns is
+// copied to B as z lines and back.
+template <typename T, int MY, int MZ>
+__device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const T* __restrict__ Ghat, FFTDims d,
+                                                    const V2<T>* __restrict__ twy, const V2<T>* __restrict__ twz,
+                                                    const int bx_, const int by_) {
+    using LY = Lay<MY>;
+    using LZ = Lay<MZ>;
+    constexpr int KC = slab_kc<T>();
+    extern __shared__ unsigned char smraw[];
+    V2<T>* tY = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* tZ = tY + MY;
+    V2<T>* A = tZ + MZ;                        // [nz][LY::LS]
+    V2<T>* B = A + d.nz * LY::LS;              // [KC][LZ::LS]
+    const int kx = bx_, p = by_;
+    const int nz = d.nz, ny = d.ny;
+    for (int j = threadIdx.x; j < MY; j += blockDim.x) tY[j] = twy[j];
+    for (int j = threadIdx.x; j < MZ; j += blockDim.x) tZ[j] = twz[j];
+    V2<T>* slab = X1 + ((int64_t)p * d.Mx + kx) * nz * ny;
+    for (int t = threadIdx.x; t < nz * ny; t += blockDim.x) {
+        const int z = t / ny, y = t % ny;
+        A[z * LY::LS + LY::pos(y)] = slab[t];
+    }
+    __syncthreads();
+    // forward y: step 1 (inputs y >= ny are zero), step 2 in place -> k1-major spectra
+    step1<T, MY, false>(A, nz, tY, true);
+    __syncthreads();
+    for (int w = threadIdx.x; w < nz * LY::R1; w += blockDim.x)
+        step2_fwd_inplace<T, MY>(A + (w % nz) * LY::LS, w / nz);
+    __syncthreads();
+    const int kxr = kx <= d.nx ? kx : d.Mx - kx;
+    const T* Gp = Ghat + (int64_t)kxr * (d.nz + 1) * (d.ny + 1);     // plane [kz'][ky']
+    for (int c0 = 0; c0 < MY; c0 += KC) {
+        for (int t = threadIdx.x; t < KC * nz; t += blockDim.x) {
+            const int j = t % KC, z = t / KC;
+            B[j * LZ::LS + LZ::pos(z)] = A[z * LY::LS + kmajor_pos<MY>(c0 + j)];
+        }
+        __syncthreads();
+        step1<T, MZ, false>(B, KC, tZ, true);
+        __syncthreads();
+        // per (column, k1): forward R2-point DFT, times Ghat, first half of the inverse
+        for (int w = threadIdx.x; w < KC * LZ::R1; w += blockDim.x) {
+            const int j = w % KC, k1 = w / KC;
+            const int ky = c0 + j;
+            const int kyr = ky <= ny ? ky : MY - ky;
+            V2<T>* line = B + j * LZ::LS;
+            V2<T> v[LZ::R2];
+#pragma unroll
+            for (int n2 = 0; n2 < LZ::R2; ++n2) v[n2] = line[k1 * (LZ::R2 + 1) + n2];
+            dft_reg<T, LZ::R2, false>(v);
+            V2<T> u[LZ::R2];
+#pragma unroll
+            for (int k2 = 0; k2 < LZ::R2; ++k2) {
+                const int kz = k1 + LZ::R1 * k2;
+                const int kzr = kz <= nz ? kz : MZ - kz;
+                const T gh = Gp[kzr * (ny + 1) + kyr];
+                u[k2] = v[brev_c(k2, log2_c(LZ::R2))];
+                u[k2].x *= gh;
+                u[k2].y *= gh;
+            }
+            inv_half1_store<T, MZ>(line, k1, u, tZ);
+        }
+        __syncthreads();
+        // per (column, n2): second half of the inverse, outputs z < nz back into A
+        for (int w = threadIdx.x; w < KC * LZ::R2; w += blockDim.x) {
+            const int j = w % KC, n2 = w / KC;
+            V2<T> o[LZ::R1];
+            inv_half2<T, MZ>(B + j * LZ::LS, n2, o);
+            const int pa = kmajor_pos<MY>(c0 + j);
+#pragma unroll
+            for (int n1 = 0; n1 < LZ::R1 / 2; ++n1) A[(LZ::R2 * n1 + n2) * LY::LS + pa] = o[n1];
+        }
+        __syncthreads();
+    }
+    // inverse y from the k1-major spectra: first half in place per (z, k1) ...
+    for (int w = threadIdx.x; w < nz * LY::R1; w += blockDim.x) {
+        const int z = w % nz, k1 = w / nz;
+        V2<T>* line = A + z * LY::LS;
+        V2<T> u[LY::R2];
+#pragma unroll
+        for (int k2 = 0; k2 < LY::R2; ++k2) u[k2] = line[k1 * (LY::R2 + 1) + brev_c(k2, log2_c(LY::R2))];
+        inv_half1_store<T, MY>(line, k1, u, tY);
+    }
+    __syncthreads();
+    // ... then per (z, n2), outputs y < ny to the slab (n2 fastest: consecutive y)
+    for (int w = threadIdx.x; w < nz * LY::R2; w += blockDim.x) {
+        const int n2 = w % LY::R2, z = w / LY::R2;
+        V2<T> o[LY::R1];
+        inv_half2<T, MY>(A + z * LY::LS, n2, o);
+#pragma unroll
+        for (int n1 = 0; n1 < LY::R1 / 2; ++n1) slab[z * ny + LY::R2 * n1 + n2] = o[n1];
+    }
+}
+
+template <typename T, int MY, int MZ>
+static __global__ void __launch_bounds__(256) fftyz_kernel(V2<T>* __restrict__ X1, const T* __restrict__ Ghat, FFTDims d,
+                                                             const V2<T>* __restrict__ twy, const V2<T>* __restrict__ twz) {
+    fftyz_kernel_body<T, MY, MZ>(X1, Ghat, d, twy, twz, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// x pass, inverse: X1 [p][kx][z][y] for rows (z, y0 .. y0 + yt - 1) -> phi rows
+// (x < nx), channel scaling and 1/(Mx My Mz) undone, staged so each row is
+// stored contiguously (stage rows padded by one word against bank conflicts)
+template <typename T, int M>
+__device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__ X1, T* __restrict__ phi, FFTDims d,
+                                                         const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax,
+                                                         int yt, const int bx_, const int by_) {
+    using L = Lay<M>;
+    extern __shared__ unsigned char smraw[];
+    V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
+    T* sc = reinterpret_cast<T*>(twM + M);
+    V2<T>* buf = reinterpret_cast<V2<T>*>(sc + 16);
+    const int nl = yt * d.npair;
+    T* stage = reinterpret_cast<T*>(buf + nl * L::LS);   // [yt][nx * CP + 1]
+    const int SR = d.nx * d.CP + 1;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
+    if (threadIdx.x < d.CP) sc[threadIdx.x] = (T)d.norm * chan_scale<T>(chmax, threadIdx.x, true);
+    const int y0 = bx_ * yt, z = by_;
+    const int64_t kstride = (int64_t)d.nz * d.ny;
+    const V2<T>* src0 = X1 + (int64_t)z * d.ny + y0;
+    for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
+        const int r = t % yt, rest = t / yt;
+        const int kx = rest % M, p = rest / M;
+        buf[(p * yt + r) * L::LS + L::pos(kx)] = src0[((int64_t)p * M + kx) * kstride + r];
+    }
+    __syncthreads();
+    step1<T, M, true>(buf, nl, twM, false);
+    __syncthreads();
+    for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
+        const int line = w % nl, k1 = w / nl;
+        const int r = line % yt, p = line / yt;
+        V2<T> v[L::R2];
+        step2<T, M, true>(buf, line, k1, v);
+        const T sa = sc[2 * p], sb = sc[2 * p + 1];
+#pragma unroll
+        for (int k2 = 0; k2 < L::R2; ++k2) {
+            const int x = k1 + L::R1 * k2;
+            if (x < d.nx) {
+                const V2<T> q = v[brev_c(k2, log2_c(L::R2))];
+                stage[r * SR + x * d.CP + 2 * p] = q.x * sa;
+                stage[r * SR + x * d.CP + 2 * p + 1] = q.y * sb;
+            }
+        }
+    }
+    __syncthreads();
+    T* dst = phi + ((int64_t)z * d.ny + y0) * d.nx * d.CP;
+    const int rowlen = d.nx * d.CP;
+    for (int t = threadIdx.x; t < yt * rowlen; t += blockDim.x) {
+        const int r = t / rowlen, rem = t % rowlen;
+        const int c = rem % d.CP;
+        dst[t] = c < d.C ? stage[r * SR + rem] : (T)0;
+    }
+}
+
+template <typename T, int M>
+static __global__ void __launch_bounds__(256) fftx_inv_t_kernel(const V2<T>* __restrict__ X1, T* __restrict__ phi,
+                                                                  FFTDims d, const V2<T>* __restrict__ tw,
+                                                                  const Ord<T>* __restrict__ chmax, int yt) {
+    fftx_inv_t_kernel_body<T, M>(X1, phi, d, tw, chmax, yt, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 }  // namespace adpic

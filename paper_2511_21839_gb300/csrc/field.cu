@@ -18,20 +18,28 @@ void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream
 
 template <typename T>
 void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, double* corner, T* G, T* Gtmp, T* Ghat,
-                  const T* dct_x, const T* dct_y, const T* dct_z, cudaStream_t s) {
+                  const T* dct_x, const T* dct_y, const T* dct_z, int order, cudaStream_t s) {
     (void)exact;
     const int64_t nc = (int64_t)(nx + 2) * (ny + 2) * (nz + 2);
     green_corner_kernel<<<(unsigned)((nc + 63) / 64), 64, 0, s>>>(geom, nx, ny, nz, corner);
     const int64_t ng = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-    green_cell_kernel<T><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(geom, nx, ny, nz, corner, G);
-    // G [z][y][x] -> pass x -> [x'][z][y] -> pass y -> [y'][x'][z] -> pass z -> [z'][y'][x']
+    green_cell_kernel<T><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(geom, nx, ny, nz, corner, G, order);
+    // each pass transforms the contiguous axis and makes it the outermost one
     auto pass = [&](const T* in, T* out, const T* D, int L, int64_t BA) {
         const size_t sm = sizeof(T) * ((size_t)L * L + (size_t)kDctLines * L);
         dct_kernel<T><<<(unsigned)((BA + kDctLines - 1) / kDctLines), 256, sm, s>>>(in, out, D, L, BA);
     };
-    pass(G, Gtmp, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));
-    pass(Gtmp, G, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1));
-    pass(G, Ghat, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1));
+    if (order == 0) {
+        // G [z][y][x] -> pass x -> [x'][z][y] -> pass y -> [y'][x'][z] -> pass z -> [z'][y'][x']
+        pass(G, Gtmp, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));
+        pass(Gtmp, G, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1));
+        pass(G, Ghat, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1));
+    } else {
+        // G [x][z][y] -> pass y -> [y'][x][z] -> pass z -> [z'][y'][x] -> pass x -> [x'][z'][y']
+        pass(G, Gtmp, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1));
+        pass(Gtmp, G, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1));
+        pass(G, Ghat, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));
+    }
 }
 
 template <typename T>
@@ -49,7 +57,7 @@ void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int
     template void launch_geom<T>(Ord<T>*, int, int, int, double, GeomDev*, Ord<T>*, int, cudaStream_t);          \
     template void launch_chmax<T>(const T*, int64_t, int, Ord<T>*, cudaStream_t);                                 \
     template void launch_green<T>(const GeomDev*, int, int, int, bool, double*, T*, T*, T*, const T*, const T*,    \
-                                  const T*, cudaStream_t);                                                        \
+                                  const T*, int, cudaStream_t);                                                   \
     template void launch_field<T>(const T*, const GeomDev*, int, int, int, int, T*, cudaStream_t);             \
     template void setup_green<T>();
 ADPIC_FIELD_INST(float)

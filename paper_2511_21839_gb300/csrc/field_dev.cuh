@@ -70,20 +70,38 @@ static __global__ void geom_kernel(Ord<T>* mm, int nx, int ny, int nz, double ga
     geom_kernel_body<T>(mm, nx, ny, nz, gamma0, g, chmax, CP, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
 }
 
-// per-channel max |rho| (ordered bits of a non-negative value are its bits)
+// per-channel max |rho| (ordered bits of a non-negative value are its bits).
+// Each thread keeps four independent running maxima over a grid-stride loop
+// (element t belongs to channel t % CP; the stride is a multiple of CP).
 template <typename T>
 __device__ __forceinline__ void chmax_kernel_body(const T* __restrict__ rho, int64_t nodes, int CP, Ord<T>* chmax,
     const int bx_, const int by_, const int bz_, const int nbx_) {
     const int64_t t0 = bx_ * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)nbx_ * blockDim.x;   // multiple of CP
-    T m = (T)0;
-    for (int64_t t = t0; t < nodes * CP; t += stride) m = fmax(m, fabs(rho[t]));
+    const int64_t total = nodes * CP;
+    T m0 = (T)0, m1 = (T)0, m2 = (T)0, m3 = (T)0;
+    int64_t t = t0;
+    for (; t + 3 * stride < total; t += 4 * stride) {
+        m0 = fmax(m0, fabs(rho[t]));
+        m1 = fmax(m1, fabs(rho[t + stride]));
+        m2 = fmax(m2, fabs(rho[t + 2 * stride]));
+        m3 = fmax(m3, fabs(rho[t + 3 * stride]));
+    }
+    for (; t < total; t += stride) m0 = fmax(m0, fabs(rho[t]));
+    T m = fmax(fmax(m0, m1), fmax(m2, m3));
     for (int o = CP; o < 32; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) < CP) {
+    // across the block's warps, then one atomic per channel
+    __shared__ T wm[32][16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane < CP) wm[w][lane] = m;
+    __syncthreads();
+    if ((int)threadIdx.x < CP) {
+        T b = wm[0][threadIdx.x];
+        for (int j = 1; j < nw; ++j) b = fmax(b, wm[j][threadIdx.x]);
         if constexpr (sizeof(T) == 4)
-            atomicMax(&chmax[threadIdx.x & 31], __float_as_uint(m));
+            atomicMax(&chmax[threadIdx.x], __float_as_uint(b));
         else
-            atomicMax(&chmax[threadIdx.x & 31], (unsigned long long)__double_as_longlong(m));
+            atomicMax(&chmax[threadIdx.x], (unsigned long long)__double_as_longlong(b));
     }
 }
 
@@ -128,14 +146,20 @@ static __global__ void green_corner_kernel(const GeomDev* __restrict__ g, int nx
 // f_dd = (3 d^2 - r^2)/r^5, f_dddd = 3 (35 d^4 - 30 d^2 r^2 + 3 r^4)/r^9,
 // f_ddee = 3 (35 d^2 e^2 - 5 r^2 (d^2 + e^2) + r^4)/r^9; its O(h^6) remainder
 // is below FP32 rounding beyond 10 h_max.
+// G is stored [k][j][i] (order 0, i fastest) or [i][k][j] (order 1, j fastest).
 template <typename T>
 __device__ __forceinline__ void green_cell_kernel_body(const GeomDev* __restrict__ g, int nx, int ny, int nz,
                                   const double* __restrict__ F, T* __restrict__ G,
-    const int bx_, const int by_, const int bz_, const int nbx_) {
+    const int bx_, const int by_, const int bz_, const int nbx_, int order = 0) {
     const int t = bx_ * blockDim.x + threadIdx.x;     // < 129^3
     const int gx = nx + 1, gy = ny + 1, gz = nz + 1;
     if (t >= gx * gy * gz) return;
-    const int i = t % gx, j = (t / gx) % gy, k = t / (gx * gy);
+    int i, j, k;
+    if (order == 0) {
+        i = t % gx; j = (t / gx) % gy; k = t / (gx * gy);
+    } else {
+        j = t % gy; k = (t / gy) % gz; i = t / (gy * gz);
+    }
     const double hx = g->hr[0], hy = g->hr[1], hz = g->hr[2];
     const double k4 = 1.0 / (4.0 * 3.14159265358979323846 * 8.8541878128e-12);
     if (i <= g->R[0] && j <= g->R[1] && k <= g->R[2]) {
@@ -167,8 +191,9 @@ __device__ __forceinline__ void green_cell_kernel_body(const GeomDev* __restrict
 
 template <typename T>
 static __global__ void green_cell_kernel(const GeomDev* __restrict__ g, int nx, int ny, int nz,
-                                  const double* __restrict__ F, T* __restrict__ G) {
-    green_cell_kernel_body<T>(g, nx, ny, nz, F, G, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+                                  const double* __restrict__ F, T* __restrict__ G, int order) {
+    green_cell_kernel_body<T>(g, nx, ny, nz, F, G, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x,
+                              order);
 }
 
 // One DCT-I pass over the contiguous axis of in [BA][L] (L = n+1) into
@@ -243,27 +268,28 @@ static __global__ void dct_kernel(const T* __restrict__ in, T* __restrict__ out,
 // ------------------------------------------------------------------ field
 
 // E = -grad(phi) by central differences on interior nodes, rest-frame
-// spacings (hx, hy, gamma0 hz); E layout [node][3][CP].
+// spacings (hx, hy, gamma0 hz); E layout [node][3][CP]. One thread per
+// (node, channel); nx, ny, CP are powers of two, so the node coordinates come
+// from shifts and masks (32-bit: nodes * CP < 2^31).
 template <typename T>
 __device__ __forceinline__ void field_kernel_body(const T* __restrict__ phi, const GeomDev* __restrict__ g, int nx, int ny, int nz, int CP,
                              T* __restrict__ E,
     const int bx_, const int by_, const int bz_, const int nbx_) {
-    const int64_t t = bx_ * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nodes = (int64_t)nx * ny * nz;
-    if (t >= nodes * CP) return;
-    const int c = (int)(t % CP);
-    const int64_t node = t / CP;
-    const int i = (int)(node % nx), j = (int)((node / nx) % ny), k = (int)(node / ((int64_t)nx * ny));
+    const unsigned t = (unsigned)bx_ * blockDim.x + threadIdx.x;
+    const unsigned total = (unsigned)nx * ny * nz * CP;
+    if (t >= total) return;
+    const int lcp = __ffs(CP) - 1, lx = __ffs(nx) - 1, ly = __ffs(ny) - 1;
+    const unsigned c = t & (CP - 1), node = t >> lcp;
+    const int i = node & (nx - 1), j = (node >> lx) & (ny - 1), k = node >> (lx + ly);
     if (i < 1 || i > nx - 2 || j < 1 || j > ny - 2 || k < 1 || k > nz - 2) return;
     const T ax = sizeof(T) == 4 ? (T)g->fdf[0] : (T)g->fdd[0];
     const T ay = sizeof(T) == 4 ? (T)g->fdf[1] : (T)g->fdd[1];
     const T az = sizeof(T) == 4 ? (T)g->fdf[2] : (T)g->fdd[2];
-    const int64_t sx = CP, sy = (int64_t)nx * CP, sz = (int64_t)nx * ny * CP;
-    const int64_t a = node * CP + c;
-    T* e = E + node * 3 * CP + c;
-    e[0] = -(phi[a + sx] - phi[a - sx]) * ax;
-    e[CP] = -(phi[a + sy] - phi[a - sy]) * ay;
-    e[2 * CP] = -(phi[a + sz] - phi[a - sz]) * az;
+    const unsigned sx = CP, sy = (unsigned)nx * CP, sz = (unsigned)nx * ny * CP;
+    T* e = E + (size_t)node * 3 * CP + c;
+    e[0] = -(phi[t + sx] - phi[t - sx]) * ax;
+    e[CP] = -(phi[t + sy] - phi[t - sy]) * ay;
+    e[2 * CP] = -(phi[t + sz] - phi[t - sz]) * az;
 }
 
 template <typename T>

@@ -25,6 +25,11 @@ struct ad_pic {
     int64_t kick = 0;
     bool first_record = true;
     cudaStream_t own_stream = nullptr, stream = nullptr;
+    // the Green's function depends on the grid geometry only: it runs on a side
+    // stream concurrently with deposit, scan and channel maxima (fork after the
+    // geometry kernel, join before the convolution; captured graphs keep both branches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // device memory
     void* state = nullptr;
     void* state2 = nullptr;      // the other buffer of the cell-sorting push

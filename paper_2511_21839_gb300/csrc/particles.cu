@@ -23,19 +23,55 @@ void launch_convert_out(const T* src, double* dst, int64_t N, int C, cudaStream_
     if (tot > 0) convert_out_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, 6 * N, C);
 }
 
+// resident CTAs of the persistent push, per instantiation (set by setup_push)
+template <typename T, int C, int CP, bool TRACK>
+static int& push_grid() {
+    static int g = 0;
+    return g;
+}
+
+template <typename T, int C, int CP, bool TRACK>
+static void push_attrs() {
+    constexpr int TP = push_tile<T, CP>();
+    const int smem = (int)(2 * 6 * TP * CP * sizeof(T));
+    cudaFuncSetAttribute(push_tma_kernel<T, C, CP, TRACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, push_tma_kernel<T, C, CP, TRACK>, TP, smem);
+    push_grid<T, C, CP, TRACK>() = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
+template <typename T, int C, int CP>
+void setup_push() {
+    push_attrs<T, C, CP, true>();
+    push_attrs<T, C, CP, false>();
+}
+
+template <typename T, int C, int CP, bool TRACK>
+static void launch_push_t(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx,
+                          int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, Ord<T>* mm, int* err,
+                          const SortBuf& sb, cudaStream_t s) {
+    constexpr int TP = push_tile<T, CP>();
+    const int64_t tiles = (N + TP - 1) / TP;
+    const int64_t g = push_grid<T, C, CP, TRACK>();
+    const unsigned grid = (unsigned)(tiles < g ? tiles : g);
+    const size_t smem = 2 * 6 * (size_t)TP * CP * sizeof(T);
+    push_tma_kernel<T, C, CP, TRACK><<<grid, TP, smem, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm,
+                                                             err, sb);
+}
+
 template <typename T, int C, int CP>
 void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
                  const SortBuf& sb, cudaStream_t s) {
     if (N <= 0) return;
-    unsigned blocks = (unsigned)((N + 255) / 256);
     if (track)
-        push_kernel<T, C, CP, true><<<blocks, 256, 0, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err,
-                                                          sb);
+        launch_push_t<T, C, CP, true>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, s);
     else
-        push_kernel<T, C, CP, false><<<blocks, 256, 0, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm,
-                                                           err, sb);
-}   // cells per block of the scan
+        launch_push_t<T, C, CP, false>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, s);
+}
+
 int scan_blocks(int ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
 
 void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s) {
@@ -73,13 +109,19 @@ template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho, int* err,
                     const SortBuf& sb, cudaStream_t s) {
     if (N <= 0) return;
-    // register-resident runs for the FP32 8-channel dual; the other variants take one particle per
-    // thread (their eight node records would not fit in registers)
-    constexpr int RUN = (CP == 8 && sizeof(T) == 4) ? 8 : 1;
-    const int64_t threads = (N + RUN - 1) / RUN;
-    constexpr int BS = RUN > 1 ? 128 : 256;
-    deposit_kernel<T, C, CP, RUN><<<(unsigned)((threads + BS - 1) / BS), BS, 0, s>>>(state, N, geom, nx, ny, nz, qm,
-                                                                                    rho, err, sb);
+    // warp-sorted, on-chip summed deposition (see deposit_tile_body)
+    constexpr int W = dep_tile_warps<CP, T>();
+    const size_t sm = sizeof(T) * (size_t)W * 8 * CP * 33;
+    const int64_t warps = (N + 31) / 32;
+    deposit_tile_kernel<T, C, CP, W><<<(unsigned)((warps + W - 1) / W), W * 32, sm, s>>>(state, N, geom, nx, ny, nz,
+                                                                                       qm, rho, err, sb);
+}
+
+template <typename T, int C, int CP>
+void setup_deposit() {
+    constexpr int W = dep_tile_warps<CP, T>();
+    cudaFuncSetAttribute(deposit_tile_kernel<T, C, CP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * (size_t)W * 8 * CP * 33));
 }
 
 // ------------------------------------------------------------------ instantiations
@@ -91,7 +133,9 @@ void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int 
     template void launch_boundary<T, C, CP>(T*, int64_t, const MapCoef<T, CP>&, bool, bool, double*, int,       \
                                             Ord<T>*, cudaStream_t);                                              \
     template void launch_deposit<T, C, CP>(const T*, int64_t, const GeomDev*, int, int, int, T, T*, int*,        \
-                                           const SortBuf&, cudaStream_t);
+                                           const SortBuf&, cudaStream_t);                                        \
+    template void setup_deposit<T, C, CP>();                                                                     \
+    template void setup_push<T, C, CP>();
 ADPIC_INST(float, 8, 8)
 ADPIC_INST(float, 14, 16)
 ADPIC_INST(double, 8, 8)

@@ -209,92 +209,101 @@ static __global__ void convert_out_kernel(const T* __restrict__ src, double* __r
 // only that component's CP accumulators and its three interpolant gradients
 // are live: E_p,k = sum W E_k + sum_d (x_d,k / h_d) sum dW/du_d E_0 (Eq. 2 on
 // the weight product), then p_k += a0 E_p,k + a_k E_p,0 in one rounding.
+// Gather + kick + dual map of one particle held in registers (u[6][CP]).
+template <typename T, int C, int CP>
+__device__ __forceinline__ void push_core(T (&u)[6][CP], const T* __restrict__ E, const GeomDev* __restrict__ geom,
+                                          int nx, int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K,
+                                          int* __restrict__ err) {
+    if (E != nullptr) {
+        const GeomDev& g = *geom;
+        const int n[3] = {nx, ny, nz};
+        T f[3], ih[3];
+        int idx[3];
+        int bad = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ih[d] = geom_ih<T>(g, d);
+            idx[d] = cell_of<T>(u[2 * d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
+        }
+        if (bad) atomicOr(err, bad);
+        const T* e0 = E + (((int64_t)idx[2] * ny + idx[1]) * nx + idx[0]) * (3 * CP);
+        const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            T Ev[CP];
+            T gx = (T)0, gy = (T)0, gz = (T)0;
+#pragma unroll
+            for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T wz = c ? f[2] : (T)1 - f[2];
+                const T sz_ = c ? (T)1 : (T)-1;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const T wy = b ? f[1] : (T)1 - f[1];
+                    const T sy_ = b ? (T)1 : (T)-1;
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        const T wx = a ? f[0] : (T)1 - f[0];
+                        const T sx_ = a ? (T)1 : (T)-1;
+                        const T W = wx * wy * wz;
+                        T en[CP];
+                        ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en);
+#pragma unroll
+                        for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[k], Ev[k]);
+                        gx = fma(sx_ * wy * wz, en[0], gx);
+                        gy = fma(wx * sy_ * wz, en[0], gy);
+                        gz = fma(wx * wy * sz_, en[0], gz);
+                    }
+                }
+            }
+            gx *= ih[0];
+            gy *= ih[1];
+            gz *= ih[2];
+            T* p = u[2 * q + 1];
+            const T a0 = K.a[q][0], E0 = Ev[0];
+#pragma unroll
+            for (int k = 1; k < CP; ++k) {
+                const T Ek = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[k])));
+                p[k] = fma(a0, Ek, fma(K.a[q][k], E0, p[k]));
+            }
+            p[0] = fma(a0, E0, p[0]);
+        }
+    }
+    // dual map
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+        T* x = u[2 * pl];
+        T* p = u[2 * pl + 1];
+        const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
+        const T x0 = x[0], p0 = p[0];
+#pragma unroll
+        for (int k = 1; k < CP; ++k) {
+            const T xk = x[k], pk = p[k];
+            x[k] = fma(a0, xk, fma(b0, pk, fma(A.m[pl][0][k], x0, A.m[pl][1][k] * p0)));
+            p[k] = fma(c0, xk, fma(d0, pk, fma(A.m[pl][2][k], x0, A.m[pl][3][k] * p0)));
+        }
+        x[0] = fma(a0, x0, b0 * p0);
+        p[0] = fma(c0, x0, d0 * p0);
+    }
+}
+
 template <typename T, int C, int CP, bool TRACK>
 __device__ __forceinline__ void push_kernel_body(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
                 const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP>& A,
                 const KickCoef<T, CP>& K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb,
     const int bx_, const int by_, const int bz_, const int nbx_) {
-    const int64_t i = bx_ * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = bx_ * (int64_t)blockDim.x + threadIdx.x;
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
-    if (i < N) {
+    if (t < N) {
+        // particle i to slot dst (see SortBuf)
+        const int64_t i = t;
+        const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
         T u[6][CP];
 #pragma unroll
         for (int c = 0; c < 6; ++c) ldv<T, CP>(state + (c * N + i) * CP, u[c]);
-        if (E != nullptr) {
-            const GeomDev& g = *geom;
-            const int n[3] = {nx, ny, nz};
-            T f[3], ih[3];
-            int idx[3];
-            int bad = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                ih[d] = geom_ih<T>(g, d);
-                idx[d] = cell_of<T>(u[2 * d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
-            }
-            if (bad) atomicOr(err, bad);
-            const T* e0 = E + (((int64_t)idx[2] * ny + idx[1]) * nx + idx[0]) * (3 * CP);
-            const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                T Ev[CP];
-                T gx = (T)0, gy = (T)0, gz = (T)0;
-#pragma unroll
-                for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const T wz = c ? f[2] : (T)1 - f[2];
-                    const T sz_ = c ? (T)1 : (T)-1;
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const T wy = b ? f[1] : (T)1 - f[1];
-                        const T sy_ = b ? (T)1 : (T)-1;
-#pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            const T wx = a ? f[0] : (T)1 - f[0];
-                            const T sx_ = a ? (T)1 : (T)-1;
-                            const T W = wx * wy * wz;
-                            T en[CP];
-                            ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en);
-#pragma unroll
-                            for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[k], Ev[k]);
-                            gx = fma(sx_ * wy * wz, en[0], gx);
-                            gy = fma(wx * sy_ * wz, en[0], gy);
-                            gz = fma(wx * wy * sz_, en[0], gz);
-                        }
-                    }
-                }
-                gx *= ih[0];
-                gy *= ih[1];
-                gz *= ih[2];
-                T* p = u[2 * q + 1];
-                const T a0 = K.a[q][0], E0 = Ev[0];
-#pragma unroll
-                for (int k = 1; k < CP; ++k) {
-                    const T Ek = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[k])));
-                    p[k] = fma(a0, Ek, fma(K.a[q][k], E0, p[k]));
-                }
-                p[0] = fma(a0, E0, p[0]);
-            }
-        }
-        // dual map
-#pragma unroll
-        for (int pl = 0; pl < 3; ++pl) {
-            T* x = u[2 * pl];
-            T* p = u[2 * pl + 1];
-            const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
-            const T x0 = x[0], p0 = p[0];
-#pragma unroll
-            for (int k = 1; k < CP; ++k) {
-                const T xk = x[k], pk = p[k];
-                x[k] = fma(a0, xk, fma(b0, pk, fma(A.m[pl][0][k], x0, A.m[pl][1][k] * p0)));
-                p[k] = fma(c0, xk, fma(d0, pk, fma(A.m[pl][2][k], x0, A.m[pl][3][k] * p0)));
-            }
-            x[0] = fma(a0, x0, b0 * p0);
-            p[0] = fma(c0, x0, d0 * p0);
-        }
-        // cell-sorted slot of this particle (cell and rank from this kick's deposit)
-        const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
+        push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
         if (sb.ids_out) sb.ids_out[dst] = sb.ids_in[i];
 #pragma unroll
         for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
@@ -312,6 +321,145 @@ static __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
                 const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
                 const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
     push_kernel_body<T, C, CP, TRACK>(state, out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// ------------------------------------------------------------------ push over bulk-copied tiles
+
+// Shared-memory barrier and bulk-copy primitives (PTX). A tile copy is six
+// contiguous runs (one per coordinate) of TP particles' dual records.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded: gives up after 2^20 polls (well under a second)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// particles per tile: 8 KB per coordinate run
+template <typename T, int CP>
+__host__ __device__ constexpr int push_tile() {
+    return (int)(8192 / (CP * sizeof(T)));
+}
+
+// Persistent push: each CTA walks tiles blockIdx.x, +gridDim.x, ... and keeps
+// two tiles of the dual state in flight in a two-stage shared-memory ring
+// (one mbarrier per stage), so the DRAM reads run ahead of the gather and
+// the map without holding registers. One thread per particle of a tile; the
+// results go to their cell-sorted slots as in push_kernel. Every wait is
+// bounded; the CTA agrees on the outcome with a barrier vote, and on a timeout
+// it records kErrTimeout, lets its copies land (bounded) and stops.
+template <typename T, int C, int CP, bool TRACK>
+__device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __restrict__ out, int64_t N,
+                                              const T* __restrict__ E, const GeomDev* __restrict__ geom, int nx,
+                                              int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K,
+                                              Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
+    constexpr int TP = push_tile<T, CP>();
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* ring = reinterpret_cast<T*>(smraw);      // [2][6][TP][CP]
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x;
+    const int64_t ntiles = (N + TP - 1) / TP;
+    const int64_t step = gridDim.x;
+    auto issue = [&](int64_t tl, int s) {
+        const int64_t p0 = tl * TP;
+        const int n = (int)min((int64_t)TP, N - p0);
+        const unsigned bytes = (unsigned)n * CP * (unsigned)sizeof(T);
+        mbar_expect_tx(&bar[s], 6u * bytes);
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            bulk_g2s(ring + ((size_t)(s * 6 + c) * TP) * CP, state + ((size_t)c * N + p0) * CP, bytes, &bar[s]);
+    };
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int64_t tile = blockIdx.x;
+    if (tid == 0) {
+        if (tile < ntiles) issue(tile, 0);
+        if (tile + step < ntiles) issue(tile + step, 1);
+    }
+    T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
+    T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
+    int it = 0;
+    bool ok = true;
+    for (; tile < ntiles; tile += step, ++it) {
+        const int s = it & 1;
+        const bool got = mbar_wait(&bar[s], (unsigned)((it >> 1) & 1));
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            break;
+        }
+        const int64_t i = tile * TP + tid;
+        const bool valid = i < N;
+        T u[6][CP];
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) ldv<T, CP>(ring + ((size_t)(s * 6 + c) * TP + tid) * CP, u[c]);
+        }
+        __syncthreads();                         // stage s is free again
+        if (tid == 0 && tile + 2 * step < ntiles) {
+            fence_proxy_async_smem();
+            issue(tile + 2 * step, s);
+        }
+        if (valid) {
+            const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
+            push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
+            if (sb.ids_out) sb.ids_out[dst] = sb.ids_in[i];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
+            if (TRACK) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    mn[d] = fmin(mn[d], u[2 * d][0]);
+                    mx[d] = fmax(mx[d], u[2 * d][0]);
+                }
+            }
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicOr(err, kErrTimeout);
+        const int s = it & 1;
+        mbar_wait(&bar[s], (unsigned)((it >> 1) & 1));
+        if (tile + step < ntiles) mbar_wait(&bar[1 - s], (unsigned)(((it + 1) >> 1) & 1));
+    }
+    if (TRACK) block_minmax<T>(mn, mx, mm);
+}
+
+template <typename T, int C, int CP, bool TRACK>
+static __global__ void __launch_bounds__(push_tile<T, CP>(), 2)
+    push_tma_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
+                    const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
+                    const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
+    push_tma_body<T, C, CP, TRACK>(state, out, N, E, geom, nx, ny, nz, A, K, mm, err, sb);
 }
 
 // ------------------------------------------------------------------ cell sort: scan, ids
@@ -717,6 +865,145 @@ static __global__ void __launch_bounds__(RUN > 1 ? 128 : 256, RUN > 1 ? 3 : 1) d
                                                       T qm, T* __restrict__ rho, int* __restrict__ err,
                                                       const SortBuf sb) {
     deposit_kernel_body<T, C, CP, RUN>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// ------------------------------------------------------------------ warp-sorted deposition
+
+// Deposition with the summation over particles done on chip before the atomics.
+// Each warp takes 32 consecutive particles and sorts them by cell with a
+// bitonic network on the keys (cell << 5 | lane), so the particles of one cell
+// occupy consecutive lanes. Every lane writes its particle's 8 node records
+// (8 x CP values) as a column of a per-warp shared tile [8 CP][33] (odd
+// stride: conflict-free both ways); then lane j owns tile rows j, j + 32, ...
+// (node nd = row / CP, channel row % CP) and, for each run of lanes sharing a
+// cell, sums its rows over the run and issues one scalar atomic per (run, node,
+// channel). Consecutive lanes then address consecutive channels of
+// neighbouring nodes, so one warp atomic touches a few contiguous sectors. The
+// cell sort's rank is the lane's offset in its run plus one counting atomic
+// per run.
+template <int CP, typename T>
+__host__ __device__ constexpr int dep_tile_warps() {
+    return (sizeof(T) * 8 * CP * 33 * 8 <= 72 * 1024) ? 8 : ((sizeof(T) * 8 * CP * 33 * 4 <= 72 * 1024) ? 4 : 2);
+}
+
+template <typename T, int C, int CP, int WARPS>
+__device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, int64_t N,
+                                                    const GeomDev* __restrict__ geom, int nx, int ny, int nz, T qm,
+                                                    T* __restrict__ rho, int* __restrict__ err, const SortBuf sb,
+                                                    const int bx_) {
+    constexpr int ROWS = 8 * CP;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ unsigned char smraw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* tile = reinterpret_cast<T*>(smraw) + (size_t)warp * ROWS * 33;
+    const int64_t i0 = ((int64_t)bx_ * WARPS + warp) * 32;
+    if (i0 >= N) return;                                  // whole warp
+    const int64_t i = i0 + lane;
+    const bool valid = i < N;
+    const GeomDev& g = *geom;
+    const int n[3] = {nx, ny, nz};
+    T ih[3], o[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ih[d] = geom_ih<T>(g, d);
+        o[d] = geom_o<T>(g, d);
+    }
+    int bad = 0;
+    int key = 0x7fffffff;
+    T f0[3] = {(T)0, (T)0, (T)0};
+    if (valid) {
+        int idx[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(state[((2 * d) * N + i) * CP], o[d], ih[d], n[d], f0[d], bad);
+        key = (((idx[2] * ny + idx[1]) * nx + idx[0]) << 5) | lane;
+    }
+    // bitonic sort of the 32 keys, ascending in lane order
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int other = __shfl_xor_sync(FULL, key, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            key = (lower == up) ? min(key, other) : max(key, other);
+        }
+    }
+    const int nv = __popc(__ballot_sync(FULL, valid));    // sorted lanes [0, nv) hold particles
+    const bool sv = lane < nv;
+    const int cell = key >> 5;
+    const int src = key & 31;
+    const int64_t ps = i0 + src;
+    T f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f[d] = __shfl_sync(FULL, f0[d], src);
+    // runs of equal cells
+    const int prev = __shfl_up_sync(FULL, cell, 1);
+    const bool head = sv && (lane == 0 || prev != cell);
+    const unsigned heads = __ballot_sync(FULL, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    if (sb.key) {
+        const unsigned after = heads & ~(0xffffffffu >> (31 - lane));
+        const int end = after ? __ffs(after) - 2 : nv - 1;
+        int base = 0;
+        if (head) base = atomicAdd(&sb.hist[cell], end - lane + 1);
+        base = __shfl_sync(FULL, base, start & 31);
+        if (sv) {
+            sb.key[ps] = cell;
+            sb.rank[ps] = base + lane - start;
+        }
+    }
+    // node records of this lane's particle into tile column `lane`
+    if (sv) {
+        T x[3][CP];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + ps) * CP, x[d]);
+#pragma unroll
+        for (int nd = 0; nd < 8; ++nd) {
+            const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+            const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
+            const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
+            const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
+            const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
+            T* col = tile + (nd * CP) * 33 + lane;
+            col[0] = qm * (wx * wy * wz);
+#pragma unroll
+            for (int k = 1; k < CP; ++k) col[k * 33] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
+        }
+    }
+    __syncwarp();
+    // rows of this lane: node nd = r / CP of the cell (node index = cell index + offset, as cells
+    // and nodes share the linearisation), channel r % CP
+    constexpr int RL = ROWS / 32;
+    int64_t roff[RL];
+#pragma unroll
+    for (int q = 0; q < RL; ++q) {
+        const int r = lane + 32 * q, nd = r / CP, ch = r % CP;
+        roff[q] = ((int64_t)(nd >> 2) * nx * ny + ((nd >> 1) & 1) * nx + (nd & 1)) * CP + ch;
+    }
+    // per run: row sums and one atomic per (node, channel)
+    for (unsigned m = heads; m; m &= m - 1) {
+        const int s0 = __ffs(m) - 1;
+        const unsigned rest = m & (m - 1);
+        const int s1 = rest ? __ffs(rest) - 2 : nv - 1;
+        T* base = rho + (int64_t)__shfl_sync(FULL, cell, s0) * CP;
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int r = lane + 32 * q;
+            if (r % CP >= C) continue;
+            const T* row = tile + r * 33;
+            T acc = row[s0];
+            for (int j = s0 + 1; j <= s1; ++j) acc += row[j];
+            atomicAdd(base + roff[q], acc);
+        }
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+template <typename T, int C, int CP, int WARPS>
+static __global__ void __launch_bounds__(WARPS * 32) deposit_tile_kernel(const T* __restrict__ state, int64_t N,
+                                                                           const GeomDev* __restrict__ geom, int nx,
+                                                                           int ny, int nz, T qm, T* __restrict__ rho,
+                                                                           int* __restrict__ err, const SortBuf sb) {
+    deposit_tile_body<T, C, CP, WARPS>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x);
 }
 
 }  // namespace adpic

@@ -170,7 +170,8 @@ def objective(y, dy, target, scale=1.0):
 def bfgs(fg, x0, lo, hi, max_iter=50, ftol=0.0, gtol=1e-14, max_evals=None, first_step=0.1):
     """Projected BFGS inside the box [lo, hi]: inverse-Hessian update of the variable-metric method,
     initial inverse Hessian rescaled by s.y / y.y after the first step, backtracking Armijo line
-    search along the projected step. fg(x) -> (f, g). Returns (x, f, calls to fg)."""
+    search along the projected step; a failed line search restarts from the steepest-descent step
+    once before giving up. fg(x) -> (f, g). Returns (x, f, calls to fg)."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     x = np.clip(np.asarray(x0, dtype=np.float64), lo, hi)
@@ -204,7 +205,10 @@ def bfgs(fg, x0, lo, hi, max_iter=50, ftol=0.0, gtol=1e-14, max_evals=None, firs
             if t < 1e-6:
                 break
         if not accepted:
-            break
+            if Hinv is None:
+                break
+            Hinv = None             # restart once from the scaled steepest-descent step
+            continue
         yv = gn - g
         sy = s @ yv
         if sy > 1e-300:
