@@ -630,15 +630,32 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
         for (int q = 0; q < 5; ++q) { acc[pl][q] = 0.0; ah[pl][q] = 0.f; al[pl][q] = 0.f; }
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
-    for (int64_t base = warp * PPW; base < N; base += nwarps * PPW) {
-        const int64_t i = base + lane / CP;
-        const bool valid = i < N;
+    // four particle groups per trip: their 24 loads are issued before any use
+    constexpr int U = 4;
+    const int64_t stride = nwarps * PPW;
+    for (int64_t base = warp * PPW; base < N; base += U * stride) {
+        T uu[U][3], pv[U][3];
+        bool vd[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int64_t i = base + j * stride + lane / CP;
+            vd[j] = i < N;
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) {
+                uu[j][pl] = vd[j] ? state[((2 * pl) * N + i) * CP + k] : (T)0;
+                pv[j][pl] = vd[j] ? state[((2 * pl + 1) * N + i) * CP + k] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+        const int64_t i = base + j * stride + lane / CP;
+        const bool valid = vd[j];
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
             T* pu = state + ((2 * pl) * N + i) * CP + k;
             T* pp = state + ((2 * pl + 1) * N + i) * CP + k;
-            T u = valid ? *pu : (T)0;
-            T p = valid ? *pp : (T)0;
+            T u = uu[j][pl];
+            T p = pv[j][pl];
             T u0 = __shfl_sync(0xffffffffu, u, src);
             T p0 = __shfl_sync(0xffffffffu, p, src);
             if (MOM && valid) {
@@ -688,6 +705,7 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
                 *pu = un;
                 *pp = pn;
             }
+        }
         }
     }
     if (APPLY) block_minmax<T>(mn, mx, mm);
