@@ -124,8 +124,9 @@ JOB(job_clear) {
         in.rho[t] = (T)0;
 }
 JOB(job_deposit) {
-    deposit_kernel_body<T, kCP, kCP, 1>(in.state[st.from], in.N, in.geom, in.n, in.n, in.n, in.qm, in.rho, in.err,
-                                        sort_of(in, st.from), lb, 0, 0, 0);
+    // warp-sorted deposit, 8 warps of 32 particles per virtual block
+    deposit_tile_body<T, kCP, kCP, 8>(in.state[st.from], in.N, in.geom, in.n, in.n, in.n, in.qm, in.rho, in.err,
+                                      sort_of(in, st.from), lb);
 }
 JOB(job_corner) { green_corner_kernel_body(in.geom, in.n, in.n, in.n, in.corner, lb, 0, 0, 0); }
 JOB(job_scansum) { scan_sum_kernel_body(in.cellcount, in.n * in.n * in.n, in.bsum, lb, 0, 0, 0); }
@@ -407,7 +408,8 @@ size_t lane_smem(int n) {
     const size_t x = sizeof(V2<T>) * (M + (size_t)kRowsX * (kCP / 2) * LS(M)) + sizeof(T) * kRowsX * n * kCP;
     const size_t yz = sizeof(V2<T>) * (M + (size_t)kTile * LS(M));
     const size_t dct = sizeof(T) * ((size_t)(n + 1) * (n + 1) + (size_t)kDctLines * (n + 2));
-    return std::max(x, std::max(yz, dct));
+    const size_t dep = sizeof(T) * (size_t)8 * 8 * kCP * 33;    // deposit tiles of 8 warps
+    return std::max(std::max(x, dep), std::max(yz, dct));
 }
 
 template <typename T>

@@ -234,27 +234,32 @@ __device__ __forceinline__ void push_core(T (&u)[6][CP], const T* __restrict__ E
             T gx = (T)0, gy = (T)0, gz = (T)0;
 #pragma unroll
             for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
+            // nodes nd = a + 2b + 4c in batches: a batch's loads are all issued before
+            // its accumulation, so one L2 round trip serves NB nodes
+            constexpr int NB = (CP * sizeof(T) <= 32) ? 4 : 2;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const T wz = c ? f[2] : (T)1 - f[2];
-                const T sz_ = c ? (T)1 : (T)-1;
+            for (int nb0 = 0; nb0 < 8; nb0 += NB) {
+                T en[NB][CP];
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
+                for (int j = 0; j < NB; ++j) {
+                    const int nd = nb0 + j, a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+                    ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const int nd = nb0 + j, a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+                    const T wz = c ? f[2] : (T)1 - f[2];
+                    const T sz_ = c ? (T)1 : (T)-1;
                     const T wy = b ? f[1] : (T)1 - f[1];
                     const T sy_ = b ? (T)1 : (T)-1;
+                    const T wx = a ? f[0] : (T)1 - f[0];
+                    const T sx_ = a ? (T)1 : (T)-1;
+                    const T W = wx * wy * wz;
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        const T wx = a ? f[0] : (T)1 - f[0];
-                        const T sx_ = a ? (T)1 : (T)-1;
-                        const T W = wx * wy * wz;
-                        T en[CP];
-                        ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en);
-#pragma unroll
-                        for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[k], Ev[k]);
-                        gx = fma(sx_ * wy * wz, en[0], gx);
-                        gy = fma(wx * sy_ * wz, en[0], gy);
-                        gz = fma(wx * wy * sz_, en[0], gz);
-                    }
+                    for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[j][k], Ev[k]);
+                    gx = fma(sx_ * wy * wz, en[j][0], gx);
+                    gy = fma(wx * sy_ * wz, en[j][0], gy);
+                    gz = fma(wx * wy * sz_, en[j][0], gz);
                 }
             }
             gx *= ih[0];
@@ -431,9 +436,11 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
             issue(tile + 2 * step, s);
         }
         if (valid) {
+            // slot and id loads first: their latency overlaps the gather
             const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
+            const int idv = sb.ids_out ? sb.ids_in[i] : 0;
             push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
-            if (sb.ids_out) sb.ids_out[dst] = sb.ids_in[i];
+            if (sb.ids_out) sb.ids_out[dst] = idv;
 #pragma unroll
             for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
             if (TRACK) {
