@@ -367,10 +367,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// particles per tile: 8 KB per coordinate run
+// particles per tile (one thread each) and resident CTAs per SM the register
+// budget is sized for: 4 KB coordinate runs and three 128-thread CTAs for the
+// 32-byte records (168 registers, no spills), 8 KB runs and two CTAs otherwise
 template <typename T, int CP>
 __host__ __device__ constexpr int push_tile() {
-    return (int)(8192 / (CP * sizeof(T)));
+    return CP * sizeof(T) == 32 ? 128 : (int)(8192 / (CP * sizeof(T)));
+}
+template <typename T, int CP>
+__host__ __device__ constexpr int push_min_blocks() {
+    return CP * sizeof(T) == 32 ? 3 : 2;
 }
 
 // Persistent push: each CTA walks tiles blockIdx.x, +gridDim.x, ... and keeps
@@ -462,7 +468,7 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
 }
 
 template <typename T, int C, int CP, bool TRACK>
-static __global__ void __launch_bounds__(push_tile<T, CP>(), 2)
+static __global__ void __launch_bounds__(push_tile<T, CP>(), push_min_blocks<T, CP>())
     push_tma_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
                     const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
                     const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
