@@ -43,6 +43,7 @@ struct Inst {
     T qm;
     double gamma0;
     FFTDims d;
+    int yt;             // rows per CTA of the slab x passes
     T* state[2];
     int* ids[2];
     int *key, *rank, *cellcount, *offs, *bsum;
@@ -65,20 +66,20 @@ struct Inst {
 
 enum Job {
     J_GEOM, J_CLEAR, J_DEPOSIT, J_CORNER, J_SCANSUM, J_CHMAX, J_CELL, J_SCANTOP, J_DCTX, J_SCANAPPLY, J_DCTY,
-    J_DCTZ, J_FFTX, J_FFTY, J_FFTZ, J_FFTYI, J_FFTXI, J_FIELD, J_PUSH, J_BOUND, J_REDUCE, J_COUNT
+    J_DCTZ, J_FFTX, J_FFTYZ, J_FFTXI, J_FIELD, J_PUSH, J_BOUND, J_REDUCE, J_COUNT
 };
 
 // phases of one kick: the jobs of a phase depend only on earlier phases
-enum Phase { PH_GEOM, PH_DEP, PH_2, PH_3, PH_4, PH_5, PH_FFTY, PH_FFTZ, PH_FFTYI, PH_FFTXI, PH_FIELD, PH_PUSH,
-             PH_BOUND, PH_REDUCE, PH_COUNT };
+enum Phase { PH_GEOM, PH_DEP, PH_2, PH_3, PH_4, PH_5, PH_FFTYZ, PH_FFTXI, PH_FIELD, PH_PUSH, PH_BOUND, PH_REDUCE,
+             PH_COUNT };
 __constant__ int c_phase_jobs[PH_COUNT][3] = {
     {J_GEOM, J_CLEAR, -1}, {J_DEPOSIT, J_CORNER, -1}, {J_SCANSUM, J_CHMAX, J_CELL}, {J_SCANTOP, J_DCTX, -1},
-    {J_SCANAPPLY, J_DCTY, -1}, {J_DCTZ, J_FFTX, -1}, {J_FFTY, -1, -1}, {J_FFTZ, -1, -1}, {J_FFTYI, -1, -1},
-    {J_FFTXI, -1, -1}, {J_FIELD, -1, -1}, {J_PUSH, -1, -1}, {J_BOUND, -1, -1}, {J_REDUCE, -1, -1}};
+    {J_SCANAPPLY, J_DCTY, -1}, {J_DCTZ, J_FFTX, -1}, {J_FFTYZ, -1, -1}, {J_FFTXI, -1, -1}, {J_FIELD, -1, -1},
+    {J_PUSH, -1, -1}, {J_BOUND, -1, -1}, {J_REDUCE, -1, -1}};
 const int h_phase_jobs[PH_COUNT][3] = {
     {J_GEOM, J_CLEAR, -1}, {J_DEPOSIT, J_CORNER, -1}, {J_SCANSUM, J_CHMAX, J_CELL}, {J_SCANTOP, J_DCTX, -1},
-    {J_SCANAPPLY, J_DCTY, -1}, {J_DCTZ, J_FFTX, -1}, {J_FFTY, -1, -1}, {J_FFTZ, -1, -1}, {J_FFTYI, -1, -1},
-    {J_FFTXI, -1, -1}, {J_FIELD, -1, -1}, {J_PUSH, -1, -1}, {J_BOUND, -1, -1}, {J_REDUCE, -1, -1}};
+    {J_SCANAPPLY, J_DCTY, -1}, {J_DCTZ, J_FFTX, -1}, {J_FFTYZ, -1, -1}, {J_FFTXI, -1, -1}, {J_FIELD, -1, -1},
+    {J_PUSH, -1, -1}, {J_BOUND, -1, -1}, {J_REDUCE, -1, -1}};
 
 // What one phase does at kick g (map/kick table entries, push mode, boundary mode)
 struct Step {
@@ -131,7 +132,7 @@ JOB(job_deposit) {
 JOB(job_corner) { green_corner_kernel_body(in.geom, in.n, in.n, in.n, in.corner, lb, 0, 0, 0); }
 JOB(job_scansum) { scan_sum_kernel_body(in.cellcount, in.n * in.n * in.n, in.bsum, lb, 0, 0, 0); }
 JOB(job_chmax) { chmax_kernel_body<T>(in.rho, (int64_t)in.n * in.n * in.n, kCP, in.chmax, lb, 0, 0, kChmaxBlocks); }
-JOB(job_cell) { green_cell_kernel_body<T>(in.geom, in.n, in.n, in.n, in.corner, in.G, lb, 0, 0, 0); }
+JOB(job_cell) { green_cell_kernel_body<T>(in.geom, in.n, in.n, in.n, in.corner, in.G, lb, 0, 0, 0, 1); }
 JOB(job_scantop) {
     scan_top_kernel_body(in.bsum, (in.n * in.n * in.n + kScanChunk - 1) / kScanChunk, 0, 0, 0, 1);
 }
@@ -139,25 +140,22 @@ JOB(job_scanapply) { scan_apply_kernel_body(in.cellcount, in.n * in.n * in.n, in
 JOB(job_dctx) { dct_kernel_body<T>(in.G, in.Gtmp, in.dct, in.n + 1, (int64_t)(in.n + 1) * (in.n + 1), lb, 0, 0, 0); }
 JOB(job_dcty) { dct_kernel_body<T>(in.Gtmp, in.G, in.dct, in.n + 1, (int64_t)(in.n + 1) * (in.n + 1), lb, 0, 0, 0); }
 JOB(job_dctz) { dct_kernel_body<T>(in.G, in.Ghat, in.dct, in.n + 1, (int64_t)(in.n + 1) * (in.n + 1), lb, 0, 0, 0); }
+// the slab-path convolution (Ghat stored [kx'][kz'][ky'], see job_cell)
 template <typename T, int M>
 __device__ __noinline__ void job_fft(int job, const Inst<T>& in, int lb) {
     const FFTDims& d = in.d;
-    const int tx = M / kTile;
+    const int tiles = d.ny / in.yt;
     switch (job) {
-        case J_FFTX: fftx_fwd_kernel_body<T, M>(in.rho, in.X1, d, in.tw, in.chmax, lb, 0, 0, 0); break;
-        case J_FFTY:
-            ffty_kernel_body<T, M, false>(in.X1, in.X2, d, in.tw, lb % tx, (lb / tx) % d.nz, lb / (tx * d.nz), 0);
-            break;
-        case J_FFTZ:
-            fftz_kernel_body<T, M>(in.X2, in.Ghat, d, in.tw, lb % tx, (lb / tx) % d.My, lb / (tx * d.My), 0);
-            break;
-        case J_FFTYI:
-            ffty_kernel_body<T, M, true>(in.X2, in.X1, d, in.tw, lb % tx, (lb / tx) % d.nz, lb / (tx * d.nz), 0);
-            break;
-        default: fftx_inv_kernel_body<T, M>(in.X1, in.phi, d, in.tw, in.chmax, lb, 0, 0, 0); break;
+        case J_FFTX: fftx_fwd_t_kernel_body<T, M>(in.rho, in.X1, d, in.tw, in.chmax, in.yt, lb % tiles, lb / tiles); break;
+        case J_FFTYZ: fftyz_kernel_body<T, M, M>(in.X1, in.Ghat, d, in.tw, in.tw, lb % d.Mx, lb / d.Mx); break;
+        default: fftx_inv_t_kernel_body<T, M>(in.X1, in.phi, d, in.tw, in.chmax, in.yt, lb % tiles, lb / tiles); break;
     }
 }
-JOB(job_field) { field_kernel_body<T>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb, 0, 0, 0); }
+constexpr int kFieldPer = 8;            // 256-thread field blocks per virtual block
+JOB(job_field) {
+    for (int r = 0; r < kFieldPer; ++r)
+        field_kernel_body<T>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb * kFieldPer + r, 0, 0, 0);
+}
 JOB(job_push_track) {
     const int slot = (int)(st.g % st.kpp);
     push_kernel_body<T, kCP, kCP, true>(in.state[st.from], in.state[1 - st.from], in.N, in.E, in.geom, in.n, in.n,
@@ -204,9 +202,7 @@ __device__ __forceinline__ void do_job(int job, const Inst<T>& in, int lb, const
         case J_DCTY: job_dcty<T>(in, lb, st); break;
         case J_DCTZ: job_dctz<T>(in, lb, st); break;
         case J_FFTX:
-        case J_FFTY:
-        case J_FFTZ:
-        case J_FFTYI:
+        case J_FFTYZ:
         case J_FFTXI:
             if (in.M == 64) job_fft<T, 64>(job, in, lb);
             else job_fft<T, 128>(job, in, lb);
@@ -401,15 +397,27 @@ void batch_free_graphs(ad_pic_batch* b) {
     b->graphs.clear();
 }
 
+// FFT dimensions of a cubic instance with n^3 nodes
+FFTDims h_dims(int n) {
+    FFTDims d{};
+    d.nx = d.ny = d.nz = n;
+    d.Mx = d.My = d.Mz = 2 * n;
+    int l = 0;
+    while ((1 << l) < 2 * n) ++l;
+    d.lx = d.ly = d.lz = l;
+    d.C = kCP;
+    d.CP = kCP;
+    d.npair = kCP / 2;
+    d.norm = 1.0 / ((double)(2 * n) * (2 * n) * (2 * n));
+    return d;
+}
+
 template <typename T>
 size_t lane_smem(int n) {
-    const int M = 2 * n;
-    auto LS = [](int m) { return m == 64 ? Lay<64>::LS : Lay<128>::LS; };
-    const size_t x = sizeof(V2<T>) * (M + (size_t)kRowsX * (kCP / 2) * LS(M)) + sizeof(T) * kRowsX * n * kCP;
-    const size_t yz = sizeof(V2<T>) * (M + (size_t)kTile * LS(M));
     const size_t dct = sizeof(T) * ((size_t)(n + 1) * (n + 1) + (size_t)kDctLines * (n + 2));
     const size_t dep = sizeof(T) * (size_t)8 * 8 * kCP * 33;    // deposit tiles of 8 warps
-    return std::max(std::max(x, dep), std::max(yz, dct));
+    const size_t slab = fft_slab_smem<T>(h_dims(n));
+    return std::max(std::max(slab, dep), dct);
 }
 
 template <typename T>
@@ -421,7 +429,7 @@ int build_tables(ad_pic_batch* b) {
         ad_pic* h = b->h[i];
         const int n = h->nx;
         const int64_t nodes = (int64_t)n * n * n;
-        const int M = 2 * n, tx = M / kTile;
+        const int M = 2 * n;
         const int npair = kCP / 2;
         int* bl = blocks.data();
         auto set = [&](int j, int64_t v) { bl[(size_t)j * ni + i] = (int)v; };
@@ -437,12 +445,11 @@ int build_tables(ad_pic_batch* b) {
         set(J_SCANAPPLY, scan_blocks((int)nodes));
         set(J_DCTY, ceil_div((int64_t)(n + 1) * (n + 1), kDctLines));
         set(J_DCTZ, ceil_div((int64_t)(n + 1) * (n + 1), kDctLines));
-        set(J_FFTX, ceil_div((int64_t)n * n, kRowsX));
-        set(J_FFTY, (int64_t)tx * n * npair);
-        set(J_FFTZ, (int64_t)tx * M * npair);
-        set(J_FFTYI, (int64_t)tx * n * npair);
-        set(J_FFTXI, ceil_div((int64_t)n * n, kRowsX));
-        set(J_FIELD, ceil_div(nodes * kCP, 256));
+        const int yt = fft_slab_yt<T>(h_dims(n));
+        set(J_FFTX, (int64_t)(n / yt) * n);
+        set(J_FFTYZ, (int64_t)M * npair);
+        set(J_FFTXI, (int64_t)(n / yt) * n);
+        set(J_FIELD, ceil_div(nodes * kCP, 256 * kFieldPer));
         set(J_PUSH, ceil_div(h->N, 256));
         set(J_BOUND, kBoundBlocks);
         set(J_REDUCE, 15 * kCP);
@@ -515,6 +522,7 @@ int upload_instances(ad_pic_batch* b, int nrec) {
         in.d.CP = kCP;
         in.d.npair = kCP / 2;
         in.d.norm = 1.0 / ((double)in.M * in.M * in.M);
+        in.yt = fft_slab_yt<T>(in.d);
         in.state[0] = (T*)h->state;
         in.state[1] = (T*)h->state2;
         in.ids[0] = h->ids[0];

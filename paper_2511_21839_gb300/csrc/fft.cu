@@ -20,6 +20,8 @@
 //   fftx_inv   X1 rows (all Mx)         -> phi rows (x < nx), scaled back
 // Grids with nz <= 64 take the three-launch slab path instead (fftx_fwd_t,
 // fftyz, fftx_inv_t in fft_dev.cuh), with Ghat stored [kx'][kz'][ky'].
+#include <algorithm>
+
 #include "fft_dev.cuh"
 
 namespace adpic {
@@ -118,6 +120,15 @@ bool fft_slab_path(const FFTDims& d) {
 
 int fft_conv_launches(bool slab) { return slab ? 3 : 5; }
 
+template <typename T>
+int fft_slab_yt(const FFTDims& d) { return slab_yt<T>(d); }
+
+template <typename T>
+size_t fft_slab_smem(const FFTDims& d) {
+    const int yt = slab_yt<T>(d);
+    return std::max(std::max(sm_fwd_t<T>(d, yt), sm_inv_t<T>(d, yt)), sm_yz<T>(d));
+}
+
 template <typename T, int MX, int MY, int MZ>
 void conv_slab(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
                const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
@@ -207,6 +218,8 @@ template void launch_fft_conv<double>(const double*, double2*, double2*, const d
                                       const double2*, const double2*, const double2*, const unsigned long long*,
                                       cudaStream_t);
 template bool fft_slab_path<float>(const FFTDims&);
+template int fft_slab_yt<float>(const FFTDims&);
+template size_t fft_slab_smem<float>(const FFTDims&);
 template bool fft_slab_path<double>(const FFTDims&);
 template void setup_fft<float>();
 template void setup_fft<double>();
