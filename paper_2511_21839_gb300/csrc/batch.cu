@@ -152,10 +152,7 @@ __device__ __noinline__ void job_fft(int job, const Inst<T>& in, int lb) {
     }
 }
 constexpr int kFieldPer = 8;            // 256-thread field blocks per virtual block
-JOB(job_field) {
-    for (int r = 0; r < kFieldPer; ++r)
-        field_kernel_body<T>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb * kFieldPer + r, 0, 0, 0);
-}
+JOB(job_field) { field_multi_body<T, kFieldPer>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb); }
 JOB(job_push_track) {
     const int slot = (int)(st.g % st.kpp);
     push_kernel_body<T, kCP, kCP, true>(in.state[st.from], in.state[1 - st.from], in.N, in.E, in.geom, in.n, in.n,
@@ -320,13 +317,14 @@ __global__ void __launch_bounds__(256) batch_phase_kernel(const Inst<T>* __restr
 // host twin of run_sequence for the phased mode
 template <typename T>
 void enqueue_phased(const Inst<T>* I, int n_inst, const int* cum, const std::vector<int>& phase_blocks,
-                    const RunSpec& rs, size_t smem, cudaStream_t s) {
+                    const RunSpec& rs, const std::vector<size_t>& phase_smem, cudaStream_t s) {
     Step st{};
     st.kpp = rs.kpp;
     st.from = rs.from;
+    // each phase launches with the shared memory of its own jobs only
     auto launch = [&](int ph) {
         const int nb = phase_blocks[ph];
-        if (nb > 0) batch_phase_kernel<T><<<nb, 256, smem, s>>>(I, n_inst, cum, ph, st);
+        if (nb > 0) batch_phase_kernel<T><<<nb, 256, phase_smem[ph], s>>>(I, n_inst, cum, ph, st);
     };
     if (rs.n == 0) {
         st.g = rs.g0 - 1;
@@ -375,6 +373,7 @@ struct ad_pic_batch {
     void* inst_dev = nullptr;                 // Inst<T>[n_inst]
     int* cum_dev = nullptr;                   // [J_COUNT][n_inst + 1]
     std::vector<int> phase_blocks;            // virtual blocks per phase
+    std::vector<size_t> phase_smem;           // dynamic shared memory per phase (phased mode)
     void* coef_dev = nullptr;                 // per-instance half/comp/kick tables
     size_t coef_bytes = 0;
     double* records = nullptr;                // [n_inst][rec_cap][15][CP]
@@ -420,6 +419,21 @@ size_t lane_smem(int n) {
     return std::max(std::max(slab, dep), dct);
 }
 
+// dynamic shared memory of one job on a cubic n^3 instance
+template <typename T>
+size_t job_smem(int job, int n) {
+    switch (job) {
+        case J_DEPOSIT: return sizeof(T) * (size_t)8 * 8 * kCP * 33;
+        case J_DCTX:
+        case J_DCTY:
+        case J_DCTZ: return sizeof(T) * ((size_t)(n + 1) * (n + 1) + (size_t)kDctLines * (n + 2));
+        case J_FFTX: return fft_slab_smem<T>(h_dims(n), 0);
+        case J_FFTYZ: return fft_slab_smem<T>(h_dims(n), 1);
+        case J_FFTXI: return fft_slab_smem<T>(h_dims(n), 2);
+        default: return 0;
+    }
+}
+
 template <typename T>
 int build_tables(ad_pic_batch* b) {
     const int ni = b->n_inst;
@@ -461,6 +475,12 @@ int build_tables(ad_pic_batch* b) {
         for (int i = 0; i < ni; ++i)
             cum[(size_t)j * (ni + 1) + i + 1] = cum[(size_t)j * (ni + 1) + i] + blocks[(size_t)j * ni + i];
     }
+    b->phase_smem.assign(PH_COUNT, 0);
+    for (int i = 0; i < ni; ++i)
+        for (int ph = 0; ph < PH_COUNT; ++ph)
+            for (int q = 0; q < 3; ++q)
+                if (h_phase_jobs[ph][q] >= 0)
+                    b->phase_smem[ph] = std::max(b->phase_smem[ph], job_smem<T>(h_phase_jobs[ph][q], b->h[i]->nx));
     b->phase_blocks.assign(PH_COUNT, 0);
     for (int ph = 0; ph < PH_COUNT; ++ph)
         for (int q = 0; q < 3; ++q)
@@ -569,7 +589,7 @@ template <typename T>
 int launch_mode(ad_pic_batch* b, int mode, const RunSpec& rs) {
     const Inst<T>* I = (const Inst<T>*)b->inst_dev;
     if (mode == 3) {
-        enqueue_phased<T>(I, b->n_inst, b->cum_dev, b->phase_blocks, rs, b->smem, b->stream);
+        enqueue_phased<T>(I, b->n_inst, b->cum_dev, b->phase_blocks, rs, b->phase_smem, b->stream);
         return cudaGetLastError() == cudaSuccess ? AD_PIC_OK : AD_PIC_ERR_CUDA;
     }
     int dev = 0, sms = 0, per_sm = 0;

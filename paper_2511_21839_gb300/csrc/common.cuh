@@ -120,12 +120,13 @@ void setup_fft();
 template <typename T>
 bool fft_slab_path(const FFTDims& d);
 int fft_conv_launches(bool slab);
-// rows per CTA of the slab path's x passes, and the largest dynamic shared
-// memory of its three kernels (for callers that run their bodies elsewhere)
+// rows per CTA of the slab path's x passes, and the dynamic shared memory of
+// its kernels (which: 0 x pass, 1 (y, z) slab, 2 inverse x pass, else the
+// largest), for callers that run their bodies elsewhere
 template <typename T>
 int fft_slab_yt(const FFTDims& d);
 template <typename T>
-size_t fft_slab_smem(const FFTDims& d);
+size_t fft_slab_smem(const FFTDims& d, int which = -1);
 template <typename T>
 void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
                      const V2<T>* twx, const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s);

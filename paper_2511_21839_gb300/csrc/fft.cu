@@ -124,8 +124,11 @@ template <typename T>
 int fft_slab_yt(const FFTDims& d) { return slab_yt<T>(d); }
 
 template <typename T>
-size_t fft_slab_smem(const FFTDims& d) {
+size_t fft_slab_smem(const FFTDims& d, int which) {
     const int yt = slab_yt<T>(d);
+    if (which == 0) return sm_fwd_t<T>(d, yt);
+    if (which == 1) return sm_yz<T>(d);
+    if (which == 2) return sm_inv_t<T>(d, yt);
     return std::max(std::max(sm_fwd_t<T>(d, yt), sm_inv_t<T>(d, yt)), sm_yz<T>(d));
 }
 
@@ -219,7 +222,7 @@ template void launch_fft_conv<double>(const double*, double2*, double2*, const d
                                       cudaStream_t);
 template bool fft_slab_path<float>(const FFTDims&);
 template int fft_slab_yt<float>(const FFTDims&);
-template size_t fft_slab_smem<float>(const FFTDims&);
+template size_t fft_slab_smem<float>(const FFTDims&, int);
 template bool fft_slab_path<double>(const FFTDims&);
 template void setup_fft<float>();
 template void setup_fft<double>();

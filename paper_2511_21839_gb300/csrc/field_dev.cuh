@@ -292,6 +292,41 @@ __device__ __forceinline__ void field_kernel_body(const T* __restrict__ phi, con
     e[2 * CP] = -(phi[t + sz] - phi[t - sz]) * az;
 }
 
+// The same field for R consecutive 256-element blocks (rb = R bx + r): the
+// loads of all R are issued before any store, for callers whose block
+// dispatch is costly.
+template <typename T, int R>
+__device__ __forceinline__ void field_multi_body(const T* __restrict__ phi, const GeomDev* __restrict__ g, int nx,
+                                                 int ny, int nz, int CP, T* __restrict__ E, const int bx_) {
+    const unsigned total = (unsigned)nx * ny * nz * CP;
+    const int lcp = __ffs(CP) - 1, lx = __ffs(nx) - 1, ly = __ffs(ny) - 1;
+    const T ax = sizeof(T) == 4 ? (T)g->fdf[0] : (T)g->fdd[0];
+    const T ay = sizeof(T) == 4 ? (T)g->fdf[1] : (T)g->fdd[1];
+    const T az = sizeof(T) == 4 ? (T)g->fdf[2] : (T)g->fdd[2];
+    const unsigned sx = CP, sy = (unsigned)nx * CP, sz = (unsigned)nx * ny * CP;
+    T dx[R], dy[R], dz[R];
+    bool ok[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned t = ((unsigned)bx_ * R + r) * blockDim.x + threadIdx.x;
+        const unsigned node = t >> lcp;
+        const int i = node & (nx - 1), j = (node >> lx) & (ny - 1), k = node >> (lx + ly);
+        ok[r] = t < total && i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+        dx[r] = ok[r] ? phi[t + sx] - phi[t - sx] : (T)0;
+        dy[r] = ok[r] ? phi[t + sy] - phi[t - sy] : (T)0;
+        dz[r] = ok[r] ? phi[t + sz] - phi[t - sz] : (T)0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (!ok[r]) continue;
+        const unsigned t = ((unsigned)bx_ * R + r) * blockDim.x + threadIdx.x;
+        T* e = E + (size_t)(t >> lcp) * 3 * CP + (t & (CP - 1));
+        e[0] = -dx[r] * ax;
+        e[CP] = -dy[r] * ay;
+        e[2 * CP] = -dz[r] * az;
+    }
+}
+
 template <typename T>
 static __global__ void field_kernel(const T* __restrict__ phi, const GeomDev* __restrict__ g, int nx, int ny, int nz, int CP,
                              T* __restrict__ E) {
