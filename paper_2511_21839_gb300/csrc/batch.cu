@@ -76,7 +76,7 @@ __constant__ int c_phase_jobs[PH_COUNT][3] = {
     {J_GEOM, J_CLEAR, -1}, {J_DEPOSIT, J_CORNER, -1}, {J_SCANSUM, J_CHMAX, J_CELL}, {J_SCANTOP, J_DCTX, -1},
     {J_SCANAPPLY, J_DCTY, -1}, {J_DCTZ, J_FFTX, -1}, {J_FFTYZ, -1, -1}, {J_FFTXI, -1, -1}, {J_FIELD, -1, -1},
     {J_PUSH, -1, -1}, {J_BOUND, -1, -1}, {J_REDUCE, -1, -1}};
-const int h_phase_jobs[PH_COUNT][3] = {
+constexpr int h_phase_jobs[PH_COUNT][3] = {
     {J_GEOM, J_CLEAR, -1}, {J_DEPOSIT, J_CORNER, -1}, {J_SCANSUM, J_CHMAX, J_CELL}, {J_SCANTOP, J_DCTX, -1},
     {J_SCANAPPLY, J_DCTY, -1}, {J_DCTZ, J_FFTX, -1}, {J_FFTYZ, -1, -1}, {J_FFTXI, -1, -1}, {J_FIELD, -1, -1},
     {J_PUSH, -1, -1}, {J_BOUND, -1, -1}, {J_REDUCE, -1, -1}};
@@ -307,11 +307,50 @@ __global__ void __launch_bounds__(256, MINB)
     run_sequence<T>(I, n_inst, cum, rs, (int)blockIdx.x, (int)gridDim.x, [&]() { grid.sync(); });
 }
 
-// phased mode: one launch per phase, one virtual block per block
+// phased mode: one kernel per phase whose jobs are compile-time constants, so
+// each kernel holds (and allocates registers for) only its own job bodies
+template <typename T, int J>
+__device__ __forceinline__ void run_job_blocks(const Inst<T>* I, int n_inst, const int* cum, const Step& st,
+                                               int local_vb) {
+    const int* c = cum + J * (n_inst + 1);
+    const int inst = locate<T>(c, n_inst, local_vb);
+    do_job<T>(J, I[inst], local_vb - c[inst], st);
+}
+
+template <typename T, int PH>
+__global__ void __launch_bounds__(256, 2) batch_phase_kernel(const Inst<T>* __restrict__ I, int n_inst,
+                                                          const int* __restrict__ cum, Step st) {
+    constexpr int J0 = h_phase_jobs[PH][0], J1 = h_phase_jobs[PH][1], J2 = h_phase_jobs[PH][2];
+    const int t0 = cum[J0 * (n_inst + 1) + n_inst];
+    const int t1 = t0 + (J1 >= 0 ? cum[(J1 >= 0 ? J1 : 0) * (n_inst + 1) + n_inst] : 0);
+    const int t2 = t1 + (J2 >= 0 ? cum[(J2 >= 0 ? J2 : 0) * (n_inst + 1) + n_inst] : 0);
+    for (int vb = (int)blockIdx.x; vb < t2; vb += (int)gridDim.x) {
+        if (vb < t0) run_job_blocks<T, J0>(I, n_inst, cum, st, vb);
+        else if constexpr (J1 >= 0) {
+            if (vb < t1) run_job_blocks<T, J1>(I, n_inst, cum, st, vb - t0);
+            else if constexpr (J2 >= 0) run_job_blocks<T, J2>(I, n_inst, cum, st, vb - t1);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) batch_phase_kernel(const Inst<T>* __restrict__ I, int n_inst,
-                                                          const int* __restrict__ cum, int ph, Step st) {
-    run_phase<T>(ph, I, n_inst, cum, st, (int)blockIdx.x, (int)gridDim.x);
+void launch_phase(int ph, int nb, size_t smem, cudaStream_t s, const Inst<T>* I, int n_inst, const int* cum,
+                  const Step& st) {
+    switch (ph) {
+#define ADPIC_PHASE(P) \
+    case P: batch_phase_kernel<T, P><<<nb, 256, smem, s>>>(I, n_inst, cum, st); break;
+        ADPIC_PHASE(0) ADPIC_PHASE(1) ADPIC_PHASE(2) ADPIC_PHASE(3) ADPIC_PHASE(4) ADPIC_PHASE(5)
+        ADPIC_PHASE(6) ADPIC_PHASE(7) ADPIC_PHASE(8) ADPIC_PHASE(9) ADPIC_PHASE(10) ADPIC_PHASE(11)
+#undef ADPIC_PHASE
+        default: break;
+    }
+}
+
+template <typename T, int PH>
+void phase_attrs(int mx) {
+    cudaFuncSetAttribute(batch_phase_kernel<T, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if constexpr (PH + 1 < PH_COUNT) phase_attrs<T, PH + 1>(mx);
 }
 
 // host twin of run_sequence for the phased mode
@@ -324,7 +363,7 @@ void enqueue_phased(const Inst<T>* I, int n_inst, const int* cum, const std::vec
     // each phase launches with the shared memory of its own jobs only
     auto launch = [&](int ph) {
         const int nb = phase_blocks[ph];
-        if (nb > 0) batch_phase_kernel<T><<<nb, 256, phase_smem[ph], s>>>(I, n_inst, cum, ph, st);
+        if (nb > 0) launch_phase<T>(ph, nb, phase_smem[ph], s, I, n_inst, cum, st);
     };
     if (rs.n == 0) {
         st.g = rs.g0 - 1;
@@ -492,7 +531,7 @@ int build_tables(ad_pic_batch* b) {
     const int mx = 200 * 1024;
     cudaFuncSetAttribute(batch_persistent_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(batch_persistent_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(batch_phase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    phase_attrs<T, 0>(mx);
     return AD_PIC_OK;
 }
 
