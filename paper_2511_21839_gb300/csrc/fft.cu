@@ -138,7 +138,7 @@ void conv_slab(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d,
     const int yt = slab_yt<T>(d);
     const dim3 gx((unsigned)(d.ny / yt), (unsigned)d.nz);
     fftx_fwd_t_kernel<T, MX><<<gx, 256, sm_fwd_t<T>(d, yt), s>>>(rho, X1, d, twx, chmax, yt);
-    fftyz_kernel<T, MY, MZ><<<dim3((unsigned)d.Mx, (unsigned)d.npair), 256, sm_yz<T>(d), s>>>(X1, Ghat, d, twy, twz);
+    fftyz_kernel<T, MY, MZ><<<dim3((unsigned)d.Mx, (unsigned)d.npair), 512, sm_yz<T>(d), s>>>(X1, Ghat, d, twy, twz);
     fftx_inv_t_kernel<T, MX><<<gx, 256, sm_inv_t<T>(d, yt), s>>>(X1, phi, d, twx, chmax, yt);
 }
 template <typename T, int MX, int MY>

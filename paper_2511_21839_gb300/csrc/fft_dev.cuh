@@ -602,7 +602,7 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
 }
 
 template <typename T, int MY, int MZ>
-static __global__ void __launch_bounds__(256) fftyz_kernel(V2<T>* __restrict__ X1, const T* __restrict__ Ghat, FFTDims d,
+static __global__ void __launch_bounds__(512) fftyz_kernel(V2<T>* __restrict__ X1, const T* __restrict__ Ghat, FFTDims d,
                                                              const V2<T>* __restrict__ twy, const V2<T>* __restrict__ twz) {
     fftyz_kernel_body<T, MY, MZ>(X1, Ghat, d, twy, twz, (int)blockIdx.x, (int)blockIdx.y);
 }

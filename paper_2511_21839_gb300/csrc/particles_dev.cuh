@@ -320,13 +320,6 @@ __device__ __forceinline__ void push_kernel_body(const T* __restrict__ state, T*
     if (TRACK) block_minmax<T>(mn, mx, mm);
 }
 
-template <typename T, int C, int CP, bool TRACK>
-static __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
-    push_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
-                const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
-                const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
-    push_kernel_body<T, C, CP, TRACK>(state, out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
-}
 
 // ------------------------------------------------------------------ push over bulk-copied tiles
 
@@ -778,125 +771,6 @@ static __global__ void moments_reduce_kernel(const double* __restrict__ partial,
     moments_reduce_kernel_body(partial, nblocks, CP, N, out, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
 }
 
-// ------------------------------------------------------------------ deposition
-
-// CIC weights of the value part and their derivatives through the particle's
-// derivative channels; node charge q_m W for channel 0 and q_m dW/dp_k for
-// channel k. Each thread takes RUN consecutive particles (the push keeps them
-// cell-sorted), accumulates the eight node records in registers while the
-// cell does not change, and flushes them with 128-bit float atomics (FP32) or
-// FP64 atomics when it does. Records every particle's cell and its rank among
-// that cell's particles for the sort.
-template <typename T, int C, int CP, int RUN>
-__device__ __forceinline__ void deposit_kernel_body(const T* __restrict__ state, int64_t N,
-                                                      const GeomDev* __restrict__ geom, int nx, int ny, int nz,
-                                                      T qm, T* __restrict__ rho, int* __restrict__ err,
-                                                      const SortBuf sb,
-    const int bx_, const int by_, const int bz_, const int nbx_) {
-    const int64_t first = (bx_ * (int64_t)blockDim.x + threadIdx.x) * RUN;
-    if (first >= N) return;
-    const GeomDev& g = *geom;
-    const int n[3] = {nx, ny, nz};
-    T ih[3], o[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        ih[d] = geom_ih<T>(g, d);
-        o[d] = geom_o<T>(g, d);
-    }
-    T acc[RUN > 1 ? 8 : 1][RUN > 1 ? CP : 1];
-    int cur = -1;
-    int bad = 0;
-    auto flush = [&](int cell) {
-        const int i0 = cell % nx, j0 = (cell / nx) % ny, k0 = cell / (nx * ny);
-#pragma unroll
-        for (int nd = 0; nd < 8; ++nd) {
-            const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-            const int64_t node = ((int64_t)(k0 + c) * ny + (j0 + b)) * nx + (i0 + a);
-            T* dst = rho + node * CP;
-            if constexpr (RUN > 1 && sizeof(T) == 4) {
-#pragma unroll
-                for (int v = 0; v < CP / 4; ++v)
-                    atomicAdd(reinterpret_cast<float4*>(dst) + v,
-                              make_float4(acc[nd][4 * v], acc[nd][4 * v + 1], acc[nd][4 * v + 2], acc[nd][4 * v + 3]));
-            } else if constexpr (RUN > 1) {
-#pragma unroll
-                for (int k = 0; k < C; ++k) atomicAdd(dst + k, acc[nd][k]);
-            }
-        }
-    };
-    for (int r = 0; r < RUN; ++r) {
-        const int64_t i = first + r;
-        if (i >= N) break;
-        T x[3][CP];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
-        T f[3];
-        int idx[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(x[d][0], o[d], ih[d], n[d], f[d], bad);
-        const int cell = (idx[2] * ny + idx[1]) * nx + idx[0];
-        if (sb.key) {
-            sb.key[i] = cell;
-            sb.rank[i] = atomicAdd(&sb.hist[cell], 1);
-        }
-        if constexpr (RUN == 1) {
-            // one particle per thread: add each node record at once
-#pragma unroll
-            for (int nd = 0; nd < 8; ++nd) {
-                const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
-                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
-                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
-                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
-                T q[CP];
-                q[0] = qm * (wx * wy * wz);
-#pragma unroll
-                for (int k = 1; k < CP; ++k) q[k] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
-                const int64_t node = ((int64_t)(idx[2] + c) * ny + (idx[1] + b)) * nx + (idx[0] + a);
-                T* dst = rho + node * CP;
-                if constexpr (sizeof(T) == 4) {
-#pragma unroll
-                    for (int v = 0; v < CP / 4; ++v)
-                        atomicAdd(reinterpret_cast<float4*>(dst) + v,
-                                  make_float4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]));
-                } else {
-#pragma unroll
-                    for (int k = 0; k < C; ++k) atomicAdd(dst + k, q[k]);
-                }
-            }
-        } else {
-            if (cell != cur) {
-                if (cur >= 0) flush(cur);
-                cur = cell;
-#pragma unroll
-                for (int nd = 0; nd < 8; ++nd)
-#pragma unroll
-                    for (int k = 0; k < CP; ++k) acc[nd][k] = (T)0;
-            }
-#pragma unroll
-            for (int nd = 0; nd < 8; ++nd) {
-                const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
-                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
-                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
-                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
-                acc[nd][0] = fma(qm, wx * wy * wz, acc[nd][0]);
-#pragma unroll
-                for (int k = 1; k < CP; ++k) acc[nd][k] = fma(x[0][k], gx, fma(x[1][k], gy, fma(x[2][k], gz, acc[nd][k])));
-            }
-        }
-    }
-    if (RUN > 1 && cur >= 0) flush(cur);
-    if (bad) atomicOr(err, bad);
-}
-
-template <typename T, int C, int CP, int RUN>
-static __global__ void __launch_bounds__(RUN > 1 ? 128 : 256, RUN > 1 ? 3 : 1) deposit_kernel(const T* __restrict__ state, int64_t N,
-                                                      const GeomDev* __restrict__ geom, int nx, int ny, int nz,
-                                                      T qm, T* __restrict__ rho, int* __restrict__ err,
-                                                      const SortBuf sb) {
-    deposit_kernel_body<T, C, CP, RUN>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
-}
 
 // ------------------------------------------------------------------ warp-sorted deposition
 
