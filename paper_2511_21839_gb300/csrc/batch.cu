@@ -317,8 +317,13 @@ __device__ __forceinline__ void run_job_blocks(const Inst<T>* I, int n_inst, con
     do_job<T>(J, I[inst], local_vb - c[inst], st);
 }
 
+// threads per CTA of a phase kernel: the slab FFT phase takes 512 (its bodies
+// stride by blockDim), every other phase 256
+template <int PH>
+__host__ __device__ constexpr int phase_threads() { return PH == PH_FFTYZ ? 512 : 256; }
+
 template <typename T, int PH>
-__global__ void __launch_bounds__(256, 2) batch_phase_kernel(const Inst<T>* __restrict__ I, int n_inst,
+__global__ void __launch_bounds__(phase_threads<PH>(), 2) batch_phase_kernel(const Inst<T>* __restrict__ I, int n_inst,
                                                           const int* __restrict__ cum, Step st) {
     constexpr int J0 = h_phase_jobs[PH][0], J1 = h_phase_jobs[PH][1], J2 = h_phase_jobs[PH][2];
     const int t0 = cum[J0 * (n_inst + 1) + n_inst];
@@ -339,7 +344,7 @@ void launch_phase(int ph, int nb, size_t smem, cudaStream_t s, const Inst<T>* I,
                   const Step& st) {
     switch (ph) {
 #define ADPIC_PHASE(P) \
-    case P: batch_phase_kernel<T, P><<<nb, 256, smem, s>>>(I, n_inst, cum, st); break;
+    case P: batch_phase_kernel<T, P><<<nb, phase_threads<P>(), smem, s>>>(I, n_inst, cum, st); break;
         ADPIC_PHASE(0) ADPIC_PHASE(1) ADPIC_PHASE(2) ADPIC_PHASE(3) ADPIC_PHASE(4) ADPIC_PHASE(5)
         ADPIC_PHASE(6) ADPIC_PHASE(7) ADPIC_PHASE(8) ADPIC_PHASE(9) ADPIC_PHASE(10) ADPIC_PHASE(11)
 #undef ADPIC_PHASE
