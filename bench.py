@@ -54,6 +54,27 @@ def workload_config(w, extra=None):
     return cfg
 
 
+def rank_seed(w, rank):
+    """Seed of a rank's replica: every rank advances its own, independent instance."""
+    return w.seed + 1000 * rank
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (the job ends when its last rank does)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, particles, kicks, ms):
+    """Whole-job dual particle-steps/s: all ranks' particle-steps over the slowest rank's time."""
+    return ws * particles * kicks / (ms / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -241,7 +262,7 @@ def run_native(args):
     dev = torch.cuda.current_device()
     w = I.workload(args.workload)
     kicks = w.kicks_per_period
-    nrm = I.normals(w.seed + 1000 * rank, w.n_particles)
+    nrm = I.normals(rank_seed(w, rank), w.n_particles)
     stream = torch.cuda.Stream()        # one non-default stream shared by the library and the events
     torch.cuda.set_stream(stream)
 
@@ -281,11 +302,8 @@ def run_native(args):
     launches = sim.launches() - l0
     tpush = sim.timing()["push"]
     push_ms = tpush[0] / max(tpush[1], 1)
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ws * w.n_particles * kicks / (ms_step / 1000.0)
+    ms_step = max_over_ranks(ms_step, dist, "cuda")
+    value = job_rate(ws, w.n_particles, kicks, ms_step)
 
     # ---- end to end through the public API with host buffers: upload the step's dual state
     # from pinned host memory, run the period, read the emittances back
