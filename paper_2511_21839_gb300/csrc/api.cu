@@ -294,9 +294,9 @@ struct Impl {
         tend(h, K_MISC, cap);
     }
 
-    // kernels launched by one enqueue_field (geometry 1, deposit 1, scan 3,
+    // kernels launched by one enqueue_field (geometry 1, deposit 1, scan 2,
     // chmax 1, Green's function 5, convolution 3 or 5, field 1; the memset is not a kernel)
-    static int field_launches(ad_pic* h) { return 12 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
+    static int field_launches(ad_pic* h) { return 11 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
 
     // the launch sequence of one run; returns the number of moment records
     // `from` is the buffer holding the particles at the start; each push moves

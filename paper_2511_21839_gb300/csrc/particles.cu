@@ -77,8 +77,7 @@ int scan_blocks(int ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
 void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s) {
     const int nb = scan_blocks(ncells);
     scan_sum_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum);
-    scan_top_kernel<<<1, 256, 0, s>>>(bsum, nb);
-    scan_apply_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum, offs);
+    scan_apply_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum, offs);   // each block prefixes the chunk totals
 }
 void launch_iota(int* ids, int64_t N, cudaStream_t s) {
     if (N > 0) iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ids, N);
@@ -98,7 +97,7 @@ void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, b
     else if (mom)
         boundary_kernel<T, C, CP, true, false><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
     else if (apply)
-        boundary_kernel<T, C, CP, false, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
+        halfmap_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(state, N, A, mm);
 }
 
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s) {

@@ -534,24 +534,33 @@ __device__ __forceinline__ void scan_top_kernel_body(int* __restrict__ bsum, int
     }
 }
 
-static __global__ void scan_top_kernel(int* __restrict__ bsum, int nb) {
-    scan_top_kernel_body(bsum, nb, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
-}
 
-// exclusive offsets of every cell; clears hist for the next kick
+// exclusive offsets of every cell; clears hist for the next kick. With
+// `prefixed` bsum holds the exclusive prefixes of the chunk totals (scan_top
+// ran); otherwise it holds the totals and each block sums those before it.
 __device__ __forceinline__ void scan_apply_kernel_body(int* __restrict__ hist, int ncells, const int* __restrict__ bsum,
                                   int* __restrict__ offs,
-    const int bx_, const int by_, const int bz_, const int nbx_) {
+    const int bx_, const int by_, const int bz_, const int nbx_, bool prefixed = true) {
     __shared__ int sm[32];
     constexpr int PER = kScanChunk / 256;
     const int base = bx_ * kScanChunk + threadIdx.x * PER;
+    int before;
+    if (prefixed) {
+        before = bsum[bx_];
+    } else {
+        int t = 0;
+        for (int b = threadIdx.x; b < bx_; b += blockDim.x) t += bsum[b];
+        int tot;
+        block_excl_scan(t, sm, tot);
+        before = tot;
+    }
     int v[PER], s = 0;
     for (int q = 0; q < PER; ++q) {
         v[q] = base + q < ncells ? hist[base + q] : 0;
         s += v[q];
     }
     int total;
-    int run = block_excl_scan(s, sm, total) + bsum[bx_];
+    int run = block_excl_scan(s, sm, total) + before;
     for (int q = 0; q < PER; ++q) {
         if (base + q < ncells) {
             offs[base + q] = run;
@@ -563,7 +572,8 @@ __device__ __forceinline__ void scan_apply_kernel_body(int* __restrict__ hist, i
 
 static __global__ void scan_apply_kernel(int* __restrict__ hist, int ncells, const int* __restrict__ bsum,
                                   int* __restrict__ offs) {
-    scan_apply_kernel_body(hist, ncells, bsum, offs, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+    scan_apply_kernel_body(hist, ncells, bsum, offs, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x,
+                           false);
 }
 
 __device__ __forceinline__ void iota_kernel_body(int* ids, int64_t N,
@@ -592,6 +602,42 @@ template <typename T, int CP>
 static __global__ void convert_out_perm_kernel(const T* __restrict__ src, const int* __restrict__ ids, double* __restrict__ dst,
                                         int64_t N, int C) {
     convert_out_perm_kernel_body<T, CP>(src, ids, dst, N, C, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// ------------------------------------------------------------------ half map alone
+
+// The dual half map A applied in place to every particle (one thread per
+// particle, 128-bit loads and stores), with the value-part extrema of the new
+// positions for the next grid geometry: the opening pass of a run.
+template <typename T, int C, int CP>
+static __global__ void __launch_bounds__(256) halfmap_kernel(T* __restrict__ state, int64_t N, const MapCoef<T, CP> A,
+                                                             Ord<T>* __restrict__ mm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
+    T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
+    if (i < N) {
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            T x[CP], p[CP];
+            ldv<T, CP>(state + ((2 * pl) * N + i) * CP, x);
+            ldv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
+            const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
+            const T x0 = x[0], p0 = p[0];
+#pragma unroll
+            for (int k = 1; k < CP; ++k) {
+                const T xk = x[k], pk = p[k];
+                x[k] = fma(a0, xk, fma(b0, pk, fma(A.m[pl][0][k], x0, A.m[pl][1][k] * p0)));
+                p[k] = fma(c0, xk, fma(d0, pk, fma(A.m[pl][2][k], x0, A.m[pl][3][k] * p0)));
+            }
+            x[0] = fma(a0, x0, b0 * p0);
+            p[0] = fma(c0, x0, d0 * p0);
+            stv<T, CP>(state + ((2 * pl) * N + i) * CP, x);
+            stv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
+            mn[pl] = x[0];
+            mx[pl] = x[0];
+        }
+    }
+    block_minmax<T>(mn, mx, mm);
 }
 
 // ------------------------------------------------------------------ period boundary: moments + half map
