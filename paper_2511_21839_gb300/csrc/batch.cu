@@ -19,6 +19,8 @@
 #include <map>
 #include <new>
 #include <vector>
+#include <string>
+#include <mutex>
 
 #include "ad_pic.h"
 #include "field_dev.cuh"
@@ -674,7 +676,7 @@ int enqueue(ad_pic_batch* b, int mode, const RunSpec& rs) {
 
 // time one kick of the real batch in each mode on a snapshot of the particles; keep the fastest
 template <typename T>
-int autotune(ad_pic_batch* b, const RunSpec& base) {
+int autotune_measure(ad_pic_batch* b, const RunSpec& base) {
     size_t need = 0;
     for (ad_pic* h : b->h) need += sizeof(T) * 6 * h->N * kCP;
     if (need > b->snapshot_bytes) {
@@ -729,6 +731,52 @@ int autotune(ad_pic_batch* b, const RunSpec& base) {
     cudaEventDestroy(e1);
     b->tuned_mode = best_mode;
     return AD_PIC_OK;
+}
+
+// Tuned modes of earlier batches with the same composition (grid size and
+// particle-count octave of every instance) on the same device: a batch like
+// one already timed reuses its choice instead of timing the modes again.
+struct TuneEntry {
+    int mode;
+    double ms[4];
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune_cache;
+
+std::string tune_key(const ad_pic_batch* b) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::map<std::pair<int, int>, int> counts;
+    for (const ad_pic* h : b->h) {
+        int oct = 0;
+        while (((int64_t)1 << (oct + 1)) <= h->N) ++oct;
+        counts[{h->nx, oct}]++;
+    }
+    std::string k = std::to_string(dev) + "|" + std::to_string(b->h[0]->prec) + "|";
+    for (const auto& kv : counts)
+        k += std::to_string(kv.first.first) + "/" + std::to_string(kv.first.second) + "x" + std::to_string(kv.second) + ";";
+    return k;
+}
+
+template <typename T>
+int autotune(ad_pic_batch* b, const RunSpec& base) {
+    const std::string key = tune_key(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->tuned_mode = it->second.mode;
+            for (int m = 0; m < 4; ++m) b->tune_ms[m] = it->second.ms[m];
+            return AD_PIC_OK;
+        }
+    }
+    const int st = autotune_measure<T>(b, base);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    TuneEntry e;
+    e.mode = b->tuned_mode;
+    for (int m = 0; m < 4; ++m) e.ms[m] = b->tune_ms[m];
+    g_tune_cache[key] = e;
+    return st;
 }
 
 template <typename T>

@@ -112,3 +112,35 @@ def test_batch_rejects_unsupported(adpic):
     with pytest.raises(adpic.AdPicError) as e:
         adpic.Batch([(32, 32, 16)], [100])
     assert e.value.status == -1
+
+
+def test_tuning_is_cached_for_batches_of_the_same_composition(adpic):
+    """A second batch with the same grids and particle-count octaves reuses the first one's tuned mode
+    and timings instead of timing the modes again, and still matches the single-instance runs."""
+    params, npart, grids = scan_instances(4, seed=9)
+    w = I.workload("fodo_10k_32")
+
+    def make():
+        b = adpic.Batch(grids, npart)
+        for i, p in enumerate(params):
+            b.set_beam(i, w.beam, I.normals(300 + i, npart[i]))
+            b.set_lattice(i, I.Lattice.from_params(p))
+        return b
+
+    b1 = make()
+    b1.run(2)
+    m1, ms1 = b1.tuning()
+    b1.close()
+    b2 = make()
+    b2.run(2)
+    m2, ms2 = b2.tuning()
+    assert m2 == m1 and np.array_equal(ms1, ms2)
+    sim = adpic.ADPIC(grids[0], npart[0], 7, adpic.AD_PIC_FP32_MIXED)
+    sim.set_beam(w.beam, I.normals(300, npart[0]))
+    sim.set_lattice(I.Lattice.from_params(params[0]))
+    sim.run(2)
+    v1, d1 = sim.moments()
+    v2, d2 = b2.moments(0)
+    assert rel_eps(v2, v1).max() < 1e-6 and rel_grad(d2, d1).max() < 1e-4
+    sim.close()
+    b2.close()
