@@ -460,7 +460,7 @@ FFTDims h_dims(int n) {
 template <typename T>
 size_t lane_smem(int n) {
     const size_t dct = sizeof(T) * ((size_t)(n + 1) * (n + 1) + (size_t)kDctLines * (n + 2));
-    const size_t dep = sizeof(T) * (size_t)8 * 8 * kCP * 33;    // deposit tiles of 8 warps
+    const size_t dep = 8 * dep_tile_bytes_per_warp<kCP, T>();    // deposit tiles of 8 warps
     const size_t slab = fft_slab_smem<T>(h_dims(n));
     return std::max(std::max(slab, dep), dct);
 }
@@ -469,7 +469,7 @@ size_t lane_smem(int n) {
 template <typename T>
 size_t job_smem(int job, int n) {
     switch (job) {
-        case J_DEPOSIT: return sizeof(T) * (size_t)8 * 8 * kCP * 33;
+        case J_DEPOSIT: return 8 * dep_tile_bytes_per_warp<kCP, T>();
         case J_DCTX:
         case J_DCTY:
         case J_DCTZ: return sizeof(T) * ((size_t)(n + 1) * (n + 1) + (size_t)kDctLines * (n + 2));

@@ -110,7 +110,7 @@ void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int 
     if (N <= 0) return;
     // warp-sorted, on-chip summed deposition (see deposit_tile_body)
     constexpr int W = dep_tile_warps<CP, T>();
-    const size_t sm = sizeof(T) * (size_t)W * 8 * CP * 33;
+    const size_t sm = (size_t)W * dep_tile_bytes_per_warp<CP, T>();
     const int64_t warps = (N + 31) / 32;
     deposit_tile_kernel<T, C, CP, W><<<(unsigned)((warps + W - 1) / W), W * 32, sm, s>>>(state, N, geom, nx, ny, nz,
                                                                                        qm, rho, err, sb);
@@ -120,7 +120,7 @@ template <typename T, int C, int CP>
 void setup_deposit() {
     constexpr int W = dep_tile_warps<CP, T>();
     cudaFuncSetAttribute(deposit_tile_kernel<T, C, CP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (size_t)W * 8 * CP * 33));
+                         (int)((size_t)W * dep_tile_bytes_per_warp<CP, T>()));
 }
 
 // ------------------------------------------------------------------ instantiations

@@ -820,22 +820,29 @@ static __global__ void moments_reduce_kernel(const double* __restrict__ partial,
 
 // ------------------------------------------------------------------ warp-sorted deposition
 
+// row stride of a lane's node records in the deposit tile (16-byte aligned;
+// 4 mod 32 words apart so the vector stores of 8 lanes hit distinct banks)
+template <int CP>
+__host__ __device__ constexpr int dep_tile_stride() { return 8 * CP + 4; }
+template <int CP, typename T>
+__host__ __device__ constexpr size_t dep_tile_bytes_per_warp() { return sizeof(T) * 32 * dep_tile_stride<CP>(); }
+template <int CP, typename T>
+__host__ __device__ constexpr int dep_tile_warps() {
+    return (dep_tile_bytes_per_warp<CP, T>() * 8 <= 72 * 1024) ? 8 : ((dep_tile_bytes_per_warp<CP, T>() * 4 <= 72 * 1024) ? 4 : 2);
+}
+
 // Deposition with the summation over particles done on chip before the atomics.
 // Each warp takes 32 consecutive particles and sorts them by cell with a
 // bitonic network on the keys (cell << 5 | lane), so the particles of one cell
 // occupy consecutive lanes. Every lane writes its particle's 8 node records
-// (8 x CP values) as a column of a per-warp shared tile [8 CP][33] (odd
-// stride: conflict-free both ways); then lane j owns tile rows j, j + 32, ...
-// (node nd = row / CP, channel row % CP) and, for each run of lanes sharing a
-// cell, sums its rows over the run and issues one scalar atomic per (run, node,
+// (8 x CP values) as a row of a per-warp shared tile [32][8 CP + 4] with vector
+// stores; then lane j owns tile columns j, j + 32, ... (node nd = column / CP,
+// channel column % CP) and, for each run of lanes sharing a cell, sums its
+// columns over the run and issues one scalar atomic per (run, node,
 // channel). Consecutive lanes then address consecutive channels of
 // neighbouring nodes, so one warp atomic touches a few contiguous sectors. The
 // cell sort's rank is the lane's offset in its run plus one counting atomic
 // per run.
-template <int CP, typename T>
-__host__ __device__ constexpr int dep_tile_warps() {
-    return (sizeof(T) * 8 * CP * 33 * 8 <= 72 * 1024) ? 8 : ((sizeof(T) * 8 * CP * 33 * 4 <= 72 * 1024) ? 4 : 2);
-}
 
 template <typename T, int C, int CP, int WARPS>
 __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, int64_t N,
@@ -846,7 +853,8 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T* tile = reinterpret_cast<T*>(smraw) + (size_t)warp * ROWS * 33;
+    constexpr int RS = dep_tile_stride<CP>();
+    T* tile = reinterpret_cast<T*>(smraw) + (size_t)warp * 32 * RS;    // [sorted lane][8 CP (+4)]
     const int64_t i0 = ((int64_t)bx_ * WARPS + warp) * 32;
     if (i0 >= N) return;                                  // whole warp
     const int64_t i = i0 + lane;
@@ -902,7 +910,7 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
             sb.rank[ps] = base + lane - start;
         }
     }
-    // node records of this lane's particle into tile column `lane`
+    // node records of this lane's particle into tile row `lane`
     if (sv) {
         T x[3][CP];
 #pragma unroll
@@ -914,10 +922,11 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
             const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
             const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
             const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
-            T* col = tile + (nd * CP) * 33 + lane;
-            col[0] = qm * (wx * wy * wz);
+            T rec[CP];
+            rec[0] = qm * (wx * wy * wz);
 #pragma unroll
-            for (int k = 1; k < CP; ++k) col[k * 33] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
+            for (int k = 1; k < CP; ++k) rec[k] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
+            stv<T, CP>(tile + lane * RS + nd * CP, rec);
         }
     }
     __syncwarp();
@@ -940,9 +949,9 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
         for (int q = 0; q < RL; ++q) {
             const int r = lane + 32 * q;
             if (r % CP >= C) continue;
-            const T* row = tile + r * 33;
-            T acc = row[s0];
-            for (int j = s0 + 1; j <= s1; ++j) acc += row[j];
+            const T* colr = tile + r;
+            T acc = colr[s0 * RS];
+            for (int j = s0 + 1; j <= s1; ++j) acc += colr[j * RS];
             atomicAdd(base + roff[q], acc);
         }
     }
