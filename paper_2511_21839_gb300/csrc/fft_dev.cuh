@@ -70,11 +70,18 @@ __host__ __device__ constexpr int log2_c(int n) { return n <= 1 ? 0 : 1 + log2_c
 
 // R-point DFT in registers (R <= 16): radix-2 decimation in frequency, natural
 // input order, output X[k] in v[brev(k)]. INV uses the conjugate twiddles.
-template <typename T, int R, bool INV>
+// HZ: the upper half of the inputs is zero, so the first stage only copies
+// and rotates (no additions with zero).
+template <typename T, int R, bool INV, bool HZ = false>
 __device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
 #pragma unroll
     for (int len = R; len >= 2; len >>= 1) {
         const int half = len >> 1;
+        if (HZ && len == R) {
+#pragma unroll
+            for (int j = 0; j < half; ++j) v[j + half] = mul_w16<T, INV>(v[j], j * (16 / len));
+            continue;
+        }
 #pragma unroll
         for (int g = 0; g < R; g += len) {
 #pragma unroll
@@ -116,12 +123,15 @@ __device__ __forceinline__ void step1(V2<T>* buf, int nlines, const V2<T>* twM, 
         const int line = w % nlines, n2 = w / nlines;
         V2<T>* b = buf + line * L::LS + n2;
         V2<T> v[R1];
+        if (half_zero) {
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) {
-            if (half_zero && n1 >= R1 / 2) { v[n1].x = (T)0; v[n1].y = (T)0; }
-            else v[n1] = b[n1 * (R2 + 1)];
+            for (int n1 = 0; n1 < R1 / 2; ++n1) v[n1] = b[n1 * (R2 + 1)];
+            dft_reg<T, R1, INV, true>(v);
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = b[n1 * (R2 + 1)];
+            dft_reg<T, R1, INV>(v);
         }
-        dft_reg<T, R1, INV>(v);
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) {
             V2<T> y = v[brev_c(k1, log2_c(R1))];
@@ -411,6 +421,7 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho
     __syncthreads();
     const int y0 = bx_ * yt, z = by_;
     const T* src = rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP;
+#pragma unroll 8
     for (int t = threadIdx.x; t < yt * d.nx * d.CP; t += blockDim.x) {
         const int c = t % d.CP, x = (t / d.CP) % d.nx, r = t / (d.CP * d.nx);
         if (c >= d.C) continue;
@@ -526,6 +537,7 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
     for (int j = threadIdx.x; j < MY; j += blockDim.x) tY[j] = twy[j];
     for (int j = threadIdx.x; j < MZ; j += blockDim.x) tZ[j] = twz[j];
     V2<T>* slab = X1 + ((int64_t)p * d.Mx + kx) * nz * ny;
+#pragma unroll 8
     for (int t = threadIdx.x; t < nz * ny; t += blockDim.x) {
         const int z = t / ny, y = t % ny;
         A[z * LY::LS + LY::pos(y)] = slab[t];
@@ -627,6 +639,7 @@ __device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__
     const int y0 = bx_ * yt, z = by_;
     const int64_t kstride = (int64_t)d.nz * d.ny;
     const V2<T>* src0 = X1 + (int64_t)z * d.ny + y0;
+#pragma unroll 8
     for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
         const int r = t % yt, rest = t / yt;
         const int kx = rest % M, p = rest / M;
