@@ -71,8 +71,9 @@ __host__ __device__ constexpr int log2_c(int n) { return n <= 1 ? 0 : 1 + log2_c
 // R-point DFT in registers (R <= 16): radix-2 decimation in frequency, natural
 // input order, output X[k] in v[brev(k)]. INV uses the conjugate twiddles.
 // HZ: the upper half of the inputs is zero, so the first stage only copies
-// and rotates (no additions with zero).
-template <typename T, int R, bool INV, bool HZ = false>
+// and rotates (no additions with zero). HO: only the outputs X[k], k < R/2
+// are wanted (v at even positions), so the last stage skips the differences.
+template <typename T, int R, bool INV, bool HZ = false, bool HO = false>
 __device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
 #pragma unroll
     for (int len = R; len >= 2; len >>= 1) {
@@ -80,6 +81,14 @@ __device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
         if (HZ && len == R) {
 #pragma unroll
             for (int j = 0; j < half; ++j) v[j + half] = mul_w16<T, INV>(v[j], j * (16 / len));
+            continue;
+        }
+        if (HO && len == 2) {
+#pragma unroll
+            for (int g = 0; g < R; g += 2) {
+                v[g].x = v[g].x + v[g + 1].x;
+                v[g].y = v[g].y + v[g + 1].y;
+            }
             continue;
         }
 #pragma unroll
@@ -147,14 +156,15 @@ __device__ __forceinline__ void step1(V2<T>* buf, int nlines, const V2<T>* twM, 
 
 // Step 2 loads for work item w of nlines * R1 (line = w % nlines, k1 = w / nlines)
 // the R2 values of row k1 and transforms them; X[k1 + R1 k2] = v[brev(k2)].
-template <typename T, int M, bool INV>
+// HO: only X[k1 + R1 k2] with k2 < R2/2 are used.
+template <typename T, int M, bool INV, bool HO = false>
 __device__ __forceinline__ void step2(const V2<T>* buf, int line, int k1, V2<T> (&v)[Lay<M>::R2]) {
     using L = Lay<M>;
     constexpr int R2 = L::R2;
     const V2<T>* b = buf + line * L::LS + k1 * (R2 + 1);
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = b[n2];
-    dft_reg<T, R2, INV>(v);
+    dft_reg<T, R2, INV, false, HO>(v);
 }
 
 template <typename T>
@@ -246,7 +256,7 @@ __device__ __forceinline__ void ffty_kernel_body(const V2<T>* __restrict__ in, V
     for (int w = threadIdx.x; w < kTile * L::R1; w += blockDim.x) {
         const int j = w % kTile, k1 = w / kTile;
         V2<T> v[L::R2];
-        step2<T, M, INV>(buf, j, k1, v);
+        step2<T, M, INV, INV>(buf, j, k1, v);       // the inverse keeps y < ny
 #pragma unroll
         for (int k2 = 0; k2 < L::R2; ++k2) {
             const int y = k1 + L::R1 * k2;
@@ -316,7 +326,7 @@ __device__ __forceinline__ void fftz_kernel_body(V2<T>* __restrict__ X2, const T
     for (int w = threadIdx.x; w < kTile * L::R1; w += blockDim.x) {
         const int j = w % kTile, k1 = w / kTile;
         V2<T> v[L::R2];
-        step2<T, M, true>(buf, j, k1, v);
+        step2<T, M, true, true>(buf, j, k1, v);     // keeps z < nz
 #pragma unroll
         for (int k2 = 0; k2 < L::R2; ++k2) {
             const int z = k1 + L::R1 * k2;
@@ -367,7 +377,7 @@ __device__ __forceinline__ void fftx_inv_kernel_body(const V2<T>* __restrict__ X
     for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
         const int line = w % nl, k1 = w / nl;
         V2<T> v[L::R2];
-        step2<T, M, true>(buf, line, k1, v);
+        step2<T, M, true, true>(buf, line, k1, v);   // keeps x < nx
         const int r = line / d.npair, p = line % d.npair;
         const T sa = norm * chan_scale<T>(chmax, 2 * p, true);
         const T sb = norm * chan_scale<T>(chmax, 2 * p + 1, true);
@@ -494,16 +504,16 @@ __device__ __forceinline__ void inv_half1_store(V2<T>* line, int k1, V2<T> (&u)[
 }
 
 // second half of the inverse for one n2: R1-point inverse DFT over k1 of
-// line[k1 (R2+1) + n2]; out[n1] = y[R2 n1 + n2]
+// line[k1 (R2+1) + n2]; out[n1] = y[R2 n1 + n2] for n1 < R1/2 (the kept half)
 template <typename T, int M>
 __device__ __forceinline__ void inv_half2(const V2<T>* line, int n2, V2<T> (&out)[Lay<M>::R1]) {
     using L = Lay<M>;
     V2<T> v[L::R1];
 #pragma unroll
     for (int k1 = 0; k1 < L::R1; ++k1) v[k1] = line[k1 * (L::R2 + 1) + n2];
-    dft_reg<T, L::R1, true>(v);
+    dft_reg<T, L::R1, true, false, true>(v);     // callers keep n1 < R1/2
 #pragma unroll
-    for (int n1 = 0; n1 < L::R1; ++n1) out[n1] = v[brev_c(n1, log2_c(L::R1))];
+    for (int n1 = 0; n1 < L::R1 / 2; ++n1) out[n1] = v[brev_c(n1, log2_c(L::R1))];
 }
 
 template <int M>
@@ -652,7 +662,7 @@ __device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__
         const int line = w % nl, k1 = w / nl;
         const int r = line % yt, p = line / yt;
         V2<T> v[L::R2];
-        step2<T, M, true>(buf, line, k1, v);
+        step2<T, M, true, true>(buf, line, k1, v);   // keeps x < nx
         const T sa = sc[2 * p], sb = sc[2 * p + 1];
 #pragma unroll
         for (int k2 = 0; k2 < L::R2; ++k2) {
