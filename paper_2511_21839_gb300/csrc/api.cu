@@ -272,8 +272,14 @@ struct Impl {
         launch_deposit<T, C, CP>(buf(h, from), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
                                  sortbuf(h, from), s);
         tend(h, K_DEPOSIT, cap);
+        // cell offsets for the push on the side stream, behind the Green's function
+        cudaEventRecord(h->ev_dep, s);
+        cudaStreamWaitEvent(h->side, h->ev_dep, 0);
+        tbegin(h, K_MISC, cap, h->side);
+        launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, h->side);
+        tend(h, K_MISC, cap, h->side);
+        cudaEventRecord(h->ev_scan, h->side);
         tbegin(h, K_MISC, cap);
-        launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, s);
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
         tend(h, K_MISC, cap);
         cudaStreamWaitEvent(s, h->ev_join, 0);
@@ -286,6 +292,7 @@ struct Impl {
         tbegin(h, K_FIELD, cap);
         launch_field<T>((const T*)h->phi, h->geom, h->nx, h->ny, h->nz, CP, (T*)h->E, s);
         tend(h, K_FIELD, cap);
+        cudaStreamWaitEvent(s, h->ev_scan, 0);     // the push reads the cell offsets
     }
 
     static void record(ad_pic* h, int r, bool cap) {
@@ -761,7 +768,9 @@ int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int
     h->stream = h->own_stream;
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_dep, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_scan, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         ad_pic_destroy(h);
         return AD_PIC_ERR_CUDA;
@@ -926,6 +935,8 @@ void ad_pic_destroy(ad_pic* h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_dep) cudaEventDestroy(h->ev_dep);
+    if (h->ev_scan) cudaEventDestroy(h->ev_scan);
     cudaGetLastError();
     delete h;
 }

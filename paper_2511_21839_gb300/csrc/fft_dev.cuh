@@ -121,15 +121,39 @@ struct Lay {
     __device__ static __forceinline__ int pos(int n) { return (n / R2) * (R2 + 1) + n % R2; }
 };
 
+// q = n / d and n - q d for 0 <= n < 2^31 and a divisor d >= 1 that is only
+// known at run time, by one multiply-high with a precomputed magic number
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, q = (umulhi(m, n) + n) >> l.
+struct DivMod {
+    int d, l;
+    unsigned m;
+    __device__ int div(int n) const { return (int)((__umulhi(m, (unsigned)n) + (unsigned)n) >> l); }
+};
+__device__ __forceinline__ DivMod divmod_of(int d) {
+    DivMod r;
+    r.d = d;
+    r.l = 32 - __clz(d - 1);
+    r.m = (unsigned)((((unsigned long long)1 << 32) * (((unsigned long long)1 << r.l) - (unsigned)d)) / (unsigned)d + 1);
+    return r;
+}
+__device__ __forceinline__ int lcount(int n) { return n; }
+__device__ __forceinline__ int lcount(const DivMod& n) { return n.d; }
+__device__ __forceinline__ int ldiv(int w, int n) { return w / n; }
+__device__ __forceinline__ int ldiv(int w, const DivMod& n) { return n.div(w); }
+
 // Step 1 for work item w of nlines * R2 (line = w % nlines, n2 = w / nlines):
 // R1-point DFT over n1 in place, times W_M^(n2 k1). `half_zero`: inputs with
-// n >= M/2 are zero (zero padding) and not read.
-template <typename T, int M, bool INV>
-__device__ __forceinline__ void step1(V2<T>* buf, int nlines, const V2<T>* twM, bool half_zero) {
+// n >= M/2 are zero (zero padding) and not read. `nlines` is an int (folded
+// when it is a constant of the caller) or a DivMod.
+template <typename T, int M, bool INV, typename NL = int>
+__device__ __forceinline__ void step1(V2<T>* buf, NL nlines, const V2<T>* twM, bool half_zero) {
     using L = Lay<M>;
     constexpr int R1 = L::R1, R2 = L::R2;
-    for (int w = threadIdx.x; w < nlines * R2; w += blockDim.x) {
-        const int line = w % nlines, n2 = w / nlines;
+    const int nl = lcount(nlines);
+    for (int w = threadIdx.x; w < nl * R2; w += blockDim.x) {
+        const int n2 = ldiv(w, nlines), line = w - n2 * nl;
         V2<T>* b = buf + line * L::LS + n2;
         V2<T> v[R1];
         if (half_zero) {
@@ -430,23 +454,30 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho
     if (threadIdx.x < d.CP) sc[threadIdx.x] = chan_scale<T>(chmax, threadIdx.x, false);
     __syncthreads();
     const int y0 = bx_ * yt, z = by_;
-    const T* src = rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP;
+    // channel pairs (2p, 2p+1) of a node are one V2 load; nx = M/2, CP and yt
+    // are powers of two, so the indices are shifts and masks
+    constexpr int LNX = log2_c(M) - 1;
+    const int lpn = __ffs(d.CP) - 2;                  // log2(CP / 2)
+    const int lyt = __ffs(yt) - 1;
+    const V2<T>* src = reinterpret_cast<const V2<T>*>(rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP);
 #pragma unroll 8
-    for (int t = threadIdx.x; t < yt * d.nx * d.CP; t += blockDim.x) {
-        const int c = t % d.CP, x = (t / d.CP) % d.nx, r = t / (d.CP * d.nx);
-        if (c >= d.C) continue;
-        const T v = src[t] * sc[c];
-        V2<T>& dst = buf[((c >> 1) * yt + r) * L::LS + L::pos(x)];
-        if (c & 1) dst.y = v; else dst.x = v;
+    for (int t = threadIdx.x; t < (yt << (LNX + lpn)); t += blockDim.x) {
+        const int p = t & ((1 << lpn) - 1), x = (t >> lpn) & ((1 << LNX) - 1), r = t >> (lpn + LNX);
+        if (p >= d.npair) continue;
+        V2<T> v = src[t];
+        v.x *= sc[2 * p];
+        v.y *= sc[2 * p + 1];
+        buf[(p * yt + r) * L::LS + L::pos(x)] = v;
     }
     __syncthreads();
-    step1<T, M, false>(buf, nl, twM, true);
+    step1<T, M, false>(buf, divmod_of(nl), twM, true);
     __syncthreads();
     const int64_t kstride = (int64_t)d.nz * d.ny;
     V2<T>* dst0 = X1 + (int64_t)z * d.ny + y0;
+    // work items with r fastest (consecutive y in the stores), then k1, then p
     for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
-        const int line = w % nl, k1 = w / nl;
-        const int r = line % yt, p = line / yt;
+        const int r = w & (yt - 1), k1 = (w >> lyt) & (L::R1 - 1), p = w >> (lyt + log2_c(L::R1));
+        const int line = p * yt + r;
         V2<T> v[L::R2];
         step2<T, M, false>(buf, line, k1, v);
         V2<T>* o = dst0 + (int64_t)p * M * kstride + r;
@@ -543,7 +574,7 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
     V2<T>* A = tZ + MZ;                        // [nz][LY::LS]
     V2<T>* B = A + d.nz * LY::LS;              // [KC][LZ::LS]
     const int kx = bx_, p = by_;
-    const int nz = d.nz, ny = d.ny;
+    constexpr int nz = MZ / 2, ny = MY / 2;         // zero-padded lengths M = 2n
     for (int j = threadIdx.x; j < MY; j += blockDim.x) tY[j] = twy[j];
     for (int j = threadIdx.x; j < MZ; j += blockDim.x) tZ[j] = twz[j];
     V2<T>* slab = X1 + ((int64_t)p * d.Mx + kx) * nz * ny;
@@ -624,7 +655,7 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
 }
 
 template <typename T, int MY, int MZ>
-static __global__ void __launch_bounds__(512) fftyz_kernel(V2<T>* __restrict__ X1, const T* __restrict__ Ghat, FFTDims d,
+static __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) fftyz_kernel(V2<T>* __restrict__ X1, const T* __restrict__ Ghat, FFTDims d,
                                                              const V2<T>* __restrict__ twy, const V2<T>* __restrict__ twz) {
     fftyz_kernel_body<T, MY, MZ>(X1, Ghat, d, twy, twz, (int)blockIdx.x, (int)blockIdx.y);
 }
@@ -649,18 +680,19 @@ __device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__
     const int y0 = bx_ * yt, z = by_;
     const int64_t kstride = (int64_t)d.nz * d.ny;
     const V2<T>* src0 = X1 + (int64_t)z * d.ny + y0;
+    const int lyt = __ffs(yt) - 1;                    // yt, nx, CP are powers of two
 #pragma unroll 8
     for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
-        const int r = t % yt, rest = t / yt;
-        const int kx = rest % M, p = rest / M;
+        const int r = t & (yt - 1), rest = t >> lyt;
+        const int kx = rest & (M - 1), p = rest >> log2_c(M);
         buf[(p * yt + r) * L::LS + L::pos(kx)] = src0[((int64_t)p * M + kx) * kstride + r];
     }
     __syncthreads();
-    step1<T, M, true>(buf, nl, twM, false);
+    step1<T, M, true>(buf, divmod_of(nl), twM, false);
     __syncthreads();
     for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
-        const int line = w % nl, k1 = w / nl;
-        const int r = line % yt, p = line / yt;
+        const int r = w & (yt - 1), k1 = (w >> lyt) & (L::R1 - 1), p = w >> (lyt + log2_c(L::R1));
+        const int line = p * yt + r;
         V2<T> v[L::R2];
         step2<T, M, true, true>(buf, line, k1, v);   // keeps x < nx
         const T sa = sc[2 * p], sb = sc[2 * p + 1];
@@ -676,10 +708,10 @@ __device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__
     }
     __syncthreads();
     T* dst = phi + ((int64_t)z * d.ny + y0) * d.nx * d.CP;
-    const int rowlen = d.nx * d.CP;
-    for (int t = threadIdx.x; t < yt * rowlen; t += blockDim.x) {
-        const int r = t / rowlen, rem = t % rowlen;
-        const int c = rem % d.CP;
+    const int lrow = log2_c(M) - 1 + __ffs(d.CP) - 1;      // log2(nx CP)
+    for (int t = threadIdx.x; t < (yt << lrow); t += blockDim.x) {
+        const int r = t >> lrow, rem = t & ((1 << lrow) - 1);
+        const int c = rem & (d.CP - 1);
         dst[t] = c < d.C ? stage[r * SR + rem] : (T)0;
     }
 }

@@ -13,7 +13,13 @@ void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geo
 
 template <typename T>
 void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream_t s) {
-    chmax_kernel<T><<<152 * 2, 256, 0, s>>>(rho, nodes, CP, chmax);
+    // rho is cudaMalloc'ed (256-byte aligned) with CP in {8, 16}
+    if (CP == 8)
+        chmax_vec_kernel<T, 8><<<152 * 2, 256, 0, s>>>(rho, nodes, chmax);
+    else if (CP == 16)
+        chmax_vec_kernel<T, 16><<<152 * 2, 256, 0, s>>>(rho, nodes, chmax);
+    else
+        chmax_kernel<T><<<152 * 2, 256, 0, s>>>(rho, nodes, CP, chmax);
 }
 
 template <typename T>

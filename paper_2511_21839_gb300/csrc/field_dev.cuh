@@ -6,6 +6,8 @@
 // dual channels, and the central finite-difference field.
 #include <cfloat>
 #include <cmath>
+#include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -108,6 +110,56 @@ __device__ __forceinline__ void chmax_kernel_body(const T* __restrict__ rho, int
 template <typename T>
 static __global__ void chmax_kernel(const T* __restrict__ rho, int64_t nodes, int CP, Ord<T>* chmax) {
     chmax_kernel_body<T>(rho, nodes, CP, chmax, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// The same maxima with 16-byte loads: vector j of rho holds the EPV channels
+// starting at (j % VPN) EPV of node j / VPN. The grid stride and the block
+// size are multiples of VPN, so a thread's channel group is that of its lane
+// and stays fixed; lanes whose indices differ by a multiple of VPN share it.
+template <typename T, int CP>
+static __global__ void __launch_bounds__(256) chmax_vec_kernel(const T* __restrict__ rho, int64_t nodes, Ord<T>* chmax) {
+    constexpr int EPV = 16 / (int)sizeof(T), VPN = CP / EPV;
+    static_assert(CP % EPV == 0 && (VPN & (VPN - 1)) == 0 && VPN <= 32, "channel groups");
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const V* r = reinterpret_cast<const V*>(rho);
+    const int64_t nv = nodes * VPN;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    T m[EPV];
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) m[e] = (T)0;
+    auto upd = [&](const V& a) {
+        T v[EPV];
+        memcpy(v, &a, sizeof(V));
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) m[e] = fmax(m[e], fabs(v[e]));
+    };
+    for (; t + 3 * stride < nv; t += 4 * stride) {
+        V a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = r[t + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) upd(a[u]);
+    }
+    for (; t < nv; t += stride) upd(r[t]);
+#pragma unroll
+    for (int o = VPN; o < 32; o <<= 1)
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) m[e] = fmax(m[e], __shfl_xor_sync(0xffffffffu, m[e], o));
+    __shared__ T wm[8][CP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane < VPN)
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) wm[w][lane * EPV + e] = m[e];
+    __syncthreads();
+    if ((int)threadIdx.x < CP) {
+        T b = wm[0][threadIdx.x];
+        for (int j = 1; j < nw; ++j) b = fmax(b, wm[j][threadIdx.x]);
+        if constexpr (sizeof(T) == 4)
+            atomicMax(&chmax[threadIdx.x], __float_as_uint(b));
+        else
+            atomicMax(&chmax[threadIdx.x], (unsigned long long)__double_as_longlong(b));
+    }
 }
 
 // ------------------------------------------------------------------ Green's function

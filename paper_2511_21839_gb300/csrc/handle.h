@@ -26,10 +26,12 @@ struct ad_pic {
     bool first_record = true;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     // the Green's function depends on the grid geometry only: it runs on a side
-    // stream concurrently with deposit, scan and channel maxima (fork after the
-    // geometry kernel, join before the convolution; captured graphs keep both branches)
+    // stream concurrently with deposit and channel maxima (fork after the
+    // geometry kernel, join before the convolution). The cell-offset scan is
+    // needed by the push only: it follows on the side stream after the deposit
+    // (ev_dep) and joins before the push (ev_scan). Captured graphs keep the branches.
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dep = nullptr, ev_scan = nullptr;
     // device memory
     void* state = nullptr;
     void* state2 = nullptr;      // the other buffer of the cell-sorting push
