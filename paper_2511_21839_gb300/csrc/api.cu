@@ -173,7 +173,8 @@ struct Impl {
     // gather + kick + map A from buffer `from` into the other one, in cell-sorted order
     static void push(ad_pic* h, int& from, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track) {
         launch_push<T, C, CP>(buf(h, from), buf(h, 1 - from), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, A,
-                              K, track, (Ord<T>*)h->mm, h->err, sortbuf(h, from), h->stream);
+                              K, track, (Ord<T>*)h->mm, h->err, sortbuf(h, from), track ? gfuse(h) : no_fuse(),
+                              h->stream);
         from = 1 - from;
     }
 
@@ -249,13 +250,29 @@ struct Impl {
         return d;
     }
 
-    // geometry -> deposit -> Green -> convolution -> field for the current state
+    // the fused geometry step for the kernel that produces the extrema
+    static GeomFuse gfuse(ad_pic* h) {
+        GeomFuse f;
+        f.count = h->gcount;
+        f.nx = h->nx; f.ny = h->ny; f.nz = h->nz; f.CP = CP;
+        f.gamma0 = h->gamma0;
+        f.g = h->geom;
+        f.chmax = h->chmax;
+        return f;
+    }
+    static GeomFuse no_fuse() {
+        GeomFuse f{};
+        f.count = nullptr;
+        return f;
+    }
+
+    // deposit -> Green -> convolution -> field for the current state. The grid
+    // geometry was derived by the last block of the kernel before (the push
+    // that tracked the extrema, or the half map at a run or period start).
+    // The convolution leaves rho zero for the next deposit.
     static void enqueue_field(ad_pic* h, int from, bool cap) {
         cudaStream_t s = h->stream;
         const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
-        tbegin(h, K_GEOM, cap);
-        launch_geom<T>((Ord<T>*)h->mm, h->nx, h->ny, h->nz, h->gamma0, h->geom, (Ord<T>*)h->chmax, CP, s);
-        tend(h, K_GEOM, cap);
         // Green's function on the side stream (it needs only the geometry)
         cudaEventRecord(h->ev_fork, s);
         cudaStreamWaitEvent(h->side, h->ev_fork, 0);
@@ -265,9 +282,6 @@ struct Impl {
                         fft_slab_path<T>(dims(h)) ? 1 : 0, h->side);
         tend(h, K_GREEN, cap, h->side);
         cudaEventRecord(h->ev_join, h->side);
-        tbegin(h, K_MISC, cap);
-        cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s);
-        tend(h, K_MISC, cap);
         tbegin(h, K_DEPOSIT, cap);
         launch_deposit<T, C, CP>(buf(h, from), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
                                  sortbuf(h, from), s);
@@ -285,7 +299,7 @@ struct Impl {
         cudaStreamWaitEvent(s, h->ev_join, 0);
         tbegin(h, K_FFT, cap);
         FFTDims d = dims(h);
-        launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
+        launch_fft_conv<T>((T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
                            (const Ord<T>*)h->chmax, s);
         tend(h, K_FFT, cap);
@@ -301,9 +315,9 @@ struct Impl {
         tend(h, K_MISC, cap);
     }
 
-    // kernels launched by one enqueue_field (geometry 1, deposit 1, scan 2,
-    // chmax 1, Green's function 5, convolution 3 or 5, field 1; the memset is not a kernel)
-    static int field_launches(ad_pic* h) { return 11 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
+    // kernels launched by one enqueue_field (deposit 1, scan 2, chmax 1,
+    // Green's function 5, convolution 3 or 5, field 1)
+    static int field_launches(ad_pic* h) { return 10 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
 
     // the launch sequence of one run; returns the number of moment records
     // `from` is the buffer holding the particles at the start; each push moves
@@ -315,14 +329,16 @@ struct Impl {
         cudaMemsetAsync(h->err, 0, sizeof(int), s);
         if (n == 0) {
             tbegin(h, K_BOUNDARY, cap);
-            launch_boundary<T, C, CP>(buf(h, from), h->N, identity(), false, true, h->partial, nb, (Ord<T>*)h->mm, s);
+            launch_boundary<T, C, CP>(buf(h, from), h->N, identity(), false, true, h->partial, nb, (Ord<T>*)h->mm,
+                                      no_fuse(), s);
             tend(h, K_BOUNDARY, cap);
             record(h, nrec++, cap);
             return nrec;
         }
         // opening half map M1(tau/2) of the first kick (+ initial moments)
         tbegin(h, K_BOUNDARY, cap);
-        launch_boundary<T, C, CP>(buf(h, from), h->N, half(h, g0), true, first, h->partial, nb, (Ord<T>*)h->mm, s);
+        launch_boundary<T, C, CP>(buf(h, from), h->N, half(h, g0), true, first, h->partial, nb, (Ord<T>*)h->mm,
+                                  gfuse(h), s);
         tend(h, K_BOUNDARY, cap);
         if (first) record(h, nrec++, cap);
         for (int i = 0; i < n; ++i) {
@@ -338,7 +354,7 @@ struct Impl {
                 tend(h, K_PUSH, cap);
                 tbegin(h, K_BOUNDARY, cap);
                 launch_boundary<T, C, CP>(buf(h, from), h->N, half(h, g + 1), !last, true, h->partial, nb,
-                                          (Ord<T>*)h->mm, s);
+                                          (Ord<T>*)h->mm, last ? no_fuse() : gfuse(h), s);
                 tend(h, K_BOUNDARY, cap);
                 record(h, nrec++, cap);
             } else {
@@ -451,8 +467,8 @@ struct Impl {
         if (n == 0) return 2 * (on(K_BOUNDARY) + on(K_MISC));
         int pend = nrec - (first ? 1 : 0);   // boundary+record pairs inside the loop
         int e = on(K_BOUNDARY) + (first ? on(K_MISC) : 0);
-        e += n * (on(K_GEOM) + 2 * on(K_MISC) + on(K_DEPOSIT) + on(K_GREEN) + on(K_FFT) + on(K_FIELD) + on(K_PUSH));
-        // (the scan and chmax share one MISC event pair; the memset has its own)
+        e += n * (2 * on(K_MISC) + on(K_DEPOSIT) + on(K_GREEN) + on(K_FFT) + on(K_FIELD) + on(K_PUSH));
+        // (the scan and chmax have one MISC event pair each)
         e += pend * (on(K_BOUNDARY) + on(K_MISC));
         return 2 * e;
     }
@@ -573,8 +589,7 @@ struct Impl {
         const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
         CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
         launch_boundary<T, C, CP>(st(h), h->N, identity(), true, false, h->partial, boundary_blocks(),
-                                  (Ord<T>*)h->mm, s);
-        launch_geom<T>((Ord<T>*)h->mm, h->nx, h->ny, h->nz, h->gamma0, h->geom, (Ord<T>*)h->chmax, CP, s);
+                                  (Ord<T>*)h->mm, gfuse(h), s);     // with the geometry step
         if (which == 0) {
             GeomDev g;
             CK(cudaMemcpyAsync(&g, h->geom, sizeof(g), cudaMemcpyDeviceToHost, s));
@@ -582,7 +597,7 @@ struct Impl {
             for (int d = 0; d < 3; ++d) { out[d] = g.o[d]; out[3 + d] = g.h[d]; }
             return AD_PIC_OK;
         }
-        // the geometry kernel already ran: do not run it twice (it resets the extrema)
+        // rho is zero between kicks (the convolution clears it); cleared here too
         CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s));
         launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
                                  sortbuf(h, h->cur), s);
@@ -591,6 +606,7 @@ struct Impl {
         if (which == 1) {
             buf.resize(nodes * CP);
             CK(cudaMemcpyAsync(buf.data(), h->rho, sizeof(T) * buf.size(), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s));   // no convolution follows
             CK(cudaStreamSynchronize(s));
             grid_out(buf, 1, nodes, out);
             return check_err(h);
@@ -600,7 +616,7 @@ struct Impl {
                         (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2],
                         fft_slab_path<T>(dims(h)) ? 1 : 0, s);
         FFTDims d = dims(h);
-        launch_fft_conv<T>((const T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
+        launch_fft_conv<T>((T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
                            (const Ord<T>*)h->chmax, s);
         if (which == 2) {
@@ -664,10 +680,13 @@ struct Impl {
         r |= dalloc(h, &h->mm, sizeof(Ord<T>) * 6);
         r |= dalloc(h, &h->chmax, sizeof(Ord<T>) * CP);
         r |= dalloc(h, (void**)&h->err, sizeof(int));
+        r |= dalloc(h, (void**)&h->gcount, sizeof(unsigned));
         r |= dalloc(h, (void**)&h->partial, sizeof(double) * boundary_blocks() * 15 * CP);
         if (r) return AD_PIC_ERR_OOM;
         CK(cudaMemsetAsync(h->state, 0, sizeof(T) * 6 * h->N * CP, h->stream));
         CK(cudaMemsetAsync(h->cellcount, 0, sizeof(int) * nodes, h->stream));
+        CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, h->stream));
+        CK(cudaMemsetAsync(h->gcount, 0, sizeof(unsigned), h->stream));
         launch_iota(h->ids[0], h->N, h->stream);
         CK(cudaMemsetAsync(h->E, 0, sizeof(T) * nodes * 3 * CP, h->stream));
         std::vector<Ord<T>> mm0 = {~(Ord<T>)0, ~(Ord<T>)0, ~(Ord<T>)0, 0, 0, 0};

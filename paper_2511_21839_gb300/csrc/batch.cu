@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "ad_pic.h"
+#define ADPIC_RECORD_ACCESS_16
 #include "field_dev.cuh"
 #include "fft_dev.cuh"
 #include "handle.h"
@@ -148,7 +149,7 @@ __device__ __noinline__ void job_fft(int job, const Inst<T>& in, int lb) {
     const FFTDims& d = in.d;
     const int tiles = d.ny / in.yt;
     switch (job) {
-        case J_FFTX: fftx_fwd_t_kernel_body<T, M>(in.rho, in.X1, d, in.tw, in.chmax, in.yt, lb % tiles, lb / tiles); break;
+        case J_FFTX: fftx_fwd_t_kernel_body<T, M>(in.rho, in.X1, d, in.tw, in.chmax, in.yt, false, lb % tiles, lb / tiles); break;
         case J_FFTYZ: fftyz_kernel_body<T, M, M>(in.X1, in.Ghat, d, in.tw, in.tw, lb % d.Mx, lb / d.Mx); break;
         default: fftx_inv_t_kernel_body<T, M>(in.X1, in.phi, d, in.tw, in.chmax, in.yt, lb % tiles, lb / tiles); break;
     }

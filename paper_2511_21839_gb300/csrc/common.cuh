@@ -4,8 +4,8 @@
 //   state  T [6][N][CP]         coordinates (x, px, y, py, z, delta); channel 0 value,
 //                               channels 1..C-1 derivatives, C..CP-1 zero padding so a
 //                               particle's coordinate is 32 B (FP32, CP=8) / 64 B and
-//                               loads are 128-bit
-//   rho    T [nz][ny][nx][CP]   node charges, channel-minor (one 128-bit atomic per 4 channels)
+//                               moves in 32-byte pieces
+//   rho    T [nz][ny][nx][CP]   node charges, channel-minor
 //   phi    T [nz][ny][nx][CP]   potential
 //   E      T [nz][ny][nx][3][CP] rest-frame field; boundary nodes stay zero
 //   X1     V2 [npair][nz][ny][Mx]   spectrum after the x pass (M = 2n, zero padded)
@@ -32,6 +32,125 @@ template <> struct OrdT<float> { using type = unsigned int; };
 template <> struct OrdT<double> { using type = unsigned long long; };
 template <typename T> using Ord = typename OrdT<T>::type;
 
+// ---------------------------------------------------------------- record access
+// A record is the CP channels of one particle coordinate or one grid node:
+// CP * sizeof(T) bytes, 16-byte aligned.
+template <typename T, int CP>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&v)[CP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q) {
+            float4 f = reinterpret_cast<const float4*>(p)[q];
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 2; ++q) {
+            double2 f = reinterpret_cast<const double2*>(p)[q];
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    }
+}
+
+template <typename T, int CP>
+__device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[CP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+    }
+}
+
+// Global accesses of whole records in 32-byte pieces (one request per piece):
+// records are CP * sizeof(T) bytes with CP in {8, 16}, a multiple of 32, and
+// every record starts on a 32-byte boundary of a cudaMalloc'ed array.
+// ldg_v reads through the non-coherent path (data read-only in the kernel),
+// ldr_v through the coherent one, stg_v stores. A translation unit that
+// defines ADPIC_RECORD_ACCESS_16 before the include gets 16-byte pieces (the
+// batched kernels: the assembler fails on their 32-byte form).
+#ifdef ADPIC_RECORD_ACCESS_16
+template <typename T, int CP>
+__device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q) {
+            float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 2; ++q) {
+            double2 f = __ldg(reinterpret_cast<const double2*>(p) + q);
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    }
+}
+template <typename T, int CP>
+__device__ __forceinline__ void ldr_v(const T* p, T (&v)[CP]) { ldv<T, CP>(p, v); }
+template <typename T, int CP>
+__device__ __forceinline__ void stg_v(T* p, const T (&v)[CP]) { stv<T, CP>(p, v); }
+#else
+template <typename T, int CP>
+__device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
+    static_assert(CP * sizeof(T) % 32 == 0, "32-byte pieces");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 8; ++q)
+            asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=f"(v[8 * q]), "=f"(v[8 * q + 1]), "=f"(v[8 * q + 2]), "=f"(v[8 * q + 3]), "=f"(v[8 * q + 4]),
+                  "=f"(v[8 * q + 5]), "=f"(v[8 * q + 6]), "=f"(v[8 * q + 7])
+                : "l"(p + 8 * q));
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q)
+            asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+                : "=d"(v[4 * q]), "=d"(v[4 * q + 1]), "=d"(v[4 * q + 2]), "=d"(v[4 * q + 3])
+                : "l"(p + 4 * q));
+    }
+}
+template <typename T, int CP>
+__device__ __forceinline__ void ldr_v(const T* p, T (&v)[CP]) {
+    static_assert(CP * sizeof(T) % 32 == 0, "32-byte pieces");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 8; ++q)
+            asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=f"(v[8 * q]), "=f"(v[8 * q + 1]), "=f"(v[8 * q + 2]), "=f"(v[8 * q + 3]), "=f"(v[8 * q + 4]),
+                           "=f"(v[8 * q + 5]), "=f"(v[8 * q + 6]), "=f"(v[8 * q + 7])
+                         : "l"(p + 8 * q)
+                         : "memory");
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q)
+            asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                         : "=d"(v[4 * q]), "=d"(v[4 * q + 1]), "=d"(v[4 * q + 2]), "=d"(v[4 * q + 3])
+                         : "l"(p + 4 * q)
+                         : "memory");
+    }
+}
+template <typename T, int CP>
+__device__ __forceinline__ void stg_v(T* p, const T (&v)[CP]) {
+    static_assert(CP * sizeof(T) % 32 == 0, "32-byte pieces");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 8; ++q)
+            asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p + 8 * q), "f"(v[8 * q]),
+                         "f"(v[8 * q + 1]), "f"(v[8 * q + 2]), "f"(v[8 * q + 3]), "f"(v[8 * q + 4]), "f"(v[8 * q + 5]),
+                         "f"(v[8 * q + 6]), "f"(v[8 * q + 7])
+                         : "memory");
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q)
+            asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 4 * q), "d"(v[4 * q]), "d"(v[4 * q + 1]),
+                         "d"(v[4 * q + 2]), "d"(v[4 * q + 3])
+                         : "memory");
+    }
+}
+#endif
+
 // Grid geometry of one kick, computed on the device from the value-part extrema.
 struct GeomDev {
     double o[3];    // origin (lab, m)
@@ -42,6 +161,16 @@ struct GeomDev {
     float fdf[3];          // 1/(2 hr): central-difference factors (FP32 copy)
     double fdd[3];         // 1/(2 hr)
     int R[3];              // near-field box of the Green's function (cells per dimension)
+};
+
+// What a kernel that produces the value-part extrema needs to derive the grid
+// geometry in its last block (count == nullptr: it does not).
+struct GeomFuse {
+    unsigned* count;        // finished blocks; zero between launches
+    int nx, ny, nz, CP;
+    double gamma0;
+    GeomDev* g;
+    void* chmax;            // Ord<T>[CP], reset with the extrema
 };
 
 // Dual 2x2 map per plane, entries (m11, m12, m21, m22).
@@ -79,10 +208,13 @@ struct SortBuf {
     int* ids_out;
 };
 
+// track: also reduce the value-part extrema of the new positions into mm; the
+// last block then derives the next grid geometry when gf.count is set
+// (launch_boundary likewise when it applies a map)
 template <typename T, int C, int CP>
 void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
-                 const SortBuf& sb, cudaStream_t s);
+                 const SortBuf& sb, const GeomFuse& gf, cudaStream_t s);
 void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s);
 int scan_blocks(int ncells);
 void launch_iota(int* ids, int64_t N, cudaStream_t s);
@@ -90,7 +222,7 @@ template <typename T, int CP>
 void launch_convert_out_perm(const T* src, const int* ids, double* dst, int64_t N, int C, cudaStream_t s);
 template <typename T, int C, int CP>
 void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
-                     int nblocks, Ord<T>* mm, cudaStream_t s);
+                     int nblocks, Ord<T>* mm, const GeomFuse& gf, cudaStream_t s);
 int boundary_blocks();
 template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho,
@@ -127,8 +259,9 @@ template <typename T>
 int fft_slab_yt(const FFTDims& d);
 template <typename T>
 size_t fft_slab_smem(const FFTDims& d, int which = -1);
+// rho is read and left zero (ready for the next deposit)
 template <typename T>
-void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
+void launch_fft_conv(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
                      const V2<T>* twx, const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s);
 template <typename T>
 void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int CP, T* E, cudaStream_t s);

@@ -44,7 +44,7 @@ struct Conv {
 };
 
 template <typename T, int MX, int MY, int MZ>
-void conv_run(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
+void conv_run(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
               const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     const int rows = d.ny * d.nz;
     const unsigned gx = (unsigned)((rows + kRowsX - 1) / kRowsX);
@@ -55,7 +55,7 @@ void conv_run(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const F
     fftx_inv_kernel<T, MX><<<gx, 256, Conv<T, MX>::sm_x(d), s>>>(X1, phi, d, twx, chmax);
 }
 template <typename T, int MX, int MY>
-void conv_z(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
+void conv_z(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
             const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     switch (d.Mz) {
         case 16: conv_run<T, MX, MY, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
@@ -67,7 +67,7 @@ void conv_z(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFT
 }
 
 template <typename T, int MX>
-void conv_y(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
+void conv_y(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
             const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     switch (d.My) {
         case 16: conv_z<T, MX, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
@@ -133,7 +133,7 @@ size_t fft_slab_smem(const FFTDims& d, int which) {
 }
 
 template <typename T, int MX, int MY, int MZ>
-void conv_slab(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
+void conv_slab(T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
                const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     const int yt = slab_yt<T>(d);
     const dim3 gx((unsigned)(d.ny / yt), (unsigned)d.nz);
@@ -142,7 +142,7 @@ void conv_slab(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d,
     fftx_inv_t_kernel<T, MX><<<gx, 256, sm_inv_t<T>(d, yt), s>>>(X1, phi, d, twx, chmax, yt);
 }
 template <typename T, int MX, int MY>
-void conv_slab_z(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
+void conv_slab_z(T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
                  const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     switch (d.Mz) {
         case 16: conv_slab<T, MX, MY, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
@@ -152,7 +152,7 @@ void conv_slab_z(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& 
     }
 }
 template <typename T, int MX>
-void conv_slab_y(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
+void conv_slab_y(T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
                  const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     switch (d.My) {
         case 16: conv_slab_z<T, MX, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
@@ -163,7 +163,7 @@ void conv_slab_y(const T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& 
 }
 
 template <typename T>
-void launch_fft_conv(const T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
+void launch_fft_conv(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
                      const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
     if (fft_slab_path<T>(d)) {
         switch (d.Mx) {
@@ -215,9 +215,9 @@ void setup_fft() {
     slab_yz_attrs<T, 128>();
 }
 
-template void launch_fft_conv<float>(const float*, float2*, float2*, const float*, float*, const FFTDims&,
+template void launch_fft_conv<float>(float*, float2*, float2*, const float*, float*, const FFTDims&,
                                      const float2*, const float2*, const float2*, const unsigned int*, cudaStream_t);
-template void launch_fft_conv<double>(const double*, double2*, double2*, const double*, double*, const FFTDims&,
+template void launch_fft_conv<double>(double*, double2*, double2*, const double*, double*, const FFTDims&,
                                       const double2*, const double2*, const double2*, const unsigned long long*,
                                       cudaStream_t);
 template bool fft_slab_path<float>(const FFTDims&);

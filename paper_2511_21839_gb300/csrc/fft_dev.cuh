@@ -212,9 +212,12 @@ constexpr int kTile = 16;   // columns per CTA in the y and z passes
 // (2p, 2p+1) becomes one complex line (the spectrum of G is real and even, so
 // the two real convolutions separate again at the end); each channel is
 // scaled by a power of two so both halves of a pair have comparable magnitude.
+// clear: zero each rho value after reading it, so rho is zero for the next
+// deposit (read and cleared through one pointer).
 template <typename T, int M>
-__device__ __forceinline__ void fftx_fwd_kernel_body(const T* __restrict__ rho, V2<T>* __restrict__ X1, FFTDims d,
+__device__ __forceinline__ void fftx_fwd_kernel_body(T* rho, V2<T>* __restrict__ X1, FFTDims d,
                                                        const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax,
+                                                       bool clear,
     const int bx_, const int by_, const int bz_, const int nbx_) {
     using L = Lay<M>;
     extern __shared__ unsigned char smraw[];
@@ -224,16 +227,24 @@ __device__ __forceinline__ void fftx_fwd_kernel_body(const T* __restrict__ rho, 
     for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
     const int64_t row0 = (int64_t)bx_ * kRowsX;
     const int nrows = d.ny * d.nz;
-    for (int t = threadIdx.x; t < kRowsX * d.nx * d.CP; t += blockDim.x) {
-        const int r = t / (d.nx * d.CP);
-        const int rem = t % (d.nx * d.CP);
-        const int x = rem / d.CP, c = rem % d.CP;
+    const int lcp = __ffs(d.CP) - 1;                  // nx = M/2 and CP are powers of two
+    constexpr int LNX = log2_c(M) - 1;
+    for (int t = threadIdx.x; t < (kRowsX << (LNX + lcp)); t += blockDim.x) {
+        const int r = t >> (LNX + lcp);
+        const int x = (t >> lcp) & ((1 << LNX) - 1), c = t & (d.CP - 1);
         if (row0 + r >= nrows || c >= d.C) continue;
-        const T v = rho[((row0 + r) * d.nx + x) * d.CP + c] * chan_scale<T>(chmax, c, false);
+        const int64_t at = ((row0 + r) * d.nx + x) * d.CP + c;
+        const T v = rho[at] * chan_scale<T>(chmax, c, false);
         V2<T>& dst = buf[(r * d.npair + (c >> 1)) * L::LS + L::pos(x)];
         if (c & 1) dst.y = v; else dst.x = v;
     }
     __syncthreads();
+    if (clear) {
+        // the rows just read (contiguous) are cleared after every load of the block
+        const int rows = (int)min((int64_t)kRowsX, (int64_t)nrows - row0);
+        T* zr = rho + row0 * d.nx * d.CP;
+        for (int t = threadIdx.x; t < (rows << (LNX + lcp)); t += blockDim.x) zr[t] = (T)0;
+    }
     step1<T, M, false>(buf, nl, twM, true);
     __syncthreads();
     for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
@@ -250,9 +261,9 @@ __device__ __forceinline__ void fftx_fwd_kernel_body(const T* __restrict__ rho, 
 }
 
 template <typename T, int M>
-static __global__ void __launch_bounds__(256) fftx_fwd_kernel(const T* __restrict__ rho, V2<T>* __restrict__ X1, FFTDims d,
+static __global__ void __launch_bounds__(256) fftx_fwd_kernel(T* rho, V2<T>* __restrict__ X1, FFTDims d,
                                                        const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax) {
-    fftx_fwd_kernel_body<T, M>(rho, X1, d, tw, chmax, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+    fftx_fwd_kernel_body<T, M>(rho, X1, d, tw, chmax, true, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
 }
 
 // y pass over a tile of kTile consecutive kx for one (z, pair).
@@ -441,9 +452,9 @@ static __global__ void __launch_bounds__(256) fftx_inv_kernel(const V2<T>* __res
 
 // x pass, forward: rows (z, y0 .. y0 + yt - 1) of every pair -> X1 [p][kx][z][y]
 template <typename T, int M>
-__device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho, V2<T>* __restrict__ X1, FFTDims d,
+__device__ __forceinline__ void fftx_fwd_t_kernel_body(T* rho, V2<T>* __restrict__ X1, FFTDims d,
                                                          const V2<T>* __restrict__ tw, const Ord<T>* __restrict__ chmax,
-                                                         int yt, const int bx_, const int by_) {
+                                                         int yt, bool clear, const int bx_, const int by_) {
     using L = Lay<M>;
     extern __shared__ unsigned char smraw[];
     V2<T>* twM = reinterpret_cast<V2<T>*>(smraw);
@@ -459,7 +470,7 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho
     constexpr int LNX = log2_c(M) - 1;
     const int lpn = __ffs(d.CP) - 2;                  // log2(CP / 2)
     const int lyt = __ffs(yt) - 1;
-    const V2<T>* src = reinterpret_cast<const V2<T>*>(rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP);
+    V2<T>* src = reinterpret_cast<V2<T>*>(rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP);
 #pragma unroll 8
     for (int t = threadIdx.x; t < (yt << (LNX + lpn)); t += blockDim.x) {
         const int p = t & ((1 << lpn) - 1), x = (t >> lpn) & ((1 << LNX) - 1), r = t >> (lpn + LNX);
@@ -470,6 +481,13 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho
         buf[(p * yt + r) * L::LS + L::pos(x)] = v;
     }
     __syncthreads();
+    if (clear) {
+        // the rows just read (contiguous: yt rows of nx CP values) are cleared
+        // with 16-byte stores, after every load of the block
+        float4* zr = reinterpret_cast<float4*>(src);
+        const int n16 = (yt << (LNX + lpn)) * (int)sizeof(V2<T>) / 16;
+        for (int t = threadIdx.x; t < n16; t += blockDim.x) zr[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     step1<T, M, false>(buf, divmod_of(nl), twM, true);
     __syncthreads();
     const int64_t kstride = (int64_t)d.nz * d.ny;
@@ -487,10 +505,10 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(const T* __restrict__ rho
 }
 
 template <typename T, int M>
-static __global__ void __launch_bounds__(256) fftx_fwd_t_kernel(const T* __restrict__ rho, V2<T>* __restrict__ X1,
+static __global__ void __launch_bounds__(256) fftx_fwd_t_kernel(T* rho, V2<T>* __restrict__ X1,
                                                                   FFTDims d, const V2<T>* __restrict__ tw,
                                                                   const Ord<T>* __restrict__ chmax, int yt) {
-    fftx_fwd_t_kernel_body<T, M>(rho, X1, d, tw, chmax, yt, (int)blockIdx.x, (int)blockIdx.y);
+    fftx_fwd_t_kernel_body<T, M>(rho, X1, d, tw, chmax, yt, true, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Pieces of the two-step transform used by the slab kernel (M = R1 R2, see

@@ -55,8 +55,17 @@ void setup_green() {
 
 template <typename T>
 void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int CP, T* E, cudaStream_t s) {
-    const int64_t tot = (int64_t)nx * ny * nz * CP;
-    field_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(phi, geom, nx, ny, nz, CP, E);
+    // one thread per 32-byte piece of a node's channels (CP in {8, 16})
+    const int64_t pieces = (int64_t)nx * ny * nz * CP * (int64_t)sizeof(T) / 32;
+    const unsigned grid = (unsigned)((pieces + 255) / 256);
+    if (CP == 8)
+        field_vec_kernel<T, 8><<<grid, 256, 0, s>>>(phi, geom, nx, ny, nz, E);
+    else if (CP == 16)
+        field_vec_kernel<T, 16><<<grid, 256, 0, s>>>(phi, geom, nx, ny, nz, E);
+    else {
+        const int64_t tot = (int64_t)nx * ny * nz * CP;
+        field_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(phi, geom, nx, ny, nz, CP, E);
+    }
 }
 
 #define ADPIC_FIELD_INST(T)                                                                                       \

@@ -33,7 +33,7 @@ __device__ __forceinline__ void geom_kernel_body(Ord<T>* mm, int nx, int ny, int
     const int d = threadIdx.x;
     if (d < 3) {
         const int n = d == 0 ? nx : (d == 1 ? ny : nz);
-        double lo = (double)ord_dec(mm[d]), hi = (double)ord_dec(mm[3 + d]);
+        double lo = (double)ord_dec(__ldcg(&mm[d])), hi = (double)ord_dec(__ldcg(&mm[3 + d]));
         if (!(lo <= hi)) { lo = 0.0; hi = 0.0; }
         double w = hi - lo;
         if (!(w > 0.0)) w = 1e-6;
@@ -70,6 +70,31 @@ __device__ __forceinline__ void geom_kernel_body(Ord<T>* mm, int nx, int ny, int
 template <typename T>
 static __global__ void geom_kernel(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* g, Ord<T>* chmax, int CP) {
     geom_kernel_body<T>(mm, nx, ny, nz, gamma0, g, chmax, CP, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+
+// The geometry step run by the last block of the kernel that produced the
+// extrema (every block calls this after its extrema atomics; all threads of
+// the block take part): a counter of finished blocks picks the last one,
+// which derives the geometry and resets the counter. Fences order each
+// block's atomics before its count and the last block's reads after it.
+// (a call, not inlined: the host kernel's register allocation stays its own)
+template <typename T>
+__device__ __noinline__ void geom_step(const GeomFuse gf, Ord<T>* mm) {
+    geom_kernel_body<T>(mm, gf.nx, gf.ny, gf.nz, gf.gamma0, gf.g, reinterpret_cast<Ord<T>*>(gf.chmax), gf.CP, 0, 0, 0, 1);
+}
+template <typename T>
+__device__ __forceinline__ void geom_last_block(const GeomFuse& gf, Ord<T>* mm) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(gf.count, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    geom_step<T>(gf, mm);
+    if (threadIdx.x == 0) *gf.count = 0u;
 }
 
 // per-channel max |rho| (ordered bits of a non-negative value are its bits).
@@ -159,6 +184,36 @@ static __global__ void __launch_bounds__(256) chmax_vec_kernel(const T* __restri
             atomicMax(&chmax[threadIdx.x], __float_as_uint(b));
         else
             atomicMax(&chmax[threadIdx.x], (unsigned long long)__double_as_longlong(b));
+    }
+}
+
+// The central differences with one thread per (node, 32-byte piece of its
+// channels): six 32-byte loads of phi and three 32-byte stores of E, the
+// same arithmetic per value as field_kernel_body.
+template <typename T, int CP>
+static __global__ void __launch_bounds__(256) field_vec_kernel(const T* __restrict__ phi, const GeomDev* __restrict__ g,
+                                                              int nx, int ny, int nz, T* __restrict__ E) {
+    constexpr int EPC = 32 / (int)sizeof(T), CPN = CP / EPC, LCPN = CPN == 1 ? 0 : (CPN == 2 ? 1 : 2);
+    static_assert(CP % EPC == 0 && CPN <= 4, "32-byte pieces");
+    const unsigned t = (unsigned)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ((unsigned)nx * ny * nz << LCPN)) return;
+    const int lx = __ffs(nx) - 1, ly = __ffs(ny) - 1;
+    const unsigned piece = t & (CPN - 1), node = t >> LCPN;
+    const int i = node & (nx - 1), j = (node >> lx) & (ny - 1), k = node >> (lx + ly);
+    if (i < 1 || i > nx - 2 || j < 1 || j > ny - 2 || k < 1 || k > nz - 2) return;
+    const T a[3] = {sizeof(T) == 4 ? (T)g->fdf[0] : (T)g->fdd[0], sizeof(T) == 4 ? (T)g->fdf[1] : (T)g->fdd[1],
+                    sizeof(T) == 4 ? (T)g->fdf[2] : (T)g->fdd[2]};
+    const int64_t s[3] = {CP, (int64_t)nx * CP, (int64_t)nx * ny * CP};
+    const T* p = phi + (int64_t)node * CP + piece * EPC;
+    T* e = E + (int64_t)node * 3 * CP + piece * EPC;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        T hi[EPC], lo[EPC], r[EPC];
+        ldg_v<T, EPC>(p + s[d], hi);
+        ldg_v<T, EPC>(p - s[d], lo);
+#pragma unroll
+        for (int c = 0; c < EPC; ++c) r[c] = -(hi[c] - lo[c]) * a[d];
+        stg_v<T, EPC>(e + d * CP, r);
     }
 }
 

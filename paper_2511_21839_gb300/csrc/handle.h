@@ -42,7 +42,8 @@ struct ad_pic {
     int* cellcount = nullptr;    // particles per cell (zero between kicks)
     int* offs = nullptr;         // exclusive cell offsets
     int* bsum = nullptr;         // scan chunk totals
-    void* rho = nullptr;
+    void* rho = nullptr;         // zero between kicks: the convolution's x pass clears it
+    unsigned* gcount = nullptr;  // finished blocks of a kernel with the fused geometry step
     void* phi = nullptr;
     void* E = nullptr;
     void* X1 = nullptr;

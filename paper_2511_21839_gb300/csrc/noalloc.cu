@@ -50,11 +50,12 @@ int moments_noalloc(const void* state, int64_t N, double* mom, cudaStream_t s) {
     int st = partials_address(&partial);
     if (st) return st;
     MapCoef<T, CP> unused{};
+    GeomFuse no_geometry{};          // count == nullptr: no geometry step
     // the MOM variant of the boundary kernel never writes the state and never
     // touches the extrema buffer; every block overwrites all of its partials,
     // so nothing needs clearing between calls
     launch_boundary<T, C, CP>(const_cast<T*>(static_cast<const T*>(state)), N, unused, false, true,
-                              static_cast<double*>(partial), kNoAllocBlocks, nullptr, s);
+                              static_cast<double*>(partial), kNoAllocBlocks, nullptr, no_geometry, s);
     launch_moments_reduce(static_cast<const double*>(partial), kNoAllocBlocks, CP, N, mom, s);
     return cudaGetLastError() == cudaSuccess ? AD_PIC_OK : AD_PIC_ERR_CUDA;
 }

@@ -51,25 +51,25 @@ void setup_push() {
 template <typename T, int C, int CP, bool TRACK>
 static void launch_push_t(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx,
                           int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, Ord<T>* mm, int* err,
-                          const SortBuf& sb, cudaStream_t s) {
+                          const SortBuf& sb, const GeomFuse& gf, cudaStream_t s) {
     constexpr int TP = push_tile<T, CP>();
     const int64_t tiles = (N + TP - 1) / TP;
     const int64_t g = push_grid<T, C, CP, TRACK>();
     const unsigned grid = (unsigned)(tiles < g ? tiles : g);
     const size_t smem = 2 * 6 * (size_t)TP * CP * sizeof(T);
     push_tma_kernel<T, C, CP, TRACK><<<grid, TP, smem, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm,
-                                                             err, sb);
+                                                             err, sb, gf);
 }
 
 template <typename T, int C, int CP>
 void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
-                 const SortBuf& sb, cudaStream_t s) {
+                 const SortBuf& sb, const GeomFuse& gf, cudaStream_t s) {
     if (N <= 0) return;
     if (track)
-        launch_push_t<T, C, CP, true>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, s);
+        launch_push_t<T, C, CP, true>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, gf, s);
     else
-        launch_push_t<T, C, CP, false>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, s);
+        launch_push_t<T, C, CP, false>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, gf, s);
 }
 
 int scan_blocks(int ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
@@ -91,13 +91,13 @@ int boundary_blocks() { return kBoundaryBlocks; }
 
 template <typename T, int C, int CP>
 void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
-                     int nblocks, Ord<T>* mm, cudaStream_t s) {
+                     int nblocks, Ord<T>* mm, const GeomFuse& gf, cudaStream_t s) {
     if (apply && mom)
-        boundary_kernel<T, C, CP, true, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
+        boundary_kernel<T, C, CP, true, true><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm, gf);
     else if (mom)
-        boundary_kernel<T, C, CP, true, false><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm);
+        boundary_kernel<T, C, CP, true, false><<<nblocks, 256, 0, s>>>(state, N, A, partial, mm, gf);
     else if (apply)
-        halfmap_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(state, N, A, mm);
+        halfmap_kernel<T, C, CP><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(state, N, A, mm, gf);
 }
 
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s) {
@@ -128,9 +128,9 @@ void setup_deposit() {
     template void launch_init<T, C, CP>(const double*, int64_t, const double*, T*, cudaStream_t);                \
     template void launch_push<T, C, CP>(const T*, T*, int64_t, const T*, const GeomDev*, int, int, int,         \
                                         const MapCoef<T, CP>&, const KickCoef<T, CP>&, bool, Ord<T>*, int*,      \
-                                        const SortBuf&, cudaStream_t);                                           \
+                                        const SortBuf&, const GeomFuse&, cudaStream_t);                          \
     template void launch_boundary<T, C, CP>(T*, int64_t, const MapCoef<T, CP>&, bool, bool, double*, int,       \
-                                            Ord<T>*, cudaStream_t);                                              \
+                                            Ord<T>*, const GeomFuse&, cudaStream_t);                             \
     template void launch_deposit<T, C, CP>(const T*, int64_t, const GeomDev*, int, int, int, T, T*, int*,        \
                                            const SortBuf&, cudaStream_t);                                        \
     template void setup_deposit<T, C, CP>();                                                                     \

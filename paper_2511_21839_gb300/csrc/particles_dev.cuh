@@ -9,56 +9,13 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "field_dev.cuh"
 
 namespace adpic {
 
 // ------------------------------------------------------------------ helpers
 
-template <typename T, int CP>
-__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&v)[CP]) {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int q = 0; q < CP / 4; ++q) {
-            float4 f = reinterpret_cast<const float4*>(p)[q];
-            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < CP / 2; ++q) {
-            double2 f = reinterpret_cast<const double2*>(p)[q];
-            v[2 * q] = f.x; v[2 * q + 1] = f.y;
-        }
-    }
-}
 
-template <typename T, int CP>
-__device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int q = 0; q < CP / 4; ++q) {
-            float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
-            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < CP / 2; ++q) {
-            double2 f = __ldg(reinterpret_cast<const double2*>(p) + q);
-            v[2 * q] = f.x; v[2 * q + 1] = f.y;
-        }
-    }
-}
-
-template <typename T, int CP>
-__device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[CP]) {
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int q = 0; q < CP / 4; ++q)
-            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < CP / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
-    }
-}
 
 __device__ __forceinline__ unsigned int ord_enc(float f) {
     unsigned int u = __float_as_uint(f);
@@ -157,8 +114,8 @@ __device__ __forceinline__ void init_kernel_body(const double* __restrict__ nrm,
             u[k] = (T)(a[k] * n1);
             p[k] = (T)(b[0] * (-al[k] * n1) + b[k] * s0);
         }
-        stv<T, CP>(state + ((2 * pl) * N + i) * CP, u);
-        stv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
+        stg_v<T, CP>(state + ((2 * pl) * N + i) * CP, u);
+        stg_v<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
     }
 }
 
@@ -307,11 +264,11 @@ __device__ __forceinline__ void push_kernel_body(const T* __restrict__ state, T*
         const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
         T u[6][CP];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) ldv<T, CP>(state + (c * N + i) * CP, u[c]);
+        for (int c = 0; c < 6; ++c) ldg_v<T, CP>(state + (c * N + i) * CP, u[c]);
         push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
         if (sb.ids_out) sb.ids_out[dst] = sb.ids_in[i];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
+        for (int c = 0; c < 6; ++c) stg_v<T, CP>(out + (c * N + dst) * CP, u[c]);
         if (TRACK) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) { mn[d] = u[2 * d][0]; mx[d] = u[2 * d][0]; }
@@ -441,7 +398,7 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
             push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
             if (sb.ids_out) sb.ids_out[dst] = idv;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) stv<T, CP>(out + (c * N + dst) * CP, u[c]);
+            for (int c = 0; c < 6; ++c) stg_v<T, CP>(out + (c * N + dst) * CP, u[c]);
             if (TRACK) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -464,8 +421,12 @@ template <typename T, int C, int CP, bool TRACK>
 static __global__ void __launch_bounds__(push_tile<T, CP>(), push_min_blocks<T, CP>())
     push_tma_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
                     const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
-                    const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
+                    const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb,
+                    const GeomFuse gf) {
     push_tma_body<T, C, CP, TRACK>(state, out, N, E, geom, nx, ny, nz, A, K, mm, err, sb);
+    // every block has finished its gathers before it counts itself done, so the
+    // last block may overwrite the geometry they read
+    if (TRACK && gf.count) geom_last_block<T>(gf, mm);
 }
 
 // ------------------------------------------------------------------ cell sort: scan, ids
@@ -607,11 +568,11 @@ static __global__ void convert_out_perm_kernel(const T* __restrict__ src, const 
 // ------------------------------------------------------------------ half map alone
 
 // The dual half map A applied in place to every particle (one thread per
-// particle, 128-bit loads and stores), with the value-part extrema of the new
+// particle, 32-byte loads and stores), with the value-part extrema of the new
 // positions for the next grid geometry: the opening pass of a run.
 template <typename T, int C, int CP>
 static __global__ void __launch_bounds__(256) halfmap_kernel(T* __restrict__ state, int64_t N, const MapCoef<T, CP> A,
-                                                             Ord<T>* __restrict__ mm) {
+                                                             Ord<T>* __restrict__ mm, const GeomFuse gf) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
@@ -619,8 +580,8 @@ static __global__ void __launch_bounds__(256) halfmap_kernel(T* __restrict__ sta
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
             T x[CP], p[CP];
-            ldv<T, CP>(state + ((2 * pl) * N + i) * CP, x);
-            ldv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
+            ldr_v<T, CP>(state + ((2 * pl) * N + i) * CP, x);
+            ldr_v<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
             const T a0 = A.m[pl][0][0], b0 = A.m[pl][1][0], c0 = A.m[pl][2][0], d0 = A.m[pl][3][0];
             const T x0 = x[0], p0 = p[0];
 #pragma unroll
@@ -631,13 +592,14 @@ static __global__ void __launch_bounds__(256) halfmap_kernel(T* __restrict__ sta
             }
             x[0] = fma(a0, x0, b0 * p0);
             p[0] = fma(c0, x0, d0 * p0);
-            stv<T, CP>(state + ((2 * pl) * N + i) * CP, x);
-            stv<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
+            stg_v<T, CP>(state + ((2 * pl) * N + i) * CP, x);
+            stg_v<T, CP>(state + ((2 * pl + 1) * N + i) * CP, p);
             mn[pl] = x[0];
             mx[pl] = x[0];
         }
     }
     block_minmax<T>(mn, mx, mm);
+    if (gf.count) geom_last_block<T>(gf, mm);
 }
 
 // ------------------------------------------------------------------ period boundary: moments + half map
@@ -790,8 +752,10 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
 
 template <typename T, int C, int CP, bool MOM, bool APPLY>
 static __global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ state, int64_t N, const MapCoef<T, CP> A,
-                                                       double* __restrict__ partial, Ord<T>* __restrict__ mm) {
+                                                       double* __restrict__ partial, Ord<T>* __restrict__ mm,
+                                                       const GeomFuse gf) {
     boundary_kernel_body<T, C, CP, MOM, APPLY>(state, N, A, partial, mm, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+    if (APPLY && gf.count) geom_last_block<T>(gf, mm);
 }
 
 // partial [nblocks][15][CP] -> out [15][CP] / N: one block per output value,
@@ -914,7 +878,7 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
     if (sv) {
         T x[3][CP];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) ldv<T, CP>(state + ((2 * d) * N + ps) * CP, x[d]);
+        for (int d = 0; d < 3; ++d) ldg_v<T, CP>(state + ((2 * d) * N + ps) * CP, x[d]);
 #pragma unroll
         for (int nd = 0; nd < 8; ++nd) {
             const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
