@@ -798,9 +798,10 @@ __host__ __device__ constexpr int dep_tile_warps() {
 // Deposition with the summation over particles done on chip before the atomics.
 // Each warp takes 32 consecutive particles and sorts them by cell with a
 // bitonic network on the keys (cell << 5 | lane), so the particles of one cell
-// occupy consecutive lanes. Every lane writes its particle's 8 node records
-// (8 x CP values) as a row of a per-warp shared tile [32][8 CP + 4] with vector
-// stores; then lane j owns tile columns j, j + 32, ... (node nd = column / CP,
+// occupy consecutive sorted positions. Every lane keeps its own particle in
+// registers and writes its 8 node records (8 x CP values) as row (its sorted
+// position) of a per-warp shared tile [32][8 CP + 4] with vector stores; then
+// lane j owns tile columns j, j + 32, ... (node nd = column / CP,
 // channel column % CP) and, for each run of lanes sharing a cell, sums its
 // columns over the run and issues one scalar atomic per (run, node,
 // channel). Consecutive lanes then address consecutive channels of
@@ -832,12 +833,16 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
         o[d] = geom_o<T>(g, d);
     }
     int bad = 0;
-    int key = 0x7fffffff;
-    T f0[3] = {(T)0, (T)0, (T)0};
+    // this lane's particle: its x, y, z records stay in registers through the sort
+    int key = (0x3ffffff << 5) | lane;                    // invalid lanes sort last
+    T f[3] = {(T)0, (T)0, (T)0};
+    T x[3][CP];
     if (valid) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ldg_v<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
         int idx[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(state[((2 * d) * N + i) * CP], o[d], ih[d], n[d], f0[d], bad);
+        for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(x[d][0], o[d], ih[d], n[d], f[d], bad);
         key = (((idx[2] * ny + idx[1]) * nx + idx[0]) << 5) | lane;
     }
     // bitonic sort of the 32 keys, ascending in lane order
@@ -855,9 +860,11 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
     const int cell = key >> 5;
     const int src = key & 31;
     const int64_t ps = i0 + src;
-    T f[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) f[d] = __shfl_sync(FULL, f0[d], src);
+    // sorted position of this lane's own particle (sorted lane j holds lane src_j's)
+    __shared__ int spos[WARPS][32];
+    spos[warp][src] = lane;
+    __syncwarp();
+    const int mypos = spos[warp][lane];
     // runs of equal cells
     const int prev = __shfl_up_sync(FULL, cell, 1);
     const bool head = sv && (lane == 0 || prev != cell);
@@ -874,11 +881,8 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
             sb.rank[ps] = base + lane - start;
         }
     }
-    // node records of this lane's particle into tile row `lane`
-    if (sv) {
-        T x[3][CP];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) ldg_v<T, CP>(state + ((2 * d) * N + ps) * CP, x[d]);
+    // node records of this lane's particle into tile row `mypos` (sorted order)
+    if (valid) {
 #pragma unroll
         for (int nd = 0; nd < 8; ++nd) {
             const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
@@ -890,7 +894,7 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
             rec[0] = qm * (wx * wy * wz);
 #pragma unroll
             for (int k = 1; k < CP; ++k) rec[k] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
-            stv<T, CP>(tile + lane * RS + nd * CP, rec);
+            stv<T, CP>(tile + mypos * RS + nd * CP, rec);
         }
     }
     __syncwarp();
