@@ -26,6 +26,40 @@ template <> struct V2T<float> { using type = float2; };
 template <> struct V2T<double> { using type = double2; };
 template <typename T> using V2 = typename V2T<T>::type;
 
+// Lane-wise arithmetic on pairs. For FP32 one packed f32x2 instruction does
+// both lanes (each lane rounds exactly as the scalar operation); FP64 pairs
+// use two scalar operations.
+#define ADPIC_F2_BINARY(name, op, fallback)                                                              \
+    __device__ __forceinline__ float2 name(float2 a, float2 b) {                                         \
+        float2 d;                                                                                        \
+        asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n " op            \
+            " rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"                                                     \
+            : "=f"(d.x), "=f"(d.y)                                                                       \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                   \
+        return d;                                                                                        \
+    }                                                                                                    \
+    __device__ __forceinline__ double2 name(double2 a, double2 b) {                                      \
+        double2 d;                                                                                       \
+        d.x = a.x fallback b.x;                                                                          \
+        d.y = a.y fallback b.y;                                                                          \
+        return d;                                                                                        \
+    }
+ADPIC_F2_BINARY(v2_add, "add.rn.f32x2", +)
+ADPIC_F2_BINARY(v2_sub, "sub.rn.f32x2", -)
+ADPIC_F2_BINARY(v2_mul, "mul.rn.f32x2", *)
+#undef ADPIC_F2_BINARY
+__device__ __forceinline__ float2 v2_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ double2 v2_fma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
 // ordered-integer encoding of floating point for atomicMin/atomicMax
 template <typename T> struct OrdT;
 template <> struct OrdT<float> { using type = unsigned int; };

@@ -85,10 +85,7 @@ __device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
         }
         if (HO && len == 2) {
 #pragma unroll
-            for (int g = 0; g < R; g += 2) {
-                v[g].x = v[g].x + v[g + 1].x;
-                v[g].y = v[g].y + v[g + 1].y;
-            }
+            for (int g = 0; g < R; g += 2) v[g] = v2_add(v[g], v[g + 1]);
             continue;
         }
 #pragma unroll
@@ -96,12 +93,8 @@ __device__ __forceinline__ void dft_reg(V2<T> (&v)[R]) {
 #pragma unroll
             for (int j = 0; j < half; ++j) {
                 const V2<T> a = v[g + j], b = v[g + j + half];
-                v[g + j].x = a.x + b.x;
-                v[g + j].y = a.y + b.y;
-                V2<T> d;
-                d.x = a.x - b.x;
-                d.y = a.y - b.y;
-                v[g + j + half] = mul_w16<T, INV>(d, j * (16 / len));
+                v[g + j] = v2_add(a, b);
+                v[g + j + half] = mul_w16<T, INV>(v2_sub(a, b), j * (16 / len));
             }
         }
     }

@@ -784,10 +784,10 @@ static __global__ void moments_reduce_kernel(const double* __restrict__ partial,
 
 // ------------------------------------------------------------------ warp-sorted deposition
 
-// row stride of a lane's node records in the deposit tile (16-byte aligned;
-// 4 mod 32 words apart so the vector stores of 8 lanes hit distinct banks)
+// row stride of a lane's node records (4 nodes) in the deposit tile (16-byte
+// aligned; 4 mod 32 words apart so the vector stores of 8 lanes hit distinct banks)
 template <int CP>
-__host__ __device__ constexpr int dep_tile_stride() { return 8 * CP + 4; }
+__host__ __device__ constexpr int dep_tile_stride() { return 4 * CP + 4; }
 template <int CP, typename T>
 __host__ __device__ constexpr size_t dep_tile_bytes_per_warp() { return sizeof(T) * 32 * dep_tile_stride<CP>(); }
 template <int CP, typename T>
@@ -799,22 +799,22 @@ __host__ __device__ constexpr int dep_tile_warps() {
 // Each warp takes 32 consecutive particles and sorts them by cell with a
 // bitonic network on the keys (cell << 5 | lane), so the particles of one cell
 // occupy consecutive sorted positions. Every lane keeps its own particle in
-// registers and writes its 8 node records (8 x CP values) as row (its sorted
-// position) of a per-warp shared tile [32][8 CP + 4] with vector stores; then
-// lane j owns tile columns j, j + 32, ... (node nd = column / CP,
-// channel column % CP) and, for each run of lanes sharing a cell, sums its
-// columns over the run and issues one scalar atomic per (run, node,
-// channel). Consecutive lanes then address consecutive channels of
-// neighbouring nodes, so one warp atomic touches a few contiguous sectors. The
-// cell sort's rank is the lane's offset in its run plus one counting atomic
-// per run.
+// registers. For each z plane of the stencil in turn, it writes its 4 node
+// records (4 x CP values) as row (its sorted position) of a per-warp shared
+// tile [32][4 CP + 4] with vector stores; then lane j owns tile columns j,
+// j + 32, ... (node = column / CP, channel column % CP) and, for each run of
+// lanes sharing a cell, sums its columns over the run and issues one scalar
+// atomic per (run, node, channel). Consecutive lanes then address consecutive
+// channels of neighbouring nodes, so one warp atomic touches a few contiguous
+// sectors. The cell sort's rank is the lane's offset in its run plus one
+// counting atomic per run.
 
 template <typename T, int C, int CP, int WARPS>
 __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, int64_t N,
                                                     const GeomDev* __restrict__ geom, int nx, int ny, int nz, T qm,
                                                     T* __restrict__ rho, int* __restrict__ err, const SortBuf sb,
                                                     const int bx_) {
-    constexpr int ROWS = 8 * CP;
+    constexpr int ROWS = 4 * CP;                            // tile columns: 4 nodes x CP
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -845,14 +845,18 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
         for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(x[d][0], o[d], ih[d], n[d], f[d], bad);
         key = (((idx[2] * ny + idx[1]) * nx + idx[0]) << 5) | lane;
     }
-    // bitonic sort of the 32 keys, ascending in lane order
+    // bitonic sort of the 32 (distinct) keys, ascending in lane order; skipped
+    // when they already are (slots follow the previous kick's cell order)
+    const int next_key = __shfl_down_sync(FULL, key, 1);
+    if (!__all_sync(FULL, lane == 31 || key < next_key)) {
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
+        for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int other = __shfl_xor_sync(FULL, key, j);
-            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
-            key = (lower == up) ? min(key, other) : max(key, other);
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int other = __shfl_xor_sync(FULL, key, j);
+                const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                key = (lower == up) ? min(key, other) : max(key, other);
+            }
         }
     }
     const int nv = __popc(__ballot_sync(FULL, valid));    // sorted lanes [0, nv) hold particles
@@ -881,46 +885,61 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
             sb.rank[ps] = base + lane - start;
         }
     }
-    // node records of this lane's particle into tile row `mypos` (sorted order)
-    if (valid) {
+    // Two halves of the stencil, the nodes of the lower (c = 0) then the upper
+    // (c = 1) z plane: the tile holds one half (4 node records per row), so it
+    // takes half the shared memory and twice the warps fit on an SM.
 #pragma unroll
-        for (int nd = 0; nd < 8; ++nd) {
-            const int a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-            const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
-            const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
-            const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
-            const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
-            T rec[CP];
-            rec[0] = qm * (wx * wy * wz);
+    for (int c = 0; c < 2; ++c) {
+        if (c) __syncwarp();                              // the lower half's sums are read
+        // node records of this lane's particle into tile row `mypos` (sorted order)
+        if (valid) {
 #pragma unroll
-            for (int k = 1; k < CP; ++k) rec[k] = fma(x[0][k], gx, fma(x[1][k], gy, x[2][k] * gz));
-            stv<T, CP>(tile + mypos * RS + nd * CP, rec);
+            for (int nb = 0; nb < 4; ++nb) {
+                const int a = nb & 1, b = nb >> 1;
+                const T wx = a ? f[0] : (T)1 - f[0], sx = a ? (T)1 : (T)-1;
+                const T wy = b ? f[1] : (T)1 - f[1], sy = b ? (T)1 : (T)-1;
+                const T wz = c ? f[2] : (T)1 - f[2], sz = c ? (T)1 : (T)-1;
+                const T gx = qm * ih[0] * sx * wy * wz, gy = qm * ih[1] * wx * sy * wz, gz = qm * ih[2] * wx * wy * sz;
+                // rec[k] = x_k gx + y_k gy + z_k gz (k >= 1), lane pairs at once; rec[0] = q W
+                T rec[CP];
+                const V2<T> gx2 = {gx, gx}, gy2 = {gy, gy}, gz2 = {gz, gz};
+#pragma unroll
+                for (int k = 0; k < CP; k += 2) {
+                    const V2<T> r = v2_fma(V2<T>{x[0][k], x[0][k + 1]}, gx2,
+                                           v2_fma(V2<T>{x[1][k], x[1][k + 1]}, gy2,
+                                                  v2_mul(V2<T>{x[2][k], x[2][k + 1]}, gz2)));
+                    rec[k] = r.x;
+                    rec[k + 1] = r.y;
+                }
+                rec[0] = qm * (wx * wy * wz);
+                stv<T, CP>(tile + mypos * RS + nb * CP, rec);
+            }
         }
-    }
-    __syncwarp();
-    // rows of this lane: node nd = r / CP of the cell (node index = cell index + offset, as cells
-    // and nodes share the linearisation), channel r % CP
-    constexpr int RL = ROWS / 32;
-    int64_t roff[RL];
-#pragma unroll
-    for (int q = 0; q < RL; ++q) {
-        const int r = lane + 32 * q, nd = r / CP, ch = r % CP;
-        roff[q] = ((int64_t)(nd >> 2) * nx * ny + ((nd >> 1) & 1) * nx + (nd & 1)) * CP + ch;
-    }
-    // per run: row sums and one atomic per (node, channel)
-    for (unsigned m = heads; m; m &= m - 1) {
-        const int s0 = __ffs(m) - 1;
-        const unsigned rest = m & (m - 1);
-        const int s1 = rest ? __ffs(rest) - 2 : nv - 1;
-        T* base = rho + (int64_t)__shfl_sync(FULL, cell, s0) * CP;
+        __syncwarp();
+        // columns of this lane: node nb = r / CP of the half (node index = cell index +
+        // offset, as cells and nodes share the linearisation), channel r % CP
+        constexpr int RL = ROWS / 32;
+        int64_t roff[RL];
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
-            const int r = lane + 32 * q;
-            if (r % CP >= C) continue;
-            const T* colr = tile + r;
-            T acc = colr[s0 * RS];
-            for (int j = s0 + 1; j <= s1; ++j) acc += colr[j * RS];
-            atomicAdd(base + roff[q], acc);
+            const int r = lane + 32 * q, nb = r / CP, ch = r % CP;
+            roff[q] = ((int64_t)c * nx * ny + (nb >> 1) * nx + (nb & 1)) * CP + ch;
+        }
+        // per run: column sums and one atomic per (node, channel)
+        for (unsigned m = heads; m; m &= m - 1) {
+            const int s0 = __ffs(m) - 1;
+            const unsigned rest = m & (m - 1);
+            const int s1 = rest ? __ffs(rest) - 2 : nv - 1;
+            T* base = rho + (int64_t)__shfl_sync(FULL, cell, s0) * CP;
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const int r = lane + 32 * q;
+                if (r % CP >= C) continue;
+                const T* colr = tile + r;
+                T acc = colr[s0 * RS];
+                for (int jj = s0 + 1; jj <= s1; ++jj) acc += colr[jj * RS];
+                atomicAdd(base + roff[q], acc);
+            }
         }
     }
     if (bad) atomicOr(err, bad);
