@@ -315,7 +315,9 @@ static __global__ void green_cell_kernel(const GeomDev* __restrict__ g, int nx, 
 constexpr int kDctLines = 32;
 constexpr int kDctAcc = 8;
 
-template <typename T>
+// ACC accumulators per lane: with ACC >= L / 8 one sweep over l covers every
+// output (the single-instance launcher picks ACC = ceil(L / 8)).
+template <typename T, int ACC = kDctAcc>
 __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
     const int bx_, const int by_, const int bz_, const int nbx_) {
     extern __shared__ unsigned char smraw[];
@@ -344,22 +346,22 @@ __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __r
     __syncthreads();
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const T* x = xs + l * L;
-    for (int k0 = w; k0 < L; k0 += nw * kDctAcc) {
-        T acc[kDctAcc];
-        const T* row[kDctAcc];
+    for (int k0 = w; k0 < L; k0 += nw * ACC) {
+        T acc[ACC];
+        const T* row[ACC];
 #pragma unroll
-        for (int q = 0; q < kDctAcc; ++q) {
+        for (int q = 0; q < ACC; ++q) {
             acc[q] = (T)0;
             row[q] = Ds + min(k0 + q * nw, L - 1) * L;
         }
         for (int c = 0; c < L; ++c) {
             const T xv = x[c];
 #pragma unroll
-            for (int q = 0; q < kDctAcc; ++q) acc[q] = fma(row[q][c], xv, acc[q]);
+            for (int q = 0; q < ACC; ++q) acc[q] = fma(row[q][c], xv, acc[q]);
         }
         if (l < nl) {
 #pragma unroll
-            for (int q = 0; q < kDctAcc; ++q) {
+            for (int q = 0; q < ACC; ++q) {
                 const int k = k0 + q * nw;
                 if (k < L) out[(int64_t)k * BA + ba0 + l] = acc[q];
             }
@@ -367,9 +369,9 @@ __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __r
     }
 }
 
-template <typename T>
+template <typename T, int ACC = kDctAcc>
 static __global__ void dct_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA) {
-    dct_kernel_body<T>(in, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+    dct_kernel_body<T, ACC>(in, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
 }
 
 // ------------------------------------------------------------------ field
