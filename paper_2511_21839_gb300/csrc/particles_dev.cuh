@@ -790,6 +790,11 @@ template <int CP>
 __host__ __device__ constexpr int dep_tile_stride() { return 4 * CP + 4; }
 template <int CP, typename T>
 __host__ __device__ constexpr size_t dep_tile_bytes_per_warp() { return sizeof(T) * 32 * dep_tile_stride<CP>(); }
+// resident blocks per SM the deposit's registers are budgeted for
+template <typename T, int CP>
+__host__ __device__ constexpr int dep_min_blocks() {
+    return sizeof(T) == 4 ? (CP == 8 ? 4 : 3) : 2;
+}
 template <int CP, typename T>
 __host__ __device__ constexpr int dep_tile_warps() {
     return (dep_tile_bytes_per_warp<CP, T>() * 8 <= 72 * 1024) ? 8 : ((dep_tile_bytes_per_warp<CP, T>() * 4 <= 72 * 1024) ? 4 : 2);
@@ -925,20 +930,24 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
             const int r = lane + 32 * q, nb = r / CP, ch = r % CP;
             roff[q] = ((int64_t)c * nx * ny + (nb >> 1) * nx + (nb & 1)) * CP + ch;
         }
-        // per run: column sums and one atomic per (node, channel)
-        for (unsigned m = heads; m; m &= m - 1) {
-            const int s0 = __ffs(m) - 1;
-            const unsigned rest = m & (m - 1);
-            const int s1 = rest ? __ffs(rest) - 2 : nv - 1;
-            T* base = rho + (int64_t)__shfl_sync(FULL, cell, s0) * CP;
+        // one sweep over the sorted rows: column sums per run, and at the last
+        // row of each run one atomic per (node, channel) (the run tests are
+        // warp-uniform; each sum adds the run's rows in order)
+        T acc[RL];
 #pragma unroll
-            for (int q = 0; q < RL; ++q) {
-                const int r = lane + 32 * q;
-                if (r % CP >= C) continue;
-                const T* colr = tile + r;
-                T acc = colr[s0 * RS];
-                for (int jj = s0 + 1; jj <= s1; ++jj) acc += colr[jj * RS];
-                atomicAdd(base + roff[q], acc);
+        for (int q = 0; q < RL; ++q) acc[q] = (T)0;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            if (jj >= nv) break;
+#pragma unroll
+            for (int q = 0; q < RL; ++q) acc[q] += tile[jj * RS + lane + 32 * q];
+            if (jj == nv - 1 || ((heads >> (jj + 1)) & 1u)) {
+                T* base = rho + (int64_t)__shfl_sync(FULL, cell, jj) * CP;
+#pragma unroll
+                for (int q = 0; q < RL; ++q) {
+                    if ((lane + 32 * q) % CP < C) atomicAdd(base + roff[q], acc[q]);
+                    acc[q] = (T)0;
+                }
             }
         }
     }
@@ -946,7 +955,7 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
 }
 
 template <typename T, int C, int CP, int WARPS>
-static __global__ void __launch_bounds__(WARPS * 32) deposit_tile_kernel(const T* __restrict__ state, int64_t N,
+static __global__ void __launch_bounds__(WARPS * 32, dep_min_blocks<T, CP>()) deposit_tile_kernel(const T* __restrict__ state, int64_t N,
                                                                            const GeomDev* __restrict__ geom, int nx,
                                                                            int ny, int nz, T qm, T* __restrict__ rho,
                                                                            int* __restrict__ err, const SortBuf sb) {
