@@ -464,14 +464,26 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(T* rho, V2<T>* __restrict
     const int lpn = __ffs(d.CP) - 2;                  // log2(CP / 2)
     const int lyt = __ffs(yt) - 1;
     V2<T>* src = reinterpret_cast<V2<T>*>(rho + ((int64_t)z * d.ny + y0) * d.nx * d.CP);
-#pragma unroll 8
-    for (int t = threadIdx.x; t < (yt << (LNX + lpn)); t += blockDim.x) {
-        const int p = t & ((1 << lpn) - 1), x = (t >> lpn) & ((1 << LNX) - 1), r = t >> (lpn + LNX);
-        if (p >= d.npair) continue;
-        V2<T> v = src[t];
-        v.x *= sc[2 * p];
-        v.y *= sc[2 * p + 1];
-        buf[(p * yt + r) * L::LS + L::pos(x)] = v;
+    // batches of 16 independent loads per thread (one latency per batch)
+    constexpr int NBL = 16;
+    const int total = yt << (LNX + lpn);
+    for (int t0 = threadIdx.x; t0 < total; t0 += NBL * blockDim.x) {
+        V2<T> v[NBL];
+#pragma unroll
+        for (int b = 0; b < NBL; ++b) {
+            const int t = t0 + b * blockDim.x;
+            if (t < total && (t & ((1 << lpn) - 1)) < d.npair) v[b] = src[t];
+        }
+#pragma unroll
+        for (int b = 0; b < NBL; ++b) {
+            const int t = t0 + b * blockDim.x;
+            const int p = t & ((1 << lpn) - 1), x = (t >> lpn) & ((1 << LNX) - 1), r = t >> (lpn + LNX);
+            if (t < total && p < d.npair) {
+                v[b].x *= sc[2 * p];
+                v[b].y *= sc[2 * p + 1];
+                buf[(p * yt + r) * L::LS + L::pos(x)] = v[b];
+            }
+        }
     }
     __syncthreads();
     if (clear) {
@@ -692,11 +704,24 @@ __device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__
     const int64_t kstride = (int64_t)d.nz * d.ny;
     const V2<T>* src0 = X1 + (int64_t)z * d.ny + y0;
     const int lyt = __ffs(yt) - 1;                    // yt, nx, CP are powers of two
-#pragma unroll 8
-    for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
-        const int r = t & (yt - 1), rest = t >> lyt;
-        const int kx = rest & (M - 1), p = rest >> log2_c(M);
-        buf[(p * yt + r) * L::LS + L::pos(kx)] = src0[((int64_t)p * M + kx) * kstride + r];
+    // batches of 16 independent loads per thread (one latency per batch)
+    constexpr int NBL = 16;
+    for (int t0 = threadIdx.x; t0 < nl * M; t0 += NBL * blockDim.x) {
+        V2<T> v[NBL];
+#pragma unroll
+        for (int b = 0; b < NBL; ++b) {
+            const int t = t0 + b * blockDim.x;
+            const int r = t & (yt - 1), rest = t >> lyt;
+            const int kx = rest & (M - 1), p = rest >> log2_c(M);
+            if (t < nl * M) v[b] = src0[((int64_t)p * M + kx) * kstride + r];
+        }
+#pragma unroll
+        for (int b = 0; b < NBL; ++b) {
+            const int t = t0 + b * blockDim.x;
+            const int r = t & (yt - 1), rest = t >> lyt;
+            const int kx = rest & (M - 1), p = rest >> log2_c(M);
+            if (t < nl * M) buf[(p * yt + r) * L::LS + L::pos(kx)] = v[b];
+        }
     }
     __syncthreads();
     step1<T, M, true>(buf, divmod_of(nl), twM, false);
