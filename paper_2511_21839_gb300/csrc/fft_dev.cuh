@@ -136,6 +136,23 @@ __device__ __forceinline__ int lcount(const DivMod& n) { return n.d; }
 __device__ __forceinline__ int ldiv(int w, int n) { return w / n; }
 __device__ __forceinline__ int ldiv(int w, const DivMod& n) { return n.div(w); }
 
+// End of a step-1 item: the R1 outputs (bit-reversed in v) times W_M^(n2 k1),
+// stored at b[k1 (R2 + 1)], b = line + n2.
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void step1_store(const V2<T> (&v)[Lay<M>::R1], V2<T>* b, int n2, const V2<T>* twM) {
+    constexpr int R1 = Lay<M>::R1, R2 = Lay<M>::R2;
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        V2<T> y = v[brev_c(k1, log2_c(R1))];
+        if (k1 != 0 && n2 != 0) {
+            V2<T> t = twM[(n2 * k1) & (M - 1)];
+            if (INV) t.y = -t.y;
+            y = cmul<T>(y, t);
+        }
+        b[k1 * (R2 + 1)] = y;
+    }
+}
+
 // Step 1 for work item w of nlines * R2 (line = w % nlines, n2 = w / nlines):
 // R1-point DFT over n1 in place, times W_M^(n2 k1). `half_zero`: inputs with
 // n >= M/2 are zero (zero padding) and not read. `nlines` is an int (folded
@@ -158,16 +175,7 @@ __device__ __forceinline__ void step1(V2<T>* buf, NL nlines, const V2<T>* twM, b
             for (int n1 = 0; n1 < R1; ++n1) v[n1] = b[n1 * (R2 + 1)];
             dft_reg<T, R1, INV>(v);
         }
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) {
-            V2<T> y = v[brev_c(k1, log2_c(R1))];
-            if (k1 != 0 && n2 != 0) {
-                V2<T> t = twM[(n2 * k1) & (M - 1)];
-                if (INV) t.y = -t.y;
-                y = cmul<T>(y, t);
-            }
-            b[k1 * (R2 + 1)] = y;
-        }
+        step1_store<T, M, INV>(v, b, n2, twM);
     }
 }
 
@@ -601,14 +609,18 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
     for (int j = threadIdx.x; j < MY; j += blockDim.x) tY[j] = twy[j];
     for (int j = threadIdx.x; j < MZ; j += blockDim.x) tZ[j] = twz[j];
     V2<T>* slab = X1 + ((int64_t)p * d.Mx + kx) * nz * ny;
-#pragma unroll 8
-    for (int t = threadIdx.x; t < nz * ny; t += blockDim.x) {
-        const int z = t / ny, y = t % ny;
-        A[z * LY::LS + LY::pos(y)] = slab[t];
-    }
     __syncthreads();
-    // forward y: step 1 (inputs y >= ny are zero), step 2 in place -> k1-major spectra
-    step1<T, MY, false>(A, nz, tY, true);
+    // forward y: step 1 straight from the slab (inputs y >= ny are zero; item
+    // (z, n2) reads y = R2 n1 + n2, consecutive threads take consecutive n2 so
+    // the loads are coalesced) into A, then step 2 in place -> k1-major spectra
+    for (int w = threadIdx.x; w < nz * LY::R2; w += blockDim.x) {
+        const int n2 = w % LY::R2, z = w / LY::R2;
+        V2<T> v[LY::R1];
+#pragma unroll
+        for (int n1 = 0; n1 < LY::R1 / 2; ++n1) v[n1] = slab[z * ny + LY::R2 * n1 + n2];
+        dft_reg<T, LY::R1, false, true>(v);
+        step1_store<T, MY, false>(v, A + z * LY::LS + n2, n2, tY);
+    }
     __syncthreads();
     for (int w = threadIdx.x; w < nz * LY::R1; w += blockDim.x)
         step2_fwd_inplace<T, MY>(A + (w % nz) * LY::LS, w / nz);
@@ -616,12 +628,17 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
     const int kxr = kx <= d.nx ? kx : d.Mx - kx;
     const T* Gp = Ghat + (int64_t)kxr * (d.nz + 1) * (d.ny + 1);     // plane [kz'][ky']
     for (int c0 = 0; c0 < MY; c0 += KC) {
-        for (int t = threadIdx.x; t < KC * nz; t += blockDim.x) {
-            const int j = t % KC, z = t / KC;
-            B[j * LZ::LS + LZ::pos(z)] = A[z * LY::LS + kmajor_pos<MY>(c0 + j)];
+        // forward z step 1 for KC columns, read straight from the y spectra in A
+        // (column c0 + j of row z is A[z][kmajor(c0 + j)]; rows z >= nz are zero)
+        for (int w = threadIdx.x; w < KC * LZ::R2; w += blockDim.x) {
+            const int j = w % KC, n2 = w / KC;
+            const V2<T>* a = A + kmajor_pos<MY>(c0 + j);
+            V2<T> v[LZ::R1];
+#pragma unroll
+            for (int n1 = 0; n1 < LZ::R1 / 2; ++n1) v[n1] = a[(LZ::R2 * n1 + n2) * LY::LS];
+            dft_reg<T, LZ::R1, false, true>(v);
+            step1_store<T, MZ, false>(v, B + j * LZ::LS + n2, n2, tZ);
         }
-        __syncthreads();
-        step1<T, MZ, false>(B, KC, tZ, true);
         __syncthreads();
         // per (column, k1): forward R2-point DFT, times Ghat, first half of the inverse
         for (int w = threadIdx.x; w < KC * LZ::R1; w += blockDim.x) {
