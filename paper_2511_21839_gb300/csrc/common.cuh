@@ -105,6 +105,14 @@ __device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[CP]) {
 // ldr_v through the coherent one, stg_v stores. A translation unit that
 // defines ADPIC_RECORD_ACCESS_16 before the include gets 16-byte pieces (the
 // batched kernels: the assembler fails on their 32-byte form).
+// L2 policy for data that is streamed through once (the particle state read by
+// the deposit): its lines are evicted first, so the charge grid that the same
+// kernel accumulates into stays resident in L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 #ifdef ADPIC_RECORD_ACCESS_16
 template <typename T, int CP>
 __device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
@@ -126,6 +134,8 @@ template <typename T, int CP>
 __device__ __forceinline__ void ldr_v(const T* p, T (&v)[CP]) { ldv<T, CP>(p, v); }
 template <typename T, int CP>
 __device__ __forceinline__ void stg_v(T* p, const T (&v)[CP]) { stv<T, CP>(p, v); }
+template <typename T, int CP>
+__device__ __forceinline__ void ldg_v_stream(const T* __restrict__ p, T (&v)[CP], uint64_t) { ldg_v<T, CP>(p, v); }
 #else
 template <typename T, int CP>
 __device__ __forceinline__ void ldg_v(const T* __restrict__ p, T (&v)[CP]) {
@@ -181,6 +191,25 @@ __device__ __forceinline__ void stg_v(T* p, const T (&v)[CP]) {
             asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 4 * q), "d"(v[4 * q]), "d"(v[4 * q + 1]),
                          "d"(v[4 * q + 2]), "d"(v[4 * q + 3])
                          : "memory");
+    }
+}
+// a load with an L2 policy (l2_evict_first) for streamed records
+template <typename T, int CP>
+__device__ __forceinline__ void ldg_v_stream(const T* __restrict__ p, T (&v)[CP], uint64_t pol) {
+    static_assert(CP * sizeof(T) % 32 == 0, "32-byte pieces");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < CP / 8; ++q)
+            asm("ld.global.nc.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+                : "=f"(v[8 * q]), "=f"(v[8 * q + 1]), "=f"(v[8 * q + 2]), "=f"(v[8 * q + 3]), "=f"(v[8 * q + 4]),
+                  "=f"(v[8 * q + 5]), "=f"(v[8 * q + 6]), "=f"(v[8 * q + 7])
+                : "l"(p + 8 * q), "l"(pol));
+    } else {
+#pragma unroll
+        for (int q = 0; q < CP / 4; ++q)
+            asm("ld.global.nc.L2::cache_hint.v4.f64 {%0,%1,%2,%3}, [%4], %5;"
+                : "=d"(v[4 * q]), "=d"(v[4 * q + 1]), "=d"(v[4 * q + 2]), "=d"(v[4 * q + 3])
+                : "l"(p + 4 * q), "l"(pol));
     }
 }
 #endif

@@ -31,20 +31,19 @@ void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, doubl
     const int64_t ng = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
     green_cell_kernel<T><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(geom, nx, ny, nz, corner, G, order);
     // each pass transforms the contiguous axis and makes it the outermost one
-    // ACC = ceil(L / 8) accumulators: the 8 warps cover all L = n + 1 outputs in one sweep
+    // 16 warps per block and ACC = ceil(L / 16) accumulators: the warps cover
+    // all L = n + 1 outputs in one sweep
     auto pass = [&](const T* in, T* out, const T* D, int L, int64_t BA) {
         const size_t sm = sizeof(T) * ((size_t)L * L + (size_t)kDctLines * L);
         const unsigned grid = (unsigned)((BA + kDctLines - 1) / kDctLines);
-        if (L <= 9)
-            dct_kernel<T, 2><<<grid, 256, sm, s>>>(in, out, D, L, BA);
-        else if (L <= 17)
-            dct_kernel<T, 3><<<grid, 256, sm, s>>>(in, out, D, L, BA);
+        if (L <= 17)
+            dct_kernel<T, 2><<<grid, 512, sm, s>>>(in, out, D, L, BA);
         else if (L <= 33)
-            dct_kernel<T, 5><<<grid, 256, sm, s>>>(in, out, D, L, BA);
+            dct_kernel<T, 3><<<grid, 512, sm, s>>>(in, out, D, L, BA);
         else if (L <= 65)
-            dct_kernel<T, 9><<<grid, 256, sm, s>>>(in, out, D, L, BA);
+            dct_kernel<T, 5><<<grid, 512, sm, s>>>(in, out, D, L, BA);
         else
-            dct_kernel<T, 17><<<grid, 256, sm, s>>>(in, out, D, L, BA);
+            dct_kernel<T, 9><<<grid, 512, sm, s>>>(in, out, D, L, BA);
     };
     if (order == 0) {
         // G [z][y][x] -> pass x -> [x'][z][y] -> pass y -> [y'][x'][z] -> pass z -> [z'][y'][x']
@@ -65,7 +64,6 @@ void setup_green() {
     cudaFuncSetAttribute(dct_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(dct_kernel<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(dct_kernel<T, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(dct_kernel<T, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 template <typename T>

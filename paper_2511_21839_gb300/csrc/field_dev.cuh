@@ -307,16 +307,16 @@ static __global__ void green_cell_kernel(const GeomDev* __restrict__ g, int nx, 
 // out [L][BA]: out[k][ba] = sum_l D[k][l] in[ba][l], D[k][l] = w_l cos(pi l k / n),
 // w_0 = w_n = 1, else 2. Three passes (rotating the axes) give the real
 // spectrum of the even extension of G to the 2n-periodic grid. A block of
-// 256 threads stages kDctLines = 32 input lines and the matrix D in shared
-// memory; lane l of warp w accumulates out[k][line l] for k = w, w + 8, ...
+// nw warps stages kDctLines = 32 input lines and the matrix D in shared
+// memory; lane l of warp w accumulates out[k][line l] for k = w, w + nw, ...
 // in registers (the D reads are warp-wide broadcasts, the line stride L is
 // odd so the line reads are conflict-free, and the stores of one k are 32
 // consecutive words).
 constexpr int kDctLines = 32;
 constexpr int kDctAcc = 8;
 
-// ACC accumulators per lane: with ACC >= L / 8 one sweep over l covers every
-// output (the single-instance launcher picks ACC = ceil(L / 8)).
+// ACC accumulators per lane: one sweep over l covers every output when
+// ACC * (warps per block) >= L.
 template <typename T, int ACC = kDctAcc>
 __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
     const int bx_, const int by_, const int bz_, const int nbx_) {

@@ -844,7 +844,7 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
     T x[3][CP];
     if (valid) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) ldg_v<T, CP>(state + ((2 * d) * N + i) * CP, x[d]);
+        for (int d = 0; d < 3; ++d) ldg_v_stream<T, CP>(state + ((2 * d) * N + i) * CP, x[d], l2_evict_first());
         int idx[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) idx[d] = cell_of<T>(x[d][0], o[d], ih[d], n[d], f[d], bad);
