@@ -322,11 +322,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // 32-byte records (168 registers, no spills), 8 KB runs and two CTAs otherwise
 template <typename T, int CP>
 __host__ __device__ constexpr int push_tile() {
-    return CP * sizeof(T) == 32 ? 128 : (int)(8192 / (CP * sizeof(T)));
+    return CP * sizeof(T) == 32 ? 64 : (int)(8192 / (CP * sizeof(T)));
 }
 template <typename T, int CP>
 __host__ __device__ constexpr int push_min_blocks() {
-    return CP * sizeof(T) == 32 ? 3 : 2;
+    return CP * sizeof(T) == 32 ? 6 : 2;
 }
 
 // Persistent push: each CTA walks tiles blockIdx.x, +gridDim.x, ... and keeps
