@@ -318,8 +318,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // particles per tile (one thread each) and resident CTAs per SM the register
-// budget is sized for: 4 KB coordinate runs and three 128-thread CTAs for the
-// 32-byte records (168 registers, no spills), 8 KB runs and two CTAs otherwise
+// budget is sized for: 2 KB coordinate runs and six 64-thread CTAs for the
+// 32-byte records (168 registers, no spills; two warps per tile barrier), 8 KB
+// runs and two CTAs otherwise
 template <typename T, int CP>
 __host__ __device__ constexpr int push_tile() {
     return CP * sizeof(T) == 32 ? 64 : (int)(8192 / (CP * sizeof(T)));
