@@ -199,6 +199,30 @@ def test_split_runs_and_graph_replay(adpic):
         assert ev < 1e-12 and ed < 1e-10
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stages_leave_the_run_unchanged(adpic, prec):
+    """Stage calls between runs (deposit only, or through the convolution) leave no trace in the
+    next run: rho is zero again for its first deposit, the cell sort and the fused geometry step
+    start clean, so the run equals the same run on a fresh handle."""
+    N, grid = 3000, (16, 16, 16)
+    w = I.workload("fodo_10k_32")
+    nrm = I.normals(46, N)
+    res = []
+    for stages in ((), (1,), (2, 1), (0, 3)):
+        sim = adpic.ADPIC(grid, N, 7, prec)
+        sim.set_beam(w.beam, nrm)
+        sim.set_lattice(w.lattice)
+        for k in stages:
+            sim.stage(k)
+        sim.run(20)
+        v, d = sim.moments()
+        res.append(np.concatenate([v[:, None], d], axis=1))
+        sim.close()
+    for r in res[1:]:
+        ev, ed = report(f"stages then run ({prec})", r[:, 0], r[:, 1:], res[0])
+        assert ev < (1e-12 if prec == 0 else 1e-6) and ed < (1e-10 if prec == 0 else 1e-5)
+
+
 def test_multi_period_records(adpic):
     N, grid = 2000, (16, 16, 16)
     o, sim, w, b = make_pair(adpic, N, grid, 7, 0)
