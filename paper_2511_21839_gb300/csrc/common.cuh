@@ -297,9 +297,6 @@ void setup_push();
 void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N, double* out, cudaStream_t s);
 
 template <typename T>
-void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geom, Ord<T>* chmax, int CP,
-                 cudaStream_t s);
-template <typename T>
 void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream_t s);
 // Ghat order 0: [kz'][ky'][kx'] (x fastest); order 1: [kx'][kz'][ky'] (y fastest)
 template <typename T>

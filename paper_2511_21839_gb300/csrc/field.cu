@@ -6,12 +6,6 @@
 namespace adpic {
 
 template <typename T>
-void launch_geom(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* geom, Ord<T>* chmax, int CP,
-                 cudaStream_t s) {
-    geom_kernel<T><<<1, 32, 0, s>>>(mm, nx, ny, nz, gamma0, geom, chmax, CP);
-}
-
-template <typename T>
 void launch_chmax(const T* rho, int64_t nodes, int CP, Ord<T>* chmax, cudaStream_t s) {
     // rho is cudaMalloc'ed (256-byte aligned) with CP in {8, 16}
     if (CP == 8)
@@ -82,7 +76,6 @@ void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int
 }
 
 #define ADPIC_FIELD_INST(T)                                                                                       \
-    template void launch_geom<T>(Ord<T>*, int, int, int, double, GeomDev*, Ord<T>*, int, cudaStream_t);          \
     template void launch_chmax<T>(const T*, int64_t, int, Ord<T>*, cudaStream_t);                                 \
     template void launch_green<T>(const GeomDev*, int, int, int, bool, double*, T*, T*, T*, const T*, const T*,    \
                                   const T*, int, cudaStream_t);                                                   \

@@ -67,11 +67,6 @@ __device__ __forceinline__ void geom_kernel_body(Ord<T>* mm, int nx, int ny, int
     for (int c = d; c < CP; c += blockDim.x) chmax[c] = (Ord<T>)0;
 }
 
-template <typename T>
-static __global__ void geom_kernel(Ord<T>* mm, int nx, int ny, int nz, double gamma0, GeomDev* g, Ord<T>* chmax, int CP) {
-    geom_kernel_body<T>(mm, nx, ny, nz, gamma0, g, chmax, CP, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
-}
-
 // The geometry step run by the last block of the kernel that produced the
 // extrema (every block calls this after its extrema atomics; all threads of
 // the block take part): a counter of finished blocks picks the last one,

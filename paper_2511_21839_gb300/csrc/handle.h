@@ -27,7 +27,8 @@ struct ad_pic {
     cudaStream_t own_stream = nullptr, stream = nullptr;
     // the Green's function depends on the grid geometry only: it runs on a side
     // stream concurrently with deposit and channel maxima (fork after the
-    // geometry kernel, join before the convolution). The cell-offset scan is
+    // kernel whose last block derived the geometry, join before the
+    // convolution). The cell-offset scan is
     // needed by the push only: it follows on the side stream after the deposit
     // (ev_dep) and joins before the push (ev_scan). Captured graphs keep the branches.
     cudaStream_t side = nullptr;
