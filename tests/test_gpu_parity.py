@@ -218,9 +218,13 @@ def test_stages_leave_the_run_unchanged(adpic, prec):
         v, d = sim.moments()
         res.append(np.concatenate([v[:, None], d], axis=1))
         sim.close()
+    # runs differ only by the order of the deposit's atomic additions: FP64 at rounding level; in
+    # FP32 the derivative vectors differ by about 1e-5 after a period (measured 5e-6 to 1.2e-5)
+    # and the emittances by about 1e-9, while a stale charge grid in the first kick changes the
+    # emittances by orders of magnitude more
     for r in res[1:]:
         ev, ed = report(f"stages then run ({prec})", r[:, 0], r[:, 1:], res[0])
-        assert ev < (1e-12 if prec == 0 else 1e-6) and ed < (1e-10 if prec == 0 else 1e-5)
+        assert ev < (1e-12 if prec == 0 else 1e-6) and ed < (1e-10 if prec == 0 else 1e-4)
 
 
 def test_multi_period_records(adpic):
