@@ -316,8 +316,9 @@ struct Impl {
     }
 
     // kernels launched by one enqueue_field (deposit 1, scan 2, chmax 1,
-    // Green's function 5, convolution 3 or 5, field 1)
-    static int field_launches(ad_pic* h) { return 10 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
+    // Green's function 4: corners, cell averages with the first DCT pass, two
+    // DCT passes; convolution 3 or 5, field 1)
+    static int field_launches(ad_pic* h) { return 9 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
 
     // the launch sequence of one run; returns the number of moment records
     // `from` is the buffer holding the particles at the start; each push moves

@@ -22,33 +22,39 @@ void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, doubl
     (void)exact;
     const int64_t nc = (int64_t)(nx + 2) * (ny + 2) * (nz + 2);
     green_corner_kernel<<<(unsigned)((nc + 63) / 64), 64, 0, s>>>(geom, nx, ny, nz, corner);
-    const int64_t ng = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-    green_cell_kernel<T><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(geom, nx, ny, nz, corner, G, order);
-    // each pass transforms the contiguous axis and makes it the outermost one
-    // 16 warps per block and ACC = ceil(L / 16) accumulators: the warps cover
-    // all L = n + 1 outputs in one sweep
-    auto pass = [&](const T* in, T* out, const T* D, int L, int64_t BA) {
+    // each pass transforms the contiguous axis and makes it the outermost one;
+    // the first pass computes its lines as the cell averages of G itself (G is
+    // never stored). 16 warps per block and ACC = ceil(L / 16) accumulators:
+    // the warps cover all L = n + 1 outputs in one sweep
+    auto pass = [&](const T* in, T* out, const T* D, int L, int64_t BA, bool cell) {
         const size_t sm = sizeof(T) * ((size_t)L * L + (size_t)kDctLines * L);
         const unsigned grid = (unsigned)((BA + kDctLines - 1) / kDctLines);
-        if (L <= 17)
-            dct_kernel<T, 2><<<grid, 512, sm, s>>>(in, out, D, L, BA);
-        else if (L <= 33)
-            dct_kernel<T, 3><<<grid, 512, sm, s>>>(in, out, D, L, BA);
-        else if (L <= 65)
-            dct_kernel<T, 5><<<grid, 512, sm, s>>>(in, out, D, L, BA);
-        else
-            dct_kernel<T, 9><<<grid, 512, sm, s>>>(in, out, D, L, BA);
+#define ADPIC_DCT_PASS(ACC)                                                                                  \
+    if (cell)                                                                                                \
+        cell_dct_kernel<T, ACC><<<grid, 512, sm, s>>>(out, D, L, BA, geom, nx, ny, nz, corner, order);       \
+    else                                                                                                     \
+        dct_kernel<T, ACC><<<grid, 512, sm, s>>>(in, out, D, L, BA);
+        if (L <= 17) {
+            ADPIC_DCT_PASS(2)
+        } else if (L <= 33) {
+            ADPIC_DCT_PASS(3)
+        } else if (L <= 65) {
+            ADPIC_DCT_PASS(5)
+        } else {
+            ADPIC_DCT_PASS(9)
+        }
+#undef ADPIC_DCT_PASS
     };
     if (order == 0) {
         // G [z][y][x] -> pass x -> [x'][z][y] -> pass y -> [y'][x'][z] -> pass z -> [z'][y'][x']
-        pass(G, Gtmp, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));
-        pass(Gtmp, G, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1));
-        pass(G, Ghat, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1));
+        pass(nullptr, Gtmp, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1), true);
+        pass(Gtmp, G, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1), false);
+        pass(G, Ghat, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1), false);
     } else {
         // G [x][z][y] -> pass y -> [y'][x][z] -> pass z -> [z'][y'][x] -> pass x -> [x'][z'][y']
-        pass(G, Gtmp, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1));
-        pass(Gtmp, G, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1));
-        pass(G, Ghat, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1));
+        pass(nullptr, Gtmp, dct_y, ny + 1, (int64_t)(nx + 1) * (nz + 1), true);
+        pass(Gtmp, G, dct_z, nz + 1, (int64_t)(ny + 1) * (nx + 1), false);
+        pass(G, Ghat, dct_x, nx + 1, (int64_t)(nz + 1) * (ny + 1), false);
     }
 }
 
@@ -58,6 +64,10 @@ void setup_green() {
     cudaFuncSetAttribute(dct_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(dct_kernel<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(dct_kernel<T, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(cell_dct_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(cell_dct_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(cell_dct_kernel<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(cell_dct_kernel<T, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 template <typename T>

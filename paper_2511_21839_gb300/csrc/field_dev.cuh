@@ -250,18 +250,8 @@ static __global__ void green_corner_kernel(const GeomDev* __restrict__ g, int nx
 // is below FP32 rounding beyond 10 h_max.
 // G is stored [k][j][i] (order 0, i fastest) or [i][k][j] (order 1, j fastest).
 template <typename T>
-__device__ __forceinline__ void green_cell_kernel_body(const GeomDev* __restrict__ g, int nx, int ny, int nz,
-                                  const double* __restrict__ F, T* __restrict__ G,
-    const int bx_, const int by_, const int bz_, const int nbx_, int order = 0) {
-    const int t = bx_ * blockDim.x + threadIdx.x;     // < 129^3
-    const int gx = nx + 1, gy = ny + 1, gz = nz + 1;
-    if (t >= gx * gy * gz) return;
-    int i, j, k;
-    if (order == 0) {
-        i = t % gx; j = (t / gx) % gy; k = t / (gx * gy);
-    } else {
-        j = t % gy; k = (t / gy) % gz; i = t / (gy * gz);
-    }
+__device__ __forceinline__ T green_cell_value(const GeomDev* __restrict__ g, int nx, int ny,
+                                              const double* __restrict__ F, int i, int j, int k) {
     const double hx = g->hr[0], hy = g->hr[1], hz = g->hr[2];
     const double k4 = 1.0 / (4.0 * 3.14159265358979323846 * 8.8541878128e-12);
     if (i <= g->R[0] && j <= g->R[1] && k <= g->R[2]) {
@@ -269,26 +259,49 @@ __device__ __forceinline__ void green_cell_kernel_body(const GeomDev* __restrict
         auto at = [&](int a, int b, int c) { return F[((int64_t)c * cy + b) * cx + a]; };
         double s = at(i + 1, j + 1, k + 1) - at(i, j + 1, k + 1) - at(i + 1, j, k + 1) - at(i + 1, j + 1, k) +
                    at(i, j, k + 1) + at(i, j + 1, k) + at(i + 1, j, k) - at(i, j, k);
-        G[t] = (T)(k4 * s / (hx * hy * hz));
-    } else {
-        // in units of r: direction cosines c_d = d / r and ratios t_d = h_d / r
-        const T x = (T)i * (T)hx, y = (T)j * (T)hy, z = (T)k * (T)hz;
-        const T ir = rsqrt(x * x + y * y + z * z);
-        const T c2[3] = {x * x * ir * ir, y * y * ir * ir, z * z * ir * ir};
-        const T t2[3] = {(T)hx * (T)hx * ir * ir, (T)hy * (T)hy * ir * ir, (T)hz * (T)hz * ir * ir};
-        T s2 = (T)0, s4 = (T)0, s22 = (T)0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            s2 += t2[d] * ((T)3 * c2[d] - (T)1);
-            s4 += t2[d] * t2[d] * (T)3 * ((T)35 * c2[d] * c2[d] - (T)30 * c2[d] + (T)3);
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int e = (d + 1) % 3;
-            s22 += t2[d] * t2[e] * (T)3 * ((T)35 * c2[d] * c2[e] - (T)5 * (c2[d] + c2[e]) + (T)1);
-        }
-        G[t] = (T)k4 * ir * ((T)1 + s2 / (T)24 + s4 / (T)1920 + s22 / (T)576);
+        return (T)(k4 * s / (hx * hy * hz));
     }
+    // in units of r: direction cosines c_d = d / r and ratios t_d = h_d / r
+    const T x = (T)i * (T)hx, y = (T)j * (T)hy, z = (T)k * (T)hz;
+    const T ir = rsqrt(x * x + y * y + z * z);
+    const T c2[3] = {x * x * ir * ir, y * y * ir * ir, z * z * ir * ir};
+    const T t2[3] = {(T)hx * (T)hx * ir * ir, (T)hy * (T)hy * ir * ir, (T)hz * (T)hz * ir * ir};
+    T s2 = (T)0, s4 = (T)0, s22 = (T)0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        s2 += t2[d] * ((T)3 * c2[d] - (T)1);
+        s4 += t2[d] * t2[d] * (T)3 * ((T)35 * c2[d] * c2[d] - (T)30 * c2[d] + (T)3);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int e = (d + 1) % 3;
+        s22 += t2[d] * t2[e] * (T)3 * ((T)35 * c2[d] * c2[e] - (T)5 * (c2[d] + c2[e]) + (T)1);
+    }
+    return (T)k4 * ir * ((T)1 + s2 / (T)24 + s4 / (T)1920 + s22 / (T)576);
+}
+
+// (i, j, k) of element l of DCT line ba in G's layout: order 0 G[z][y][x]
+// (lines along x), order 1 G[x][z][y] (lines along y)
+__device__ __forceinline__ void green_cell_index(int ba, int l, int nx, int ny, int nz, int order, int& i, int& j,
+                                                 int& k) {
+    if (order == 0) {
+        i = l; j = ba % (ny + 1); k = ba / (ny + 1);
+    } else {
+        j = l; k = ba % (nz + 1); i = ba / (nz + 1);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void green_cell_kernel_body(const GeomDev* __restrict__ g, int nx, int ny, int nz,
+                                  const double* __restrict__ F, T* __restrict__ G,
+    const int bx_, const int by_, const int bz_, const int nbx_, int order = 0) {
+    const int t = bx_ * blockDim.x + threadIdx.x;     // < 129^3
+    const int gx = nx + 1, gy = ny + 1, gz = nz + 1;
+    if (t >= gx * gy * gz) return;
+    const int L = order == 0 ? gx : gy;
+    int i, j, k;
+    green_cell_index(t / L, t % L, nx, ny, nz, order, i, j, k);
+    G[t] = green_cell_value<T>(g, nx, ny, F, i, j, k);
 }
 
 template <typename T>
@@ -312,9 +325,13 @@ constexpr int kDctAcc = 8;
 
 // ACC accumulators per lane: one sweep over l covers every output when
 // ACC * (warps per block) >= L.
-template <typename T, int ACC = kDctAcc>
+// CELL: the lines are not read from `in` but computed here as the cell
+// averages of the Green's function (green_cell_value; lines of G's layout for
+// `order`), so the cell pass and the first DCT pass are one launch.
+template <typename T, int ACC = kDctAcc, bool CELL = false>
 __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
-    const int bx_, const int by_, const int bz_, const int nbx_) {
+    const int bx_, const int by_, const int bz_, const int nbx_, const GeomDev* __restrict__ g = nullptr,
+    int nx = 0, int ny = 0, int nz = 0, const double* __restrict__ F = nullptr, int order = 0) {
     extern __shared__ unsigned char smraw[];
     T* Ds = reinterpret_cast<T*>(smraw);            // [L][L]
     T* xs = Ds + L * L;                             // [kDctLines][L] (room for [kDctLines][L + 1])
@@ -337,7 +354,20 @@ __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __r
         }
     };
     stage(D, Ds, L * L, L * L);
-    stage(in + ba0 * L, xs, nl * L, kDctLines * L);
+    if constexpr (CELL) {
+        for (int t = threadIdx.x; t < kDctLines * L; t += blockDim.x) {
+            const int line = t / L, lp = t - line * L;
+            T v = (T)0;
+            if (line < nl) {
+                int i, j, k;
+                green_cell_index((int)(ba0 + line), lp, nx, ny, nz, order, i, j, k);
+                v = green_cell_value<T>(g, nx, ny, F, i, j, k);
+            }
+            xs[t] = v;
+        }
+    } else {
+        stage(in + ba0 * L, xs, nl * L, kDctLines * L);
+    }
     __syncthreads();
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const T* x = xs + l * L;
@@ -367,6 +397,14 @@ __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __r
 template <typename T, int ACC = kDctAcc>
 static __global__ void dct_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA) {
     dct_kernel_body<T, ACC>(in, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
+}
+// Green's cell averages and the first DCT pass in one launch
+template <typename T, int ACC>
+static __global__ void cell_dct_kernel(T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
+                                       const GeomDev* __restrict__ g, int nx, int ny, int nz,
+                                       const double* __restrict__ F, int order) {
+    dct_kernel_body<T, ACC, true>(nullptr, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                  (int)gridDim.x, g, nx, ny, nz, F, order);
 }
 
 // ------------------------------------------------------------------ field
