@@ -1,6 +1,8 @@
 // Grid-side kernels: per-kick geometry, the integrated Green's function and
 // its real even spectrum, the zero-padded (Hockney) FFT convolution of all
 // dual channels, and the central finite-difference field.
+#include <algorithm>
+
 #include "field_dev.cuh"
 
 namespace adpic {
@@ -20,8 +22,14 @@ template <typename T>
 void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, double* corner, T* G, T* Gtmp, T* Ghat,
                   const T* dct_x, const T* dct_y, const T* dct_z, int order, cudaStream_t s) {
     (void)exact;
+    // FP32: the near box is a small part of the corner lattice, so a fixed grid
+    // of 608 blocks strides over it; FP64 (box = whole lattice): one thread per corner
     const int64_t nc = (int64_t)(nx + 2) * (ny + 2) * (nz + 2);
-    green_corner_kernel<<<(unsigned)((nc + 63) / 64), 64, 0, s>>>(geom, nx, ny, nz, corner);
+    if (sizeof(T) == 4)
+        green_corner_strided_kernel<<<(unsigned)std::min<int64_t>((nc + 63) / 64, 152 * 4), 64, 0, s>>>(geom, nx, ny,
+                                                                                                      nz, corner);
+    else
+        green_corner_kernel<<<(unsigned)((nc + 63) / 64), 64, 0, s>>>(geom, nx, ny, nz, corner);
     // each pass transforms the contiguous axis and makes it the outermost one;
     // the first pass computes its lines as the cell averages of G itself (G is
     // never stored). 16 warps per block and ACC = ceil(L / 16) accumulators:

@@ -240,6 +240,19 @@ static __global__ void green_corner_kernel(const GeomDev* __restrict__ g, int nx
     green_corner_kernel_body(g, nx, ny, nz, F, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x);
 }
 
+// The same integrals from a fixed grid of blocks that strides over the near
+// box (its size is known on the device only), instead of one thread per
+// corner of the whole lattice of which all but the box return at once.
+static __global__ void __launch_bounds__(64) green_corner_strided_kernel(const GeomDev* __restrict__ g, int nx, int ny,
+                                                                       int nz, double* __restrict__ F) {
+    const int ex = g->R[0] + 2, ey = g->R[1] + 2, ez = g->R[2] + 2;
+    const int cx = nx + 2, cy = ny + 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ex * ey * ez; t += gridDim.x * blockDim.x) {
+        const int i = t % ex, j = (t / ex) % ey, k = t / (ex * ey);
+        F[((int64_t)k * cy + j) * cx + i] = igf_F((i - 0.5) * g->hr[0], (j - 0.5) * g->hr[1], (k - 0.5) * g->hr[2]);
+    }
+}
+
 // Cell average of 1/(4 pi eps0 r) over the cell centred at offset (i, j, k):
 // the 8-corner difference of F in FP64 inside the near box (every cell on
 // the FP64 path), else the Taylor expansion of the box average of a smooth
