@@ -345,7 +345,7 @@ def run_native(args):
     alg_bytes = w.n_particles * 2 * 6 * C * 4 + 3 * C * nodes * 4
     achieved = alg_bytes / (push_ms / 1000.0) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
-    roof = {"bound": "hbm", "kernel": "push_kernel (CIC gather + kick + dual maps)", "achieved": achieved,
+    roof = {"bound": "hbm", "kernel": "push_tma_kernel (CIC gather + kick + dual maps)", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": push_ms,
