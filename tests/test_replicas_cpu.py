@@ -61,3 +61,20 @@ def test_two_replicas_take_the_slowest_rank_and_sum_the_work():
     w = I.workload("fodo_1m_64")
     assert rate0 == rate1 == pytest.approx(2 * w.n_particles * w.kicks_per_period / 7.5e-3)
     assert s0 != s1 and f0 != f1                           # independent replicas
+
+
+def test_push_traffic_record_is_read_only_for_its_source():
+    """bench.py reports the push's DRAM traffic from the committed ncu record only while the push
+    sources hash to the value stored with it."""
+    import re
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    text = open(os.path.join(ROOT, "profiles", "push_fodo_1m_64.md")).read()
+    stored = re.search(r"kernel_src_sha256:\s*([0-9a-f]{64})", text).group(1)
+    b = int(re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text).group(1))
+    assert bench.traffic_from_profile("fodo_1m_64", stored) == b
+    assert bench.traffic_from_profile("fodo_1m_64", "0" * 64) is None
+    assert bench.traffic_from_profile("no_such_workload", stored) is None
+    assert re.fullmatch(r"[0-9a-f]{64}", bench.kernel_src_hash())
