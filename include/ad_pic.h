@@ -118,7 +118,9 @@ int ad_pic_set_lattice(ad_pic* h, const ad_pic_lattice* lattice);
 /* Advance n_steps >= 0 space-charge kicks (each M1(tau/2) M2(tau) M1(tau/2)),
    continuing the kick counter; moments are reduced at every period end and
    after the last kick. Synchronizes before returning; returns
-   AD_PIC_ERR_OUT_OF_GRID / _NONFINITE if a kernel flagged a particle. */
+   AD_PIC_ERR_OUT_OF_GRID / _NONFINITE if a kernel flagged a particle, and
+   AD_PIC_ERR_TIMEOUT if the push gave up a bounded wait for a state tile
+   (the particle state is then not valid). */
 int ad_pic_run(ad_pic* h, int n_steps);
 
 /* Emittances of the latest moment record: values[2] = (eps_x, eps_y),

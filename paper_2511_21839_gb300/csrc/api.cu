@@ -449,6 +449,7 @@ struct Impl {
         CK(cudaStreamSynchronize(h->stream));
         if (h->tmask) tcollect(h, h->ev_used / 2);
         finish(h, rec.data(), nrec, n);
+        if (errw & kErrTimeout) return AD_PIC_ERR_TIMEOUT;     // a bulk copy was not waited for
         if (errw & kErrNonfinite) return AD_PIC_ERR_NONFINITE;
         if (errw & kErrOutOfGrid) return AD_PIC_ERR_OUT_OF_GRID;
         return AD_PIC_OK;
@@ -644,6 +645,7 @@ struct Impl {
         int errw = 0;
         CK(cudaMemcpy(&errw, h->err, sizeof(int), cudaMemcpyDeviceToHost));
         CK(cudaGetLastError());
+        if (errw & kErrTimeout) return AD_PIC_ERR_TIMEOUT;     // a bulk copy was not waited for
         if (errw & kErrNonfinite) return AD_PIC_ERR_NONFINITE;
         if (errw & kErrOutOfGrid) return AD_PIC_ERR_OUT_OF_GRID;
         return AD_PIC_OK;
