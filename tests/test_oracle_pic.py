@@ -380,6 +380,65 @@ def test_kick_matches_paper_perveance_for_long_beam():
     assert slope == pytest.approx(pred_slope, rel=0.03)
 
 
+def test_kick_constants_closed_form():
+    """Kick coefficients from the Lorentz force alone, recomputed here from CODATA: over a path
+    tau (time tau / v0) the longitudinal field, which a boost along z leaves unchanged, changes
+    p_z by q E_z tau / v0, so delta = dp / p0 changes by q E_z,rest tau / (p0 v0); the transverse
+    electric and magnetic forces of the co-moving bunch combine to q E_perp,lab / gamma0^2 =
+    q E_perp,rest / gamma0, so p_x / p0 changes by q E_perp,rest tau / (gamma0 p0 v0) (Sec. 4, map
+    M2, the Coulomb and vector potentials combined)."""
+    o = make()
+    c = o.constants()
+    mp = I.PROTON_MASS_EV
+    E = 1e9 + mp
+    pc = math.sqrt(E * E - mp * mp)
+    p0 = pc * QE / CL                                     # kg m / s
+    v0 = pc / E * CL
+    g0 = E / mp
+    assert c["kappa_z"] == pytest.approx(QE / (p0 * v0), rel=1e-13)
+    assert c["kappa_perp"] == pytest.approx(QE / (g0 * p0 * v0), rel=1e-13)
+    assert c["kappa_perp"] / c["kappa_z"] == pytest.approx(1.0 / g0, rel=1e-14)
+
+
+def test_longitudinal_kick_inside_uniform_sphere():
+    """The energy kick of Sec. 4's map M2 inside a uniformly charged sphere (rest frame): the
+    rest-frame field E_z = rho z_rest / (3 eps0) is exact inside, so delta changes by
+    q tau rho z_rest / (3 eps0 p0 v0), with p0 and v0 of the reference particle. An extra factor
+    1/gamma0 (as in the transverse kick) or 1/beta0 in the longitudinal coefficient fails this by
+    50 % or 14 %."""
+    o_probe = make(n=32, N=1, P=0)
+    c0 = o_probe.constants()
+    g0 = c0["gamma0"]
+    a = 1e-3
+    X, Y, Zr = _quiet_ellipsoid(a, a, a, 0.04e-3)
+    N = X.size
+    Q = 1e-10
+    o = make(n=32, N=N, P=0, q=Q)
+    st = np.zeros((6, N, 1))
+    st[0, :, 0], st[2, :, 0], st[4, :, 0] = X, Y, Zr / g0     # lab z = rest z / gamma0
+    geom = o.geometry(st)
+    E = o.field(geom, o.solve(geom, o.deposit(st, geom)))
+    before = st.copy()
+    o.kick(st, geom, E, 0)                                   # a D1 kick: tau = 0.5 m / 4
+    tau = 0.5 / 4
+    ddelta = st[5, :, 0] - before[5, :, 0]
+    assert np.array_equal(st[4], before[4]) and np.array_equal(st[0], before[0])
+    inner = X ** 2 + Y ** 2 + Zr ** 2 < (0.5 * a) ** 2
+    mp = I.PROTON_MASS_EV
+    Etot = 1e9 + mp
+    pc = math.sqrt(Etot * Etot - mp * mp)
+    p0 = pc * QE / CL
+    v0 = pc / Etot * CL
+    rho_rest = Q / (4.0 / 3.0 * math.pi * a ** 3)
+    pred_slope = QE * tau * rho_rest / (3 * EPS0 * p0 * v0)   # d(delta) / d(z_rest)
+    slope = np.sum(ddelta[inner] * Zr[inner]) / np.sum(Zr[inner] ** 2)
+    assert slope == pytest.approx(pred_slope, rel=0.03)
+    # and the transverse kick of the same sphere, for the ratio of the two coefficients
+    dpx = st[1, :, 0] - before[1, :, 0]
+    slope_x = np.sum(dpx[inner] * X[inner]) / np.sum(X[inner] ** 2)
+    assert slope_x / slope == pytest.approx(1.0 / g0, rel=0.03)
+
+
 # ---------------------------------------------------------------- P8: emittance of a constructed ensemble
 
 def test_emittance_constructed_ensemble():
