@@ -753,6 +753,21 @@ int orc_kick(const orc_config* cfg, double* state, const double* geom, const dou
 /* Dual beam moments and emittance (Sec. 4, D eps_x)                    */
 /* ------------------------------------------------------------------ */
 
+/* Neumaier's compensated summation (the Kahan-Babuska improvement of Kahan's
+   method): *s holds the running sum and *c the accumulated rounding errors, so
+   s + c is the sum up to about one rounding, whatever the order of the terms. */
+static void nsum_add(double* s, double* c, double x) {
+    const double t = *s + x;
+    if (fabs(*s) >= fabs(x)) *c += (*s - t) + x;
+    else *c += (x - t) + *s;
+    *s = t;
+}
+
+/* Dual moments <u>, <p>, <u^2>, <u p>, <p^2> per plane (Sec. 4, the means of
+   the dual emittance), each an average over particles. The emittance
+   derivatives cancel strongly (the emittance barely changes while the second
+   moments do), so the sums are compensated: their rounding does not depend
+   on the summation order (thread count) at the level the derivatives need. */
 void orc_moments(const orc_config* cfg, const double* state, double* mom) {
     const int C = cfg->P + 1;
     const int64_t N = cfg->N;
@@ -760,37 +775,49 @@ void orc_moments(const orc_config* cfg, const double* state, double* mom) {
 #ifdef _OPENMP
     nthreads = omp_get_max_threads();
 #endif
-    double* part = (double*)malloc(sizeof(double) * nthreads * 5 * ORC_MAXC);
+    /* per thread: [5][ORC_MAXC] sums then [5][ORC_MAXC] compensations */
+    double* part = (double*)malloc(sizeof(double) * nthreads * 10 * ORC_MAXC);
     for (int pl = 0; pl < 3; ++pl) {
-        dual s[5];
-        for (int q = 0; q < 5; ++q) d_const(C, 0.0, s[q]);
 #pragma omp parallel
         {
             int tid = 0;
 #ifdef _OPENMP
             tid = omp_get_thread_num();
 #endif
-            double* t = part + (int64_t)tid * 5 * ORC_MAXC;
+            double* t = part + (int64_t)tid * 10 * ORC_MAXC;
+            double* tc = t + 5 * ORC_MAXC;
             dual a;
-            for (int q = 0; q < 5; ++q) d_const(C, 0.0, t + q * ORC_MAXC);
+            for (int j = 0; j < 10 * ORC_MAXC; ++j) t[j] = 0.0;
 #pragma omp for schedule(static)
             for (int64_t i = 0; i < N; ++i) {
                 const double* u = ccoord(state, N, C, 2 * pl, i);
                 const double* p = ccoord(state, N, C, 2 * pl + 1, i);
-                d_add(C, t + 0 * ORC_MAXC, u, t + 0 * ORC_MAXC);
-                d_add(C, t + 1 * ORC_MAXC, p, t + 1 * ORC_MAXC);
-                d_mul(C, u, u, a); d_add(C, t + 2 * ORC_MAXC, a, t + 2 * ORC_MAXC);
-                d_mul(C, u, p, a); d_add(C, t + 3 * ORC_MAXC, a, t + 3 * ORC_MAXC);
-                d_mul(C, p, p, a); d_add(C, t + 4 * ORC_MAXC, a, t + 4 * ORC_MAXC);
+                for (int k = 0; k < C; ++k) {
+                    nsum_add(t + 0 * ORC_MAXC + k, tc + 0 * ORC_MAXC + k, u[k]);
+                    nsum_add(t + 1 * ORC_MAXC + k, tc + 1 * ORC_MAXC + k, p[k]);
+                }
+                d_mul(C, u, u, a);
+                for (int k = 0; k < C; ++k) nsum_add(t + 2 * ORC_MAXC + k, tc + 2 * ORC_MAXC + k, a[k]);
+                d_mul(C, u, p, a);
+                for (int k = 0; k < C; ++k) nsum_add(t + 3 * ORC_MAXC + k, tc + 3 * ORC_MAXC + k, a[k]);
+                d_mul(C, p, p, a);
+                for (int k = 0; k < C; ++k) nsum_add(t + 4 * ORC_MAXC + k, tc + 4 * ORC_MAXC + k, a[k]);
             }
         }
-        /* partial sums combined in thread order: the result is reproducible */
-        for (int th = 0; th < nthreads; ++th)
-            for (int q = 0; q < 5; ++q) d_add(C, s[q], part + ((int64_t)th * 5 + q) * ORC_MAXC, s[q]);
+        /* thread partials (sums and compensations) combined in thread order */
         for (int q = 0; q < 5; ++q) {
-            dual nd;
+            dual sq, nd;
+            for (int k = 0; k < C; ++k) {
+                double s = 0.0, c = 0.0;
+                for (int th = 0; th < nthreads; ++th) {
+                    const double* t = part + (int64_t)th * 10 * ORC_MAXC;
+                    nsum_add(&s, &c, t[q * ORC_MAXC + k]);
+                    nsum_add(&s, &c, t[(5 + q) * ORC_MAXC + k]);
+                }
+                sq[k] = s + c;
+            }
             d_const(C, N > 0 ? (double)N : 1.0, nd);
-            d_div(C, s[q], nd, mom + (pl * 5 + q) * C);
+            d_div(C, sq, nd, mom + (pl * 5 + q) * C);
         }
     }
     free(part);
