@@ -27,6 +27,11 @@ class OrcConfig(ct.Structure):
     ]
 
 
+class OrcElement(ct.Structure):
+    _fields_ = [("type", ct.c_int32), ("slot_L", ct.c_int32), ("slot_k", ct.c_int32), ("pad", ct.c_int32),
+                ("L", ct.c_double), ("k", ct.c_double)]
+
+
 _lib = None
 
 
@@ -57,6 +62,10 @@ def lib():
             "orc_moments": (None, [cp, dp, dp]),
             "orc_emittance": (None, [cp, dp, dp]),
             "orc_run": (ct.c_int, [cp, dp, ct.c_int64, ct.c_int, dp, dp, ct.c_int]),
+            "orc_beamline_matrix": (None, [ct.c_int, ct.POINTER(OrcElement), ct.c_int, dp]),
+            "orc_twiss": (None, [ct.c_int, ct.POINTER(OrcElement), ct.c_int, dp, dp]),
+            "orc_periodic_twiss": (ct.c_int, [ct.c_int, ct.POINTER(OrcElement), ct.c_int, dp]),
+            "orc_track": (None, [ct.c_int, ct.POINTER(OrcElement), ct.c_int, ct.c_int64, ct.c_int64, dp, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -222,3 +231,41 @@ def igf(x, y, z, hx, hy, hz):
 
 def threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# ---------------------------------------------------------------- single-particle dual optics (Sec. 3)
+
+def elements(beamline):
+    """ctypes array of OrcElement from (type, L, k, slot_L, slot_k) tuples."""
+    arr = (OrcElement * len(beamline))()
+    for i, (t, L, k, sL, sk) in enumerate(beamline):
+        arr[i] = OrcElement(int(t), int(sL), int(sk), 0, float(L), float(k))
+    return arr
+
+
+def beamline_matrix(beamline, P):
+    m = np.zeros((2, 4, P + 1))
+    lib().orc_beamline_matrix(P, elements(beamline), len(beamline), _p(m))
+    return m
+
+
+def twiss(beamline, P, twiss0):
+    out = np.zeros((4, P + 1))
+    lib().orc_twiss(P, elements(beamline), len(beamline), _p(np.ascontiguousarray(twiss0, dtype=np.float64)),
+                    _p(out))
+    return out
+
+
+def periodic_twiss(beamline, P):
+    out = np.zeros((4, P + 1))
+    st = lib().orc_periodic_twiss(P, elements(beamline), len(beamline), _p(out))
+    if st != 0:
+        raise ValueError("unstable cell")
+    return out
+
+
+def track(beamline, P, x0, n_repeat):
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    out = np.zeros((x0.shape[0], 4, P + 1))
+    lib().orc_track(P, elements(beamline), len(beamline), int(n_repeat), x0.shape[0], _p(x0), _p(out))
+    return out

@@ -884,3 +884,128 @@ int orc_run(const orc_config* cfg, double* state, int64_t kick0, int n_kicks, do
     free(rho); free(phi); free(E);
     return st ? st : rec;
 }
+
+/* ------------------------------------------------------------------ */
+/* Single-particle dual optics (Sec. 3): transfer matrices of a beamline */
+/* of drifts and thick quadrupoles, Twiss transport (Eq. 5), periodic    */
+/* Twiss functions of a cell, and element-by-element particle tracking. */
+/* ------------------------------------------------------------------ */
+
+/* element map of one plane: quad strength +k in x, -k in y, over length L (Eq. quadtr) */
+static void element_plane_map(int C, const orc_element* e, int plane, double m[4][ORC_MAXC]) {
+    dual L, k;
+    d_var(C, e->L, e->slot_L, L);
+    d_var(C, e->type == 1 ? e->k : 0.0, e->type == 1 ? e->slot_k : -1, k);
+    if (plane == 1)
+        for (int j = 0; j < C; ++j) k[j] = -k[j];
+    plane_map(C, k, L, m);
+}
+
+/* B A for dual 2x2 matrices (A first along the beam) */
+static void mat_mul2(int C, double b[4][ORC_MAXC], double a[4][ORC_MAXC], double out[4][ORC_MAXC]) {
+    dual t1, t2, r[4];
+    d_mul(C, b[0], a[0], t1); d_mul(C, b[1], a[2], t2); d_add(C, t1, t2, r[0]);
+    d_mul(C, b[0], a[1], t1); d_mul(C, b[1], a[3], t2); d_add(C, t1, t2, r[1]);
+    d_mul(C, b[2], a[0], t1); d_mul(C, b[3], a[2], t2); d_add(C, t1, t2, r[2]);
+    d_mul(C, b[2], a[1], t1); d_mul(C, b[3], a[3], t2); d_add(C, t1, t2, r[3]);
+    for (int i = 0; i < 4; ++i) d_copy(C, r[i], out[i]);
+}
+
+void orc_beamline_matrix(int P, const orc_element* el, int n, double* m) {
+    const int C = P + 1;
+    for (int pl = 0; pl < 2; ++pl) {
+        double acc[4][ORC_MAXC], em[4][ORC_MAXC];
+        d_const(C, 1.0, acc[0]); d_const(C, 0.0, acc[1]); d_const(C, 0.0, acc[2]); d_const(C, 1.0, acc[3]);
+        for (int i = 0; i < n; ++i) {
+            element_plane_map(C, &el[i], pl, em);
+            mat_mul2(C, em, acc, acc);
+        }
+        for (int j = 0; j < 4; ++j) d_copy(C, acc[j], m + (pl * 4 + j) * C);
+    }
+}
+
+/* Eq. 5: (beta, alpha) at s from (beta0, alpha0, gamma0) at 0 and the matrix m from 0 to s */
+static void twiss_transport(int C, double m[4][ORC_MAXC], const double* b0, const double* a0, double* b, double* a) {
+    dual one, g0, t, u, v;
+    d_const(C, 1.0, one);
+    d_mul(C, a0, a0, t);
+    d_add(C, one, t, t);
+    d_div(C, t, b0, g0);                                  /* gamma0 = (1 + alpha0^2) / beta0 */
+    /* beta = m11^2 beta0 - 2 m11 m12 alpha0 + m12^2 gamma0 */
+    d_mul(C, m[0], m[0], t); d_mul(C, t, b0, u);
+    d_mul(C, m[0], m[1], t); d_mul(C, t, a0, t); d_cmul(C, 2.0, t, t); d_sub(C, u, t, u);
+    d_mul(C, m[1], m[1], t); d_mul(C, t, g0, t); d_add(C, u, t, v);
+    d_copy(C, v, b);
+    /* alpha = -m11 m21 beta0 + (m11 m22 + m12 m21) alpha0 - m12 m22 gamma0 */
+    d_mul(C, m[0], m[2], t); d_mul(C, t, b0, u);
+    for (int k = 0; k < C; ++k) u[k] = -u[k];
+    d_mul(C, m[0], m[3], t); d_mul(C, m[1], m[2], v); d_add(C, t, v, t); d_mul(C, t, a0, t); d_add(C, u, t, u);
+    d_mul(C, m[1], m[3], t); d_mul(C, t, g0, t); d_sub(C, u, t, u);
+    d_copy(C, u, a);
+}
+
+void orc_twiss(int P, const orc_element* el, int n, const double* twiss0, double* out) {
+    const int C = P + 1;
+    double m[2 * 4 * ORC_MAXC];
+    orc_beamline_matrix(P, el, n, m);
+    for (int pl = 0; pl < 2; ++pl) {
+        double mm[4][ORC_MAXC];
+        dual b0, a0;
+        for (int j = 0; j < 4; ++j) d_copy(C, m + (pl * 4 + j) * C, mm[j]);
+        d_const(C, twiss0[2 * pl], b0);
+        d_const(C, twiss0[2 * pl + 1], a0);
+        twiss_transport(C, mm, b0, a0, out + (2 * pl) * C, out + (2 * pl + 1) * C);
+    }
+}
+
+/* periodic solution of the cell: cos mu = (m11 + m22) / 2, sin mu with the sign of m12,
+   beta = m12 / sin mu, alpha = (m11 - m22) / (2 sin mu) */
+int orc_periodic_twiss(int P, const orc_element* el, int n, double* out) {
+    const int C = P + 1;
+    double m[2 * 4 * ORC_MAXC];
+    orc_beamline_matrix(P, el, n, m);
+    for (int pl = 0; pl < 2; ++pl) {
+        const double* m11 = m + (pl * 4 + 0) * C;
+        const double* m12 = m + (pl * 4 + 1) * C;
+        const double* m22 = m + (pl * 4 + 3) * C;
+        dual cs, t, one, s;
+        d_add(C, m11, m22, t);
+        d_cmul(C, 0.5, t, cs);
+        if (!(fabs(cs[0]) < 1.0)) return -1;               /* unstable cell */
+        d_const(C, 1.0, one);
+        d_mul(C, cs, cs, t);
+        d_sub(C, one, t, t);
+        d_sqrt(C, t, s);
+        if (m12[0] < 0.0)
+            for (int k = 0; k < C; ++k) s[k] = -s[k];
+        d_div(C, m12, s, out + (2 * pl) * C);
+        d_sub(C, m11, m22, t);
+        d_cmul(C, 0.5, t, t);
+        d_div(C, t, s, out + (2 * pl + 1) * C);
+    }
+    return 0;
+}
+
+void orc_track(int P, const orc_element* el, int n, int64_t n_repeat, int64_t N, const double* x0, double* out) {
+    const int C = P + 1;
+    /* the element maps do not change from turn to turn */
+    double* maps = (double*)malloc(sizeof(double) * (size_t)n * 2 * 4 * ORC_MAXC);
+    for (int i = 0; i < n; ++i)
+        for (int pl = 0; pl < 2; ++pl) element_plane_map(C, &el[i], pl, (double(*)[ORC_MAXC])(maps + ((size_t)i * 2 + pl) * 4 * ORC_MAXC));
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < N; ++p) {
+        dual z[4], t1, t2, nx, np;
+        for (int c = 0; c < 4; ++c) d_const(C, x0[p * 4 + c], z[c]);
+        for (int64_t r = 0; r < n_repeat; ++r)
+            for (int i = 0; i < n; ++i)
+                for (int pl = 0; pl < 2; ++pl) {
+                    double(*mm)[ORC_MAXC] = (double(*)[ORC_MAXC])(maps + ((size_t)i * 2 + pl) * 4 * ORC_MAXC);
+                    d_mul(C, mm[0], z[2 * pl], t1); d_mul(C, mm[1], z[2 * pl + 1], t2); d_add(C, t1, t2, nx);
+                    d_mul(C, mm[2], z[2 * pl], t1); d_mul(C, mm[3], z[2 * pl + 1], t2); d_add(C, t1, t2, np);
+                    d_copy(C, nx, z[2 * pl]);
+                    d_copy(C, np, z[2 * pl + 1]);
+                }
+        for (int c = 0; c < 4; ++c) d_copy(C, z[c], out + (p * 4 + c) * C);
+    }
+    free(maps);
+}

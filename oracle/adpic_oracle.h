@@ -93,4 +93,26 @@ void orc_emittance(const orc_config* cfg, const double* mom, double* eps /*[3][C
 int orc_run(const orc_config* cfg, double* state, int64_t kick0, int n_kicks,
             double* mom_hist, double* geom_io, int geom_mode);
 
+/* ---- single-particle dual optics (Sec. 3) ---- */
+
+/* one element of a beamline: type 0 drift, 1 thick quadrupole of normalised
+   strength k (1/m^2; > 0 focuses in x, defocuses in y); slot_L, slot_k are
+   the derivative slots of L and k (-1 = constant) */
+typedef struct {
+    int32_t type, slot_L, slot_k, pad;
+    double L, k;
+} orc_element;
+
+/* dual 2x2 matrices of the beamline (elements in beam order):
+   m[plane x, y][m11, m12, m21, m22][C] */
+void orc_beamline_matrix(int P, const orc_element* el, int n, double* m);
+/* Twiss transport (Sec. 3, Eq. 5) through the beamline from constant
+   twiss0[4] = (beta_x, alpha_x, beta_y, alpha_y): out[4][C] */
+void orc_twiss(int P, const orc_element* el, int n, const double* twiss0, double* out);
+/* periodic Twiss functions of a cell, out[4][C]; -1 if the cell is unstable */
+int orc_periodic_twiss(int P, const orc_element* el, int n, double* out);
+/* particles x0[N][4] (x, px, y, py) through the beamline n_repeat times,
+   element by element: out[N][4][C] */
+void orc_track(int P, const orc_element* el, int n, int64_t n_repeat, int64_t N, const double* x0, double* out);
+
 #endif
