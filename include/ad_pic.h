@@ -51,7 +51,8 @@ enum {
     AD_PIC_ERR_NONFINITE = -5,   /* a particle coordinate became NaN or Inf */
     AD_PIC_ERR_OUT_OF_GRID = -6, /* a particle fell outside the grid stencil */
     AD_PIC_ERR_TIMEOUT = -7,     /* a bounded device wait gave up */
-    AD_PIC_ERR_UNSUPPORTED = -8  /* valid request this build does not implement */
+    AD_PIC_ERR_UNSUPPORTED = -8, /* valid request this build does not implement */
+    AD_PIC_ERR_IO = -9           /* a checkpoint file could not be read or written */
 };
 
 enum { AD_PIC_FP64 = 0, AD_PIC_FP32_MIXED = 1 };
@@ -120,8 +121,44 @@ int ad_pic_set_lattice(ad_pic* h, const ad_pic_lattice* lattice);
    after the last kick. Synchronizes before returning; returns
    AD_PIC_ERR_OUT_OF_GRID / _NONFINITE if a kernel flagged a particle, and
    AD_PIC_ERR_TIMEOUT if the push gave up a bounded wait for a state tile
-   (the particle state is then not valid). */
+   (the particle state is then not valid: ad_pic_run and ad_pic_get_particles
+   return AD_PIC_ERR_STATE until ad_pic_set_beam with normals,
+   ad_pic_set_particles or ad_pic_load sets it again). The host-side fault
+   injection of the failure tests (no GPU fault) reads the environment:
+   ADPIC_FAULT=launch makes the run's launch fail (AD_PIC_ERR_CUDA, nothing
+   advanced); ADPIC_FAULT=alloc:K makes every device allocation of a handle
+   after its first K fail (AD_PIC_ERR_OOM). */
 int ad_pic_run(ad_pic* h, int n_steps);
+
+/* Checkpoint and resume (Sec. 4's periodic-lattice runs are long; a run must
+   survive a restart). ad_pic_save writes the dual particle state in the
+   handle's precision with the caller's index of every particle, the kick
+   counter, the lattice, the reference-particle constants and the moment
+   history to `path` (synchronizes the handle's stream; AD_PIC_ERR_STATE if
+   no particles are set, AD_PIC_ERR_IO if the file cannot be written).
+   ad_pic_load reads such a file into a handle created with the same grid,
+   particle count, n_deriv and precision (AD_PIC_ERR_INVALID_ARG otherwise);
+   a following ad_pic_run continues the saved run. A failed load leaves the
+   handle without particles (AD_PIC_ERR_STATE until they are set). The format
+   is the library's own, native byte order. */
+int ad_pic_save(const ad_pic* h, const char* path);
+int ad_pic_load(ad_pic* h, const char* path);
+
+/* Poll limit of the push's waits for a bulk-copied state tile: polls >= 0
+   sets it (0: a wait gives up at once, without polling), polls < 0 restores
+   the default of 2^18 polls (each failed poll suspends for a system-dependent
+   time, about 1.9 us on GB300, so about half a second). When a wait runs out
+   the push records a timeout, lets its copies in flight land (those waits
+   keep the default limit) and returns; ad_pic_run then reports
+   AD_PIC_ERR_TIMEOUT. A zero limit is how the failure tests make a wait run
+   out. Drops captured graphs. */
+int ad_pic_set_wait_limit(ad_pic* h, int polls);
+
+/* Device time of a bounded wait that runs out: one thread polls a
+   shared-memory barrier that nothing arrives on, `polls` times, on the
+   current device's default stream. *ms = its CUDA-event time, *failed = the
+   polls that failed (all of them). Allocates 4 bytes of device memory. */
+int ad_pic_wait_probe(int polls, double* ms, int* failed);
 
 /* Emittances of the latest moment record: values[2] = (eps_x, eps_y),
    geometric rms (m rad), centred moments; derivs[2*n_deriv] row-major
@@ -245,13 +282,27 @@ void ad_pic_mlp_destroy(ad_pic_mlp* m);
    stream: cudaStream_t as void* (NULL = default stream); the call only
    enqueues work and does not synchronise. The per-block partial sums live in
    one static device array of 583,680 bytes (304 blocks x 15 x 16 doubles)
-   that every GPU loading the library holds until exit; n_deriv other than 7
-   or 13 exceeds it and returns AD_PIC_ERR_INVALID_ARG. The first call on a
-   device looks the array's address up (cudaGetSymbolAddress) with that
-   device current; make that first call before any stream capture. All calls
-   share the array, so calls that overlap on the GPU race. */
+   that every GPU loading the library holds until exit. n_deriv must be 7 or
+   13 (AD_PIC_ERR_INVALID_ARG otherwise): only those two channel layouts are
+   compiled; the array holds up to 16 channels. Every call made outside
+   stream capture looks the array's address up (cudaGetSymbolAddress) with
+   the current device; a call made while `stream` is capturing uses the
+   address of the last such lookup on that device, so make a first call on
+   each device before any stream capture (AD_PIC_ERR_STATE otherwise). If a
+   CUDA error is already pending at entry, the call returns AD_PIC_ERR_CUDA
+   without launching and leaves that error pending. All calls share the
+   array, so calls that overlap on the GPU race. */
 int ad_pic_moments_device(const void* state_dev, int64_t n_particles, int n_deriv, int precision, double* mom_dev,
                           void* stream);
+
+/* Measured fused multiply-add throughput of the current device (the ALU
+   ceiling of the plain FP64 path and of the FP32 arithmetic of the mixed
+   path, which the paper does not state): precision AD_PIC_FP32_MIXED times
+   FP32 FMA chains, AD_PIC_FP64 FP64 FMA chains, 8 independent chains per
+   thread on 8 blocks of 256 threads per SM, best of 5 CUDA-event-timed
+   launches after a warm-up; *tflops counts an FMA as 2 flops. Changes no
+   device setting; allocates a small output buffer. */
+int ad_pic_fma_peak(int precision, double* tflops);
 
 /* Derived constants: out[8] = gamma0, beta0, p0 (kg m/s), B rho (T m),
    kappa_perp, kappa_z (1/(V/m * m)), macroparticle charge (C), q (C). */

@@ -17,7 +17,8 @@ AD_PIC_FP32_MIXED = 1
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error", -4: "call out of order",
           -5: "non-finite particle coordinate", -6: "particle outside the grid stencil",
-          -7: "bounded device wait timed out", -8: "unsupported"}
+          -7: "bounded device wait timed out", -8: "unsupported",
+          -9: "checkpoint file could not be read or written"}
 
 
 class ad_pic_grid(ct.Structure):
@@ -72,6 +73,11 @@ def lib():
             "ad_pic_constants": (ct.c_int, [vp, dp]),
             "ad_pic_launches": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
             "ad_pic_moments_device": (ct.c_int, [vp, ct.c_int64, ct.c_int, ct.c_int, vp, vp]),
+            "ad_pic_fma_peak": (ct.c_int, [ct.c_int, dp]),
+            "ad_pic_save": (ct.c_int, [vp, ct.c_char_p]),
+            "ad_pic_load": (ct.c_int, [vp, ct.c_char_p]),
+            "ad_pic_set_wait_limit": (ct.c_int, [vp, ct.c_int]),
+            "ad_pic_wait_probe": (ct.c_int, [ct.c_int, dp, ct.POINTER(ct.c_int)]),
             "ad_pic_batch_create": (ct.c_int, [ct.c_int, ct.POINTER(ad_pic_grid), ct.POINTER(ct.c_int64), ct.c_int,
                                                ct.c_int, ct.POINTER(vp)]),
             "ad_pic_batch_set_beam": (ct.c_int, [vp, ct.c_int, ct.POINTER(ad_pic_beam), dp]),
@@ -211,6 +217,31 @@ def ad_pic_moments_device(state_ptr, n_particles, n_deriv, precision, mom_ptr, s
     _ck("ad_pic_moments_device", lib().ad_pic_moments_device(ct.c_void_p(state_ptr), int(n_particles), int(n_deriv),
                                                              int(precision), ct.c_void_p(mom_ptr),
                                                              ct.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def ad_pic_fma_peak(precision):
+    t = ct.c_double()
+    _ck("ad_pic_fma_peak", lib().ad_pic_fma_peak(int(precision), ct.byref(t)))
+    return t.value
+
+
+def ad_pic_save(h, path):
+    _ck("ad_pic_save", lib().ad_pic_save(h, os.fsencode(path)))
+
+
+def ad_pic_load(h, path):
+    _ck("ad_pic_load", lib().ad_pic_load(h, os.fsencode(path)))
+
+
+def ad_pic_set_wait_limit(h, polls):
+    _ck("ad_pic_set_wait_limit", lib().ad_pic_set_wait_limit(h, int(polls)))
+
+
+def ad_pic_wait_probe(polls):
+    ms = ct.c_double()
+    failed = ct.c_int()
+    _ck("ad_pic_wait_probe", lib().ad_pic_wait_probe(int(polls), ct.byref(ms), ct.byref(failed)))
+    return ms.value, failed.value
 
 
 def ad_pic_launches(h):
@@ -447,6 +478,15 @@ class ADPIC:
 
     def timing(self):
         return ad_pic_timing(self.h)
+
+    def save(self, path):
+        ad_pic_save(self.h, path)
+
+    def load(self, path):
+        ad_pic_load(self.h, path)
+
+    def set_wait_limit(self, polls):
+        ad_pic_set_wait_limit(self.h, polls)
 
 
 class Batch:

@@ -5,6 +5,7 @@
 // timing, and the stage entry points used by the parity tests.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -107,8 +108,24 @@ namespace {
         }                                                                                      \
     } while (0)
 
+// Host-side fault injection for the failure-handling tests (no GPU fault is
+// ever made): ADPIC_FAULT=alloc:K makes every device allocation of a handle
+// after its first K fail as if cudaMalloc had run out of memory;
+// ADPIC_FAULT=launch makes ad_pic_run's launch report a failed launch.
+int fault_alloc_after() {
+    const char* f = std::getenv("ADPIC_FAULT");
+    if (!f || std::strncmp(f, "alloc", 5) != 0) return -1;
+    return f[5] == ':' ? std::atoi(f + 6) : 0;
+}
+bool fault_launch() {
+    const char* f = std::getenv("ADPIC_FAULT");
+    return f && std::strcmp(f, "launch") == 0;
+}
+
 int dalloc(ad_pic* h, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
+    const int after = fault_alloc_after();
+    if (after >= 0 && (int)h->allocs.size() >= after) { *p = nullptr; return AD_PIC_ERR_OOM; }
     if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; cudaGetLastError(); return AD_PIC_ERR_OOM; }
     h->allocs.push_back(*p);
     return AD_PIC_OK;
@@ -174,7 +191,7 @@ struct Impl {
     static void push(ad_pic* h, int& from, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track) {
         launch_push<T, C, CP>(buf(h, from), buf(h, 1 - from), h->N, (const T*)h->E, h->geom, h->nx, h->ny, h->nz, A,
                               K, track, (Ord<T>*)h->mm, h->err, sortbuf(h, from), track ? gfuse(h) : no_fuse(),
-                              h->stream);
+                              h->wait_polls, h->stream);
         from = 1 - from;
     }
 
@@ -437,8 +454,9 @@ struct Impl {
                 nrec = count_records(h, g0, n, first);
                 h->ev_used = count_events(h, n, first, nrec);
             }
-            CK(cudaGraphLaunch(it->second, h->stream));
+            CK(fault_launch() ? cudaErrorLaunchFailure : cudaGraphLaunch(it->second, h->stream));
         } else {
+            if (fault_launch()) return AD_PIC_ERR_CUDA;
             nrec = enqueue_run(h, g0, n, first, false, from);
             CK(cudaGetLastError());
         }
@@ -449,7 +467,12 @@ struct Impl {
         CK(cudaStreamSynchronize(h->stream));
         if (h->tmask) tcollect(h, h->ev_used / 2);
         finish(h, rec.data(), nrec, n);
-        if (errw & kErrTimeout) return AD_PIC_ERR_TIMEOUT;     // a bulk copy was not waited for
+        if (errw & kErrTimeout) {
+            // a push gave up waiting for a state tile: some particles were not
+            // pushed (nor their slots written), so the state must be set again
+            h->particles_set = false;
+            return AD_PIC_ERR_TIMEOUT;
+        }
         if (errw & kErrNonfinite) return AD_PIC_ERR_NONFINITE;
         if (errw & kErrOutOfGrid) return AD_PIC_ERR_OUT_OF_GRID;
         return AD_PIC_OK;
@@ -651,6 +674,109 @@ struct Impl {
         return AD_PIC_OK;
     }
 
+    // ---- checkpoint: the dual state of the handle's precision (with the
+    // caller's particle index of every slot), the kick counter, the lattice,
+    // the reference-particle constants and the moment history, so that a run
+    // resumed from the file continues the same run
+    struct FileHeader {
+        char magic[8];
+        uint32_t version, elem;
+        int32_t prec, n_deriv, chans, chans_padded, nx, ny, nz, flags, first_record, pad;
+        int64_t N, kick, hist_len;
+        double consts[8];
+        ad_pic_lattice lat;
+    };
+    static constexpr size_t kChunk = (size_t)64 << 20;   // bytes staged on the host at a time
+
+    static int save(ad_pic* h, const char* path) {
+        if (!h->particles_set) return AD_PIC_ERR_STATE;
+        FileHeader hd{};
+        std::memcpy(hd.magic, "ADPICCK", 8);
+        hd.version = 1;
+        hd.elem = sizeof(T);
+        hd.prec = h->prec; hd.n_deriv = h->P; hd.chans = C; hd.chans_padded = CP;
+        hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz;
+        hd.flags = (h->beam_set ? 1 : 0) | (h->lattice_set ? 2 : 0);
+        hd.first_record = h->first_record ? 1 : 0;
+        hd.N = h->N; hd.kick = h->kick; hd.hist_len = (int64_t)h->hist.size();
+        const double k[8] = {h->gamma0, h->beta0, h->p0, h->brho, h->kperp, h->kz, h->qm, h->q};
+        std::memcpy(hd.consts, k, sizeof(k));
+        hd.lat = h->lat;
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return AD_PIC_ERR_CUDA;
+        FILE* f = std::fopen(path, "wb");
+        if (!f) return AD_PIC_ERR_IO;
+        bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+        if (ok && !h->hist.empty()) ok = std::fwrite(h->hist.data(), sizeof(double), h->hist.size(), f) == h->hist.size();
+        std::vector<unsigned char> buf;
+        auto dump = [&](const void* dev, size_t bytes) -> int {
+            for (size_t o = 0; o < bytes && ok; o += kChunk) {
+                const size_t n = bytes - o < kChunk ? bytes - o : kChunk;
+                buf.resize(n);
+                if (cudaMemcpy(buf.data(), (const unsigned char*)dev + o, n, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return AD_PIC_ERR_CUDA;
+                ok = std::fwrite(buf.data(), 1, n, f) == n;
+            }
+            return AD_PIC_OK;
+        };
+        int st_ = dump(st(h), sizeof(T) * 6 * (size_t)h->N * CP);
+        if (!st_) st_ = dump(h->ids[h->cur], sizeof(int) * (size_t)h->N);
+        if (std::fclose(f) != 0) ok = false;
+        if (st_) return st_;
+        return ok ? AD_PIC_OK : AD_PIC_ERR_IO;
+    }
+
+    static int load(ad_pic* h, const char* path) {
+        FILE* f = std::fopen(path, "rb");
+        if (!f) return AD_PIC_ERR_IO;
+        FileHeader hd{};
+        int rc = AD_PIC_OK;
+        if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "ADPICCK", 8) != 0 || hd.version != 1)
+            rc = AD_PIC_ERR_IO;
+        else if (hd.elem != sizeof(T) || hd.prec != h->prec || hd.n_deriv != h->P || hd.nx != h->nx || hd.ny != h->ny ||
+                 hd.nz != h->nz || hd.N != h->N || hd.hist_len < 0 || hd.hist_len % (15 * C) != 0)
+            rc = AD_PIC_ERR_INVALID_ARG;      // a checkpoint of another configuration
+        std::vector<double> hist;
+        if (!rc) {
+            hist.resize((size_t)hd.hist_len);
+            if (!hist.empty() && std::fread(hist.data(), sizeof(double), hist.size(), f) != hist.size()) rc = AD_PIC_ERR_IO;
+        }
+        std::vector<unsigned char> buf;
+        auto fill = [&](void* dev, size_t bytes) {
+            for (size_t o = 0; o < bytes && !rc; o += kChunk) {
+                const size_t n = bytes - o < kChunk ? bytes - o : kChunk;
+                buf.resize(n);
+                if (std::fread(buf.data(), 1, n, f) != n) { rc = AD_PIC_ERR_IO; break; }
+                if (cudaMemcpy((unsigned char*)dev + o, buf.data(), n, cudaMemcpyHostToDevice) != cudaSuccess)
+                    rc = AD_PIC_ERR_CUDA;
+            }
+        };
+        if (!rc) {
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = AD_PIC_ERR_CUDA;
+        }
+        if (!rc) fill(h->state, sizeof(T) * 6 * (size_t)h->N * CP);
+        if (!rc) fill(h->ids[0], sizeof(int) * (size_t)h->N);
+        std::fclose(f);
+        if (rc) {
+            // the device state may be partly overwritten: it must be set again
+            h->particles_set = false;
+            cudaGetLastError();
+            return rc;
+        }
+        h->cur = 0;
+        h->gamma0 = hd.consts[0]; h->beta0 = hd.consts[1]; h->p0 = hd.consts[2]; h->brho = hd.consts[3];
+        h->kperp = hd.consts[4]; h->kz = hd.consts[5]; h->qm = hd.consts[6]; h->q = hd.consts[7];
+        h->beam_set = (hd.flags & 1) != 0;
+        h->lattice_set = (hd.flags & 2) != 0;
+        h->lat = hd.lat;
+        h->particles_set = true;
+        h->kick = hd.kick;
+        h->first_record = hd.first_record != 0;
+        h->hist.swap(hist);
+        h->coef_dirty = true;
+        free_graphs(h);
+        return AD_PIC_OK;
+    }
+
     static int allocate(ad_pic* h) {
         const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
         const int64_t gnodes = (int64_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
@@ -691,6 +817,7 @@ struct Impl {
         CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, h->stream));
         CK(cudaMemsetAsync(h->gcount, 0, sizeof(unsigned), h->stream));
         launch_iota(h->ids[0], h->N, h->stream);
+        launch_iota(h->ids[1], h->N, h->stream);
         CK(cudaMemsetAsync(h->E, 0, sizeof(T) * nodes * 3 * CP, h->stream));
         std::vector<Ord<T>> mm0 = {~(Ord<T>)0, ~(Ord<T>)0, ~(Ord<T>)0, 0, 0, 0};
         CK(cudaMemcpyAsync(h->mm, mm0.data(), sizeof(Ord<T>) * 6, cudaMemcpyHostToDevice, h->stream));
@@ -823,6 +950,7 @@ int ad_pic_set_particles(ad_pic* h, const double* state) {
 
 int ad_pic_get_particles(const ad_pic* h, double* state) {
     if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
+    if (!h->particles_set) return AD_PIC_ERR_STATE;
     DISPATCH(h, I::get_particles(h, state));
 }
 
@@ -945,6 +1073,49 @@ int ad_pic_constants(const ad_pic* h, double* out) {
     return AD_PIC_OK;
 }
 
+int ad_pic_save(const ad_pic* h, const char* path) {
+    if (!h || !path) return AD_PIC_ERR_INVALID_ARG;
+    ad_pic* hm = const_cast<ad_pic*>(h);
+    DISPATCH(hm, I::save(hm, path));
+}
+
+int ad_pic_load(ad_pic* h, const char* path) {
+    if (!h || !path) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::load(h, path));
+}
+
+int ad_pic_set_wait_limit(ad_pic* h, int polls) {
+    if (!h) return AD_PIC_ERR_INVALID_ARG;
+    h->wait_polls = polls < 0 ? -1 : polls;
+    free_graphs(h);                  // the limit is a launch argument baked into the graphs
+    return AD_PIC_OK;
+}
+
+int ad_pic_wait_probe(int polls, double* ms, int* failed) {
+    if (polls < 1 || !ms || !failed) return AD_PIC_ERR_INVALID_ARG;
+    if (cudaPeekAtLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
+    int* d = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = AD_PIC_OK;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return AD_PIC_ERR_OOM; }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = AD_PIC_ERR_CUDA;
+    if (!rc) {
+        cudaEventRecord(e0, nullptr);
+        if (launch_wait_probe(polls, d, nullptr)) rc = AD_PIC_ERR_CUDA;
+        cudaEventRecord(e1, nullptr);
+    }
+    float t = 0.f;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess ||
+                cudaMemcpy(failed, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
+        rc = AD_PIC_ERR_CUDA;
+    *ms = t;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
 void ad_pic_destroy(ad_pic* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -974,6 +1145,7 @@ const char* ad_pic_strerror(int s) {
         case AD_PIC_ERR_OUT_OF_GRID: return "particle outside the grid stencil";
         case AD_PIC_ERR_TIMEOUT: return "bounded device wait timed out";
         case AD_PIC_ERR_UNSUPPORTED: return "unsupported";
+        case AD_PIC_ERR_IO: return "checkpoint file could not be read or written";
         default: return "unknown status";
     }
 }

@@ -277,7 +277,10 @@ struct SortBuf {
 template <typename T, int C, int CP>
 void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
-                 const SortBuf& sb, const GeomFuse& gf, cudaStream_t s);
+                 const SortBuf& sb, const GeomFuse& gf, int polls, cudaStream_t s);
+// one thread polls an mbarrier nobody arrives on `polls` times (a bounded wait
+// that runs out); *failed = the failed polls
+int launch_wait_probe(int polls, int* failed, cudaStream_t s);
 void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s);
 int scan_blocks(int ncells);
 void launch_iota(int* ids, int64_t N, cudaStream_t s);

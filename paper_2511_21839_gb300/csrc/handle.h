@@ -64,6 +64,7 @@ struct ad_pic {
     int records_cap = 0;
     double* staging = nullptr;      // FP64 [6][N][C] staging buffer of set/get_particles
     int64_t launches = 0;           // kernels launched by ad_pic_run so far
+    int wait_polls = -1;            // poll limit of the push's tile waits (< 0: the default)
     std::vector<void*> allocs;
     // per-kick coefficients of the handle's precision (raw MapCoef / KickCoef)
     std::vector<unsigned char> half, comp, kcoef;

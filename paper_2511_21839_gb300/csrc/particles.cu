@@ -33,7 +33,7 @@ static int& push_grid() {
 template <typename T, int C, int CP, bool TRACK>
 static void push_attrs() {
     constexpr int TP = push_tile<T, CP>();
-    const int smem = (int)(2 * 6 * TP * CP * sizeof(T));
+    const int smem = (int)push_smem<T, CP>();
     cudaFuncSetAttribute(push_tma_kernel<T, C, CP, TRACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -51,25 +51,25 @@ void setup_push() {
 template <typename T, int C, int CP, bool TRACK>
 static void launch_push_t(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx,
                           int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, Ord<T>* mm, int* err,
-                          const SortBuf& sb, const GeomFuse& gf, cudaStream_t s) {
+                          const SortBuf& sb, const GeomFuse& gf, int polls, cudaStream_t s) {
     constexpr int TP = push_tile<T, CP>();
     const int64_t tiles = (N + TP - 1) / TP;
     const int64_t g = push_grid<T, C, CP, TRACK>();
     const unsigned grid = (unsigned)(tiles < g ? tiles : g);
-    const size_t smem = 2 * 6 * (size_t)TP * CP * sizeof(T);
+    const size_t smem = push_smem<T, CP>();
     push_tma_kernel<T, C, CP, TRACK><<<grid, TP, smem, s>>>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm,
-                                                             err, sb, gf);
+                                                             err, sb, gf, polls >= 0 ? polls : kWaitPolls);
 }
 
 template <typename T, int C, int CP>
 void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const GeomDev* geom, int nx, int ny, int nz,
                  const MapCoef<T, CP>& A, const KickCoef<T, CP>& K, bool track, Ord<T>* mm, int* err,
-                 const SortBuf& sb, const GeomFuse& gf, cudaStream_t s) {
+                 const SortBuf& sb, const GeomFuse& gf, int polls, cudaStream_t s) {
     if (N <= 0) return;
     if (track)
-        launch_push_t<T, C, CP, true>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, gf, s);
+        launch_push_t<T, C, CP, true>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, gf, polls, s);
     else
-        launch_push_t<T, C, CP, false>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, gf, s);
+        launch_push_t<T, C, CP, false>(state_in, state_out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, gf, polls, s);
 }
 
 int scan_blocks(int ncells) { return (ncells + kScanChunk - 1) / kScanChunk; }
@@ -88,6 +88,11 @@ void launch_convert_out_perm(const T* src, const int* ids, double* dst, int64_t 
     if (tot > 0) convert_out_perm_kernel<T, CP><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, ids, dst, N, C);
 }
 int boundary_blocks() { return kBoundaryBlocks; }
+
+int launch_wait_probe(int polls, int* failed, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(polls, failed);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 template <typename T, int C, int CP>
 void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, bool mom, double* partial,
@@ -128,7 +133,7 @@ void setup_deposit() {
     template void launch_init<T, C, CP>(const double*, int64_t, const double*, T*, cudaStream_t);                \
     template void launch_push<T, C, CP>(const T*, T*, int64_t, const T*, const GeomDev*, int, int, int,         \
                                         const MapCoef<T, CP>&, const KickCoef<T, CP>&, bool, Ord<T>*, int*,      \
-                                        const SortBuf&, const GeomFuse&, cudaStream_t);                          \
+                                        const SortBuf&, const GeomFuse&, int, cudaStream_t);                     \
     template void launch_boundary<T, C, CP>(T*, int64_t, const MapCoef<T, CP>&, bool, bool, double*, int,       \
                                             Ord<T>*, const GeomFuse&, cudaStream_t);                             \
     template void launch_deposit<T, C, CP>(const T*, int64_t, const GeomDev*, int, int, int, T, T*, int*,        \

@@ -166,73 +166,96 @@ static __global__ void convert_out_kernel(const T* __restrict__ src, double* __r
 // only that component's CP accumulators and its three interpolant gradients
 // are live: E_p,k = sum W E_k + sum_d (x_d,k / h_d) sum dW/du_d E_0 (Eq. 2 on
 // the weight product), then p_k += a0 E_p,k + a_k E_p,0 in one rounding.
-// Gather + kick + dual map of one particle held in registers (u[6][CP]).
-template <typename T, int C, int CP>
-__device__ __forceinline__ void push_core(T (&u)[6][CP], const T* __restrict__ E, const GeomDev* __restrict__ geom,
-                                          int nx, int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K,
-                                          int* __restrict__ err) {
-    if (E != nullptr) {
-        const GeomDev& g = *geom;
-        const int n[3] = {nx, ny, nz};
-        T f[3], ih[3];
-        int idx[3];
-        int bad = 0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            ih[d] = geom_ih<T>(g, d);
-            idx[d] = cell_of<T>(u[2 * d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
-        }
-        if (bad) atomicOr(err, bad);
-        const T* e0 = E + (((int64_t)idx[2] * ny + idx[1]) * nx + idx[0]) * (3 * CP);
-        const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            T Ev[CP];
-            T gx = (T)0, gy = (T)0, gz = (T)0;
-#pragma unroll
-            for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
-            // nodes nd = a + 2b + 4c in batches: a batch's loads are all issued before
-            // its accumulation, so one L2 round trip serves NB nodes
-            constexpr int NB = (CP * sizeof(T) <= 32) ? 4 : 2;
-#pragma unroll
-            for (int nb0 = 0; nb0 < 8; nb0 += NB) {
-                T en[NB][CP];
-#pragma unroll
-                for (int j = 0; j < NB; ++j) {
-                    const int nd = nb0 + j, a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-                    ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, en[j]);
-                }
-#pragma unroll
-                for (int j = 0; j < NB; ++j) {
-                    const int nd = nb0 + j, a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
-                    const T wz = c ? f[2] : (T)1 - f[2];
-                    const T sz_ = c ? (T)1 : (T)-1;
-                    const T wy = b ? f[1] : (T)1 - f[1];
-                    const T sy_ = b ? (T)1 : (T)-1;
-                    const T wx = a ? f[0] : (T)1 - f[0];
-                    const T sx_ = a ? (T)1 : (T)-1;
-                    const T W = wx * wy * wz;
-#pragma unroll
-                    for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[j][k], Ev[k]);
-                    gx = fma(sx_ * wy * wz, en[j][0], gx);
-                    gy = fma(wx * sy_ * wz, en[j][0], gy);
-                    gz = fma(wx * wy * sz_, en[j][0], gz);
-                }
-            }
-            gx *= ih[0];
-            gy *= ih[1];
-            gz *= ih[2];
-            T* p = u[2 * q + 1];
-            const T a0 = K.a[q][0], E0 = Ev[0];
-#pragma unroll
-            for (int k = 1; k < CP; ++k) {
-                const T Ek = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[k])));
-                p[k] = fma(a0, Ek, fma(K.a[q][k], E0, p[k]));
-            }
-            p[0] = fma(a0, E0, p[0]);
-        }
+
+// Where the eight node records of a particle's cell come from: the field
+// grid in global memory (read-only path) or a copy of the cell's stencil in
+// shared memory (nodes a + 2b + 4c, each 3 x CP values).
+template <typename T, int CP>
+struct GlobalStencil {
+    const T* e0;              // node (0, 0, 0) of the cell
+    int64_t sy, sz;           // node strides in y and z (values)
+    __device__ __forceinline__ void load(int a, int b, int c, int q, T (&v)[CP]) const {
+        ldg_v<T, CP>(e0 + c * sz + b * sy + a * 3 * CP + q * CP, v);
     }
-    // dual map
+};
+template <typename T, int CP>
+struct SharedStencil {
+    const T* w;               // the cell's stencil copy
+    __device__ __forceinline__ void load(int a, int b, int c, int q, T (&v)[CP]) const {
+        ldv<T, CP>(w + (a + 2 * b + 4 * c) * 3 * CP + q * CP, v);
+    }
+};
+
+// cell indices and in-cell offsets of one particle (value part); flags a
+// particle outside the stencil range (the index is clamped)
+template <typename T>
+__device__ __forceinline__ int locate(const T* x, const T* y, const T* z, const GeomDev& g, int nx, int ny, int nz,
+                                      int (&idx)[3], T (&f)[3], T (&ih)[3], int& bad) {
+    const int n[3] = {nx, ny, nz};
+    const T* c[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ih[d] = geom_ih<T>(g, d);
+        idx[d] = cell_of<T>(c[d][0], geom_o<T>(g, d), ih[d], n[d], f[d], bad);
+    }
+    return (idx[2] * ny + idx[1]) * nx + idx[0];
+}
+
+// gather of the dual field at the particle and the kick M2(tau)
+template <typename T, int C, int CP, typename Src>
+__device__ __forceinline__ void kick_core(T (&u)[6][CP], const T (&f)[3], const T (&ih)[3], const Src& src,
+                                          const KickCoef<T, CP>& K) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        T Ev[CP];
+        T gx = (T)0, gy = (T)0, gz = (T)0;
+#pragma unroll
+        for (int k = 0; k < CP; ++k) Ev[k] = (T)0;
+        // nodes nd = a + 2b + 4c in batches: a batch's loads are all issued before
+        // its accumulation, so one round trip serves NB nodes
+        constexpr int NB = (CP * sizeof(T) <= 32) ? 4 : 2;
+#pragma unroll
+        for (int nb0 = 0; nb0 < 8; nb0 += NB) {
+            T en[NB][CP];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const int nd = nb0 + j;
+                src.load(nd & 1, (nd >> 1) & 1, nd >> 2, q, en[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const int nd = nb0 + j, a = nd & 1, b = (nd >> 1) & 1, c = nd >> 2;
+                const T wz = c ? f[2] : (T)1 - f[2];
+                const T sz_ = c ? (T)1 : (T)-1;
+                const T wy = b ? f[1] : (T)1 - f[1];
+                const T sy_ = b ? (T)1 : (T)-1;
+                const T wx = a ? f[0] : (T)1 - f[0];
+                const T sx_ = a ? (T)1 : (T)-1;
+                const T W = wx * wy * wz;
+#pragma unroll
+                for (int k = 0; k < CP; ++k) Ev[k] = fma(W, en[j][k], Ev[k]);
+                gx = fma(sx_ * wy * wz, en[j][0], gx);
+                gy = fma(wx * sy_ * wz, en[j][0], gy);
+                gz = fma(wx * wy * sz_, en[j][0], gz);
+            }
+        }
+        gx *= ih[0];
+        gy *= ih[1];
+        gz *= ih[2];
+        T* p = u[2 * q + 1];
+        const T a0 = K.a[q][0], E0 = Ev[0];
+#pragma unroll
+        for (int k = 1; k < CP; ++k) {
+            const T Ek = fma(u[0][k], gx, fma(u[2][k], gy, fma(u[4][k], gz, Ev[k])));
+            p[k] = fma(a0, Ek, fma(K.a[q][k], E0, p[k]));
+        }
+        p[0] = fma(a0, E0, p[0]);
+    }
+}
+
+// the dual map A of every plane
+template <typename T, int CP>
+__device__ __forceinline__ void map_core(T (&u)[6][CP], const MapCoef<T, CP>& A) {
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl) {
         T* x = u[2 * pl];
@@ -248,6 +271,27 @@ __device__ __forceinline__ void push_core(T (&u)[6][CP], const T* __restrict__ E
         x[0] = fma(a0, x0, b0 * p0);
         p[0] = fma(c0, x0, d0 * p0);
     }
+}
+
+// Gather + kick + dual map of one particle held in registers (u[6][CP]), field
+// records read from global memory.
+template <typename T, int C, int CP>
+__device__ __forceinline__ void push_core(T (&u)[6][CP], const T* __restrict__ E, const GeomDev* __restrict__ geom,
+                                          int nx, int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K,
+                                          int* __restrict__ err) {
+    if (E != nullptr) {
+        int idx[3];
+        T f[3], ih[3];
+        int bad = 0;
+        locate<T>(u[0], u[2], u[4], *geom, nx, ny, nz, idx, f, ih, bad);
+        if (bad) atomicOr(err, bad);
+        GlobalStencil<T, CP> src;
+        src.e0 = E + (((int64_t)idx[2] * ny + idx[1]) * nx + idx[0]) * (3 * CP);
+        src.sy = (int64_t)nx * 3 * CP;
+        src.sz = (int64_t)nx * ny * 3 * CP;
+        kick_core<T, C, CP>(u, f, ih, src, K);
+    }
+    map_core<T, CP>(u, A);
 }
 
 template <typename T, int C, int CP, bool TRACK>
@@ -303,9 +347,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// bounded: gives up after 2^20 polls (well under a second)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 20); ++it)
+// bounded: gives up after `polls` failed polls (0: at once, without polling).
+// Each failed try_wait suspends the thread for a system-dependent time, about
+// 1.9 us measured on GB300 (ad_pic_wait_probe), so the default limit of 2^18
+// polls gives up after about half a second; a tile copy lands within microseconds
+constexpr int kWaitPolls = 1 << 18;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int polls = kWaitPolls) {
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -329,6 +377,30 @@ template <typename T, int CP>
 __host__ __device__ constexpr int push_min_blocks() {
     return CP * sizeof(T) == 32 ? 6 : 2;
 }
+// Field stencils staged in shared memory per warp and tile (FP32, P = 7): the
+// distinct cells of a warp's particles, up to this many, each as its eight
+// node records (3 x CP values each) plus 16 bytes of padding, so stencils of
+// different cells start in different banks
+template <typename T, int CP>
+__host__ __device__ constexpr int push_window_slots() {
+    return (sizeof(T) == 4 && CP == 8) ? 6 : 0;
+}
+template <typename T, int CP>
+__host__ __device__ constexpr int push_window_stride() {
+    return 8 * 3 * CP + (int)(16 / sizeof(T));
+}
+// dynamic shared memory of the persistent push: the two-stage state ring and
+// the warps' stencil windows
+template <typename T, int CP>
+__host__ __device__ constexpr size_t push_smem() {
+    return sizeof(T) * ((size_t)2 * 6 * push_tile<T, CP>() * CP +
+                        (size_t)(push_tile<T, CP>() / 32) * push_window_slots<T, CP>() * push_window_stride<T, CP>());
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Persistent push: each CTA walks tiles blockIdx.x, +gridDim.x, ... and keeps
 // two tiles of the dual state in flight in a two-stage shared-memory ring
@@ -337,14 +409,26 @@ __host__ __device__ constexpr int push_min_blocks() {
 // results go to their cell-sorted slots as in push_kernel. Every wait is
 // bounded; the CTA agrees on the outcome with a barrier vote, and on a timeout
 // it records kErrTimeout, lets its copies land (bounded) and stops.
+// With stencil windows (push_window_slots > 0) each warp finds the distinct
+// cells of its particles (the particles are sorted by cell, so a warp holds
+// few), copies each cell's eight node records once into shared memory with
+// asynchronous copies, all in flight together, and gathers from there: one
+// round trip to L2 per warp and tile instead of several per particle. A
+// particle whose cell got no slot gathers from global memory.
 template <typename T, int C, int CP, bool TRACK>
 __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __restrict__ out, int64_t N,
                                               const T* __restrict__ E, const GeomDev* __restrict__ geom, int nx,
                                               int ny, int nz, const MapCoef<T, CP>& A, const KickCoef<T, CP>& K,
-                                              Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb) {
+                                              Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb,
+                                              int polls = kWaitPolls) {
     constexpr int TP = push_tile<T, CP>();
+    constexpr int KW = push_window_slots<T, CP>();
+    constexpr int WS = push_window_stride<T, CP>();
+    constexpr int PPN = 3 * CP * (int)sizeof(T) / 16;       // 16-byte pieces per node record
     extern __shared__ __align__(128) unsigned char smraw[];
     T* ring = reinterpret_cast<T*>(smraw);      // [2][6][TP][CP]
+    T* win = ring + (size_t)2 * 6 * TP * CP;    // [TP / 32][KW][WS]
+    __shared__ int s_cell[TP / 32][KW > 0 ? KW : 1];
     __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x;
     const int64_t ntiles = (N + TP - 1) / TP;
@@ -375,7 +459,7 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
     bool ok = true;
     for (; tile < ntiles; tile += step, ++it) {
         const int s = it & 1;
-        const bool got = mbar_wait(&bar[s], (unsigned)((it >> 1) & 1));
+        const bool got = mbar_wait(&bar[s], (unsigned)((it >> 1) & 1), polls);
         if (!__syncthreads_and(got)) {
             ok = false;
             break;
@@ -392,14 +476,64 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
             fence_proxy_async_smem();
             issue(tile + 2 * step, s);
         }
+        // slot and id loads first: their latency overlaps the gather (slots and
+        // ids are 32-bit: N < 2^31)
+        int dst = 0, idv = 0;
         if (valid) {
-            // slot and id loads first: their latency overlaps the gather
-            const int64_t dst = sb.offs ? (int64_t)sb.offs[sb.key[i]] + sb.rank[i] : i;
-            const int idv = sb.ids_out ? sb.ids_in[i] : 0;
+            dst = sb.offs ? sb.offs[sb.key[i]] + sb.rank[i] : (int)i;
+            idv = sb.ids_out ? sb.ids_in[i] : 0;
+        }
+        if constexpr (KW > 0) {
+            if (E != nullptr) {
+                const int lane = tid & 31, warp = tid >> 5;
+                int idx[3];
+                T f[3], ih[3];
+                int bad = 0, L = -1;
+                if (valid) L = locate<T>(u[0], u[2], u[4], *geom, nx, ny, nz, idx, f, ih, bad);
+                if (bad) atomicOr(err, bad);
+                // the warp's distinct cells: the lowest lane of each cell owns a slot
+                const unsigned match = __match_any_sync(0xffffffffu, L);
+                const int lead = __ffs(match) - 1;
+                const unsigned heads = __ballot_sync(0xffffffffu, valid && lead == lane);
+                const int slot = __popc(heads & ((1u << lead) - 1u));
+                const int k = min(__popc(heads), KW);
+                T* wwin = win + (size_t)warp * KW * WS;
+                if (valid && lead == lane && slot < KW) s_cell[warp][slot] = L;
+                __syncwarp();
+                const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
+                for (int r = lane; r < k * 8 * PPN; r += 32) {
+                    const int sl = r / (8 * PPN), pc = r - sl * 8 * PPN, nd = pc / PPN, piece = pc - nd * PPN;
+                    const T* src = E + (int64_t)s_cell[warp][sl] * (3 * CP) + (nd >> 2) * sz + ((nd >> 1) & 1) * sy +
+                                   (nd & 1) * (3 * CP);
+                    cp_async16(wwin + sl * WS + nd * 3 * CP + piece * (16 / (int)sizeof(T)),
+                               src + piece * (16 / (int)sizeof(T)));
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                if (valid) {
+                    if (slot < KW) {
+                        SharedStencil<T, CP> st_;
+                        st_.w = wwin + slot * WS;
+                        kick_core<T, C, CP>(u, f, ih, st_, K);
+                    } else {
+                        GlobalStencil<T, CP> st_;
+                        st_.e0 = E + (int64_t)L * (3 * CP);
+                        st_.sy = sy;
+                        st_.sz = sz;
+                        kick_core<T, C, CP>(u, f, ih, st_, K);
+                    }
+                    map_core<T, CP>(u, A);
+                }
+            } else if (valid) {
+                map_core<T, CP>(u, A);
+            }
+        } else if (valid) {
             push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
+        }
+        if (valid) {
             if (sb.ids_out) sb.ids_out[dst] = idv;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) stg_v<T, CP>(out + (c * N + dst) * CP, u[c]);
+            for (int c = 0; c < 6; ++c) stg_v<T, CP>(out + (c * N + (int64_t)dst) * CP, u[c]);
             if (TRACK) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -410,6 +544,7 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
         }
     }
     if (!ok && tid == 0) {
+        // the copies still in flight land before the CTA exits (default, long limit)
         atomicOr(err, kErrTimeout);
         const int s = it & 1;
         mbar_wait(&bar[s], (unsigned)((it >> 1) & 1));
@@ -423,8 +558,8 @@ static __global__ void __launch_bounds__(push_tile<T, CP>(), push_min_blocks<T, 
     push_tma_kernel(const T* __restrict__ state, T* __restrict__ out, int64_t N, const T* __restrict__ E,
                     const GeomDev* __restrict__ geom, int nx, int ny, int nz, const MapCoef<T, CP> A,
                     const KickCoef<T, CP> K, Ord<T>* __restrict__ mm, int* __restrict__ err, const SortBuf sb,
-                    const GeomFuse gf) {
-    push_tma_body<T, C, CP, TRACK>(state, out, N, E, geom, nx, ny, nz, A, K, mm, err, sb);
+                    const GeomFuse gf, int polls) {
+    push_tma_body<T, C, CP, TRACK>(state, out, N, E, geom, nx, ny, nz, A, K, mm, err, sb, polls);
     // every block has finished its gathers before it counts itself done, so the
     // last block may overwrite the geometry they read
     if (TRACK && gf.count) geom_last_block<T>(gf, mm);
@@ -609,20 +744,31 @@ static __global__ void __launch_bounds__(256) halfmap_kernel(T* __restrict__ sta
 // accumulates, in FP64, channel k of the dual sums of u, p, u^2, u p, p^2
 // per plane (Eq. 2 for the products: d(u^2) = 2 u u_k, d(u p) = u p_k + p u_k),
 // and optionally applies the dual half map A to the state and tracks extrema.
-// error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) on a
-// double-float accumulator (hi, lo)
-__device__ __forceinline__ void df_add(float& hi, float& lo, float a) {
-    const float s = hi + a;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (a - bb);
+// Error-free transformations (Knuth's TwoSum, the FMA-based TwoProduct) on an
+// unevaluated-pair accumulator (hi, lo) of the state's type: the running sum
+// is hi + lo and its rounding does not depend on the order of the terms.
+template <typename T>
+__device__ __forceinline__ void ef_add(T& hi, T& lo, T a) {
+    const T s = hi + a;
+    const T bb = s - hi;
+    const T e = (hi - (s - bb)) + (a - bb);
     hi = s;
     lo += e;
 }
-__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
-    const float ph = a * b;
-    const float pl = fmaf(a, b, -ph);
-    df_add(hi, lo, ph);
+// a product the compiler may not contract into a following addition
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+template <typename T>
+__device__ __forceinline__ void ef_add_prod(T& hi, T& lo, T a, T b) {
+    const T ph = mul_rn(a, b);
+    const T pl = fma(a, b, -ph);
+    ef_add(hi, lo, ph);
     lo += pl;
+}
+// (hi, lo) += (bh, bl)
+__device__ __forceinline__ void dd_add(double& hi, double& lo, double bh, double bl) {
+    ef_add(hi, lo, bh);
+    lo += bl;
 }
 
 constexpr int kBoundaryBlocks = 152 * 8;
@@ -637,12 +783,11 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
     const int src = lane & ~(CP - 1);
     const int64_t warp = (bx_ * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)nbx_ * blockDim.x) >> 5;
-    double acc[3][5];
-    float ah[3][5], al[3][5];   // FP32 path: double-float partial sums
+    T ah[3][5], al[3][5];       // compensated per-lane sums (hi, lo)
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) { acc[pl][q] = 0.0; ah[pl][q] = 0.f; al[pl][q] = 0.f; }
+        for (int q = 0; q < 5; ++q) { ah[pl][q] = (T)0; al[pl][q] = (T)0; }
     T mn[3] = {tmax<T>(), tmax<T>(), tmax<T>()};
     T mx[3] = {-tmax<T>(), -tmax<T>(), -tmax<T>()};
     // four particle groups per trip: their 24 loads are issued before any use
@@ -674,35 +819,21 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
             T u0 = __shfl_sync(0xffffffffu, u, src);
             T p0 = __shfl_sync(0xffffffffu, p, src);
             if (MOM && valid) {
-                if constexpr (sizeof(T) == 8) {
-                    acc[pl][0] += u;
-                    acc[pl][1] += p;
-                    if (k == 0) {
-                        acc[pl][2] = fma(u, u, acc[pl][2]);
-                        acc[pl][3] = fma(u, p, acc[pl][3]);
-                        acc[pl][4] = fma(p, p, acc[pl][4]);
-                    } else {
-                        acc[pl][2] = fma(2.0 * u0, u, acc[pl][2]);
-                        acc[pl][3] = fma(u0, p, fma(p0, u, acc[pl][3]));
-                        acc[pl][4] = fma(2.0 * p0, p, acc[pl][4]);
-                    }
+                // every product is formed exactly as a pair (hi, lo) and added with
+                // error-free sums, so a lane's partials carry about twice the
+                // state's precision (about 48 bits in FP32, 106 in FP64)
+                const T a = (T)2 * u0;
+                ef_add(ah[pl][0], al[pl][0], u);
+                ef_add(ah[pl][1], al[pl][1], p);
+                if (k == 0) {
+                    ef_add_prod(ah[pl][2], al[pl][2], u, u);
+                    ef_add_prod(ah[pl][3], al[pl][3], u, p);
+                    ef_add_prod(ah[pl][4], al[pl][4], p, p);
                 } else {
-                    // FP32 state: every product of two FP32 values is formed exactly as an
-                    // unevaluated pair (hi, lo) and added with error-free sums, so the
-                    // per-lane partials carry ~48 significant bits before they go to FP64
-                    const float a = 2.0f * (float)u0;
-                    df_add(ah[pl][0], al[pl][0], (float)u);
-                    df_add(ah[pl][1], al[pl][1], (float)p);
-                    if (k == 0) {
-                        df_add_prod(ah[pl][2], al[pl][2], (float)u, (float)u);
-                        df_add_prod(ah[pl][3], al[pl][3], (float)u, (float)p);
-                        df_add_prod(ah[pl][4], al[pl][4], (float)p, (float)p);
-                    } else {
-                        df_add_prod(ah[pl][2], al[pl][2], a, (float)u);
-                        df_add_prod(ah[pl][3], al[pl][3], (float)u0, (float)p);
-                        df_add_prod(ah[pl][3], al[pl][3], (float)p0, (float)u);
-                        df_add_prod(ah[pl][4], al[pl][4], 2.0f * (float)p0, (float)p);
-                    }
+                    ef_add_prod(ah[pl][2], al[pl][2], a, u);
+                    ef_add_prod(ah[pl][3], al[pl][3], u0, p);
+                    ef_add_prod(ah[pl][3], al[pl][3], p0, u);
+                    ef_add_prod(ah[pl][4], al[pl][4], (T)2 * p0, p);
                 }
             }
             if (APPLY && valid) {
@@ -725,28 +856,34 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
     }
     if (APPLY) block_minmax<T>(mn, mx, mm);
     if (MOM) {
-        if constexpr (sizeof(T) == 4) {
-#pragma unroll
-            for (int pl = 0; pl < 3; ++pl)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) acc[pl][q] = (double)ah[pl][q] + (double)al[pl][q];
-        }
-        // sum over the PPW particle groups of the warp (lanes with the same k)
+        // the pairs in FP64 (a float pair converts exactly), then compensated
+        // sums over the PPW particle groups of the warp (lanes with the same k)
+        double hh[3][5], ll[3][5];
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl)
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
-                for (int o = CP; o < 32; o <<= 1) acc[pl][q] += __shfl_xor_sync(0xffffffffu, acc[pl][q], o);
+            for (int q = 0; q < 5; ++q) {
+                hh[pl][q] = (double)ah[pl][q];
+                ll[pl][q] = (double)al[pl][q];
+                for (int o = CP; o < 32; o <<= 1) {
+                    const double oh = __shfl_xor_sync(0xffffffffu, hh[pl][q], o);
+                    const double ol = __shfl_xor_sync(0xffffffffu, ll[pl][q], o);
+                    dd_add(hh[pl][q], ll[pl][q], oh, ol);
+                }
+            }
+        // a warp's pair is rounded once to FP64 (one rounding of a partial sum, which
+        // does not grow with the number of terms); the warps' partials are summed
+        // with compensation
         __shared__ double sm[8][15][CP];
         const int w = threadIdx.x >> 5;
         if (lane < CP)
             for (int pl = 0; pl < 3; ++pl)
-                for (int q = 0; q < 5; ++q) sm[w][pl * 5 + q][lane] = acc[pl][q];
+                for (int q = 0; q < 5; ++q) sm[w][pl * 5 + q][lane] = hh[pl][q] + ll[pl][q];
         __syncthreads();
         for (int t = threadIdx.x; t < 15 * CP; t += blockDim.x) {
-            double s = 0.0;
-            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += sm[ww][t / CP][t % CP];
-            partial[(int64_t)bx_ * 15 * CP + t] = s;
+            double sh = 0.0, sl = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) ef_add(sh, sl, sm[ww][t / CP][t % CP]);
+            partial[(int64_t)bx_ * 15 * CP + t] = sh + sl;
         }
     }
 }
@@ -760,15 +897,16 @@ static __global__ void __launch_bounds__(256) boundary_kernel(T* __restrict__ st
 }
 
 // partial [nblocks][15][CP] -> out [15][CP] / N: one block per output value,
-// a fixed strided split and a fixed shared-memory tree (reproducible)
+// a fixed strided split (compensated sums) and a fixed shared-memory tree
+// (reproducible; eight levels of 256 partials)
 __device__ __forceinline__ void moments_reduce_kernel_body(const double* __restrict__ partial, int nblocks, int CP, int64_t N,
                                       double* __restrict__ out,
     const int bx_, const int by_, const int bz_, const int nbx_) {
     __shared__ double sm[256];
     const int t = bx_;            // output index in [0, 15 CP)
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)b * 15 * CP + t];
-    sm[threadIdx.x] = s;
+    double sh = 0.0, sl = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) ef_add(sh, sl, partial[(int64_t)b * 15 * CP + t]);
+    sm[threadIdx.x] = sh + sl;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
@@ -961,6 +1099,21 @@ static __global__ void __launch_bounds__(WARPS * 32, dep_min_blocks<T, CP>()) de
                                                                            int ny, int nz, T qm, T* __restrict__ rho,
                                                                            int* __restrict__ err, const SortBuf sb) {
     deposit_tile_body<T, C, CP, WARPS>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x);
+}
+
+// ------------------------------------------------------------------ bounded-wait probe
+
+// One thread polls an mbarrier that no one arrives on, `polls` times, and
+// records how many polls failed: the device time of a wait that runs out.
+static __global__ void wait_probe_kernel(int polls, int* failed) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    int f = 0;
+    for (int it = 0; it < polls; ++it)
+        if (!mbar_try_wait(&bar, 0u)) ++f;
+    *failed = f;
 }
 
 }  // namespace adpic

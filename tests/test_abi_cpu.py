@@ -32,7 +32,7 @@ def cdll():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ["ad_pic_create", "ad_pic_set_lattice", "ad_pic_run", "ad_pic_moments", "ad_pic_set_beam",
-              "ad_pic_destroy", "ad_pic_strerror"]:
+              "ad_pic_destroy", "ad_pic_strerror", "ad_pic_save", "ad_pic_load"]:
         assert n in names
 
 

@@ -3,13 +3,16 @@
 Each instance of a batch (its own lattice, particle count and grid) must reproduce the same instance
 run alone through ad_pic_run, and one instance is also checked against the FP64 oracle. All runs are
 FP32-mixed; single and batched runs differ only in the order of floating-point atomic additions
-(the batch deposits one particle per thread), so the bounds are FP32-level.
+(the batch deposits one particle per thread), so the bounds are FP32-level: against the oracle 1e-5
+on emittances and parity_metrics.der_tol per derivative component (FP32 noise falls like 1/sqrt(N));
+between two FP32 runs, each within those bounds of the oracle, twice the derivative bound.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2511_21839_gb300 import inputs as I
+from parity_metrics import der_tol, rel_der_components, rel_eps
 
 pytestmark = pytest.mark.gpu
 
@@ -21,14 +24,6 @@ def adpic():
 
     build.build()
     return A
-
-
-def rel_eps(v, ref):
-    return np.abs(v - ref) / np.abs(ref)
-
-
-def rel_grad(d, ref):
-    return np.abs(d - ref).max(axis=-1) / np.abs(ref).max(axis=-1)
 
 
 def scan_instances(count=6, seed=7):
@@ -72,9 +67,9 @@ def test_batch_matches_single_instances(adpic, singles, mode):
         h = b.history(i)
         assert h.shape == h1.shape
         ev = rel_eps(v, v1).max()
-        eg = rel_grad(d, d1).max()
-        print(f"  instance {i}: grid {grids[i][0]}, N {npart[i]}: eps {ev:.2e} grad {eg:.2e}")
-        assert ev < 1e-6 and eg < 1e-4, (i, ev, eg)
+        eg = rel_der_components(d, d1).max()
+        print(f"  instance {i}: grid {grids[i][0]}, N {npart[i]}: eps {ev:.2e} derivative per component {eg:.2e}")
+        assert ev < 1e-6 and eg < 2 * der_tol(1, npart[i]), (i, ev, eg)
     b.close()
 
 
@@ -94,7 +89,9 @@ def test_batch_two_runs_continue_and_one_instance_vs_oracle(adpic):
     ref = o.emittance(hist[-1])[:2]
     v, d = b.moments(i)
     assert rel_eps(v, ref[:, 0]).max() < 1e-5
-    assert rel_grad(d, ref[:, 1:]).max() < 1e-4
+    ed = rel_der_components(d, ref[:, 1:]).max()
+    print(f"batched instance vs oracle: derivative per component {ed:.2e}")
+    assert ed < der_tol(1, npart[i])
     fin = b.get_particles(i)
     scale = np.abs(st).max(axis=1, keepdims=True)
     err = np.abs(fin - st) / np.where(scale > 0, scale, 1)
@@ -141,6 +138,6 @@ def test_tuning_is_cached_for_batches_of_the_same_composition(adpic):
     sim.run(2)
     v1, d1 = sim.moments()
     v2, d2 = b2.moments(0)
-    assert rel_eps(v2, v1).max() < 1e-6 and rel_grad(d2, d1).max() < 1e-4
+    assert rel_eps(v2, v1).max() < 1e-6 and rel_der_components(d2, d1).max() < 2 * der_tol(1, npart[0])
     sim.close()
     b2.close()

@@ -1,20 +1,28 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Tolerances (stated per result):
-  FP64 path   emittances 1e-10 relative; derivative vector 1e-10 relative (one period; 1e-9 over
-              several periods); grid stages 1e-11 of the channel's max
-  FP32 path   emittances 1e-5 relative; derivative vector 1e-4 relative; grid stages 2e-5 of the
-              channel's max
-The derivative error of an emittance is max_k |d_k - ref_k| / max_k |ref_k| (the relative error of
-its gradient vector), well defined when one derivative is zero up to rounding. The oracle run twice
-with only its summation order changed (1 vs 8 threads) differs by 3.6e-11 (one period) and 1.2e-10
-(two periods) in this measure: the FP64 bound sits at the discrete algorithm's own floor.
+  FP64 path   emittances 1e-10 relative; each emittance derivative 1e-10 relative (runs on fewer
+              than 10,000 particles: 2e-9, the algorithm's own floor there); potential and field
+              stages 1e-11 of the channel's max on small grids, growing with the Green's function's
+              cancellation on large ones (parity_metrics.grid_tol)
+  FP32 path   emittances 1e-5 relative; each emittance derivative 1e-4 relative at the 1M-particle
+              configuration, max(1e-4, 3e-2 / sqrt(N)) on N particles (parity_metrics.der_tol);
+              grid stages 2e-5 of the channel's max
+A derivative's relative error has the denominator max(|d_k|, 1e-3 max_j |d_j|) per emittance
+(tests/parity_metrics.py). Both sides sum the beam moments with compensated (error-free) sums:
+the emittance derivatives cancel strongly (the emittance barely changes while the second moments
+do), and plain FP64 sums left the oracle itself 8e-10 apart between thread counts; with the
+compensated sums two oracle runs with different summation orders agree to 1.4e-11.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2511_21839_gb300 import inputs as I
+from parity_metrics import der_tol, grid_tol, rel_der_components, rel_eps, report
 
 pytestmark = pytest.mark.gpu
 
@@ -31,22 +39,6 @@ def adpic():
     return A
 
 
-def rel_eps(v, ref):
-    return np.abs(v - ref) / np.abs(ref)
-
-
-def rel_der(d, ref):
-    scale = np.abs(ref).max(axis=-1, keepdims=True)
-    return np.abs(d - ref) / scale
-
-
-def report(name, vals, der, ref):
-    ev = rel_eps(vals, ref[:, 0]).max()
-    ed = rel_der(der, ref[:, 1:]).max()
-    print(f"{name}: eps rel err {ev:.2e}, derivative rel err {ed:.2e}")
-    return ev, ed
-
-
 def chan_close(gpu, ref, tol, axis_chan):
     """Element-wise comparison relative to the max of each channel."""
     g = np.moveaxis(gpu, axis_chan, 0).reshape(gpu.shape[axis_chan], -1)
@@ -54,6 +46,7 @@ def chan_close(gpu, ref, tol, axis_chan):
     scale = np.abs(r).max(axis=1, keepdims=True)
     scale = np.where(scale > 0, scale, 1.0)
     err = (np.abs(g - r) / scale).max()
+    print(f"  element-wise error {err:.2e} (bound {tol:.1e})")
     assert err < tol, err
     return err
 
@@ -73,10 +66,19 @@ def make_pair(adpic, N, grid, P, prec, wname="fodo_10k_32", beam=None, q=None):
 
 # ---------------------------------------------------------------- stages
 
+STAGE_CASES = [
+    ((16, 32, 16), 7, 5003),      # small anisotropic grid
+    ((16, 32, 16), 13, 5003),
+    ((64, 64, 64), 7, 4099),      # the benched grid: slab convolution (x pass, one CTA per (y, z) slab)
+    ((128, 128, 128), 13, 3001),  # the large instance's grid: five-pass convolution, 129-point DCTs
+]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("P", [7, 13])
-def test_stage_parity(adpic, prec, P):
-    N, grid = 5003, (16, 32, 16)
+@pytest.mark.parametrize("grid,P,N", STAGE_CASES, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_stage_parity(adpic, prec, grid, P, N):
+    """Every stage of one kick element-wise against the oracle on the same state: geometry, deposit,
+    potential, field (each channel relative to its max) and the kick of each momentum channel."""
     o, sim, w, b = make_pair(adpic, N, grid, P, prec)
     st = o.beam_init(I.normals(41, N))
     o.apply_half_map(st, 0)
@@ -84,13 +86,13 @@ def test_stage_parity(adpic, prec, P):
         st32 = st.astype(np.float32).astype(np.float64)   # the FP32 state the GPU holds
         st = st32
     sim.set_particles(st)
-    tol = TOL[prec]["grid"]
+    tol = grid_tol(prec, grid)
     geom = sim.stage(0)
     gref = o.geometry(st)
     np.testing.assert_allclose(geom, gref, rtol=1e-12 if prec == 0 else 1e-6)
     rho = sim.stage(1)
     rho_ref = o.deposit(st, geom)
-    chan_close(rho, rho_ref, tol, 0)
+    chan_close(rho, rho_ref, TOL[prec]["grid"], 0)
     assert abs(rho[0].sum() - o.constants()["q_macro"] * N) < 1e-6 * o.constants()["q_macro"] * N
     phi = sim.stage(2)
     phi_ref = o.solve(geom, rho_ref)
@@ -106,7 +108,7 @@ def test_stage_parity(adpic, prec, P):
     # updated momentum is also rounded to the state's precision, a bound of one ulp of |p|
     for c in (1, 3, 5):
         dref = np.abs(ref[c] - st[c]).max(axis=0, keepdims=True)
-        bound = TOL[prec]["grid"] * 10 * dref + (2.4e-7 * np.abs(ref[c]) if prec == 1 else 0.0)
+        bound = tol * 10 * dref + (2.4e-7 * np.abs(ref[c]) if prec == 1 else 0.0)
         assert np.all(np.abs(after[c] - ref[c]) <= bound + 1e-300), c
     for c in (0, 2, 4):
         assert np.array_equal(after[c], st[c])
@@ -139,7 +141,7 @@ def test_config1_single_period(adpic, config1_ref, prec):
     vals, der = sim.moments()
     ref = o.emittance(hist[-1])[:2]
     ev, ed = report(f"config1 prec={prec}", vals, der, ref)
-    assert ev < TOL[prec]["eps"] and ed < TOL[prec]["der"]
+    assert ev < TOL[prec]["eps"] and ed < der_tol(prec, w.n_particles)
     gh = sim.history()
     assert gh.shape[0] == 2
     # record 0 = moments of the initial state: second moments element-wise, means (zero up to
@@ -173,7 +175,7 @@ def test_p13_twiss_derivatives(adpic, prec):
     vals, der = sim.moments()
     ref = o.emittance(hist[-1])[:2]
     ev, ed = report(f"P=13 prec={prec}", vals, der, ref)
-    assert ev < TOL[prec]["eps"] and ed < TOL[prec]["der"]
+    assert ev < TOL[prec]["eps"] and ed < der_tol(prec, N)
     sim.close()
 
 
@@ -196,7 +198,7 @@ def test_split_runs_and_graph_replay(adpic):
         sim.close()
     for r in res[1:]:
         ev, ed = report("split/graph", r[:, 0], r[:, 1:], res[0])
-        assert ev < 1e-12 and ed < 1e-10
+        assert ev < 1e-12 and ed < der_tol(0, N)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -219,12 +221,12 @@ def test_stages_leave_the_run_unchanged(adpic, prec):
         res.append(np.concatenate([v[:, None], d], axis=1))
         sim.close()
     # runs differ only by the order of the deposit's atomic additions: FP64 at rounding level; in
-    # FP32 the derivative vectors differ by about 1e-5 after a period (measured 5e-6 to 1.2e-5)
-    # and the emittances by about 1e-9, while a stale charge grid in the first kick changes the
+    # FP32 two runs, each within 1e-4 per derivative of the oracle, may be twice that apart; the
+    # emittances differ by about 1e-9, while a stale charge grid in the first kick changes the
     # emittances by orders of magnitude more
     for r in res[1:]:
         ev, ed = report(f"stages then run ({prec})", r[:, 0], r[:, 1:], res[0])
-        assert ev < (1e-12 if prec == 0 else 1e-6) and ed < (1e-10 if prec == 0 else 1e-4)
+        assert ev < (1e-12 if prec == 0 else 1e-6) and ed < (1 if prec == 0 else 2) * der_tol(prec, N)
 
 
 def test_multi_period_records(adpic):
@@ -241,7 +243,7 @@ def test_multi_period_records(adpic):
         e_g = o.emittance(gh[r + 1])[:2]
         e_o = o.emittance(hist[r])[:2]
         ev, ed = report(f"record {r}", e_g[:, 0], e_g[:, 1:], e_o)
-        assert ev < 1e-10 and ed < 1e-9
+        assert ev < TOL[0]["eps"] and ed < der_tol(0, N)
     sim.close()
 
 
@@ -291,50 +293,44 @@ def test_call_order_and_argument_errors(adpic):
 
 # ---------------------------------------------------------------- full size (1,048,576 particles, 64^3)
 
-@pytest.fixture(scope="module")
-def full_ref():
+def oracle_records_fodo_1m_64():
+    """The FP64 oracle's emittance records of the whole 1M-particle run, written by
+    tests/golden/make_oracle_records.py (which calls only the oracle)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_fodo_1m_64.json")
+    with open(path) as f:
+        return np.array(json.load(f)["eps"])
+
+
+def test_full_size_ten_periods_vs_oracle(adpic):
+    """The launch configuration bench.py times (1,048,576 particles, 64^3, P = 7) over the whole ten
+    periods: both GPU paths against the oracle at every period end (FP64 within 1e-10, FP32 within
+    1e-5 on emittances and 1e-4 per derivative), and the FP32 path against the FP64 path."""
     w = I.workload("fodo_1m_64")
-    o = oracle.Oracle(**I.orc_kwargs(w))
+    ref = oracle_records_fodo_1m_64()                 # [record][plane][channel], record 0 = start
     nrm = I.normals(w.seed, w.n_particles)
-    st = o.beam_init(nrm)
-    hist, _ = o.run(st, 20)
-    return w, nrm, hist, o
-
-
-@pytest.mark.parametrize("prec", [0, 1])
-def test_full_size_one_period_vs_oracle(adpic, full_ref, prec):
-    """The launch configuration bench.py times (1M particles, 64^3, P = 7), one period, vs the oracle."""
-    w, nrm, hist, o = full_ref
-    sim = adpic.ADPIC(w.grid, w.n_particles, 7, prec)
-    sim.set_beam(w.beam, nrm)
-    sim.set_lattice(w.lattice)
-    sim.run(20)
-    vals, der = sim.moments()
-    ref = o.emittance(hist[-1])[:2]
-    ev, ed = report(f"full size prec={prec}", vals, der, ref)
-    assert ev < TOL[prec]["eps"] and ed < TOL[prec]["der"]
-    sim.close()
-
-
-def test_full_size_ten_periods_fp32_vs_fp64(adpic):
-    """The whole 10-period run: FP32 bulk arithmetic against the FP64 path (itself pinned to the
-    oracle above), emittance <= 1e-5 and derivatives <= 1e-4 relative at every period end."""
-    w = I.workload("fodo_1m_64")
-    nrm = I.normals(w.seed, w.n_particles)
+    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=1))
     hs = []
     for prec in (0, 1):
         sim = adpic.ADPIC(w.grid, w.n_particles, 7, prec)
         sim.set_beam(w.beam, nrm)
         sim.set_lattice(w.lattice)
         sim.run(w.n_kicks)
-        hs.append(sim.history())
+        h = sim.history()
         sim.close()
-    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=1))
-    for r in range(1, hs[0].shape[0]):      # record 0 is the initial state (derivatives zero)
+        assert h.shape[0] == ref.shape[0]
+        hs.append(h)
+        worst = (0.0, 0.0)
+        for r in range(1, h.shape[0]):
+            e = o.emittance(h[r])[:2]
+            ev, ed = report(f"period {r} prec={prec} vs oracle", e[:, 0], e[:, 1:], ref[r])
+            assert ev < TOL[prec]["eps"] and ed < TOL[prec]["der"], (prec, r, ev, ed)
+            worst = (max(worst[0], ev), max(worst[1], ed))
+        print(f"ten periods prec={prec}: worst eps {worst[0]:.2e}, worst derivative component {worst[1]:.2e}")
+    for r in range(1, hs[0].shape[0]):
         e64 = o.emittance(hs[0][r])[:2]
         e32 = o.emittance(hs[1][r])[:2]
         ev, ed = report(f"period {r} fp32 vs fp64", e32[:, 0], e32[:, 1:], e64)
-        assert ev < 1e-5 and ed < 1e-4, r
+        assert ev < 2 * TOL[1]["eps"] and ed < 2 * TOL[1]["der"], r
 
 
 @pytest.fixture(scope="module")
@@ -360,7 +356,7 @@ def test_large_grid_p13_vs_oracle(adpic, large_grid_ref, prec):
     vals, der = sim.moments()
     ref = o.emittance(hist[-1])[:2]
     ev, ed = report(f"128^3 P=13 prec={prec}", vals, der, ref)
-    assert ev < TOL[prec]["eps"] and ed < TOL[prec]["der"]
+    assert ev < TOL[prec]["eps"] and ed < der_tol(prec, N)
     fin = sim.get_particles()
     chan_close(fin[:, :, :1], st[:, :, :1], TOL[prec]["state"], 2)
     sim.close()

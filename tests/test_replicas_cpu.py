@@ -8,6 +8,7 @@ import os
 import socket
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -64,8 +65,8 @@ def test_two_replicas_take_the_slowest_rank_and_sum_the_work():
 
 
 def test_push_traffic_record_is_read_only_for_its_source():
-    """bench.py reports the push's DRAM traffic from the committed ncu record only while the push
-    sources hash to the value stored with it."""
+    """bench.py reports a figure from a committed ncu record only while the kernel sources hash to
+    the value stored with it."""
     import re
 
     sys.path.insert(0, ROOT)
@@ -74,7 +75,25 @@ def test_push_traffic_record_is_read_only_for_its_source():
     text = open(os.path.join(ROOT, "profiles", "push_fodo_1m_64.md")).read()
     stored = re.search(r"kernel_src_sha256:\s*([0-9a-f]{64})", text).group(1)
     b = int(re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text).group(1))
-    assert bench.traffic_from_profile("fodo_1m_64", stored) == b
-    assert bench.traffic_from_profile("fodo_1m_64", "0" * 64) is None
-    assert bench.traffic_from_profile("no_such_workload", stored) is None
+    assert bench.profile_value("push_fodo_1m_64.md", "dram_bytes_per_launch", stored) == b
+    assert bench.profile_value("push_fodo_1m_64.md", "dram_bytes_per_launch", "0" * 64) is None
+    assert bench.profile_value("push_no_such_workload.md", "dram_bytes_per_launch", stored) is None
     assert re.fullmatch(r"[0-9a-f]{64}", bench.kernel_src_hash())
+
+
+def test_bench_accuracy_helpers_match_the_oracle_records():
+    """The bench's host emittance helper reproduces the oracle's emittances from its stored moment
+    records, and the kick's algorithmic bytes match the figures of the roofline model."""
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    doc = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_fodo_1m_64.json")))
+    for mom, eps in zip(doc["moments"][1:], doc["eps"][1:]):
+        ev, ed = bench.rel_errors(bench.emittances(np.array(mom)), np.array(eps))
+        assert ev < 1e-14 and ed < 1e-12
+    kb = bench.kick_bytes(1_048_576, (64, 64, 64), 8, 4)
+    assert kb["particles"] == 402_653_184
+    assert kb["rho"] + kb["field"] == 67_108_864
+    assert kb["fft_model"] == 134_217_728

@@ -72,6 +72,53 @@ def test_no_alloc_moments_match_regular_entry_point(prec, P):
         assert err.max() < tol, f"call {call}: max scaled error {err.max():.3e}"
 
 
+def test_no_alloc_small_call_after_large_and_layout_change():
+    """Calls share the partial-sum array and keep what the last call left there. After a call that
+    fills all of its blocks, a call on 37 particles leaves almost every block without particles: those
+    blocks must write zero partials, so the result equals the oracle's moments of the small state.
+    Then a 13-derivative FP32 call follows a 7-derivative FP64 one (another channel layout of the
+    same array)."""
+    torch = pytest.importorskip("torch")
+    from paper_2511_21839_gb300 import adpic, build
+
+    build.build()
+    w = I.workload("fodo_10k_32")
+    stream = torch.cuda.current_stream()
+
+    def call(state, P, prec):
+        N, C = state.shape[1], P + 1
+        CP = 8 if P == 7 else 16
+        dtype = torch.float64 if prec == 0 else torch.float32
+        dev = torch.zeros((6, N, CP), dtype=dtype, device="cuda")
+        dev[:, :, :C] = torch.from_numpy(state).to(dtype=dtype, device="cuda")
+        out = torch.full((15 * CP,), float("nan"), dtype=torch.float64, device="cuda")
+        adpic.ad_pic_moments_device(dev.data_ptr(), N, P, prec, out.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        full = out.cpu().numpy().reshape(3, 5, CP)
+        assert np.all(full[:, :, C:] == 0)
+        return full[:, :, :C]
+
+    def beam(P, N, seed):
+        b = w.beam if P == 7 else I.default_beam(13)
+        o = oracle.Oracle(**I.orc_kwargs(w, n_particles=N, grid=(16, 16, 16), n_deriv=P, beam=b))
+        st = o.beam_init(I.normals(seed, N))
+        o.apply_half_map(st, 0)
+        return o, st
+
+    o_big, big = beam(7, 100_003, 62)
+    call(big, 7, 0)                                          # every block gets particles
+    o_small, small = beam(7, 37, 63)
+    got = call(small, 7, 0)
+    ref = o_small.moments(small)
+    err = np.abs(got - ref) / term_scale(small)
+    assert err.max() < 1e-12, err.max()
+    o13, st13 = beam(13, 5_001, 64)
+    got = call(st13.astype(np.float32).astype(np.float64), 13, 1)
+    ref = o13.moments(st13.astype(np.float32).astype(np.float64))
+    err = np.abs(got - ref) / term_scale(st13)
+    assert err.max() < 1e-9, err.max()
+
+
 def test_no_alloc_rejects_unsupported_sizes():
     pytest.importorskip("torch")
     from paper_2511_21839_gb300 import adpic, build
