@@ -14,6 +14,11 @@ from . import build as _build
 MAXC = 32
 
 
+class OrcElement(ct.Structure):
+    _fields_ = [("type", ct.c_int32), ("slot_L", ct.c_int32), ("slot_k", ct.c_int32), ("pad", ct.c_int32),
+                ("L", ct.c_double), ("k", ct.c_double)]
+
+
 class OrcConfig(ct.Structure):
     _fields_ = [
         ("P", ct.c_int32), ("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
@@ -24,12 +29,9 @@ class OrcConfig(ct.Structure):
         ("twiss_slot", ct.c_int32 * 6),
         ("L", ct.c_double * 5), ("g", ct.c_double * 2),
         ("kicks", ct.c_int32 * 5), ("lat_slot", ct.c_int32 * 7),
+        ("n_line", ct.c_int32), ("pad_line", ct.c_int32),
+        ("line", ct.POINTER(OrcElement)), ("line_kicks", ct.POINTER(ct.c_int32)),
     ]
-
-
-class OrcElement(ct.Structure):
-    _fields_ = [("type", ct.c_int32), ("slot_L", ct.c_int32), ("slot_k", ct.c_int32), ("pad", ct.c_int32),
-                ("L", ct.c_double), ("k", ct.c_double)]
 
 
 _lib = None
@@ -91,8 +93,16 @@ def _check(st, what):
 class Oracle:
     """FP64 oracle bound to one configuration (a plain dict of the fields of OrcConfig)."""
 
-    def __init__(self, **kw):
+    def __init__(self, line=None, line_kicks=None, **kw):
+        """kw: the fields of OrcConfig; line: a beamline [(type, L, k, slot_L, slot_k)] with
+        line_kicks kicks per element, in place of the FODO period."""
         c = OrcConfig()
+        if line is not None:
+            self._line = elements(line)
+            self._line_kicks = (ct.c_int32 * len(line))(*[int(v) for v in line_kicks])
+            c.n_line = len(line)
+            c.line = ct.cast(self._line, ct.POINTER(OrcElement))
+            c.line_kicks = ct.cast(self._line_kicks, ct.POINTER(ct.c_int32))
         for k, v in kw.items():
             f = getattr(c, k)
             if isinstance(f, ct.Array):
@@ -193,7 +203,7 @@ class Oracle:
 
     def run(self, state, n_kicks, kick0=0, geom=None, geom_mode=0):
         """Advance `state` in place; returns (moment records [R][3][5][C], geometry [n_kicks][6])."""
-        kpp = sum(self.cfg.kicks)
+        kpp = sum(self._line_kicks) if self.cfg.n_line > 0 else sum(self.cfg.kicks)
         nrec = n_kicks // max(kpp, 1) + 2
         hist = np.zeros((nrec, 3, 5, self.C))
         if geom is None:

@@ -172,20 +172,23 @@ void orc_constants(const orc_config* cfg, double out[8]) {
 /* Lattice: element of a kick, dual step length, half-step maps         */
 /* ------------------------------------------------------------------ */
 
+static int n_elements(const orc_config* cfg) { return cfg->n_line > 0 ? cfg->n_line : 5; }
+static int element_kicks(const orc_config* cfg, int e) { return cfg->n_line > 0 ? cfg->line_kicks[e] : cfg->kicks[e]; }
+
 static int kicks_per_period(const orc_config* cfg) {
     int s = 0;
-    for (int e = 0; e < 5; ++e) s += cfg->kicks[e];
+    for (int e = 0; e < n_elements(cfg); ++e) s += element_kicks(cfg, e);
     return s;
 }
 
 static int element_of_kick(const orc_config* cfg, int64_t kick) {
     int kpp = kicks_per_period(cfg);
     int s = (int)(kick % kpp);
-    for (int e = 0; e < 5; ++e) {
-        if (s < cfg->kicks[e]) return e;
-        s -= cfg->kicks[e];
+    for (int e = 0; e < n_elements(cfg); ++e) {
+        if (s < element_kicks(cfg, e)) return e;
+        s -= element_kicks(cfg, e);
     }
-    return 4;
+    return n_elements(cfg) - 1;
 }
 
 /* parameter index of each element length in lat_slot */
@@ -195,8 +198,9 @@ static const int LEN_PARAM[5] = {0, 1, 3, 4, 6};
 static void dual_tau(const orc_config* cfg, int e, double* tau) {
     const int C = cfg->P + 1;
     dual L, n;
-    d_var(C, cfg->L[e], cfg->lat_slot[LEN_PARAM[e]], L);
-    d_const(C, (double)cfg->kicks[e], n);
+    if (cfg->n_line > 0) d_var(C, cfg->line[e].L, cfg->line[e].slot_L, L);
+    else d_var(C, cfg->L[e], cfg->lat_slot[LEN_PARAM[e]], L);
+    d_const(C, (double)element_kicks(cfg, e), n);
     d_div(C, L, n, tau);
 }
 
@@ -242,7 +246,12 @@ void orc_half_map(const orc_config* cfg, int64_t kick, double* mflat) {
     dual_tau(cfg, e, tau);
     d_cmul(C, 0.5, tau, t);
     d_const(C, 0.0, zero);
-    if (e == 1 || e == 3) {
+    if (cfg->n_line > 0) {
+        /* a beamline element: its normalised strength k directly (quadrupoles) */
+        if (cfg->line[e].type == 1) d_var(C, cfg->line[e].k, cfg->line[e].slot_k, kx);
+        else d_copy(C, zero, kx);
+        for (int k = 0; k < C; ++k) ky[k] = -kx[k];
+    } else if (e == 1 || e == 3) {
         int gi = (e == 1) ? 0 : 1;
         int gslot = cfg->lat_slot[(e == 1) ? 2 : 5];
         dual g, br;

@@ -35,6 +35,14 @@
 
 #define ORC_MAXC 32
 
+/* one element of a beamline: type 0 drift, 1 thick quadrupole of normalised
+   strength k (1/m^2; > 0 focuses in x, defocuses in y); slot_L, slot_k are
+   the derivative slots of L and k (-1 = constant) */
+typedef struct {
+    int32_t type, slot_L, slot_k, pad;
+    double L, k;
+} orc_element;
+
 typedef struct {
     int32_t P;            /* derivative slots; C = P + 1 channels */
     int32_t nx, ny, nz;   /* grid nodes per dimension (powers of two, >= 8) */
@@ -51,6 +59,12 @@ typedef struct {
     double g[2];          /* gradients of QF, QD (T/m) */
     int32_t kicks[5];     /* space-charge kicks per element */
     int32_t lat_slot[7];  /* slots of (L_D1, L_QF, g_QF, L_D2, L_QD, g_QD, L_D3); -1 = constant */
+    /* a general beamline in place of the FODO period (n_line > 0): its
+       elements in beam order and the space-charge kicks of each; the period
+       (moment records, kick schedule) is then the whole beamline */
+    int32_t n_line, pad_line;
+    const orc_element* line;
+    const int32_t* line_kicks;
 } orc_config;
 
 /* derived constants: gamma0, beta0, p0 (kg m/s), Brho (T m), kappa_perp, kappa_z, q_macro (C), q (C) */
@@ -94,14 +108,6 @@ int orc_run(const orc_config* cfg, double* state, int64_t kick0, int n_kicks,
             double* mom_hist, double* geom_io, int geom_mode);
 
 /* ---- single-particle dual optics (Sec. 3) ---- */
-
-/* one element of a beamline: type 0 drift, 1 thick quadrupole of normalised
-   strength k (1/m^2; > 0 focuses in x, defocuses in y); slot_L, slot_k are
-   the derivative slots of L and k (-1 = constant) */
-typedef struct {
-    int32_t type, slot_L, slot_k, pad;
-    double L, k;
-} orc_element;
 
 /* dual 2x2 matrices of the beamline (elements in beam order):
    m[plane x, y][m11, m12, m21, m22][C] */
