@@ -31,6 +31,7 @@ class OrcConfig(ct.Structure):
         ("kicks", ct.c_int32 * 5), ("lat_slot", ct.c_int32 * 7),
         ("n_line", ct.c_int32), ("pad_line", ct.c_int32),
         ("line", ct.POINTER(OrcElement)), ("line_kicks", ct.POINTER(ct.c_int32)),
+        ("charge_slot", ct.c_int32), ("pad_q", ct.c_int32),
     ]
 
 
@@ -97,6 +98,7 @@ class Oracle:
         """kw: the fields of OrcConfig; line: a beamline [(type, L, k, slot_L, slot_k)] with
         line_kicks kicks per element, in place of the FODO period."""
         c = OrcConfig()
+        c.charge_slot = -1
         if line is not None:
             self._line = elements(line)
             self._line_kicks = (ct.c_int32 * len(line))(*[int(v) for v in line_kicks])

@@ -441,6 +441,12 @@ int orc_deposit(const orc_config* cfg, const double* state, const double* geom, 
 #endif
     double* priv = (double*)calloc((size_t)nthreads * C * nn, sizeof(double));
     if (!priv) return -1;
+    /* macroparticle charge Q / N, dual in Q when the bunch charge is an AD variable */
+    dual Qb, Nd, qmd;
+    d_var(C, cfg->bunch_charge_C, cfg->charge_slot, Qb);
+    d_const(C, N > 0 ? (double)N : 1.0, Nd);
+    d_div(C, Qb, Nd, qmd);
+    if (N <= 0) d_const(C, 0.0, qmd);
 #pragma omp parallel
     {
         int tid = 0;
@@ -463,7 +469,7 @@ int orc_deposit(const orc_config* cfg, const double* state, const double* geom, 
                         dual W, Q;
                         d_mul(C, w.w[0][a], w.w[1][b], W);
                         d_mul(C, W, w.w[2][c], W);
-                        d_cmul(C, K.qm, W, Q);  /* macroparticle charge times weight */
+                        d_mul(C, qmd, W, Q);    /* macroparticle charge times weight (Eq. 2) */
                         int64_t node = ((int64_t)(w.idx[2] + c) * n[1] + (w.idx[1] + b)) * n[0] +
                                        (w.idx[0] + a);
                         for (int k = 0; k < C; ++k) my[(int64_t)k * nn + node] += Q[k];

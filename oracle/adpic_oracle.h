@@ -65,6 +65,10 @@ typedef struct {
     int32_t n_line, pad_line;
     const orc_element* line;
     const int32_t* line_kicks;
+    /* slot of the bunch charge as an AD variable (Sec. 4: beam current as a
+       dual input), -1 = constant: the macroparticle charge Q / N is then a
+       dual number */
+    int32_t charge_slot, pad_q;
 } orc_config;
 
 /* derived constants: gamma0, beta0, p0 (kg m/s), Brho (T m), kappa_perp, kappa_z, q_macro (C), q (C) */

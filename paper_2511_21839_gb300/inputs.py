@@ -59,6 +59,7 @@ class Beam:
     alpha: tuple = (0.0, 0.0, 0.0)
     beta: tuple = (0.0, 0.0, 0.0)
     twiss_slot: tuple = (-1, -1, -1, -1, -1, -1)
+    charge_slot: int = -1          # derivative slot of the bunch charge (-1: constant)
 
 
 @dataclass
@@ -187,4 +188,5 @@ def orc_kwargs(w: Workload, n_particles=None, grid=None, n_deriv=None, lattice=N
                 eps_n=b.eps_n, alpha=b.alpha, beta=b.beta,
                 twiss_slot=[s if (0 <= s < P) else -1 for s in b.twiss_slot],
                 L=lat.L, g=lat.g, kicks=lat.kicks,
-                lat_slot=[s if (0 <= s < P) else -1 for s in lat.deriv_slot])
+                lat_slot=[s if (0 <= s < P) else -1 for s in lat.deriv_slot],
+                charge_slot=b.charge_slot if 0 <= b.charge_slot < P else -1)

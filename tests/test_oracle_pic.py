@@ -548,3 +548,46 @@ def test_split_integrator_second_order():
     # second order with the finest run as reference: e_i ~ tau_i^2 - tau_8^2, so the ratios
     # are (1 - 1/64) / (1/4 - 1/64) = 4.2 and (1/4 - 1/64) / (1/16 - 1/64) = 5
     assert abs(r1 - 4.2) < 0.8 and abs(r2 - 5.0) < 1.2, (e, r1, r2)
+
+
+# ---------------------------------------------------------------- the bunch charge as an AD variable
+
+def test_charge_channel_of_the_deposit_is_rho_over_q():
+    """With the bunch charge Q in slot 0 the deposit is linear in Q: channel 1 of rho equals
+    rho_0 / Q at every node (Sec. 4: the beam current as a dual input)."""
+    w = I.workload("fodo_10k_32")
+    b = I.Beam(**{**w.beam.__dict__, "charge_slot": 0})
+    lat = I.Lattice(deriv_slot=(-1, 1, 2, 3, 4, 5, 6))
+    o = make(n=16, N=2000, P=7, beam=b, lattice=lat)
+    st = o.beam_init(I.normals(23, o.N))
+    geom = o.geometry(st)
+    rho = o.deposit(st, geom)
+    q = b.bunch_charge_C
+    np.testing.assert_allclose(rho[1], rho[0] / q, rtol=1e-13, atol=1e-12 * np.abs(rho[0] / q).max())
+
+
+def test_charge_derivative_matches_central_fd_frozen_geometry():
+    """d eps / dQ of a whole period against central differences of value-only runs at frozen
+    geometry (best step of a sweep, as for the lattice parameters)."""
+    w = I.workload("fodo_10k_32")
+    b = I.Beam(**{**w.beam.__dict__, "charge_slot": 0})
+    lat = I.Lattice(deriv_slot=(-1, 1, 2, 3, 4, 5, 6))
+    o = make(n=16, N=3000, P=7, beam=b, lattice=lat)
+    nrm = I.normals(24, o.N)
+    st = o.beam_init(nrm)
+    hist, geom = o.run(st, 20, geom_mode=1)
+    d = o.emittance(hist[-1])[:2, 1]
+    q = b.bunch_charge_C
+    errs = []
+    for hrel in (1e-3, 1e-4, 1e-5, 1e-6):
+        h = hrel * q
+        vals = []
+        for qq in (q + h, q - h):
+            bb = I.Beam(**{**w.beam.__dict__, "bunch_charge_C": qq})
+            ov = make(n=16, N=o.N, P=0, beam=bb)
+            sv = ov.beam_init(nrm)
+            hv, _ = ov.run(sv, 20, geom=geom.copy(), geom_mode=2)
+            vals.append(ov.emittance(hv[-1])[:2, 0])
+        errs.append(np.abs((vals[0] - vals[1]) / (2 * h) - d))
+    best = np.min(errs, axis=0)
+    assert np.all(best < 1e-5 * np.abs(d)), (best, d)
