@@ -502,6 +502,57 @@ def nvml_index(dev):
     return dev
 
 
+def track_flops(P):
+    """Algorithmic FP64 flops of one particle through one element (both planes): per plane the
+    values (m11 x + m12 p, m21 x + m22 p: 2 multiplies and 2 fused multiply-adds) and, per derivative
+    channel and coordinate, 3 fused multiply-adds and a multiply (d(M z) = M dz + (dM) z)."""
+    return 2 * (6 + 14 * P)
+
+
+def tracking(adpic, P, n_part, turns, periods, fma64=None):
+    """Dual tracking of n_part particles through `turns` x `periods` FODO cells of Sec. 3 (5 elements
+    each), element by element; rate in particle-element-steps/s and the FP64 ALU roofline."""
+    from paper_2511_21839_gb300 import optics
+
+    cell = optics.fodo_cell()
+    cell = [(t, L, k, sL if sL < P else -1, sk if sk < P else -1) for (t, L, k, sL, sk) in cell]
+    rng = np.random.default_rng(11)
+    x0 = rng.normal(size=(n_part, 4)) * 1e-3
+    adpic.ad_pic_track_batch(x0[:64], cell, P, 2)            # warm-up (module load)
+    _, ms = adpic.ad_pic_track_batch(x0, cell, P, turns * periods)
+    steps = n_part * turns * periods * len(cell)
+    rate = steps / (ms / 1000.0)
+    out = {"n_deriv": P, "particles": n_part, "turns": turns, "periods": periods, "kernel_ms": ms,
+           "particle_element_steps_per_s": rate, "fp64_tflops": rate * track_flops(P) / 1e12}
+    if fma64:
+        out["frac_of_measured_fp64_fma"] = out["fp64_tflops"] / fma64
+    return out
+
+
+def run_track(args):
+    """The Sec. 3 tracking benchmark: one particle through 1000 turns x 100 FODO periods for several
+    numbers of control variables (the paper's figure), and batched throughput at the same counts."""
+    from paper_2511_21839_gb300 import adpic, build
+
+    build.build()
+    fma64 = adpic.ad_pic_fma_peak(adpic.AD_PIC_FP64)
+    rows = []
+    for P in (1, 3, 7, 13, 31):
+        single = tracking(adpic, P, 1, 1000, 100)
+        batch = tracking(adpic, P, args.track_particles, 10, 100, fma64)
+        rows.append({"n_deriv": P, "single_particle_ms": single["kernel_ms"], "batched": batch})
+    b7 = next(r for r in rows if r["n_deriv"] == 7)["batched"]
+    line = {"metric": "particle-element-steps/s, dual tracking through FODO cells (Sec. 3), P=7",
+            "value": b7["particle_element_steps_per_s"], "unit": "particle-element-steps/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": b7["kernel_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.track_particles} particles x 10 turns x 100 FODO cells (5 elements) per "
+                                   "step; single particle: 1000 turns x 100 cells", "fp64_fma_peak_tflops": fma64},
+            "sweep": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def run_native(args):
     import torch
 
@@ -625,7 +676,10 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{kicks_cpu} kicks of the {w.name} workload on the host cores ({dt:.1f} s)"}
 
-    large = batch = None
+    large = batch = track = None
+    if rank == 0 and w.name == "fodo_1m_64" and not args.no_track:
+        fma64 = fp64["fma_peaks_tflops"]["fp64"] if fp64 else adpic.ad_pic_fma_peak(adpic.AD_PIC_FP64)
+        track = tracking(adpic, 7, args.track_particles, 10, 100, fma64)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_large:
         large = large_instance(args, stream, adpic, I, torch, peaks)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_batch:
@@ -637,7 +691,8 @@ def run_native(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(w),
                 "roofline": roof, "roofline_step": roof_step, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64, "accuracy": acc,
-                "kernels": kernels, "large_instance": large, "batched_scan": batch}
+                "kernels": kernels, "large_instance": large, "batched_scan": batch,
+                "single_particle_tracking": track}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -678,7 +733,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-scan sub-result")
     ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["fodo_1m_64", "fodo_16m_128", "batch"], default="fodo_1m_64")
+    ap.add_argument("--no-track", action="store_true", help="skip the single-particle tracking sub-result")
+    ap.add_argument("--track-particles", type=int, default=65536)
+    ap.add_argument("--workload", choices=["fodo_1m_64", "fodo_16m_128", "batch", "track"], default="fodo_1m_64")
     ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -687,6 +744,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch_headline(args)
+    if args.workload == "track":
+        return run_track(args)
     return run_native(args)
 
 

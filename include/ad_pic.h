@@ -52,7 +52,8 @@ enum {
     AD_PIC_ERR_OUT_OF_GRID = -6, /* a particle fell outside the grid stencil */
     AD_PIC_ERR_TIMEOUT = -7,     /* a bounded device wait gave up */
     AD_PIC_ERR_UNSUPPORTED = -8, /* valid request this build does not implement */
-    AD_PIC_ERR_IO = -9           /* a checkpoint file could not be read or written */
+    AD_PIC_ERR_IO = -9,          /* a checkpoint file could not be read or written */
+    AD_PIC_ERR_UNSTABLE = -10    /* a cell has no periodic Twiss solution (|cos mu| >= 1) */
 };
 
 enum { AD_PIC_FP64 = 0, AD_PIC_FP32_MIXED = 1 };
@@ -82,13 +83,17 @@ typedef struct {
    with eps = eps_n / (beta0 gamma0), then the sample mean is removed
    (Sec. 4: initial distribution parameters may be AD variables).
    twiss_deriv_slot gives the slots of (alpha_x, beta_x, eps_x, alpha_y,
-   beta_y, eps_y), eps the geometric rms emittance, or -1. */
+   beta_y, eps_y), eps the geometric rms emittance, or -1.
+   charge_deriv_slot is the slot of the bunch charge (Sec. 4: the beam
+   current as an AD variable) or -1: the macroparticle charge Q / N is then a
+   dual number in the deposit, so every field and kick carries d/dQ. */
 typedef struct {
     double kinetic_eV, mass_eV, charge_e, bunch_charge_C;
     double eps_n[3];   /* normalised rms emittances (m rad), > 0 */
     double alpha[3];
     double beta[3];    /* m, > 0 */
     int twiss_deriv_slot[6];
+    int charge_deriv_slot;
 } ad_pic_beam;
 
 /* Create a handle for n_particles in [1, 2^31 - 1] macroparticles (particle
@@ -219,7 +224,8 @@ typedef struct ad_pic_batch ad_pic_batch;
 int ad_pic_batch_create(int n_inst, const ad_pic_grid* grids, const int64_t* n_particles, int n_deriv,
                         int precision, ad_pic_batch** out);
 /* Per-instance set-up and read-back; same arguments and semantics as the
-   single-instance calls (inst in [0, n_inst)). */
+   single-instance calls (inst in [0, n_inst)); a beam with the bunch charge
+   as an AD variable (charge_deriv_slot >= 0) is AD_PIC_ERR_UNSUPPORTED here. */
 int ad_pic_batch_set_beam(ad_pic_batch* b, int inst, const ad_pic_beam* beam, const double* normals);
 int ad_pic_batch_set_particles(ad_pic_batch* b, int inst, const double* state);
 int ad_pic_batch_set_lattice(ad_pic_batch* b, int inst, const ad_pic_lattice* lattice);
@@ -303,6 +309,61 @@ int ad_pic_moments_device(const void* state_dev, int64_t n_particles, int n_deri
    launches after a warm-up; *tflops counts an FMA as 2 flops. Changes no
    device setting; allocates a small output buffer. */
 int ad_pic_fma_peak(int precision, double* tflops);
+
+/* ---------------------------------------------------------------------
+   Single-particle dual optics (Sec. 3): beamlines of drifts and thick
+   quadrupoles whose lengths and strengths may be AD variables. FP64.
+   --------------------------------------------------------------------- */
+enum { AD_PIC_DRIFT = 0, AD_PIC_QUAD = 1 };
+
+/* One element. k is the normalised strength (1/m^2) of a quadrupole: the
+   thick-lens matrix of Sec. 4, Eq. "quadtr" (cos/sin with sqrt(k) in the
+   focusing plane, cosh/sinh in the other), focusing in x for k > 0. slot_L
+   and slot_k are derivative slots (0 .. n_deriv-1) or -1 for a constant. */
+typedef struct {
+    int type;          /* AD_PIC_DRIFT or AD_PIC_QUAD */
+    int slot_L, slot_k;
+    int pad;
+    double L;          /* length (m), >= 0 */
+    double k;          /* strength (1/m^2), quadrupoles only */
+} ad_pic_element;
+
+/* Twiss functions at the end of n_inst beamlines of n_elem elements each
+   (elems [n_inst][n_elem], host), with derivatives w.r.t. n_deriv <= 15
+   slots: out [n_inst][4][n_deriv+1] = (beta_x, alpha_x, beta_y, alpha_y),
+   value then derivatives. If n_cell > 0 the start values are the periodic
+   Twiss functions of the first n_cell elements of the instance (cos mu =
+   (m11 + m22)/2, beta = m12 / sin mu, alpha = (m11 - m22) / (2 sin mu),
+   sin mu with the sign of m12; dual, so they carry derivatives too) and the
+   transport (Sec. 3, Eq. 5) runs through the remaining elements; if n_cell
+   is 0 the start values are the constants twiss0 [n_inst][4] and the
+   transport runs through all elements. One GPU thread per instance.
+   AD_PIC_ERR_UNSTABLE if a cell has no periodic solution (that instance's
+   output is not valid). Allocates and frees device buffers per call. */
+int ad_pic_twiss_batch(int n_inst, int n_elem, const ad_pic_element* elems, int n_deriv, int n_cell,
+                       const double* twiss0, double* out);
+
+/* A general beamline in place of the FODO period of ad_pic_set_lattice (the
+   matching-section runs of Sec. 4): n_elem elements in beam order, kicks[e]
+   >= 1 space-charge kicks in element e (each M1(tau/2) M2(tau) M1(tau/2)
+   with tau = L / kicks, Sec. 4), quadrupole strengths k (1/m^2) and lengths
+   as dual variables through their slots (< n_deriv, or -1). The kick
+   schedule and the moment records then follow the beamline: one record at
+   the end of every pass. Lengths > 0. Replaces any lattice set before;
+   ad_pic_set_lattice replaces the beamline. Drops captured graphs. */
+int ad_pic_set_beamline(ad_pic* h, int n_elem, const ad_pic_element* elems, const int* kicks);
+
+/* Element-by-element tracking of n_part particles x0 [n_part][4] (x, px, y,
+   py; host) through the beamline repeated n_repeat times (turns x periods),
+   with derivatives w.r.t. n_deriv <= 32 slots: out [n_part][4][n_deriv+1]
+   (host). FP64; every derivative channel follows d(M z) = M dz + (dM) z with
+   the element maps M computed once on the host (dual FP64). One GPU thread
+   per particle and chunk of 8 derivative channels; the maps of all elements
+   sit in shared memory (AD_PIC_ERR_UNSUPPORTED beyond 200 KB). If ms is not
+   NULL it receives the kernel's CUDA-event time. Allocates and frees device
+   buffers per call. */
+int ad_pic_track_batch(int64_t n_part, const double* x0, int n_elem, const ad_pic_element* elems, int n_deriv,
+                       int64_t n_repeat, double* out, double* ms);
 
 /* Derived constants: out[8] = gamma0, beta0, p0 (kg m/s), B rho (T m),
    kappa_perp, kappa_z (1/(V/m * m)), macroparticle charge (C), q (C). */

@@ -18,7 +18,7 @@ AD_PIC_FP32_MIXED = 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error", -4: "call out of order",
           -5: "non-finite particle coordinate", -6: "particle outside the grid stencil",
           -7: "bounded device wait timed out", -8: "unsupported",
-          -9: "checkpoint file could not be read or written"}
+          -9: "checkpoint file could not be read or written", -10: "cell has no periodic Twiss solution"}
 
 
 class ad_pic_grid(ct.Structure):
@@ -32,7 +32,16 @@ class ad_pic_lattice(ct.Structure):
 class ad_pic_beam(ct.Structure):
     _fields_ = [("kinetic_eV", ct.c_double), ("mass_eV", ct.c_double), ("charge_e", ct.c_double),
                 ("bunch_charge_C", ct.c_double), ("eps_n", ct.c_double * 3), ("alpha", ct.c_double * 3),
-                ("beta", ct.c_double * 3), ("twiss_deriv_slot", ct.c_int * 6)]
+                ("beta", ct.c_double * 3), ("twiss_deriv_slot", ct.c_int * 6), ("charge_deriv_slot", ct.c_int)]
+
+
+AD_PIC_DRIFT = 0
+AD_PIC_QUAD = 1
+
+
+class ad_pic_element(ct.Structure):
+    _fields_ = [("type", ct.c_int), ("slot_L", ct.c_int), ("slot_k", ct.c_int), ("pad", ct.c_int),
+                ("L", ct.c_double), ("k", ct.c_double)]
 
 
 class AdPicError(RuntimeError):
@@ -74,6 +83,11 @@ def lib():
             "ad_pic_launches": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
             "ad_pic_moments_device": (ct.c_int, [vp, ct.c_int64, ct.c_int, ct.c_int, vp, vp]),
             "ad_pic_fma_peak": (ct.c_int, [ct.c_int, dp]),
+            "ad_pic_twiss_batch": (ct.c_int, [ct.c_int, ct.c_int, ct.POINTER(ad_pic_element), ct.c_int, ct.c_int,
+                                              dp, dp]),
+            "ad_pic_track_batch": (ct.c_int, [ct.c_int64, dp, ct.c_int, ct.POINTER(ad_pic_element), ct.c_int,
+                                              ct.c_int64, dp, dp]),
+            "ad_pic_set_beamline": (ct.c_int, [vp, ct.c_int, ct.POINTER(ad_pic_element), ct.POINTER(ct.c_int)]),
             "ad_pic_save": (ct.c_int, [vp, ct.c_char_p]),
             "ad_pic_load": (ct.c_int, [vp, ct.c_char_p]),
             "ad_pic_set_wait_limit": (ct.c_int, [vp, ct.c_int]),
@@ -223,6 +237,40 @@ def ad_pic_fma_peak(precision):
     t = ct.c_double()
     _ck("ad_pic_fma_peak", lib().ad_pic_fma_peak(int(precision), ct.byref(t)))
     return t.value
+
+
+def make_elements(beamlines):
+    """ad_pic_element array from a list of beamlines, each a list of (type, L, k, slot_L, slot_k)."""
+    flat = [e for bl in beamlines for e in bl]
+    arr = (ad_pic_element * len(flat))()
+    for i, (t, L, k, sL, sk) in enumerate(flat):
+        arr[i] = ad_pic_element(int(t), int(sL), int(sk), 0, float(L), float(k))
+    return arr
+
+
+def ad_pic_twiss_batch(beamlines, n_deriv, n_cell=0, twiss0=None):
+    """Twiss functions at the end of each beamline (all of equal length): [n_inst][4][n_deriv+1]."""
+    n_inst, n_elem = len(beamlines), len(beamlines[0])
+    out = np.zeros((n_inst, 4, n_deriv + 1))
+    t0 = None if twiss0 is None else np.ascontiguousarray(twiss0, dtype=np.float64).reshape(n_inst, 4)
+    _ck("ad_pic_twiss_batch", lib().ad_pic_twiss_batch(n_inst, n_elem, make_elements(beamlines), int(n_deriv),
+                                                       int(n_cell), None if t0 is None else _p(t0), _p(out)))
+    return out
+
+
+def ad_pic_track_batch(x0, beamline, n_deriv, n_repeat):
+    """Dual tracking of particles x0 [n][4]: (out [n][4][n_deriv+1], kernel ms)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    out = np.zeros((x0.shape[0], 4, n_deriv + 1))
+    ms = ct.c_double()
+    _ck("ad_pic_track_batch", lib().ad_pic_track_batch(x0.shape[0], _p(x0), len(beamline), make_elements([beamline]),
+                                                       int(n_deriv), int(n_repeat), _p(out), ct.byref(ms)))
+    return out, ms.value
+
+
+def ad_pic_set_beamline(h, beamline, kicks):
+    k = (ct.c_int * len(kicks))(*[int(v) for v in kicks])
+    _ck("ad_pic_set_beamline", lib().ad_pic_set_beamline(h, len(beamline), make_elements([beamline]), k))
 
 
 def ad_pic_save(h, path):
@@ -400,7 +448,8 @@ def ad_pic_mlp_destroy(m):
 def make_beam(b) -> ad_pic_beam:
     """ad_pic_beam from any object with the fields of inputs.Beam."""
     return ad_pic_beam(b.kinetic_eV, b.mass_eV, b.charge_e, b.bunch_charge_C, (ct.c_double * 3)(*b.eps_n),
-                       (ct.c_double * 3)(*b.alpha), (ct.c_double * 3)(*b.beta), (ct.c_int * 6)(*b.twiss_slot))
+                       (ct.c_double * 3)(*b.alpha), (ct.c_double * 3)(*b.beta), (ct.c_int * 6)(*b.twiss_slot),
+                       int(getattr(b, "charge_slot", -1)))
 
 
 def make_lattice(lat) -> ad_pic_lattice:
@@ -487,6 +536,9 @@ class ADPIC:
 
     def set_wait_limit(self, polls):
         ad_pic_set_wait_limit(self.h, polls)
+
+    def set_beamline(self, beamline, kicks):
+        ad_pic_set_beamline(self.h, beamline, kicks)
 
 
 class Batch:

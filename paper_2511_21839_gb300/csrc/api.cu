@@ -185,6 +185,7 @@ struct Impl {
         sb.offs = h->offs;
         sb.ids_in = h->ids[from];
         sb.ids_out = h->ids[1 - from];
+        sb.dst = h->dst;
         return sb;
     }
     // gather + kick + map A from buffer `from` into the other one, in cell-sorted order
@@ -212,18 +213,26 @@ struct Impl {
     static void build_coef(ad_pic* h) {
         const ad_pic_lattice& L = h->lat;
         const int len_param[5] = {0, 1, 3, 4, 6};
+        const bool use_line = !h->line.empty();
+        const int n_elem = use_line ? (int)h->line.size() : 5;
+        auto kicks_of = [&](int e) { return use_line ? h->line_kicks[e] : L.kicks[e]; };
         int kpp = 0;
-        for (int e = 0; e < 5; ++e) kpp += L.kicks[e];
+        for (int e = 0; e < n_elem; ++e) kpp += kicks_of(e);
         h->kpp = kpp;
         std::vector<HMap> halfm(kpp);
         std::vector<K> kc(kpp);
         int s = 0;
-        for (int e = 0; e < 5; ++e) {
-            HD Le = hvar(L.L[e], L.deriv_slot[len_param[e]]);
-            HD tau = hdiv(Le, hc((double)L.kicks[e]));        // D tau = D L / n (Sec. 4)
+        for (int e = 0; e < n_elem; ++e) {
+            HD Le = use_line ? hvar(h->line[e].L, h->line[e].slot_L) : hvar(L.L[e], L.deriv_slot[len_param[e]]);
+            HD tau = hdiv(Le, hc((double)kicks_of(e)));      // D tau = D L / n (Sec. 4)
             HD t = hmul(tau, hc(0.5));
             HD kx = hc(0.0), ky = hc(0.0);
-            if (e == 1 || e == 3) {
+            if (use_line) {
+                if (h->line[e].type == AD_PIC_QUAD) {        // normalised strength k, a dual of its own
+                    kx = hvar(h->line[e].k, h->line[e].slot_k);
+                    ky = hneg(kx);
+                }
+            } else if (e == 1 || e == 3) {
                 const int gi = e == 1 ? 0 : 1;
                 HD g = hvar(L.g[gi], L.deriv_slot[e == 1 ? 2 : 5]);
                 kx = hdiv(g, hc(h->brho));                   // k = q g / p0
@@ -239,7 +248,7 @@ struct Impl {
             HD ap = hmul(hc(h->kperp), tau), az = hmul(hc(h->kz), tau);
             K kk;
             for (int k = 0; k < CP; ++k) { kk.a[0][k] = (T)ap.v[k]; kk.a[1][k] = (T)ap.v[k]; kk.a[2][k] = (T)az.v[k]; }
-            for (int j = 0; j < L.kicks[e]; ++j, ++s) { halfm[s] = m; kc[s] = kk; }
+            for (int j = 0; j < kicks_of(e); ++j, ++s) { halfm[s] = m; kc[s] = kk; }
         }
         h->half.resize(sizeof(M) * kpp);
         h->comp.resize(sizeof(M) * kpp);
@@ -301,13 +310,14 @@ struct Impl {
         cudaEventRecord(h->ev_join, h->side);
         tbegin(h, K_DEPOSIT, cap);
         launch_deposit<T, C, CP>(buf(h, from), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
-                                 sortbuf(h, from), s);
+                                 sortbuf(h, from), h->qslot, s);
         tend(h, K_DEPOSIT, cap);
         // cell offsets for the push on the side stream, behind the Green's function
         cudaEventRecord(h->ev_dep, s);
         cudaStreamWaitEvent(h->side, h->ev_dep, 0);
         tbegin(h, K_MISC, cap, h->side);
         launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, h->side);
+        launch_slots(h->key, h->rank, h->offs, h->dst, h->N, h->side);
         tend(h, K_MISC, cap, h->side);
         cudaEventRecord(h->ev_scan, h->side);
         tbegin(h, K_MISC, cap);
@@ -332,10 +342,10 @@ struct Impl {
         tend(h, K_MISC, cap);
     }
 
-    // kernels launched by one enqueue_field (deposit 1, scan 2, chmax 1,
-    // Green's function 4: corners, cell averages with the first DCT pass, two
-    // DCT passes; convolution 3 or 5, field 1)
-    static int field_launches(ad_pic* h) { return 9 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
+    // kernels launched by one enqueue_field (deposit 1, scan 2, push slots 1,
+    // chmax 1, Green's function 4: corners, cell averages with the first DCT
+    // pass, two DCT passes; convolution 3 or 5, field 1)
+    static int field_launches(ad_pic* h) { return 10 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
 
     // the launch sequence of one run; returns the number of moment records
     // `from` is the buffer holding the particles at the start; each push moves
@@ -509,6 +519,7 @@ struct Impl {
         h->kperp = h->q / (h->gamma0 * h->p0 * v0);
         h->kz = h->q / (h->p0 * v0);
         h->qm = b->bunch_charge_C / (double)h->N;
+        h->qslot = b->charge_deriv_slot;
         h->beam_set = true;
         h->coef_dirty = true;
         free_graphs(h);
@@ -625,8 +636,9 @@ struct Impl {
         // rho is zero between kicks (the convolution clears it); cleared here too
         CK(cudaMemsetAsync(h->rho, 0, sizeof(T) * nodes * CP, s));
         launch_deposit<T, C, CP>(st(h), h->N, h->geom, h->nx, h->ny, h->nz, (T)h->qm, (T*)h->rho, h->err,
-                                 sortbuf(h, h->cur), s);
+                                 sortbuf(h, h->cur), h->qslot, s);
         launch_scan(h->cellcount, h->offs, h->bsum, (int)nodes, s);
+        launch_slots(h->key, h->rank, h->offs, h->dst, h->N, s);
         std::vector<T> buf;
         if (which == 1) {
             buf.resize(nodes * CP);
@@ -681,8 +693,8 @@ struct Impl {
     struct FileHeader {
         char magic[8];
         uint32_t version, elem;
-        int32_t prec, n_deriv, chans, chans_padded, nx, ny, nz, flags, first_record, pad;
-        int64_t N, kick, hist_len;
+        int32_t prec, n_deriv, chans, chans_padded, nx, ny, nz, flags, first_record, qslot;
+        int64_t N, kick, hist_len, n_line;
         double consts[8];
         ad_pic_lattice lat;
     };
@@ -692,13 +704,14 @@ struct Impl {
         if (!h->particles_set) return AD_PIC_ERR_STATE;
         FileHeader hd{};
         std::memcpy(hd.magic, "ADPICCK", 8);
-        hd.version = 1;
+        hd.version = 2;
         hd.elem = sizeof(T);
         hd.prec = h->prec; hd.n_deriv = h->P; hd.chans = C; hd.chans_padded = CP;
         hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz;
         hd.flags = (h->beam_set ? 1 : 0) | (h->lattice_set ? 2 : 0);
         hd.first_record = h->first_record ? 1 : 0;
-        hd.N = h->N; hd.kick = h->kick; hd.hist_len = (int64_t)h->hist.size();
+        hd.qslot = h->qslot;
+        hd.N = h->N; hd.kick = h->kick; hd.hist_len = (int64_t)h->hist.size(); hd.n_line = (int64_t)h->line.size();
         const double k[8] = {h->gamma0, h->beta0, h->p0, h->brho, h->kperp, h->kz, h->qm, h->q};
         std::memcpy(hd.consts, k, sizeof(k));
         hd.lat = h->lat;
@@ -707,6 +720,9 @@ struct Impl {
         if (!f) return AD_PIC_ERR_IO;
         bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
         if (ok && !h->hist.empty()) ok = std::fwrite(h->hist.data(), sizeof(double), h->hist.size(), f) == h->hist.size();
+        if (ok && !h->line.empty())
+            ok = std::fwrite(h->line.data(), sizeof(ad_pic_element), h->line.size(), f) == h->line.size() &&
+                 std::fwrite(h->line_kicks.data(), sizeof(int), h->line_kicks.size(), f) == h->line_kicks.size();
         std::vector<unsigned char> buf;
         auto dump = [&](const void* dev, size_t bytes) -> int {
             for (size_t o = 0; o < bytes && ok; o += kChunk) {
@@ -730,15 +746,25 @@ struct Impl {
         if (!f) return AD_PIC_ERR_IO;
         FileHeader hd{};
         int rc = AD_PIC_OK;
-        if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "ADPICCK", 8) != 0 || hd.version != 1)
+        if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "ADPICCK", 8) != 0 || hd.version != 2)
             rc = AD_PIC_ERR_IO;
         else if (hd.elem != sizeof(T) || hd.prec != h->prec || hd.n_deriv != h->P || hd.nx != h->nx || hd.ny != h->ny ||
-                 hd.nz != h->nz || hd.N != h->N || hd.hist_len < 0 || hd.hist_len % (15 * C) != 0)
+                 hd.nz != h->nz || hd.N != h->N || hd.hist_len < 0 || hd.hist_len % (15 * C) != 0 || hd.n_line < 0 ||
+                 hd.n_line > 100000)
             rc = AD_PIC_ERR_INVALID_ARG;      // a checkpoint of another configuration
         std::vector<double> hist;
         if (!rc) {
             hist.resize((size_t)hd.hist_len);
             if (!hist.empty() && std::fread(hist.data(), sizeof(double), hist.size(), f) != hist.size()) rc = AD_PIC_ERR_IO;
+        }
+        std::vector<ad_pic_element> line;
+        std::vector<int> line_kicks;
+        if (!rc && hd.n_line > 0) {
+            line.resize((size_t)hd.n_line);
+            line_kicks.resize((size_t)hd.n_line);
+            if (std::fread(line.data(), sizeof(ad_pic_element), line.size(), f) != line.size() ||
+                std::fread(line_kicks.data(), sizeof(int), line_kicks.size(), f) != line_kicks.size())
+                rc = AD_PIC_ERR_IO;
         }
         std::vector<unsigned char> buf;
         auto fill = [&](void* dev, size_t bytes) {
@@ -765,9 +791,12 @@ struct Impl {
         h->cur = 0;
         h->gamma0 = hd.consts[0]; h->beta0 = hd.consts[1]; h->p0 = hd.consts[2]; h->brho = hd.consts[3];
         h->kperp = hd.consts[4]; h->kz = hd.consts[5]; h->qm = hd.consts[6]; h->q = hd.consts[7];
+        h->qslot = hd.qslot >= -1 && hd.qslot < h->P ? hd.qslot : -1;
         h->beam_set = (hd.flags & 1) != 0;
         h->lattice_set = (hd.flags & 2) != 0;
         h->lat = hd.lat;
+        h->line.swap(line);
+        h->line_kicks.swap(line_kicks);
         h->particles_set = true;
         h->kick = hd.kick;
         h->first_record = hd.first_record != 0;
@@ -785,8 +814,10 @@ struct Impl {
         int r = 0;
         r |= dalloc(h, &h->state, sizeof(T) * 6 * h->N * CP);
         r |= dalloc(h, &h->state2, sizeof(T) * 6 * h->N * CP);
-        r |= dalloc(h, (void**)&h->ids[0], sizeof(int) * h->N);
-        r |= dalloc(h, (void**)&h->ids[1], sizeof(int) * h->N);
+        // id and slot arrays carry 4 padding entries: the push copies their runs in 16-byte units
+        r |= dalloc(h, (void**)&h->ids[0], sizeof(int) * (h->N + 4));
+        r |= dalloc(h, (void**)&h->ids[1], sizeof(int) * (h->N + 4));
+        r |= dalloc(h, (void**)&h->dst, sizeof(int) * (h->N + 4));
         r |= dalloc(h, (void**)&h->key, sizeof(int) * h->N);
         r |= dalloc(h, (void**)&h->rank, sizeof(int) * h->N);
         r |= dalloc(h, (void**)&h->cellcount, sizeof(int) * nodes);
@@ -940,6 +971,7 @@ int ad_pic_set_beam(ad_pic* h, const ad_pic_beam* b, const double* normals) {
         if (!(b->eps_n[d] > 0) || !(b->beta[d] > 0) || !std::isfinite(b->alpha[d])) return AD_PIC_ERR_INVALID_ARG;
     for (int j = 0; j < 6; ++j)
         if (b->twiss_deriv_slot[j] < -1 || b->twiss_deriv_slot[j] >= h->P) return AD_PIC_ERR_INVALID_ARG;
+    if (b->charge_deriv_slot < -1 || b->charge_deriv_slot >= h->P) return AD_PIC_ERR_INVALID_ARG;
     DISPATCH(h, I::set_beam(h, b, normals));
 }
 
@@ -963,6 +995,29 @@ int ad_pic_set_lattice(ad_pic* h, const ad_pic_lattice* L) {
     for (int j = 0; j < 7; ++j)
         if (L->deriv_slot[j] < -1 || L->deriv_slot[j] >= h->P) return AD_PIC_ERR_INVALID_ARG;
     h->lat = *L;
+    h->line.clear();
+    h->line_kicks.clear();
+    h->lattice_set = true;
+    h->coef_dirty = true;
+    free_graphs(h);
+    return AD_PIC_OK;
+}
+
+int ad_pic_set_beamline(ad_pic* h, int n_elem, const ad_pic_element* elems, const int* kicks) {
+    if (!h || n_elem < 1 || n_elem > 100000 || !elems || !kicks) return AD_PIC_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (int e = 0; e < n_elem; ++e) {
+        const ad_pic_element& x = elems[e];
+        if (x.type != AD_PIC_DRIFT && x.type != AD_PIC_QUAD) return AD_PIC_ERR_INVALID_ARG;
+        if (!(x.L > 0) || !std::isfinite(x.L) || (x.type == AD_PIC_QUAD && !std::isfinite(x.k)))
+            return AD_PIC_ERR_INVALID_ARG;
+        if (x.slot_L < -1 || x.slot_L >= h->P || x.slot_k < -1 || x.slot_k >= h->P) return AD_PIC_ERR_INVALID_ARG;
+        if (kicks[e] < 1 || kicks[e] > 100000) return AD_PIC_ERR_INVALID_ARG;
+        total += kicks[e];
+    }
+    if (total > 1000000) return AD_PIC_ERR_INVALID_ARG;
+    h->line.assign(elems, elems + n_elem);
+    h->line_kicks.assign(kicks, kicks + n_elem);
     h->lattice_set = true;
     h->coef_dirty = true;
     free_graphs(h);
@@ -1146,6 +1201,7 @@ const char* ad_pic_strerror(int s) {
         case AD_PIC_ERR_TIMEOUT: return "bounded device wait timed out";
         case AD_PIC_ERR_UNSUPPORTED: return "unsupported";
         case AD_PIC_ERR_IO: return "checkpoint file could not be read or written";
+        case AD_PIC_ERR_UNSTABLE: return "cell has no periodic Twiss solution";
         default: return "unknown status";
     }
 }

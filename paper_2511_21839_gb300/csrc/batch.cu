@@ -118,6 +118,7 @@ __device__ __forceinline__ SortBuf sort_of(const Inst<T>& in, int from) {
     sb.offs = in.offs;
     sb.ids_in = in.ids[from];
     sb.ids_out = in.ids[1 - from];
+    sb.dst = nullptr;
     return sb;
 }
 
@@ -903,7 +904,8 @@ int ad_pic_batch_create(int n_inst, const ad_pic_grid* grids, const int64_t* n_p
 }
 
 int ad_pic_batch_set_beam(ad_pic_batch* b, int inst, const ad_pic_beam* beam, const double* normals) {
-    if (!b || inst < 0 || inst >= b->n_inst) return AD_PIC_ERR_INVALID_ARG;
+    if (!b || inst < 0 || inst >= b->n_inst || !beam) return AD_PIC_ERR_INVALID_ARG;
+    if (beam->charge_deriv_slot != -1) return AD_PIC_ERR_UNSUPPORTED;   // the batched deposit has no charge channel
     batch_free_graphs(b);
     return ad_pic_set_beam(b->h[inst], beam, normals);
 }

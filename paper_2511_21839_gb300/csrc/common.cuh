@@ -269,6 +269,10 @@ struct SortBuf {
     const int* offs;
     const int* ids_in;
     int* ids_out;
+    // optional: the destination slot of every particle, offs[key[i]] + rank[i],
+    // computed after the scan (nullptr: the push computes it itself). With it,
+    // the persistent push copies each tile's slots and ids with its state.
+    const int* dst;
 };
 
 // track: also reduce the value-part extrema of the new positions into mm; the
@@ -282,6 +286,8 @@ void launch_push(const T* state_in, T* state_out, int64_t N, const T* E, const G
 // that runs out); *failed = the failed polls
 int launch_wait_probe(int polls, int* failed, cudaStream_t s);
 void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s);
+// dst[i] = offs[key[i]] + rank[i] for every particle
+void launch_slots(const int* key, const int* rank, const int* offs, int* dst, int64_t N, cudaStream_t s);
 int scan_blocks(int ncells);
 void launch_iota(int* ids, int64_t N, cudaStream_t s);
 template <typename T, int CP>
@@ -292,7 +298,7 @@ void launch_boundary(T* state, int64_t N, const MapCoef<T, CP>& A, bool apply, b
 int boundary_blocks();
 template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho,
-                    int* err, const SortBuf& sb, cudaStream_t s);
+                    int* err, const SortBuf& sb, int qslot, cudaStream_t s);
 template <typename T, int C, int CP>
 void setup_deposit();
 template <typename T, int C, int CP>

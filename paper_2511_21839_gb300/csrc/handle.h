@@ -20,7 +20,11 @@ struct ad_pic {
     int64_t N = 0;
     bool beam_set = false, particles_set = false, lattice_set = false, coef_dirty = true;
     double gamma0 = 0, beta0 = 0, p0 = 0, brho = 0, kperp = 0, kz = 0, qm = 0, q = 0;
+    int qslot = -1;               // derivative slot of the bunch charge (-1: constant)
     ad_pic_lattice lat{};
+    // a general beamline in place of the FODO period (empty: the FODO lattice)
+    std::vector<ad_pic_element> line;
+    std::vector<int> line_kicks;
     int kpp = 0;
     int64_t kick = 0;
     bool first_record = true;
@@ -42,6 +46,7 @@ struct ad_pic {
     int* rank = nullptr;         // rank among that cell's particles
     int* cellcount = nullptr;    // particles per cell (zero between kicks)
     int* offs = nullptr;         // exclusive cell offsets
+    int* dst = nullptr;          // destination slot of every particle in the push (N + 4 entries)
     int* bsum = nullptr;         // scan chunk totals
     void* rho = nullptr;         // zero between kicks: the convolution's x pass clears it
     unsigned* gcount = nullptr;  // finished blocks of a kernel with the fused geometry step

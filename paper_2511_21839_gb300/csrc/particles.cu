@@ -79,6 +79,9 @@ void launch_scan(int* hist, int* offs, int* bsum, int ncells, cudaStream_t s) {
     scan_sum_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum);
     scan_apply_kernel<<<nb, 256, 0, s>>>(hist, ncells, bsum, offs);   // each block prefixes the chunk totals
 }
+void launch_slots(const int* key, const int* rank, const int* offs, int* dst, int64_t N, cudaStream_t s) {
+    if (N > 0) slots_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(key, rank, offs, dst, N);
+}
 void launch_iota(int* ids, int64_t N, cudaStream_t s) {
     if (N > 0) iota_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(ids, N);
 }
@@ -111,14 +114,15 @@ void launch_moments_reduce(const double* partial, int nblocks, int CP, int64_t N
 
 template <typename T, int C, int CP>
 void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int ny, int nz, T qm, T* rho, int* err,
-                    const SortBuf& sb, cudaStream_t s) {
+                    const SortBuf& sb, int qslot, cudaStream_t s) {
     if (N <= 0) return;
     // warp-sorted, on-chip summed deposition (see deposit_tile_body)
     constexpr int W = dep_tile_warps<CP, T>();
     const size_t sm = (size_t)W * dep_tile_bytes_per_warp<CP, T>();
     const int64_t warps = (N + 31) / 32;
     deposit_tile_kernel<T, C, CP, W><<<(unsigned)((warps + W - 1) / W), W * 32, sm, s>>>(state, N, geom, nx, ny, nz,
-                                                                                       qm, rho, err, sb);
+                                                                                       qm, rho, err, sb, qslot,
+                                                                                       (T)(1.0 / (double)N));
 }
 
 template <typename T, int C, int CP>
@@ -137,7 +141,7 @@ void setup_deposit() {
     template void launch_boundary<T, C, CP>(T*, int64_t, const MapCoef<T, CP>&, bool, bool, double*, int,       \
                                             Ord<T>*, const GeomFuse&, cudaStream_t);                             \
     template void launch_deposit<T, C, CP>(const T*, int64_t, const GeomDev*, int, int, int, T, T*, int*,        \
-                                           const SortBuf&, cudaStream_t);                                        \
+                                           const SortBuf&, int, cudaStream_t);                                   \
     template void setup_deposit<T, C, CP>();                                                                     \
     template void setup_push<T, C, CP>();
 ADPIC_INST(float, 8, 8)

@@ -394,7 +394,8 @@ __host__ __device__ constexpr int push_window_stride() {
 template <typename T, int CP>
 __host__ __device__ constexpr size_t push_smem() {
     return sizeof(T) * ((size_t)2 * 6 * push_tile<T, CP>() * CP +
-                        (size_t)(push_tile<T, CP>() / 32) * push_window_slots<T, CP>() * push_window_stride<T, CP>());
+                        (size_t)(push_tile<T, CP>() / 32) * push_window_slots<T, CP>() * push_window_stride<T, CP>()) +
+           sizeof(int) * (size_t)2 * 2 * push_tile<T, CP>();     // each stage's slots and ids
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -427,20 +428,27 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
     constexpr int PPN = 3 * CP * (int)sizeof(T) / 16;       // 16-byte pieces per node record
     extern __shared__ __align__(128) unsigned char smraw[];
     T* ring = reinterpret_cast<T*>(smraw);      // [2][6][TP][CP]
-    T* win = ring + (size_t)2 * 6 * TP * CP;    // [TP / 32][KW][WS]
+    int* aux = reinterpret_cast<int*>(ring + (size_t)2 * 6 * TP * CP);   // [2][2][TP]: slots, ids
+    T* win = reinterpret_cast<T*>(aux + 2 * 2 * TP);                      // [TP / 32][KW][WS]
     __shared__ int s_cell[TP / 32][KW > 0 ? KW : 1];
+    __shared__ int s_slot[TP], s_id[TP];        // this tile's slots and ids, kept past the ring's reuse
     __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x;
     const int64_t ntiles = (N + TP - 1) / TP;
     const int64_t step = gridDim.x;
+    // the slots (sb.dst, required) and ids travel with the state
     auto issue = [&](int64_t tl, int s) {
         const int64_t p0 = tl * TP;
         const int n = (int)min((int64_t)TP, N - p0);
         const unsigned bytes = (unsigned)n * CP * (unsigned)sizeof(T);
-        mbar_expect_tx(&bar[s], 6u * bytes);
+        // slot and id runs rounded up to 16 bytes (the arrays are padded by 4 entries)
+        const unsigned ib = ((unsigned)n * 4u + 15u) & ~15u;
+        mbar_expect_tx(&bar[s], 6u * bytes + 2u * ib);
 #pragma unroll
         for (int c = 0; c < 6; ++c)
             bulk_g2s(ring + ((size_t)(s * 6 + c) * TP) * CP, state + ((size_t)c * N + p0) * CP, bytes, &bar[s]);
+        bulk_g2s(aux + (s * 2 + 0) * TP, sb.dst + p0, ib, &bar[s]);
+        bulk_g2s(aux + (s * 2 + 1) * TP, sb.ids_in + p0, ib, &bar[s]);
     };
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -466,60 +474,67 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
         }
         const int64_t i = tile * TP + tid;
         const bool valid = i < N;
+        const T* row = ring + ((size_t)s * 6 * TP + tid) * CP;     // coordinate c at row + c * TP * CP
+        // stencil windows: the cells from the value parts alone, and the copies of
+        // the distinct cells' stencils issued before the state goes to registers
+        int L = -1, slot = 0, bad = 0;
+        T f[3], ih[3];
+        const bool win_on = KW > 0 && E != nullptr;
+        if constexpr (KW > 0) {
+            if (win_on) {
+                const int lane = tid & 31, warp = tid >> 5;
+                int idx[3];
+                if (valid) L = locate<T>(row, row + 2 * TP * CP, row + 4 * TP * CP, *geom, nx, ny, nz, idx, f, ih, bad);
+                // the warp's distinct cells: the lowest lane of each cell owns a slot
+                const unsigned match = __match_any_sync(0xffffffffu, L);
+                const int lead = __ffs(match) - 1;
+                const unsigned heads = __ballot_sync(0xffffffffu, valid && lead == lane);
+                slot = __popc(heads & ((1u << lead) - 1u));
+                const int k = min(__popc(heads), KW);
+                __syncwarp();                    // the warp's gathers from its window are done
+                if (valid && lead == lane && slot < KW) s_cell[warp][slot] = L;
+                __syncwarp();
+                const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
+                T* wwin = win + (size_t)warp * KW * WS;
+                // one (stencil, node) pair per lane and trip: the node record's 16-byte pieces
+                for (int pr = lane; pr < k * 8; pr += 32) {
+                    const int sl = pr >> 3, nd = pr & 7;
+                    const T* src = E + (int64_t)s_cell[warp][sl] * (3 * CP) + (nd >> 2) * sz + ((nd >> 1) & 1) * sy +
+                                   (nd & 1) * (3 * CP);
+                    T* dstw = wwin + sl * WS + nd * 3 * CP;
+#pragma unroll
+                    for (int pc = 0; pc < PPN; ++pc)
+                        cp_async16(dstw + pc * (16 / (int)sizeof(T)), src + pc * (16 / (int)sizeof(T)));
+                }
+            }
+        }
         T u[6][CP];
         if (valid) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) ldv<T, CP>(ring + ((size_t)(s * 6 + c) * TP + tid) * CP, u[c]);
+            for (int c = 0; c < 6; ++c) ldv<T, CP>(row + (size_t)c * TP * CP, u[c]);
+            s_slot[tid] = aux[(s * 2 + 0) * TP + tid];      // slots and ids are 32-bit: N < 2^31
+            s_id[tid] = aux[(s * 2 + 1) * TP + tid];
         }
         __syncthreads();                         // stage s is free again
         if (tid == 0 && tile + 2 * step < ntiles) {
             fence_proxy_async_smem();
             issue(tile + 2 * step, s);
         }
-        // slot and id loads first: their latency overlaps the gather (slots and
-        // ids are 32-bit: N < 2^31)
-        int dst = 0, idv = 0;
-        if (valid) {
-            dst = sb.offs ? sb.offs[sb.key[i]] + sb.rank[i] : (int)i;
-            idv = sb.ids_out ? sb.ids_in[i] : 0;
-        }
         if constexpr (KW > 0) {
-            if (E != nullptr) {
-                const int lane = tid & 31, warp = tid >> 5;
-                int idx[3];
-                T f[3], ih[3];
-                int bad = 0, L = -1;
-                if (valid) L = locate<T>(u[0], u[2], u[4], *geom, nx, ny, nz, idx, f, ih, bad);
+            if (win_on) {
                 if (bad) atomicOr(err, bad);
-                // the warp's distinct cells: the lowest lane of each cell owns a slot
-                const unsigned match = __match_any_sync(0xffffffffu, L);
-                const int lead = __ffs(match) - 1;
-                const unsigned heads = __ballot_sync(0xffffffffu, valid && lead == lane);
-                const int slot = __popc(heads & ((1u << lead) - 1u));
-                const int k = min(__popc(heads), KW);
-                T* wwin = win + (size_t)warp * KW * WS;
-                if (valid && lead == lane && slot < KW) s_cell[warp][slot] = L;
-                __syncwarp();
-                const int64_t sy = (int64_t)nx * 3 * CP, sz = (int64_t)nx * ny * 3 * CP;
-                for (int r = lane; r < k * 8 * PPN; r += 32) {
-                    const int sl = r / (8 * PPN), pc = r - sl * 8 * PPN, nd = pc / PPN, piece = pc - nd * PPN;
-                    const T* src = E + (int64_t)s_cell[warp][sl] * (3 * CP) + (nd >> 2) * sz + ((nd >> 1) & 1) * sy +
-                                   (nd & 1) * (3 * CP);
-                    cp_async16(wwin + sl * WS + nd * 3 * CP + piece * (16 / (int)sizeof(T)),
-                               src + piece * (16 / (int)sizeof(T)));
-                }
                 cp_async_wait_all();
                 __syncwarp();
                 if (valid) {
                     if (slot < KW) {
                         SharedStencil<T, CP> st_;
-                        st_.w = wwin + slot * WS;
+                        st_.w = win + ((size_t)(tid >> 5) * KW + slot) * WS;
                         kick_core<T, C, CP>(u, f, ih, st_, K);
                     } else {
                         GlobalStencil<T, CP> st_;
                         st_.e0 = E + (int64_t)L * (3 * CP);
-                        st_.sy = sy;
-                        st_.sz = sz;
+                        st_.sy = (int64_t)nx * 3 * CP;
+                        st_.sz = (int64_t)nx * ny * 3 * CP;
                         kick_core<T, C, CP>(u, f, ih, st_, K);
                     }
                     map_core<T, CP>(u, A);
@@ -531,7 +546,8 @@ __device__ __forceinline__ void push_tma_body(const T* __restrict__ state, T* __
             push_core<T, C, CP>(u, E, geom, nx, ny, nz, A, K, err);
         }
         if (valid) {
-            if (sb.ids_out) sb.ids_out[dst] = idv;
+            const int dst = s_slot[tid];
+            sb.ids_out[dst] = s_id[tid];
 #pragma unroll
             for (int c = 0; c < 6; ++c) stg_v<T, CP>(out + (c * N + (int64_t)dst) * CP, u[c]);
             if (TRACK) {
@@ -671,6 +687,12 @@ static __global__ void scan_apply_kernel(int* __restrict__ hist, int ncells, con
                                   int* __restrict__ offs) {
     scan_apply_kernel_body(hist, ncells, bsum, offs, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x,
                            false);
+}
+
+static __global__ void slots_kernel(const int* __restrict__ key, const int* __restrict__ rank,
+                                    const int* __restrict__ offs, int* __restrict__ dst, int64_t N) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) dst[i] = offs[key[i]] + rank[i];
 }
 
 __device__ __forceinline__ void iota_kernel_body(int* ids, int64_t N,
@@ -953,11 +975,13 @@ __host__ __device__ constexpr int dep_tile_warps() {
 // sectors. The cell sort's rank is the lane's offset in its run plus one
 // counting atomic per run.
 
+// qslot >= 0: the bunch charge Q is the AD variable of that slot; channel
+// qslot + 1 then also gets dq_m/dQ W = W / N (qmd = 1 / N) per node (Eq. 2 on q_m W).
 template <typename T, int C, int CP, int WARPS>
 __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, int64_t N,
                                                     const GeomDev* __restrict__ geom, int nx, int ny, int nz, T qm,
                                                     T* __restrict__ rho, int* __restrict__ err, const SortBuf sb,
-                                                    const int bx_) {
+                                                    const int bx_, int qslot = -1, T qmd = (T)0) {
     constexpr int ROWS = 4 * CP;                            // tile columns: 4 nodes x CP
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ unsigned char smraw[];
@@ -1056,6 +1080,11 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
                     rec[k + 1] = r.y;
                 }
                 rec[0] = qm * (wx * wy * wz);
+                if (qslot >= 0) {                  // warp-uniform
+#pragma unroll
+                    for (int k = 1; k < CP; ++k)
+                        if (k == qslot + 1) rec[k] = fma(qmd, wx * wy * wz, rec[k]);
+                }
                 stv<T, CP>(tile + mypos * RS + nb * CP, rec);
             }
         }
@@ -1097,8 +1126,9 @@ template <typename T, int C, int CP, int WARPS>
 static __global__ void __launch_bounds__(WARPS * 32, dep_min_blocks<T, CP>()) deposit_tile_kernel(const T* __restrict__ state, int64_t N,
                                                                            const GeomDev* __restrict__ geom, int nx,
                                                                            int ny, int nz, T qm, T* __restrict__ rho,
-                                                                           int* __restrict__ err, const SortBuf sb) {
-    deposit_tile_body<T, C, CP, WARPS>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x);
+                                                                           int* __restrict__ err, const SortBuf sb,
+                                                                           int qslot, T qmd) {
+    deposit_tile_body<T, C, CP, WARPS>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x, qslot, qmd);
 }
 
 // ------------------------------------------------------------------ bounded-wait probe

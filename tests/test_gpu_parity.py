@@ -179,6 +179,30 @@ def test_p13_twiss_derivatives(adpic, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bunch_charge_derivative(adpic, prec):
+    """The bunch charge as an AD variable (slot 0, in place of the first drift length): the deposit's
+    charge channel and every derivative downstream against the oracle."""
+    N, grid = 10_000, (32, 32, 32)
+    w = I.workload("fodo_10k_32")
+    b = I.Beam(**{**w.beam.__dict__, "charge_slot": 0})
+    lat = I.Lattice(deriv_slot=(-1, 1, 2, 3, 4, 5, 6))
+    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=N, grid=grid, beam=b, lattice=lat))
+    nrm = I.normals(47, N)
+    st = o.beam_init(nrm)
+    hist, _ = o.run(st, 20)
+    sim = adpic.ADPIC(grid, N, 7, prec)
+    sim.set_beam(b, nrm)
+    sim.set_lattice(lat)
+    sim.run(20)
+    vals, der = sim.moments()
+    ref = o.emittance(hist[-1])[:2]
+    ev, ed = report(f"charge slot prec={prec}", vals, der, ref)
+    assert ev < TOL[prec]["eps"] and ed < der_tol(prec, N)
+    assert np.all(np.abs(ref[:, 1]) > 0)
+    sim.close()
+
+
 def test_split_runs_and_graph_replay(adpic):
     """run(20) equals run(7) + run(13) (period-end moments and the kick counter carry over);
     graph capture and eager launches agree."""
