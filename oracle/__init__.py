@@ -281,3 +281,115 @@ def track(beamline, P, x0, n_repeat):
     out = np.zeros((x0.shape[0], 4, P + 1))
     lib().orc_track(P, elements(beamline), len(beamline), int(n_repeat), x0.shape[0], _p(x0), _p(out))
     return out
+
+
+# ---------------------------------------------------------------- 2D PIC in a conducting pipe (Sec. 4)
+
+class Orc2DConfig(ct.Structure):
+    _fields_ = [("P", ct.c_int32), ("nx", ct.c_int32), ("ny", ct.c_int32), ("current_slot", ct.c_int32),
+                ("N", ct.c_int64), ("a", ct.c_double), ("b", ct.c_double),
+                ("kinetic_eV", ct.c_double), ("mass_eV", ct.c_double), ("charge_e", ct.c_double),
+                ("current_A", ct.c_double), ("eps_n", ct.c_double * 2), ("alpha", ct.c_double * 2),
+                ("beta", ct.c_double * 2), ("L", ct.c_double * 5), ("g", ct.c_double * 2),
+                ("kicks", ct.c_int32 * 5), ("lat_slot", ct.c_int32 * 7)]
+
+
+_lib2d = None
+
+
+def lib2d():
+    global _lib2d
+    if _lib2d is None:
+        L = lib()
+        dp = ct.POINTER(ct.c_double)
+        cp = ct.POINTER(Orc2DConfig)
+        sig = {
+            "orc2d_constants": (None, [cp, dp]),
+            "orc2d_beam_init": (ct.c_int, [cp, dp, dp]),
+            "orc2d_deposit": (ct.c_int, [cp, dp, dp]),
+            "orc2d_solve": (None, [cp, dp, dp]),
+            "orc2d_field": (None, [cp, dp, dp]),
+            "orc2d_kick": (ct.c_int, [cp, dp, dp, ct.c_int64]),
+            "orc2d_moments": (None, [cp, dp, dp]),
+            "orc2d_run": (ct.c_int, [cp, dp, ct.c_int64, ct.c_int, dp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib2d = L
+    return _lib2d
+
+
+class Oracle2D:
+    """FP64 oracle of the 2D conducting-pipe PIC bound to one configuration (fields of Orc2DConfig)."""
+
+    def __init__(self, **kw):
+        c = Orc2DConfig()
+        c.current_slot = -1
+        for k, v in kw.items():
+            f = getattr(c, k)
+            if isinstance(f, ct.Array):
+                for i, x in enumerate(v):
+                    f[i] = x
+            else:
+                setattr(c, k, v)
+        self.cfg = c
+        self.C = c.P + 1
+        self.N = c.N
+        self._L = lib2d()
+
+    @property
+    def ref(self):
+        return ct.byref(self.cfg)
+
+    def constants(self):
+        out = np.zeros(5)
+        self._L.orc2d_constants(self.ref, _p(out))
+        return dict(zip(["gamma0", "beta0", "p0", "brho", "K"], out.tolist()))
+
+    def grid_shape(self):
+        return (self.C, self.cfg.ny + 1, self.cfg.nx + 1)
+
+    def beam_init(self, normals):
+        normals = np.ascontiguousarray(normals, dtype=np.float64)
+        st = np.zeros((4, self.N, self.C))
+        _check(self._L.orc2d_beam_init(self.ref, _p(normals), _p(st)), "2d beam_init")
+        return st
+
+    def deposit(self, state):
+        n = np.zeros(self.grid_shape())
+        _check(self._L.orc2d_deposit(self.ref, _p(np.ascontiguousarray(state)), _p(n)), "2d deposit")
+        return n
+
+    def solve(self, n):
+        phi = np.zeros(self.grid_shape())
+        self._L.orc2d_solve(self.ref, _p(np.ascontiguousarray(n)), _p(phi))
+        return phi
+
+    def field(self, phi):
+        E = np.zeros((2,) + self.grid_shape())
+        self._L.orc2d_field(self.ref, _p(np.ascontiguousarray(phi)), _p(E))
+        return E
+
+    def kick(self, state, E, kick):
+        _check(self._L.orc2d_kick(self.ref, _p(state), _p(np.ascontiguousarray(E)), kick), "2d kick")
+
+    def moments(self, state):
+        m = np.zeros((2, 5, self.C))
+        self._L.orc2d_moments(self.ref, _p(np.ascontiguousarray(state)), _p(m))
+        return m
+
+    def run(self, state, n_kicks, kick0=0):
+        kpp = sum(self.cfg.kicks)
+        hist = np.zeros((n_kicks // max(kpp, 1) + 2, 2, 5, self.C))
+        r = _check(self._L.orc2d_run(self.ref, _p(state), kick0, n_kicks, _p(hist)), "2d run")
+        return hist[:r]
+
+    def emittance(self, mom):
+        """Dual rms emittances [2][C] from moments [2][5][C] (the 3D oracle's formula, planes x, y)."""
+        m3 = np.zeros((3, 5, self.C))
+        m3[:2] = mom
+        m3[2, 2, 0] = m3[2, 4, 0] = 1.0
+        o = Oracle(P=self.cfg.P, nx=8, ny=8, nz=8, N=1)
+        return o.emittance(m3)[:2]

@@ -1024,3 +1024,298 @@ void orc_track(int P, const orc_element* el, int n, int64_t n_repeat, int64_t N,
     }
     free(maps);
 }
+
+/* ------------------------------------------------------------------ */
+/* 2D PIC in a rectangular conducting pipe (Sec. 4): bilinear deposit, */
+/* sine-transform Poisson solve, central-difference field, the kick of */
+/* H2 = K phi / 2, and the same quadrupole maps in x and y.            */
+/* ------------------------------------------------------------------ */
+
+/* derived 2D constants: gamma0, beta0, p0, B rho, the paper's perveance K,
+   the kick factor 2 pi K (phi normalised to unit charge, see orc2d_solve) */
+static void consts2d(const orc2d_config* c, double* gamma0, double* beta0, double* p0, double* brho, double* K) {
+    const double mass_kg = c->mass_eV * Q_E / (C_LIGHT * C_LIGHT);
+    const double q = c->charge_e * Q_E;
+    *gamma0 = 1.0 + c->kinetic_eV / c->mass_eV;
+    *beta0 = sqrt(1.0 - 1.0 / (*gamma0 * *gamma0));
+    *p0 = *gamma0 * *beta0 * mass_kg * C_LIGHT;
+    *brho = *p0 / q;
+    const double v0 = *beta0 * C_LIGHT;
+    *K = q * c->current_A / (2.0 * PI * EPS0 * *p0 * v0 * v0 * *gamma0 * *gamma0);
+}
+
+void orc2d_constants(const orc2d_config* c, double out[5]) {
+    consts2d(c, &out[0], &out[1], &out[2], &out[3], &out[4]);
+}
+
+/* the FODO config viewed as a 3D config for the shared map code (half maps only) */
+static orc_config as3d(const orc2d_config* c) {
+    orc_config k;
+    memset(&k, 0, sizeof(k));
+    k.P = c->P;
+    k.kinetic_eV = c->kinetic_eV;
+    k.mass_eV = c->mass_eV;
+    k.charge_e = c->charge_e;
+    for (int e = 0; e < 5; ++e) { k.L[e] = c->L[e]; k.kicks[e] = c->kicks[e]; }
+    k.g[0] = c->g[0];
+    k.g[1] = c->g[1];
+    for (int j = 0; j < 7; ++j) k.lat_slot[j] = c->lat_slot[j];
+    k.charge_slot = -1;
+    return k;
+}
+
+/* bilinear weights of particle i: pipe coordinates u = (x + a/2) / hx etc.
+   (the beam axis is the pipe centre); cells [0, n-1]; a particle closer
+   than one cell to a wall is outside the stencil range */
+static int bilinear(int C, const double* state, int64_t N, int64_t i, const orc2d_config* c, int idx[2],
+                    double w[2][2][ORC_MAXC]) {
+    const double hx = c->a / c->nx, hy = c->b / c->ny;
+    const double h[2] = {hx, hy}, off[2] = {0.5 * c->a, 0.5 * c->b};
+    const int n[2] = {c->nx, c->ny};
+    for (int d = 0; d < 2; ++d) {
+        const double* x = state + ((int64_t)(2 * d) * N + i) * C;
+        const double u = (x[0] + off[d]) / h[d];
+        if (!isfinite(u)) return -5;
+        const double fl = floor(u);
+        if (!(fl >= 1.0 && fl <= (double)(n[d] - 2))) return -6;
+        idx[d] = (int)fl;
+        const double f = u - fl;
+        /* w1 = f, w0 = 1 - f; d f / d p_k = x_k / h */
+        w[d][0][0] = 1.0 - f;
+        w[d][1][0] = f;
+        for (int k = 1; k < C; ++k) {
+            w[d][1][k] = x[k] / h[d];
+            w[d][0][k] = -x[k] / h[d];
+        }
+    }
+    return 0;
+}
+
+int orc2d_deposit(const orc2d_config* c, const double* state, double* n) {
+    const int C = c->P + 1;
+    const int64_t N = c->N;
+    const int nx1 = c->nx + 1, ny1 = c->ny + 1;
+    const int64_t nn = (int64_t)nx1 * ny1;
+    const double hx = c->a / c->nx, hy = c->b / c->ny;
+    memset(n, 0, sizeof(double) * C * nn);
+    /* each macroparticle carries 1/N of the normalised density over a cell area */
+    const double q = 1.0 / ((double)N * hx * hy);
+    for (int64_t i = 0; i < N; ++i) {
+        int idx[2];
+        double w[2][2][ORC_MAXC];
+        const int st = bilinear(C, state, N, i, c, idx, w);
+        if (st) return st;
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                dual W;
+                d_mul(C, w[0][a], w[1][b], W);
+                const int64_t node = (int64_t)(idx[1] + b) * nx1 + (idx[0] + a);
+                for (int k = 0; k < C; ++k) n[(int64_t)k * nn + node] += q * W[k];
+            }
+    }
+    return 0;
+}
+
+/* Eqs. for rho^lm and phi^lm: with nodes x_i = i hx (i = 0..nx, walls at 0
+   and nx), rho^lm = (4 / (nx ny)) sum_ij rho_ij sin(l pi i / nx) sin(m pi j / ny)
+   (the quadrature of the paper's integral on the grid), phi^lm = rho^lm /
+   gamma_lm^2 with gamma_lm^2 = (l pi / a)^2 + (m pi / b)^2, and phi_ij the
+   sine sums back; l, m = 1 .. n - 1. Here the Poisson equation is
+   lap phi = -rho for the normalised density (eps0 and the current go into the
+   kick factor 2 pi K). Separable: 1D sine sums along x, then along y. */
+void orc2d_solve(const orc2d_config* c, const double* rho, double* phi) {
+    const int C = c->P + 1, nx = c->nx, ny = c->ny;
+    const int nx1 = nx + 1, ny1 = ny + 1;
+    const int64_t nn = (int64_t)nx1 * ny1;
+    double* t = (double*)malloc(sizeof(double) * nn);
+    double* u = (double*)malloc(sizeof(double) * nn);
+    for (int k = 0; k < C; ++k) {
+        const double* r = rho + (int64_t)k * nn;
+        double* p = phi + (int64_t)k * nn;
+        /* forward along x: t[j][l] = sum_i r[j][i] sin(l pi i / nx) */
+        for (int j = 0; j < ny1; ++j)
+            for (int l = 0; l < nx1; ++l) {
+                double s = 0.0;
+                if (l >= 1 && l <= nx - 1)
+                    for (int i = 1; i <= nx - 1; ++i) s += r[(int64_t)j * nx1 + i] * sin(PI * l * i / nx);
+                t[(int64_t)j * nx1 + l] = s;
+            }
+        /* forward along y and the division: u[m][l] = (4/(nx ny)) sum_j t[j][l] sin(m pi j / ny) / gamma^2 */
+        for (int m = 0; m < ny1; ++m)
+            for (int l = 0; l < nx1; ++l) {
+                double s = 0.0;
+                if (m >= 1 && m <= ny - 1 && l >= 1 && l <= nx - 1) {
+                    for (int j = 1; j <= ny - 1; ++j) s += t[(int64_t)j * nx1 + l] * sin(PI * m * j / ny);
+                    const double al = PI * l / c->a, be = PI * m / c->b;
+                    s = 4.0 / ((double)nx * ny) * s / (al * al + be * be);
+                }
+                u[(int64_t)m * nx1 + l] = s;
+            }
+        /* back along y: t[j][l] = sum_m u[m][l] sin(m pi j / ny) */
+        for (int j = 0; j < ny1; ++j)
+            for (int l = 0; l < nx1; ++l) {
+                double s = 0.0;
+                for (int m = 1; m <= ny - 1; ++m) s += u[(int64_t)m * nx1 + l] * sin(PI * m * j / ny);
+                t[(int64_t)j * nx1 + l] = s;
+            }
+        /* back along x: p[j][i] = sum_l t[j][l] sin(l pi i / nx) */
+        for (int j = 0; j < ny1; ++j)
+            for (int i = 0; i < nx1; ++i) {
+                double s = 0.0;
+                for (int l = 1; l <= nx - 1; ++l) s += t[(int64_t)j * nx1 + l] * sin(PI * l * i / nx);
+                p[(int64_t)j * nx1 + i] = s;
+            }
+    }
+    free(t);
+    free(u);
+}
+
+/* E = -grad phi by central differences at interior nodes; zero on the walls */
+void orc2d_field(const orc2d_config* c, const double* phi, double* E /*[2][C][ny+1][nx+1]*/) {
+    const int C = c->P + 1, nx1 = c->nx + 1, ny1 = c->ny + 1;
+    const int64_t nn = (int64_t)nx1 * ny1;
+    const double hx = c->a / c->nx, hy = c->b / c->ny;
+    memset(E, 0, sizeof(double) * 2 * C * nn);
+    for (int k = 0; k < C; ++k)
+        for (int j = 1; j < ny1 - 1; ++j)
+            for (int i = 1; i < nx1 - 1; ++i) {
+                const double* p = phi + (int64_t)k * nn;
+                const int64_t q = (int64_t)j * nx1 + i;
+                E[((int64_t)0 * C + k) * nn + q] = -(p[q + 1] - p[q - 1]) / (2.0 * hx);
+                E[((int64_t)1 * C + k) * nn + q] = -(p[q + nx1] - p[q - nx1]) / (2.0 * hy);
+            }
+}
+
+/* M2(tau) of Sec. 4: p -= d H2 / d r tau with H2 = K phi / 2 and phi in the
+   paper's normalisation (4 pi times the unit-charge potential of
+   orc2d_solve): p += 2 pi K E tau, E = -grad phi (dual gather of the
+   bilinear weights times the dual field) */
+int orc2d_kick(const orc2d_config* c, double* state, const double* E, int64_t kick) {
+    const int C = c->P + 1;
+    const int64_t N = c->N;
+    const int nx1 = c->nx + 1;
+    const int64_t nn = (int64_t)nx1 * (c->ny + 1);
+    double g0, b0, p0, brho, K;
+    consts2d(c, &g0, &b0, &p0, &brho, &K);
+    orc_config k3 = as3d(c);
+    dual tau, two_pi_K, KI, coef;
+    /* D tau of the kick's element, and the dual current (slot current_slot):
+       K is linear in I, K = I (q / (2 pi eps0 p0 v0^2 gamma0^2)) */
+    int e = element_of_kick(&k3, kick);
+    dual_tau(&k3, e, tau);
+    d_var(C, c->current_A, c->current_slot, KI);
+    const double v0 = b0 * C_LIGHT;
+    const double K_per_A = c->charge_e * Q_E / (2.0 * PI * EPS0 * p0 * v0 * v0 * g0 * g0);
+    (void)K;
+    d_cmul(C, 2.0 * PI * K_per_A, KI, two_pi_K);
+    d_mul(C, two_pi_K, tau, coef);
+    for (int64_t i = 0; i < N; ++i) {
+        int idx[2];
+        double w[2][2][ORC_MAXC];
+        const int st = bilinear(C, state, N, i, c, idx, w);
+        if (st) return st;
+        for (int d = 0; d < 2; ++d) {
+            dual Ep, W, t;
+            d_const(C, 0.0, Ep);
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    d_mul(C, w[0][a], w[1][b], W);
+                    const int64_t node = (int64_t)(idx[1] + b) * nx1 + (idx[0] + a);
+                    dual En;
+                    for (int k = 0; k < C; ++k) En[k] = E[((int64_t)d * C + k) * nn + node];
+                    d_mul(C, W, En, t);
+                    d_add(C, Ep, t, Ep);
+                }
+            double* p = state + ((int64_t)(2 * d + 1) * N + i) * C;
+            d_mul(C, coef, Ep, t);
+            d_add(C, p, t, p);
+        }
+    }
+    return 0;
+}
+
+void orc2d_moments(const orc2d_config* c, const double* state, double* mom /*[2][5][C]*/) {
+    orc_config k3 = as3d(c);
+    k3.N = c->N;
+    /* the 3D moment code over the first two planes (x, px, y, py) */
+    const int C = c->P + 1;
+    double* s6 = (double*)calloc((size_t)6 * c->N * C, sizeof(double));
+    memcpy(s6, state, sizeof(double) * 4 * c->N * C);
+    double m3[3 * 5 * ORC_MAXC];
+    orc_moments(&k3, s6, m3);
+    memcpy(mom, m3, sizeof(double) * 2 * 5 * C);
+    free(s6);
+}
+
+int orc2d_run(const orc2d_config* c, double* state, int64_t kick0, int n_kicks, double* mom_hist) {
+    const int C = c->P + 1;
+    const int64_t N = c->N;
+    const int64_t nn = (int64_t)(c->nx + 1) * (c->ny + 1);
+    orc_config k3 = as3d(c);
+    k3.N = N;
+    const int kpp = kicks_per_period(&k3);
+    double* rho = (double*)malloc(sizeof(double) * C * nn);
+    double* phi = (double*)malloc(sizeof(double) * C * nn);
+    double* E = (double*)malloc(sizeof(double) * 2 * C * nn);
+    int st = 0, rec = 0;
+    for (int s = 0; s < n_kicks && !st; ++s) {
+        const int64_t kick = kick0 + s;
+        double m[3 * 4 * ORC_MAXC];
+        orc_half_map(&k3, kick, m);
+        /* M1(tau/2) on the two transverse planes */
+        for (int64_t i = 0; i < N; ++i)
+            for (int pl = 0; pl < 2; ++pl) {
+                double* u = state + ((int64_t)(2 * pl) * N + i) * C;
+                double* p = state + ((int64_t)(2 * pl + 1) * N + i) * C;
+                dual a, b, un, pn;
+                d_mul(C, m + (pl * 4 + 0) * C, u, a); d_mul(C, m + (pl * 4 + 1) * C, p, b); d_add(C, a, b, un);
+                d_mul(C, m + (pl * 4 + 2) * C, u, a); d_mul(C, m + (pl * 4 + 3) * C, p, b); d_add(C, a, b, pn);
+                d_copy(C, un, u);
+                d_copy(C, pn, p);
+            }
+        st = orc2d_deposit(c, state, rho);
+        if (st) break;
+        orc2d_solve(c, rho, phi);
+        orc2d_field(c, phi, E);
+        st = orc2d_kick(c, state, E, kick);
+        if (st) break;
+        for (int64_t i = 0; i < N; ++i)
+            for (int pl = 0; pl < 2; ++pl) {
+                double* u = state + ((int64_t)(2 * pl) * N + i) * C;
+                double* p = state + ((int64_t)(2 * pl + 1) * N + i) * C;
+                dual a, b, un, pn;
+                d_mul(C, m + (pl * 4 + 0) * C, u, a); d_mul(C, m + (pl * 4 + 1) * C, p, b); d_add(C, a, b, un);
+                d_mul(C, m + (pl * 4 + 2) * C, u, a); d_mul(C, m + (pl * 4 + 3) * C, p, b); d_add(C, a, b, pn);
+                d_copy(C, un, u);
+                d_copy(C, pn, p);
+            }
+        if (((kick + 1) % kpp == 0) || s == n_kicks - 1) {
+            if (mom_hist) orc2d_moments(c, state, mom_hist + (int64_t)rec * 10 * C);
+            ++rec;
+        }
+    }
+    free(rho); free(phi); free(E);
+    return st ? st : rec;
+}
+
+/* initial distribution: per plane u = sqrt(eps beta) n1, p = sqrt(eps/beta)(n2 - alpha n1), mean removed */
+int orc2d_beam_init(const orc2d_config* c, const double* normals /*[4][N]*/, double* state) {
+    const int C = c->P + 1;
+    const int64_t N = c->N;
+    double g0, b0, p0, brho, K;
+    consts2d(c, &g0, &b0, &p0, &brho, &K);
+    memset(state, 0, sizeof(double) * 4 * N * C);
+    for (int pl = 0; pl < 2; ++pl) {
+        const double eps = c->eps_n[pl] / (b0 * g0), beta = c->beta[pl], alpha = c->alpha[pl];
+        double m1 = 0.0, m2 = 0.0;
+        for (int64_t i = 0; i < N; ++i) { m1 += normals[(2 * pl) * N + i]; m2 += normals[(2 * pl + 1) * N + i]; }
+        m1 /= (double)N;
+        m2 /= (double)N;
+        for (int64_t i = 0; i < N; ++i) {
+            const double n1 = normals[(2 * pl) * N + i] - m1, n2 = normals[(2 * pl + 1) * N + i] - m2;
+            state[((int64_t)(2 * pl) * N + i) * C] = sqrt(eps * beta) * n1;
+            state[((int64_t)(2 * pl + 1) * N + i) * C] = sqrt(eps / beta) * (n2 - alpha * n1);
+        }
+    }
+    return 0;
+}

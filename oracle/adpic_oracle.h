@@ -125,4 +125,32 @@ int orc_periodic_twiss(int P, const orc_element* el, int n, double* out);
    element by element: out[N][4][C] */
 void orc_track(int P, const orc_element* el, int n, int64_t n_repeat, int64_t N, const double* x0, double* out);
 
+/* ---- 2D PIC in a rectangular conducting pipe (Sec. 4) ---- */
+
+typedef struct {
+    int32_t P;            /* derivative slots; C = P + 1 */
+    int32_t nx, ny;       /* cells per dimension: nodes 0..nx, 0..ny, walls at 0 and n */
+    int32_t current_slot; /* slot of the beam current as an AD variable, -1 = constant */
+    int64_t N;            /* macroparticles */
+    double a, b;          /* pipe widths (m); the beam axis is the pipe centre */
+    double kinetic_eV, mass_eV, charge_e, current_A;
+    double eps_n[2], alpha[2], beta[2];   /* per plane x, y (constant Twiss) */
+    double L[5], g[2];
+    int32_t kicks[5];
+    int32_t lat_slot[7];
+} orc2d_config;
+
+/* gamma0, beta0, p0 (kg m/s), B rho (T m), K = q I / (2 pi eps0 p0 v0^2 gamma0^2) */
+void orc2d_constants(const orc2d_config* c, double out[5]);
+int orc2d_beam_init(const orc2d_config* c, const double* normals /*[4][N]*/, double* state /*[4][N][C]*/);
+/* normalised density (integral 1 over the pipe) on the nodes: n[C][ny+1][nx+1] */
+int orc2d_deposit(const orc2d_config* c, const double* state, double* n);
+/* lap phi = -n with phi = 0 on the walls by the sine series of Sec. 4 */
+void orc2d_solve(const orc2d_config* c, const double* n, double* phi);
+void orc2d_field(const orc2d_config* c, const double* phi, double* E /*[2][C][ny+1][nx+1]*/);
+int orc2d_kick(const orc2d_config* c, double* state, const double* E, int64_t kick);
+void orc2d_moments(const orc2d_config* c, const double* state, double* mom /*[2][5][C]*/);
+/* split steps; records [r][2][5][C] at every period end and after the last kick */
+int orc2d_run(const orc2d_config* c, double* state, int64_t kick0, int n_kicks, double* mom_hist);
+
 #endif
