@@ -242,6 +242,20 @@ int ad_pic_batch_set_mode(ad_pic_batch* b, int mode);
 /* Mode in use and the tuner's per-kick times ms[3] for modes 1..3 (ms; -1 =
    not possible on this device, 0 = not tuned). */
 int ad_pic_batch_tuning(const ad_pic_batch* b, int* mode, double* ms);
+/* Tile shapes of the batched jobs whose work split is free: tiles[4] =
+   (virtual blocks per instance of the moment pass, of the channel maxima, of
+   the charge-grid clear, 256-thread field blocks per field virtual block).
+   The autotuner (mode 0) picks them after the execution mode by a coordinate
+   search, each shape in turn over (4, 8, 16, 32), (2, 4, 8, 16), (4, 8, 16,
+   32), (2, 4, 8, 16) with the others held, timing one kick of the real batch
+   per choice, and caches them with the mode per batch composition.
+   ad_pic_batch_set_tiles fixes them (NULL hands them back to the tuner;
+   ranges 1..1024, 1..64, 1..64 and one of 2, 4, 8, 16, else
+   AD_PIC_ERR_INVALID_ARG) and makes the next run tune the mode again.
+   ad_pic_batch_tiles reads the shapes in use and the tuned kick time in ms
+   (0 if not tuned). */
+int ad_pic_batch_set_tiles(ad_pic_batch* b, const int* tiles);
+int ad_pic_batch_tiles(const ad_pic_batch* b, int* tiles, double* ms);
 int ad_pic_batch_set_stream(ad_pic_batch* b, void* stream);
 void ad_pic_batch_destroy(ad_pic_batch* b);
 
@@ -273,6 +287,20 @@ int ad_pic_mlp_loss_grad(ad_pic_mlp* m, const float* x, const float* t, const fl
    *loss is the loss before the step. */
 int ad_pic_mlp_adam_step(ad_pic_mlp* m, const float* x, const float* t, const float* dt, int B, float lambda, float lr,
                          double* loss);
+/* Device-resident training. ad_pic_mlp_set_dataset uploads n samples (x
+   [n][n_in], t [n][n_out], dt [n][n_out][n_in], host, already in the order
+   the mini-batches should take them) once. ad_pic_mlp_train then runs
+   `steps` Adam steps of B samples each (consecutive samples of the set,
+   wrapping around) with the Sobolev loss of weight lambda and the learning
+   rate lr0 (lr1/lr0)^(s/(steps-1)) at step s: every step is one replay of a
+   CUDA graph (batch gather, forward and tangent GEMMs, loss, backward, Adam)
+   with its counters on the device, so no host transfer or synchronisation
+   happens between steps. *loss receives the last step's loss (before its
+   update), *ms the CUDA-event time of the steps (either may be NULL). Adam's
+   step count carries over from ad_pic_mlp_adam_step and earlier runs.
+   AD_PIC_ERR_STATE without a dataset. */
+int ad_pic_mlp_set_dataset(ad_pic_mlp* m, const float* x, const float* t, const float* dt, int n);
+int ad_pic_mlp_train(ad_pic_mlp* m, int steps, int B, float lambda, float lr0, float lr1, double* loss, double* ms);
 void ad_pic_mlp_destroy(ad_pic_mlp* m);
 
 /* Allocation-free dual moments of a caller-owned device state (the paper has

@@ -104,6 +104,8 @@ def lib():
             "ad_pic_batch_set_mode": (ct.c_int, [vp, ct.c_int]),
             "ad_pic_batch_tuning": (ct.c_int, [vp, ct.POINTER(ct.c_int), dp]),
             "ad_pic_batch_set_stream": (ct.c_int, [vp, vp]),
+            "ad_pic_batch_set_tiles": (ct.c_int, [vp, ct.POINTER(ct.c_int)]),
+            "ad_pic_batch_tiles": (ct.c_int, [vp, ct.POINTER(ct.c_int), dp]),
             "ad_pic_batch_destroy": (None, [vp]),
             "ad_pic_mlp_create": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(vp)]),
             "ad_pic_mlp_num_params": (ct.c_int, [vp, ct.POINTER(ct.c_int64)]),
@@ -117,6 +119,9 @@ def lib():
             "ad_pic_mlp_adam_step": (ct.c_int, [vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float),
                                                 ct.POINTER(ct.c_float), ct.c_int, ct.c_float, ct.c_float, dp]),
             "ad_pic_mlp_destroy": (None, [vp]),
+            "ad_pic_mlp_set_dataset": (ct.c_int, [vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float),
+                                                  ct.POINTER(ct.c_float), ct.c_int]),
+            "ad_pic_mlp_train": (ct.c_int, [vp, ct.c_int, ct.c_int, ct.c_float, ct.c_float, ct.c_float, dp, dp]),
             "ad_pic_destroy": (None, [vp]),
             "ad_pic_strerror": (ct.c_char_p, [ct.c_int]),
         }
@@ -374,6 +379,18 @@ def ad_pic_batch_tuning(b):
     return m.value, ms
 
 
+def ad_pic_batch_set_tiles(b, tiles=None):
+    t = None if tiles is None else (ct.c_int * 4)(*[int(v) for v in tiles])
+    _ck("ad_pic_batch_set_tiles", lib().ad_pic_batch_set_tiles(b, t))
+
+
+def ad_pic_batch_tiles(b):
+    t = (ct.c_int * 4)()
+    ms = ct.c_double()
+    _ck("ad_pic_batch_tiles", lib().ad_pic_batch_tiles(b, t, ct.byref(ms)))
+    return list(t), ms.value
+
+
 def ad_pic_batch_set_stream(b, stream_ptr):
     _ck("ad_pic_batch_set_stream", lib().ad_pic_batch_set_stream(b, ct.c_void_p(stream_ptr) if stream_ptr else None))
 
@@ -436,6 +453,20 @@ def ad_pic_mlp_adam_step(m, x, t, dt, lam, lr):
     _ck("ad_pic_mlp_adam_step", lib().ad_pic_mlp_adam_step(m, _pf(x), _pf(t), _pf(dt), x.shape[0], float(lam),
                                                            float(lr), ct.byref(loss)))
     return loss.value
+
+
+def ad_pic_mlp_set_dataset(m, x, t, dt):
+    x, t, dt = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, t, dt))
+    _ck("ad_pic_mlp_set_dataset", lib().ad_pic_mlp_set_dataset(m, _pf(x), _pf(t), _pf(dt), x.shape[0]))
+
+
+def ad_pic_mlp_train(m, steps, B, lam, lr0, lr1):
+    """Device-resident Adam steps; returns (last loss, CUDA-event ms of the steps)."""
+    loss = ct.c_double()
+    ms = ct.c_double()
+    _ck("ad_pic_mlp_train", lib().ad_pic_mlp_train(m, int(steps), int(B), float(lam), float(lr0), float(lr1),
+                                                   ct.byref(loss), ct.byref(ms)))
+    return loss.value, ms.value
 
 
 def ad_pic_mlp_destroy(m):
@@ -585,3 +616,9 @@ class Batch:
 
     def tuning(self):
         return ad_pic_batch_tuning(self.b)
+
+    def set_tiles(self, tiles=None):
+        ad_pic_batch_set_tiles(self.b, tiles)
+
+    def tiles(self):
+        return ad_pic_batch_tiles(self.b)

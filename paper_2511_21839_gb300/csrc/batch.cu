@@ -35,9 +35,17 @@ using namespace adpic;
 namespace {
 
 constexpr int kCP = 8;                  // P = 7
-constexpr int kBoundBlocks = 8;         // boundary (moment) blocks per instance
-constexpr int kChmaxBlocks = 4;
-constexpr int kClearBlocks = 8;
+
+// Tile shapes of the jobs whose work split is free (the autotuner picks them):
+// virtual blocks per instance of the moment pass, of the channel maxima and of
+// the charge-grid clear, and 256-thread field blocks per virtual block.
+struct Tiles {
+    int bound_blocks = 8;
+    int chmax_blocks = 4;
+    int clear_blocks = 8;
+    int field_per = 8;
+};
+constexpr int kTileChoices[4][4] = {{4, 8, 16, 32}, {2, 4, 8, 16}, {4, 8, 16, 32}, {2, 4, 8, 16}};
 
 template <typename T>
 struct Inst {
@@ -65,6 +73,7 @@ struct Inst {
     const MapCoef<T, kCP>* half;
     const MapCoef<T, kCP>* comp;
     const KickCoef<T, kCP>* kick;
+    Tiles tiles;
 };
 
 enum Job {
@@ -125,7 +134,7 @@ __device__ __forceinline__ SortBuf sort_of(const Inst<T>& in, int from) {
 JOB(job_geom) { geom_kernel_body<T>(in.mm, in.n, in.n, in.n, in.gamma0, in.geom, in.chmax, kCP, 0, 0, 0, 1); }
 JOB(job_clear) {
     const int64_t tot = (int64_t)in.n * in.n * in.n * kCP;
-    for (int64_t t = (int64_t)lb * blockDim.x + threadIdx.x; t < tot; t += (int64_t)kClearBlocks * blockDim.x)
+    for (int64_t t = (int64_t)lb * blockDim.x + threadIdx.x; t < tot; t += (int64_t)in.tiles.clear_blocks * blockDim.x)
         in.rho[t] = (T)0;
 }
 JOB(job_deposit) {
@@ -135,7 +144,9 @@ JOB(job_deposit) {
 }
 JOB(job_corner) { green_corner_kernel_body(in.geom, in.n, in.n, in.n, in.corner, lb, 0, 0, 0); }
 JOB(job_scansum) { scan_sum_kernel_body(in.cellcount, in.n * in.n * in.n, in.bsum, lb, 0, 0, 0); }
-JOB(job_chmax) { chmax_kernel_body<T>(in.rho, (int64_t)in.n * in.n * in.n, kCP, in.chmax, lb, 0, 0, kChmaxBlocks); }
+JOB(job_chmax) {
+    chmax_kernel_body<T>(in.rho, (int64_t)in.n * in.n * in.n, kCP, in.chmax, lb, 0, 0, in.tiles.chmax_blocks);
+}
 JOB(job_cell) { green_cell_kernel_body<T>(in.geom, in.n, in.n, in.n, in.corner, in.G, lb, 0, 0, 0, 1); }
 JOB(job_scantop) {
     scan_top_kernel_body(in.bsum, (in.n * in.n * in.n + kScanChunk - 1) / kScanChunk, 0, 0, 0, 1);
@@ -155,8 +166,14 @@ __device__ __noinline__ void job_fft(int job, const Inst<T>& in, int lb) {
         default: fftx_inv_t_kernel_body<T, M>(in.X1, in.phi, d, in.tw, in.chmax, in.yt, lb % tiles, lb / tiles); break;
     }
 }
-constexpr int kFieldPer = 8;            // 256-thread field blocks per virtual block
-JOB(job_field) { field_multi_body<T, kFieldPer>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb); }
+JOB(job_field) {
+    switch (in.tiles.field_per) {        // 256-thread field blocks per virtual block
+        case 2: field_multi_body<T, 2>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb); break;
+        case 4: field_multi_body<T, 4>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb); break;
+        case 16: field_multi_body<T, 16>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb); break;
+        default: field_multi_body<T, 8>(in.phi, in.geom, in.n, in.n, in.n, kCP, in.E, lb); break;
+    }
+}
 JOB(job_push_track) {
     const int slot = (int)(st.g % st.kpp);
     push_kernel_body<T, kCP, kCP, true>(in.state[st.from], in.state[1 - st.from], in.N, in.E, in.geom, in.n, in.n,
@@ -173,16 +190,16 @@ JOB(job_bound) {
     const MapCoef<T, kCP>& A = in.half[(st.g + 1) % st.kpp];
     if (st.apply && st.mom)
         boundary_kernel_body<T, kCP, kCP, true, true>(in.state[st.from], in.N, A, in.partial, in.mm, lb, 0, 0,
-                                                      kBoundBlocks);
+                                                      in.tiles.bound_blocks);
     else if (st.mom)
         boundary_kernel_body<T, kCP, kCP, true, false>(in.state[st.from], in.N, A, in.partial, in.mm, lb, 0, 0,
-                                                       kBoundBlocks);
+                                                       in.tiles.bound_blocks);
     else if (st.apply)
         boundary_kernel_body<T, kCP, kCP, false, true>(in.state[st.from], in.N, A, in.partial, in.mm, lb, 0, 0,
-                                                       kBoundBlocks);
+                                                       in.tiles.bound_blocks);
 }
 JOB(job_reduce) {
-    moments_reduce_kernel_body(in.partial, kBoundBlocks, kCP, in.N, in.records + (int64_t)st.rec * 15 * kCP, lb, 0, 0,
+    moments_reduce_kernel_body(in.partial, in.tiles.bound_blocks, kCP, in.N, in.records + (int64_t)st.rec * 15 * kCP, lb, 0, 0,
                                0);
 }
 #undef JOB
@@ -433,6 +450,9 @@ struct ad_pic_batch {
     int mode = 0;                             // 0 auto, 1/2 persistent (blocks per SM), 3 phased
     int tuned_mode = 0;
     double tune_ms[4] = {0, 0, 0, 0};
+    Tiles tiles;                              // tile shapes in use
+    bool tiles_fixed = false;                 // set by the caller: the tuner keeps them
+    double tiles_ms = 0;                      // kick time with the tuned tiles (0: not tuned)
     bool use_graphs = true;
     std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
 };
@@ -496,11 +516,11 @@ int build_tables(ad_pic_batch* b) {
         int* bl = blocks.data();
         auto set = [&](int j, int64_t v) { bl[(size_t)j * ni + i] = (int)v; };
         set(J_GEOM, 1);
-        set(J_CLEAR, kClearBlocks);
+        set(J_CLEAR, b->tiles.clear_blocks);
         set(J_DEPOSIT, ceil_div(h->N, 256));
         set(J_CORNER, ceil_div((int64_t)(n + 2) * (n + 2) * (n + 2), 256));
         set(J_SCANSUM, scan_blocks((int)nodes));
-        set(J_CHMAX, kChmaxBlocks);
+        set(J_CHMAX, b->tiles.chmax_blocks);
         set(J_CELL, ceil_div((int64_t)(n + 1) * (n + 1) * (n + 1), 256));
         set(J_SCANTOP, 1);
         set(J_DCTX, ceil_div((int64_t)(n + 1) * (n + 1), kDctLines));
@@ -511,9 +531,9 @@ int build_tables(ad_pic_batch* b) {
         set(J_FFTX, (int64_t)(n / yt) * n);
         set(J_FFTYZ, (int64_t)M * npair);
         set(J_FFTXI, (int64_t)(n / yt) * n);
-        set(J_FIELD, ceil_div(nodes * kCP, 256 * kFieldPer));
+        set(J_FIELD, ceil_div(nodes * kCP, 256 * b->tiles.field_per));
         set(J_PUSH, ceil_div(h->N, 256));
-        set(J_BOUND, kBoundBlocks);
+        set(J_BOUND, b->tiles.bound_blocks);
         set(J_REDUCE, 15 * kCP);
         smem = std::max(smem, lane_smem<T>(n));
     }
@@ -534,7 +554,11 @@ int build_tables(ad_pic_batch* b) {
         for (int q = 0; q < 3; ++q)
             if (h_phase_jobs[ph][q] >= 0) b->phase_blocks[ph] += cum[(size_t)h_phase_jobs[ph][q] * (ni + 1) + ni];
     b->smem = smem;
-    if (cudaMalloc(&b->cum_dev, sizeof(int) * cum.size()) != cudaSuccess) { cudaGetLastError(); return AD_PIC_ERR_OOM; }
+    if (!b->cum_dev && cudaMalloc(&b->cum_dev, sizeof(int) * cum.size()) != cudaSuccess) {
+        cudaGetLastError();
+        b->cum_dev = nullptr;
+        return AD_PIC_ERR_OOM;
+    }
     if (cudaMemcpy(b->cum_dev, cum.data(), sizeof(int) * cum.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return AD_PIC_ERR_CUDA;
     const int mx = 200 * 1024;
@@ -620,6 +644,7 @@ int upload_instances(ad_pic_batch* b, int nrec) {
         in.half = (const MC*)dbase;
         in.comp = (const MC*)(dbase + sizeof(MC) * kpp);
         in.kick = (const KC*)(dbase + 2 * sizeof(MC) * kpp);
+        in.tiles = b->tiles;
     }
     if (!b->inst_dev && cudaMalloc(&b->inst_dev, sizeof(Inst<T>) * ni) != cudaSuccess) {
         cudaGetLastError();
@@ -676,9 +701,11 @@ int enqueue(ad_pic_batch* b, int mode, const RunSpec& rs) {
     return launch_mode<T>(b, mode, rs);
 }
 
-// time one kick of the real batch in each mode on a snapshot of the particles; keep the fastest
+// time one kick of the real batch in each mode on a snapshot of the particles and
+// keep the fastest; then, in that mode, a coordinate search over the tile shapes
+// (each shape in turn over its choices, the others held), keeping the fastest
 template <typename T>
-int autotune_measure(ad_pic_batch* b, const RunSpec& base) {
+int autotune_measure(ad_pic_batch* b, const RunSpec& base, int nrec) {
     size_t need = 0;
     for (ad_pic* h : b->h) need += sizeof(T) * 6 * h->N * kCP;
     if (need > b->snapshot_bytes) {
@@ -708,11 +735,9 @@ int autotune_measure(ad_pic_batch* b, const RunSpec& base) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     copy(true);
-    float best = 1e30f;
-    int best_mode = 3;
-    for (int mode = 1; mode <= 3; ++mode) {
+    auto time_kick = [&](int mode, bool& ok) -> float {
         float ms = 0.f;
-        bool ok = true;
+        ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {       // the first repetition warms up
             cudaEventRecord(e0, b->stream);
             ok = enqueue<T>(b, mode, rs) == AD_PIC_OK;
@@ -722,17 +747,50 @@ int autotune_measure(ad_pic_batch* b, const RunSpec& base) {
             copy(false);
         }
         cudaGetLastError();
+        return ms;
+    };
+    float best = 1e30f;
+    int best_mode = 3;
+    for (int mode = 1; mode <= 3; ++mode) {
+        bool ok = true;
+        const float ms = time_kick(mode, ok);
         b->tune_ms[mode] = ok ? ms : -1.0;
         if (ok && ms < best) {
             best = ms;
             best_mode = mode;
         }
     }
+    b->tuned_mode = best_mode;
+    int rc = AD_PIC_OK;
+    if (!b->tiles_fixed) {
+        int* knob[4] = {&b->tiles.bound_blocks, &b->tiles.chmax_blocks, &b->tiles.clear_blocks, &b->tiles.field_per};
+        for (int j = 0; j < 4 && !rc; ++j) {
+            const int keep = *knob[j];
+            int best_v = keep;
+            for (int c = 0; c < 4 && !rc; ++c) {
+                const int v = kTileChoices[j][c];
+                if (v == keep) continue;
+                *knob[j] = v;
+                rc = build_tables<T>(b);
+                if (!rc) rc = upload_instances<T>(b, nrec);
+                if (rc) break;
+                bool ok = true;
+                const float ms = time_kick(best_mode, ok);
+                if (ok && ms < best) {
+                    best = ms;
+                    best_v = v;
+                }
+            }
+            *knob[j] = best_v;
+        }
+        if (!rc) rc = build_tables<T>(b);
+        if (!rc) rc = upload_instances<T>(b, nrec);
+        b->tiles_ms = best;
+    }
     cudaStreamSynchronize(b->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->tuned_mode = best_mode;
-    return AD_PIC_OK;
+    return rc;
 }
 
 // Tuned modes of earlier batches with the same composition (grid size and
@@ -741,6 +799,8 @@ int autotune_measure(ad_pic_batch* b, const RunSpec& base) {
 struct TuneEntry {
     int mode;
     double ms[4];
+    Tiles tiles;
+    double tiles_ms;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneEntry> g_tune_cache;
@@ -761,22 +821,32 @@ std::string tune_key(const ad_pic_batch* b) {
 }
 
 template <typename T>
-int autotune(ad_pic_batch* b, const RunSpec& base) {
-    const std::string key = tune_key(b);
+int autotune(ad_pic_batch* b, const RunSpec& base, int nrec) {
+    const std::string key = tune_key(b) + (b->tiles_fixed ? "|fixed" : "");
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             b->tuned_mode = it->second.mode;
             for (int m = 0; m < 4; ++m) b->tune_ms[m] = it->second.ms[m];
+            if (!b->tiles_fixed) {
+                b->tiles = it->second.tiles;
+                b->tiles_ms = it->second.tiles_ms;
+                int rc = build_tables<T>(b);
+                if (!rc) rc = upload_instances<T>(b, nrec);
+                return rc;
+            }
             return AD_PIC_OK;
         }
     }
-    const int st = autotune_measure<T>(b, base);
+    const int st = autotune_measure<T>(b, base, nrec);
+    if (st) return st;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     TuneEntry e;
     e.mode = b->tuned_mode;
     for (int m = 0; m < 4; ++m) e.ms[m] = b->tune_ms[m];
+    e.tiles = b->tiles;
+    e.tiles_ms = b->tiles_ms;
     g_tune_cache[key] = e;
     return st;
 }
@@ -807,7 +877,10 @@ int batch_run(ad_pic_batch* b, int n) {
     rs.from = h0->cur;
     int mode = b->mode;
     if (mode == 0) {
-        if (!b->tuned_mode && n > 0) autotune<T>(b, rs);
+        if (!b->tuned_mode && n > 0) {
+            st = autotune<T>(b, rs, std::max(nrec, 1));
+            if (st) return st;
+        }
         mode = b->tuned_mode ? b->tuned_mode : 3;
     }
     if (b->use_graphs) {
@@ -952,6 +1025,37 @@ int ad_pic_batch_tuning(const ad_pic_batch* b, int* mode, double* ms) {
     if (mode) *mode = b->mode ? b->mode : b->tuned_mode;
     if (ms)
         for (int m = 0; m < 3; ++m) ms[m] = b->tune_ms[m + 1];
+    return AD_PIC_OK;
+}
+
+int ad_pic_batch_set_tiles(ad_pic_batch* b, const int* tiles) {
+    if (!b) return AD_PIC_ERR_INVALID_ARG;
+    Tiles t;
+    if (tiles) {
+        if (tiles[0] < 1 || tiles[0] > 1024 || tiles[1] < 1 || tiles[1] > 64 || tiles[2] < 1 || tiles[2] > 64 ||
+            (tiles[3] != 2 && tiles[3] != 4 && tiles[3] != 8 && tiles[3] != 16))
+            return AD_PIC_ERR_INVALID_ARG;
+        t.bound_blocks = tiles[0];
+        t.chmax_blocks = tiles[1];
+        t.clear_blocks = tiles[2];
+        t.field_per = tiles[3];
+    }
+    b->tiles = t;
+    b->tiles_fixed = tiles != nullptr;
+    b->tuned_mode = 0;                        // tune again (the mode) on the next run
+    b->tiles_ms = 0;
+    batch_free_graphs(b);
+    const int st = b->prec == AD_PIC_FP32_MIXED ? build_tables<float>(b) : AD_PIC_ERR_UNSUPPORTED;
+    return st;
+}
+
+int ad_pic_batch_tiles(const ad_pic_batch* b, int* tiles, double* ms) {
+    if (!b || !tiles) return AD_PIC_ERR_INVALID_ARG;
+    tiles[0] = b->tiles.bound_blocks;
+    tiles[1] = b->tiles.chmax_blocks;
+    tiles[2] = b->tiles.clear_blocks;
+    tiles[3] = b->tiles.field_per;
+    if (ms) *ms = b->tiles_ms;
     return AD_PIC_OK;
 }
 

@@ -238,6 +238,57 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     pb[t] = __float2bfloat16(p[t]);
 }
 
+// Adam with the step counter on the device (graph-replayable): lr follows the
+// geometric schedule lr0 (lr1 / lr0)^(s / total) of the step s of the run;
+// thread 0 of the last block advances the counters after every thread has
+// read them (a grid-wide count of finished blocks)
+__global__ void adam_dev_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                                float* __restrict__ v, __nv_bfloat16* __restrict__ pb, int64_t n, float lr0, float lr1,
+                                int total, float b1, float b2, float eps, int64_t* __restrict__ ctr,
+                                unsigned* __restrict__ done) {
+    const int64_t step = ctr[0] + 1;               // Adam's step count (1-based)
+    const float frac = total > 1 ? (float)ctr[1] / (float)(total - 1) : 0.f;
+    const float lr = lr0 * powf(lr1 / lr0, frac);
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) {
+        const float gg = g[t];
+        const float mm = b1 * m[t] + (1.f - b1) * gg;
+        const float vv = b2 * v[t] + (1.f - b2) * gg * gg;
+        m[t] = mm;
+        v[t] = vv;
+        p[t] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        pb[t] = __float2bfloat16(p[t]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            ctr[0] += 1;
+            ctr[1] += 1;
+            ctr[2] += 1;
+            *done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// the mini-batch of the current step: B samples from the device-resident
+// training set, taken in the (shuffled-at-upload) order, wrapping around
+__global__ void gather_batch_kernel(const float* __restrict__ X, const float* __restrict__ T,
+                                    const float* __restrict__ DT, int n, int B, int n_in, int n_out,
+                                    const int64_t* __restrict__ ctr, float* __restrict__ x, float* __restrict__ t,
+                                    float* __restrict__ dt) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int per = n_in + n_out + n_out * n_in;
+    if (k >= (int64_t)B * per) return;
+    const int r = (int)(k / per), c = (int)(k % per);
+    const int64_t src = (ctr[2] * (int64_t)B + r) % n;
+    if (c < n_in) x[(int64_t)r * n_in + c] = X[src * n_in + c];
+    else if (c < n_in + n_out) t[(int64_t)r * n_out + (c - n_in)] = T[src * n_out + (c - n_in)];
+    else dt[(int64_t)r * n_out * n_in + (c - n_in - n_out)] = DT[src * n_out * n_in + (c - n_in - n_out)];
+}
+
 __global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n) b[t] = __float2bfloat16(a[t]);
@@ -265,6 +316,14 @@ struct ad_pic_mlp {
     int64_t step = 0;
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
+    // device-resident training set and the counters of ad_pic_mlp_train
+    float *dx = nullptr, *dtg = nullptr, *ddt = nullptr;
+    int n_data = 0, data_cap = 0;
+    int64_t* ctr = nullptr;                  // [0] Adam steps, [1] step in the current run, [2] batches drawn
+    unsigned* done = nullptr;
+    cudaGraphExec_t train_graph = nullptr;
+    int g_B = 0, g_total = 0;
+    float g_lam = 0.f, g_lr0 = 0.f, g_lr1 = 0.f;
 };
 
 namespace {
@@ -387,6 +446,8 @@ int ad_pic_mlp_create(int n_in, int width, int hidden, int n_out, int max_batch,
     st |= mlp_alloc(h, (void**)&h->t, sizeof(float) * max_batch * n_out);
     st |= mlp_alloc(h, (void**)&h->dt, sizeof(float) * max_batch * n_out * n_in);
     st |= mlp_alloc(h, (void**)&h->loss, sizeof(double));
+    st |= mlp_alloc(h, (void**)&h->ctr, sizeof(int64_t) * 3);
+    st |= mlp_alloc(h, (void**)&h->done, sizeof(unsigned));
     if (st) {
         ad_pic_mlp_destroy(h);
         return AD_PIC_ERR_OOM;
@@ -395,6 +456,8 @@ int ad_pic_mlp_create(int n_in, int width, int hidden, int n_out, int max_batch,
     cudaMemsetAsync(h->m, 0, sizeof(float) * h->n_params, h->stream);
     cudaMemsetAsync(h->v, 0, sizeof(float) * h->n_params, h->stream);
     cudaMemsetAsync(h->pb, 0, sizeof(__nv_bfloat16) * h->n_params, h->stream);
+    cudaMemsetAsync(h->ctr, 0, sizeof(int64_t) * 3, h->stream);
+    cudaMemsetAsync(h->done, 0, sizeof(unsigned), h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
         ad_pic_mlp_destroy(h);
         return AD_PIC_ERR_CUDA;
@@ -417,7 +480,35 @@ int ad_pic_mlp_set_params(ad_pic_mlp* h, const float* params) {
     to_bf16_kernel<<<nb(h->n_params), 256, 0, s>>>(h->p, h->pb, h->n_params);
     cudaMemsetAsync(h->m, 0, sizeof(float) * h->n_params, s);
     cudaMemsetAsync(h->v, 0, sizeof(float) * h->n_params, s);
+    cudaMemsetAsync(h->ctr, 0, sizeof(int64_t) * 3, s);
     h->step = 0;
+    return cudaStreamSynchronize(s) == cudaSuccess ? AD_PIC_OK : AD_PIC_ERR_CUDA;
+}
+
+int ad_pic_mlp_set_dataset(ad_pic_mlp* h, const float* x, const float* t, const float* dt, int n) {
+    if (!h || !x || !t || !dt || n < 1) return AD_PIC_ERR_INVALID_ARG;
+    if (n > h->data_cap) {
+        for (float** q : {&h->dx, &h->dtg, &h->ddt})
+            if (*q) {
+                cudaFree(*q);
+                for (auto& a : h->allocs) if (a == *q) a = nullptr;
+                *q = nullptr;
+            }
+        int st = 0;
+        st |= mlp_alloc(h, (void**)&h->dx, sizeof(float) * (size_t)n * h->n_in);
+        st |= mlp_alloc(h, (void**)&h->dtg, sizeof(float) * (size_t)n * h->n_out);
+        st |= mlp_alloc(h, (void**)&h->ddt, sizeof(float) * (size_t)n * h->n_out * h->n_in);
+        if (st) { h->data_cap = 0; return AD_PIC_ERR_OOM; }
+        h->data_cap = n;
+    }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->dx, x, sizeof(float) * (size_t)n * h->n_in, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->dtg, t, sizeof(float) * (size_t)n * h->n_out, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->ddt, dt, sizeof(float) * (size_t)n * h->n_out * h->n_in, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return AD_PIC_ERR_CUDA;
+    h->n_data = n;
+    cudaMemsetAsync(h->ctr + 2, 0, sizeof(int64_t), s);
     return cudaStreamSynchronize(s) == cudaSuccess ? AD_PIC_OK : AD_PIC_ERR_CUDA;
 }
 
@@ -474,14 +565,65 @@ int ad_pic_mlp_adam_step(ad_pic_mlp* h, const float* x, const float* t, const fl
     const float c1 = 1.f - std::pow(b1, (float)h->step), c2 = 1.f - std::pow(b2, (float)h->step);
     adam_kernel<<<nb(h->n_params), 256, 0, h->stream>>>(h->p, h->g, h->m, h->v, h->pb, h->n_params, lr, b1, b2, 1e-8f,
                                                          c1, c2);
+    // Adam's step count on the device follows (ad_pic_mlp_train continues from it)
+    const int64_t cnt = h->step;
+    cudaMemcpyAsync(h->ctr, &cnt, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
     if (loss && cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return AD_PIC_ERR_CUDA;
     return cudaStreamSynchronize(h->stream) == cudaSuccess ? AD_PIC_OK : AD_PIC_ERR_CUDA;
 }
 
+int ad_pic_mlp_train(ad_pic_mlp* h, int steps, int B, float lam, float lr0, float lr1, double* loss, double* ms) {
+    if (!h || steps < 1 || B < 1 || B > h->max_batch || !(lam >= 0.f) || !(lr0 > 0.f) || !(lr1 > 0.f))
+        return AD_PIC_ERR_INVALID_ARG;
+    if (h->n_data < 1) return AD_PIC_ERR_STATE;
+    cudaStream_t s = h->stream;
+    // one Adam step on the next mini-batch, captured once per (B, lambda, schedule) and replayed
+    if (!h->train_graph || h->g_B != B || h->g_lam != lam || h->g_lr0 != lr0 || h->g_lr1 != lr1 ||
+        h->g_total != steps) {
+        if (h->train_graph) cudaGraphExecDestroy(h->train_graph);
+        h->train_graph = nullptr;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return AD_PIC_ERR_CUDA;
+        const int per = h->n_in + h->n_out + h->n_out * h->n_in;
+        gather_batch_kernel<<<nb((int64_t)B * per), 256, 0, s>>>(h->dx, h->dtg, h->ddt, h->n_data, B, h->n_in,
+                                                                 h->n_out, h->ctr, h->x, h->t, h->dt);
+        loss_grad(h, B, lam);
+        adam_dev_kernel<<<nb(h->n_params), 256, 0, s>>>(h->p, h->g, h->m, h->v, h->pb, h->n_params, lr0, lr1, steps,
+                                                        0.9f, 0.999f, 1e-8f, h->ctr, h->done);
+        if (cudaStreamEndCapture(s, &graph) != cudaSuccess) { cudaGetLastError(); return AD_PIC_ERR_CUDA; }
+        const cudaError_t e = cudaGraphInstantiate(&h->train_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { cudaGetLastError(); h->train_graph = nullptr; return AD_PIC_ERR_CUDA; }
+        h->g_B = B; h->g_lam = lam; h->g_lr0 = lr0; h->g_lr1 = lr1; h->g_total = steps;
+    }
+    // the step within this run restarts at 0 (the learning-rate schedule); Adam's count continues
+    if (cudaMemsetAsync(h->ctr + 1, 0, sizeof(int64_t), s) != cudaSuccess) return AD_PIC_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    int rc = AD_PIC_OK;
+    for (int i = 0; i < steps && !rc; ++i)
+        if (cudaGraphLaunch(h->train_graph, s) != cudaSuccess) rc = AD_PIC_ERR_CUDA;
+    cudaEventRecord(e1, s);
+    if (!rc && loss && cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = AD_PIC_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = AD_PIC_ERR_CUDA;
+    float t = 0.f;
+    if (!rc) cudaEventElapsedTime(&t, e0, e1);
+    if (ms) *ms = t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->step += steps;
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
 void ad_pic_mlp_destroy(ad_pic_mlp* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->train_graph) cudaGraphExecDestroy(h->train_graph);
     for (void* p : h->allocs) cudaFree(p);
     if (h->stream) cudaStreamDestroy(h->stream);
     cudaGetLastError();

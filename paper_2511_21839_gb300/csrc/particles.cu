@@ -120,15 +120,21 @@ void launch_deposit(const T* state, int64_t N, const GeomDev* geom, int nx, int 
     constexpr int W = dep_tile_warps<CP, T>();
     const size_t sm = (size_t)W * dep_tile_bytes_per_warp<CP, T>();
     const int64_t warps = (N + 31) / 32;
-    deposit_tile_kernel<T, C, CP, W><<<(unsigned)((warps + W - 1) / W), W * 32, sm, s>>>(state, N, geom, nx, ny, nz,
-                                                                                       qm, rho, err, sb, qslot,
-                                                                                       (T)(1.0 / (double)N));
+    const unsigned grid = (unsigned)((warps + W - 1) / W);
+    if (qslot >= 0)
+        deposit_tile_kernel<T, C, CP, W, true><<<grid, W * 32, sm, s>>>(state, N, geom, nx, ny, nz, qm, rho, err, sb,
+                                                                        qslot, (T)(1.0 / (double)N));
+    else
+        deposit_tile_kernel<T, C, CP, W, false><<<grid, W * 32, sm, s>>>(state, N, geom, nx, ny, nz, qm, rho, err, sb,
+                                                                         -1, (T)0);
 }
 
 template <typename T, int C, int CP>
 void setup_deposit() {
     constexpr int W = dep_tile_warps<CP, T>();
-    cudaFuncSetAttribute(deposit_tile_kernel<T, C, CP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(deposit_tile_kernel<T, C, CP, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)W * dep_tile_bytes_per_warp<CP, T>()));
+    cudaFuncSetAttribute(deposit_tile_kernel<T, C, CP, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((size_t)W * dep_tile_bytes_per_warp<CP, T>()));
 }
 

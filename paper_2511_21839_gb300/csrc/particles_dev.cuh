@@ -787,11 +787,6 @@ __device__ __forceinline__ void ef_add_prod(T& hi, T& lo, T a, T b) {
     ef_add(hi, lo, ph);
     lo += pl;
 }
-// (hi, lo) += (bh, bl)
-__device__ __forceinline__ void dd_add(double& hi, double& lo, double bh, double bl) {
-    ef_add(hi, lo, bh);
-    lo += bl;
-}
 
 constexpr int kBoundaryBlocks = 152 * 8;
 
@@ -878,20 +873,24 @@ __device__ __forceinline__ void boundary_kernel_body(T* __restrict__ state, int6
     }
     if (APPLY) block_minmax<T>(mn, mx, mm);
     if (MOM) {
-        // the pairs in FP64 (a float pair converts exactly), then compensated
-        // sums over the PPW particle groups of the warp (lanes with the same k)
+        // compensated sums over the PPW particle groups of the warp (lanes with the
+        // same k), then the pairs in FP64 (a float pair converts exactly)
+        // (in the state's type: FP64 work is slow on this part, and the float pairs
+        // keep their ~48 bits through these few additions)
         double hh[3][5], ll[3][5];
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                hh[pl][q] = (double)ah[pl][q];
-                ll[pl][q] = (double)al[pl][q];
+                T h_ = ah[pl][q], l_ = al[pl][q];
                 for (int o = CP; o < 32; o <<= 1) {
-                    const double oh = __shfl_xor_sync(0xffffffffu, hh[pl][q], o);
-                    const double ol = __shfl_xor_sync(0xffffffffu, ll[pl][q], o);
-                    dd_add(hh[pl][q], ll[pl][q], oh, ol);
+                    const T oh = __shfl_xor_sync(0xffffffffu, h_, o);
+                    const T ol = __shfl_xor_sync(0xffffffffu, l_, o);
+                    ef_add(h_, l_, oh);
+                    l_ += ol;
                 }
+                hh[pl][q] = (double)h_;
+                ll[pl][q] = (double)l_;
             }
         // a warp's pair is rounded once to FP64 (one rounding of a partial sum, which
         // does not grow with the number of terms); the warps' partials are summed
@@ -975,9 +974,9 @@ __host__ __device__ constexpr int dep_tile_warps() {
 // sectors. The cell sort's rank is the lane's offset in its run plus one
 // counting atomic per run.
 
-// qslot >= 0: the bunch charge Q is the AD variable of that slot; channel
-// qslot + 1 then also gets dq_m/dQ W = W / N (qmd = 1 / N) per node (Eq. 2 on q_m W).
-template <typename T, int C, int CP, int WARPS>
+// QS: the bunch charge Q is the AD variable of slot qslot; channel qslot + 1
+// then also gets dq_m/dQ W = W / N (qmd = 1 / N) per node (Eq. 2 on q_m W).
+template <typename T, int C, int CP, int WARPS, bool QS = false>
 __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, int64_t N,
                                                     const GeomDev* __restrict__ geom, int nx, int ny, int nz, T qm,
                                                     T* __restrict__ rho, int* __restrict__ err, const SortBuf sb,
@@ -1080,7 +1079,7 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
                     rec[k + 1] = r.y;
                 }
                 rec[0] = qm * (wx * wy * wz);
-                if (qslot >= 0) {                  // warp-uniform
+                if constexpr (QS) {
 #pragma unroll
                     for (int k = 1; k < CP; ++k)
                         if (k == qslot + 1) rec[k] = fma(qmd, wx * wy * wz, rec[k]);
@@ -1122,13 +1121,13 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
     if (bad) atomicOr(err, bad);
 }
 
-template <typename T, int C, int CP, int WARPS>
+template <typename T, int C, int CP, int WARPS, bool QS>
 static __global__ void __launch_bounds__(WARPS * 32, dep_min_blocks<T, CP>()) deposit_tile_kernel(const T* __restrict__ state, int64_t N,
                                                                            const GeomDev* __restrict__ geom, int nx,
                                                                            int ny, int nz, T qm, T* __restrict__ rho,
                                                                            int* __restrict__ err, const SortBuf sb,
                                                                            int qslot, T qmd) {
-    deposit_tile_body<T, C, CP, WARPS>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x, qslot, qmd);
+    deposit_tile_body<T, C, CP, WARPS, QS>(state, N, geom, nx, ny, nz, qm, rho, err, sb, (int)blockIdx.x, qslot, qmd);
 }
 
 // ------------------------------------------------------------------ bounded-wait probe

@@ -121,9 +121,12 @@ class Surrogate:
         self.y_shift = np.zeros(2)
         self.y_scale = np.ones(2)
 
-    def fit(self, X, Y, dY, steps=3000, lam=1.0, lr=2e-3, lr_final=2e-5, seed=0):
-        """Adam on random mini-batches of max_batch samples, learning rate decayed geometrically
-        from lr to lr_final. Returns the loss of every step."""
+    def fit(self, X, Y, dY, steps=3000, lam=1.0, lr=2e-3, lr_final=2e-5, seed=0, device=True, epochs_in_order=8):
+        """Adam on mini-batches of max_batch samples, learning rate decayed geometrically from lr to
+        lr_final. device=True: the training set goes to the device once, as `epochs_in_order`
+        shuffled passes one after the other, and every step is a graph replay on the device
+        (ad_pic_mlp_train); returns (final loss, ms of the steps). device=False: one host call per
+        step with a fresh random mini-batch (ad_pic_mlp_adam_step); returns the loss of every step."""
         self.y_shift = Y.mean(axis=0)
         self.y_scale = Y.std(axis=0) + 1e-12
         T = (Y - self.y_shift) / self.y_scale
@@ -131,6 +134,10 @@ class Surrogate:
         rng = np.random.default_rng(seed)
         n = X.shape[0]
         B = min(self.max_batch, n)
+        if device:
+            order = np.concatenate([rng.permutation(n) for _ in range(epochs_in_order)])
+            adpic.ad_pic_mlp_set_dataset(self.m, X[order], T[order], dT[order])
+            return adpic.ad_pic_mlp_train(self.m, steps, B, lam, lr, lr_final)
         decay = (lr_final / lr) ** (1.0 / max(steps - 1, 1))
         hist = np.zeros(steps)
         for s in range(steps):

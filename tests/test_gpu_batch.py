@@ -141,3 +141,36 @@ def test_tuning_is_cached_for_batches_of_the_same_composition(adpic):
     assert rel_eps(v2, v1).max() < 1e-6 and rel_der_components(d2, d1).max() < 2 * der_tol(1, npart[0])
     sim.close()
     b2.close()
+
+
+def test_tile_shapes_tuned_and_every_shape_gives_the_same_run(adpic, singles):
+    """The autotuner picks the jobs' tile shapes after the mode (a coordinate search on one kick); the
+    shapes it may pick, at both ends of every range, give the same physics as the single runs."""
+    params, npart, grids = scan_instances()
+    w = I.workload("fodo_10k_32")
+    choices = ([32, 16, 32, 2], [4, 2, 4, 16], None)
+    for tiles in choices:
+        b = adpic.Batch(grids, npart)
+        b.set_mode(0)
+        b.set_tiles(tiles)
+        for i, p in enumerate(params):
+            b.set_beam(i, w.beam, I.normals(100 + i, npart[i]))
+            b.set_lattice(i, I.Lattice.from_params(p))
+        b.run(20)
+        used, ms = b.tuning()
+        t, tms = b.tiles()
+        print(f"tiles requested {tiles}: in use {t}, mode {used}, tuned kick {tms:.3f} ms")
+        if tiles is None:
+            assert t[0] in (4, 8, 16, 32) and t[1] in (2, 4, 8, 16) and t[2] in (4, 8, 16, 32) and t[3] in (2, 4, 8, 16)
+        else:
+            assert t == tiles
+        for i in range(len(params)):
+            (v1, d1), _ = singles[i]
+            v, d = b.moments(i)
+            assert rel_eps(v, v1).max() < 1e-6
+            assert rel_der_components(d, d1).max() < 2 * der_tol(1, npart[i])
+        b.close()
+    with pytest.raises(adpic.AdPicError) as e:
+        b = adpic.Batch(grids[:1], npart[:1])
+        b.set_tiles([8, 4, 8, 3])
+    assert e.value.status == -1

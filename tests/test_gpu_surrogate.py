@@ -84,6 +84,104 @@ def test_loss_and_gradient(lib):
     lib.ad_pic_mlp_destroy(m)
 
 
+def blocks(v, sizes):
+    """(name, slice) of every weight and bias block of the flat parameter vector."""
+    out, o = [], 0
+    for l in range(len(sizes) - 1):
+        n = sizes[l] * sizes[l + 1]
+        out.append((f"W{l}", slice(o, o + n)))
+        o += n
+        out.append((f"b{l}", slice(o, o + sizes[l + 1])))
+        o += sizes[l + 1]
+    return out
+
+
+def test_gradient_element_wise(lib):
+    """Every element of the gradient against the FP64 oracle, relative to the largest element of its
+    weight or bias block. BF16 operands carry 8 significant bits; the gradient of a weight is a sum
+    over the 96 x 8 rows of products of BF16 activations and BF16 output gradients, each relatively
+    off by up to 2^-8, and the errors of the layers above add in: 2e-2 of the block's largest element."""
+    m, params, n = make(lib, seed=13)
+    rng = np.random.default_rng(14)
+    B = 96
+    x = rng.uniform(-1, 1, size=(B, 7))
+    t = rng.standard_normal((B, 2))
+    dt = rng.standard_normal((B, 2, 7)) * 0.5
+    _, g = lib.ad_pic_mlp_loss_grad(m, x, t, dt, 0.5, n)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    _, gr = mlp.loss_and_grad(params, f32(x), f32(t), f32(dt), 0.5)
+    gref = flat([(dW, db) for (dW, db) in gr]).astype(np.float64)
+    worst = 0.0
+    for name, sl in blocks(gref, SIZES):
+        err = np.abs(g[sl] - gref[sl]).max() / np.abs(gref[sl]).max()
+        print(f"  {name}: max element error {err:.2e} of the block's largest")
+        worst = max(worst, err)
+        assert err < 2e-2, name
+    lib.ad_pic_mlp_destroy(m)
+
+
+def test_adam_update_matches_a_numpy_step(lib):
+    """One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, first step) on the device gradient: the new
+    FP32 parameters element-wise against numpy's update of the same parameters with that gradient."""
+    m, params, n = make(lib, seed=15)
+    rng = np.random.default_rng(16)
+    B = 64
+    x = rng.uniform(-1, 1, size=(B, 7))
+    t = rng.standard_normal((B, 2))
+    dt = rng.standard_normal((B, 2, 7)) * 0.5
+    p0 = lib.ad_pic_mlp_get_params(m, n).astype(np.float64)
+    _, g = lib.ad_pic_mlp_loss_grad(m, x, t, dt, 0.5, n)
+    lr = 1e-3
+    lib.ad_pic_mlp_adam_step(m, x, t, dt, 0.5, lr)
+    p1 = lib.ad_pic_mlp_get_params(m, n).astype(np.float64)
+    g = g.astype(np.float64)
+    mm = 0.1 * g
+    vv = 0.001 * g * g
+    ref = p0 - lr * (mm / 0.1) / (np.sqrt(vv / 0.001) + 1e-8)
+    np.testing.assert_allclose(p1, ref, rtol=2e-6, atol=2e-9)
+    lib.ad_pic_mlp_destroy(m)
+
+
+def test_device_resident_training_matches_the_host_loop_and_is_faster(lib):
+    """The same training problem through ad_pic_mlp_train (dataset on the device, one graph replay
+    per step) and through one host call per step: both fit the map, and the device path's step rate
+    and tensor throughput are reported (GEMM flops counted: 3 passes of 2 R K N per layer)."""
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((2, 7)) * 0.4
+
+    def target(x):
+        z = x @ A.T
+        return np.sin(z) + 0.3 * z ** 2, (np.cos(z) + 0.6 * z)[:, :, None] * A[None, :, :]
+
+    X = rng.uniform(-1, 1, size=(4096, 7))
+    T, dT = target(X)
+    steps, B = 300, 512
+    m, _, n = make(lib, seed=18)
+    lib.ad_pic_mlp_set_dataset(m, X, T, dT)
+    lib.ad_pic_mlp_train(m, 5, B, 1.0, 1e-3, 1e-3)            # capture + warm-up
+    loss, ms = lib.ad_pic_mlp_train(m, steps, B, 1.0, 1e-3, 1e-4)
+    R = B * 8
+    flops = 3 * 2 * R * (7 * 256 + 256 * 256 * 2 + 256 * 2)
+    print(f"device-resident training: {ms / steps:.3f} ms per step, {flops * steps / (ms * 1e-3) / 1e12:.2f} "
+          f"TFLOP/s of GEMM work, final loss {loss:.3e}")
+    Xv = rng.uniform(-1, 1, size=(256, 7))
+    Tv, dTv = target(Xv)
+    y, dy = lib.ad_pic_mlp_forward(m, Xv, 2)
+    assert np.sqrt(np.mean((y - Tv) ** 2)) < 0.1 * np.sqrt(np.mean(Tv ** 2))
+    assert np.sqrt(np.mean((dy - dTv) ** 2)) < 0.2 * np.sqrt(np.mean(dTv ** 2))
+    lib.ad_pic_mlp_destroy(m)
+    import time
+    m2, _, _ = make(lib, seed=18)
+    t0 = time.perf_counter()
+    for s_ in range(30):
+        idx = rng.choice(4096, size=B, replace=False)
+        lib.ad_pic_mlp_adam_step(m2, X[idx], T[idx], dT[idx], 1.0, 1e-3)
+    host_ms = 1e3 * (time.perf_counter() - t0) / 30
+    print(f"host loop: {host_ms:.3f} ms per step")
+    assert ms / steps < host_ms
+    lib.ad_pic_mlp_destroy(m2)
+
+
 def test_adam_fits_a_smooth_map_with_derivatives(lib):
     """A known smooth map and its exact Jacobian: the Sobolev fit drives both errors down."""
     m, params, n = make(lib, seed=5)
