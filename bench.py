@@ -553,6 +553,29 @@ def run_track(args):
     return 0
 
 
+def pipe2d(adpic, I, torch, n_part, cells, periods=1):
+    """The 2D conducting-pipe dual PIC (Sec. 4's solver): n_part particles, cells x cells, 100 A, one
+    FODO period per step, FP32-mixed and FP64; dual particle-steps/s (CUDA events around the run)."""
+    beam = I.default_beam(7)
+    lat = I.Lattice(deriv_slot=(-1, 1, 2, 3, 4, 5, 6))
+    nrm = I.normals(53, n_part)[:4]
+    out = {"workload": f"2D pipe 20 x 20 mm, {cells}x{cells} cells, {n_part} particles, 100 A (current in slot 0), "
+                       f"P=7, step = one period of 20 kicks"}
+    for name, prec in (("fp32", adpic.AD_PIC_FP32_MIXED), ("fp64", adpic.AD_PIC_FP64)):
+        sim = adpic.Pipe2D((cells, cells), (0.02, 0.02), n_part, 7, prec)
+        sim.set_beam(beam, 100.0, 0, nrm)
+        sim.set_lattice(lat)
+        sim.run(20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.run(20 * periods)
+        torch.cuda.synchronize()
+        ms = 1000.0 * (time.perf_counter() - t0) / periods
+        sim.close()
+        out[name] = {"value": n_part * 20 / (ms / 1000.0), "ms_per_step": ms}
+    return out
+
+
 def run_native(args):
     import torch
 
@@ -676,7 +699,9 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{kicks_cpu} kicks of the {w.name} workload on the host cores ({dt:.1f} s)"}
 
-    large = batch = track = None
+    large = batch = track = pipe = None
+    if rank == 0 and w.name == "fodo_1m_64" and not args.no_pipe2d:
+        pipe = pipe2d(adpic, I, torch, 1_048_576, 128)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_track:
         fma64 = fp64["fma_peaks_tflops"]["fp64"] if fp64 else adpic.ad_pic_fma_peak(adpic.AD_PIC_FP64)
         track = tracking(adpic, 7, args.track_particles, 10, 100, fma64)
@@ -692,7 +717,7 @@ def run_native(args):
                 "roofline": roof, "roofline_step": roof_step, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64, "accuracy": acc,
                 "kernels": kernels, "large_instance": large, "batched_scan": batch,
-                "single_particle_tracking": track}
+                "single_particle_tracking": track, "pipe2d": pipe}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -734,6 +759,7 @@ def main():
     ap.add_argument("--large-steps", type=int, default=3)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--no-track", action="store_true", help="skip the single-particle tracking sub-result")
+    ap.add_argument("--no-pipe2d", action="store_true", help="skip the 2D conducting-pipe sub-result")
     ap.add_argument("--track-particles", type=int, default=65536)
     ap.add_argument("--workload", choices=["fodo_1m_64", "fodo_16m_128", "batch", "track"], default="fodo_1m_64")
     ap.add_argument("--batch-instances", type=int, default=256)

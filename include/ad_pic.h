@@ -393,6 +393,45 @@ int ad_pic_set_beamline(ad_pic* h, int n_elem, const ad_pic_element* elems, cons
 int ad_pic_track_batch(int64_t n_part, const double* x0, int n_elem, const ad_pic_element* elems, int n_deriv,
                        int64_t n_repeat, double* out, double* ms);
 
+/* ---------------------------------------------------------------------
+   2D dual PIC in a rectangular, perfectly conducting pipe (Sec. 4, the
+   paper's own solver): a coasting beam with coordinates (x, px, y, py) as
+   dual numbers; bilinear deposit of the normalised density on nx x ny cells
+   of the a x b pipe (nodes 0..nx, 0..ny, the walls at 0 and n, the beam axis
+   at the centre); Poisson's equation with phi = 0 on the walls by the sine
+   series of Sec. 4 (rho^lm = (4/(nx ny)) sum rho_ij sin(l pi i/nx) sin(m pi
+   j/ny), phi^lm = rho^lm / gamma_lm^2, gamma_lm^2 = (l pi/a)^2 + (m pi/b)^2,
+   sine sums back); central-difference fields (zero on the walls); the kick
+   p += 2 pi K E tau of H2 = K phi / 2 with K = q I / (2 pi eps0 p0 v0^2
+   gamma0^2) and phi normalised to unit charge; the FODO maps of
+   ad_pic_set_lattice in x and y. A particle within one cell of a wall is
+   flagged (AD_PIC_ERR_OUT_OF_GRID, index clamped).
+   --------------------------------------------------------------------- */
+typedef struct ad_pic2d ad_pic2d;
+
+/* nx, ny in [8, 512] cells, a, b > 0 (m), n_particles in [1, 2^31 - 1],
+   n_deriv 7 or 13, precision AD_PIC_FP64 or AD_PIC_FP32_MIXED. */
+int ad_pic2d_create(int nx, int ny, double a, double b, int64_t n_particles, int n_deriv, int precision,
+                    ad_pic2d** out);
+/* Reference particle and Twiss functions of the x and y planes from `beam`
+   (z ignored), the beam current I (A) and its derivative slot (or -1). If
+   normals is not NULL it is [4][N] standard-normal draws (n1, n2 of x, then
+   y): u = sqrt(eps beta) n1, p = sqrt(eps/beta)(n2 - alpha n1), eps =
+   eps_n / (beta0 gamma0), sample mean removed. */
+int ad_pic2d_set_beam(ad_pic2d* h, const ad_pic_beam* beam, double current_A, int current_deriv_slot,
+                      const double* normals);
+/* state [4][N][n_deriv+1] (host FP64) */
+int ad_pic2d_set_particles(ad_pic2d* h, const double* state);
+int ad_pic2d_get_particles(const ad_pic2d* h, double* state);
+int ad_pic2d_set_lattice(ad_pic2d* h, const ad_pic_lattice* lattice);
+/* n_steps kicks M1(tau/2) M2(tau) M1(tau/2); moments at period ends and after the last kick */
+int ad_pic2d_run(ad_pic2d* h, int n_steps);
+/* emittances (x, y) of the latest record and derivs [2][n_deriv]; raw moments [2][5][C]; history [n][2][5][C] */
+int ad_pic2d_moments(const ad_pic2d* h, double* values, double* derivs);
+int ad_pic2d_moments_full(const ad_pic2d* h, double* mom);
+int ad_pic2d_history(const ad_pic2d* h, double* hist, int max_records, int* n_records);
+void ad_pic2d_destroy(ad_pic2d* h);
+
 /* Derived constants: out[8] = gamma0, beta0, p0 (kg m/s), B rho (T m),
    kappa_perp, kappa_z (1/(V/m * m)), macroparticle charge (C), q (C). */
 int ad_pic_constants(const ad_pic* h, double* out);

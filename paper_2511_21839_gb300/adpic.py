@@ -88,6 +88,17 @@ def lib():
             "ad_pic_track_batch": (ct.c_int, [ct.c_int64, dp, ct.c_int, ct.POINTER(ad_pic_element), ct.c_int,
                                               ct.c_int64, dp, dp]),
             "ad_pic_set_beamline": (ct.c_int, [vp, ct.c_int, ct.POINTER(ad_pic_element), ct.POINTER(ct.c_int)]),
+            "ad_pic2d_create": (ct.c_int, [ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_int64, ct.c_int,
+                                           ct.c_int, ct.POINTER(vp)]),
+            "ad_pic2d_set_beam": (ct.c_int, [vp, ct.POINTER(ad_pic_beam), ct.c_double, ct.c_int, dp]),
+            "ad_pic2d_set_particles": (ct.c_int, [vp, dp]),
+            "ad_pic2d_get_particles": (ct.c_int, [vp, dp]),
+            "ad_pic2d_set_lattice": (ct.c_int, [vp, ct.POINTER(ad_pic_lattice)]),
+            "ad_pic2d_run": (ct.c_int, [vp, ct.c_int]),
+            "ad_pic2d_moments": (ct.c_int, [vp, dp, dp]),
+            "ad_pic2d_moments_full": (ct.c_int, [vp, dp]),
+            "ad_pic2d_history": (ct.c_int, [vp, dp, ct.c_int, ct.POINTER(ct.c_int)]),
+            "ad_pic2d_destroy": (None, [vp]),
             "ad_pic_save": (ct.c_int, [vp, ct.c_char_p]),
             "ad_pic_load": (ct.c_int, [vp, ct.c_char_p]),
             "ad_pic_set_wait_limit": (ct.c_int, [vp, ct.c_int]),
@@ -570,6 +581,104 @@ class ADPIC:
 
     def set_beamline(self, beamline, kicks):
         ad_pic_set_beamline(self.h, beamline, kicks)
+
+
+def ad_pic2d_create(nx, ny, a, b, n_particles, n_deriv, precision):
+    h = ct.c_void_p()
+    _ck("ad_pic2d_create", lib().ad_pic2d_create(int(nx), int(ny), float(a), float(b), int(n_particles),
+                                                 int(n_deriv), int(precision), ct.byref(h)))
+    return h
+
+
+def ad_pic2d_set_beam(h, beam, current_A, current_slot=-1, normals=None):
+    nrm = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64)
+    _ck("ad_pic2d_set_beam", lib().ad_pic2d_set_beam(h, ct.byref(beam), float(current_A), int(current_slot),
+                                                     None if nrm is None else _p(nrm)))
+
+
+def ad_pic2d_set_particles(h, state):
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    _ck("ad_pic2d_set_particles", lib().ad_pic2d_set_particles(h, _p(s)))
+
+
+def ad_pic2d_get_particles(h, out):
+    _ck("ad_pic2d_get_particles", lib().ad_pic2d_get_particles(h, _p(out)))
+    return out
+
+
+def ad_pic2d_set_lattice(h, lat):
+    _ck("ad_pic2d_set_lattice", lib().ad_pic2d_set_lattice(h, ct.byref(lat)))
+
+
+def ad_pic2d_run(h, n_steps):
+    _ck("ad_pic2d_run", lib().ad_pic2d_run(h, int(n_steps)))
+
+
+def ad_pic2d_moments(h, P):
+    v = np.zeros(2)
+    d = np.zeros(2 * P)
+    _ck("ad_pic2d_moments", lib().ad_pic2d_moments(h, _p(v), _p(d)))
+    return v, d.reshape(2, P)
+
+
+def ad_pic2d_moments_full(h, C):
+    m = np.zeros((2, 5, C))
+    _ck("ad_pic2d_moments_full", lib().ad_pic2d_moments_full(h, _p(m)))
+    return m
+
+
+def ad_pic2d_history(h, C):
+    n = ct.c_int()
+    _ck("ad_pic2d_history", lib().ad_pic2d_history(h, None, 0, ct.byref(n)))
+    out = np.zeros((n.value, 2, 5, C))
+    if n.value:
+        _ck("ad_pic2d_history", lib().ad_pic2d_history(h, _p(out), n.value, ct.byref(n)))
+    return out
+
+
+def ad_pic2d_destroy(h):
+    if h:
+        lib().ad_pic2d_destroy(h)
+
+
+class Pipe2D:
+    """One 2D conducting-pipe dual PIC instance (Sec. 4's solver)."""
+
+    def __init__(self, cells, widths, n_particles, n_deriv=7, precision=AD_PIC_FP64):
+        self.N, self.P, self.C = int(n_particles), int(n_deriv), int(n_deriv) + 1
+        self.h = ad_pic2d_create(cells[0], cells[1], widths[0], widths[1], self.N, self.P, precision)
+
+    def set_beam(self, beam, current_A, current_slot=-1, normals=None):
+        ad_pic2d_set_beam(self.h, make_beam(beam), current_A, current_slot, normals)
+
+    def set_lattice(self, lat):
+        ad_pic2d_set_lattice(self.h, make_lattice(lat))
+
+    def set_particles(self, state):
+        ad_pic2d_set_particles(self.h, state)
+
+    def get_particles(self):
+        return ad_pic2d_get_particles(self.h, np.zeros((4, self.N, self.C)))
+
+    def run(self, n):
+        ad_pic2d_run(self.h, n)
+
+    def moments(self):
+        return ad_pic2d_moments(self.h, self.P)
+
+    def history(self):
+        return ad_pic2d_history(self.h, self.C)
+
+    def close(self):
+        if self.h:
+            ad_pic2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libadpic.so")
-SOURCES = ["api.cu", "particles.cu", "field.cu", "fft.cu", "noalloc.cu", "batch.cu", "mlp.cu", "peaks.cu", "optics.cu"]
+SOURCES = ["api.cu", "particles.cu", "field.cu", "fft.cu", "noalloc.cu", "batch.cu", "mlp.cu", "peaks.cu", "optics.cu", "pipe2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
