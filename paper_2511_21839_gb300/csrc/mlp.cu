@@ -29,15 +29,55 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
 
-// C[m][n] (ldc) = alpha * sum_k A(m, k) B(n, k) + beta * C[m][n], with
+// one operand tile [rows][BK] of X(r, k) = X[r * sr + k * sk] (BF16) into
+// shared memory: 16-byte vector loads along k (k contiguous) or along r (r
+// contiguous, the transposed operands of the backward pass) where the strides
+// and the tile allow, bounds-checked scalar loads otherwise
+__device__ __forceinline__ void stage_tile(__nv_bfloat16 (*Xs)[BK + PADK], const __nv_bfloat16* __restrict__ X,
+                                           int64_t sr, int64_t sk, int r0, int R, int k0, int K, bool vk, bool vr) {
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    if (vk && k0 + BK <= K) {
+        for (int t = threadIdx.x; t < BM * BK / 8; t += blockDim.x) {
+            const int r = t / (BK / 8), c = (t % (BK / 8)) * 8, gr = r0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gr < R) v = *reinterpret_cast<const uint4*>(X + gr * sr + (k0 + c));
+            *reinterpret_cast<uint4*>(&Xs[r][c]) = v;
+        }
+    } else if (vr && r0 + BM <= R) {
+        for (int t = threadIdx.x; t < BM * BK / 8; t += blockDim.x) {
+            const int c = t / (BM / 8), r = (t % (BM / 8)) * 8, gk = k0 + c;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gk < K) v = *reinterpret_cast<const uint4*>(X + (r0 + r) + gk * sk);
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Xs[r + q][c] = e[q];
+        }
+    } else {
+        for (int t = threadIdx.x; t < BM * BK; t += blockDim.x) {
+            const int r = sk == 1 ? t / BK : t % BM, c = sk == 1 ? t % BK : t / BM;
+            const int gr = r0 + r, gk = k0 + c;
+            Xs[r][c] = (gr < R && gk < K) ? X[gr * sr + gk * sk] : zero;
+        }
+    }
+}
+
+// C[m][n] (ldc) = sum_k A(m, k) B(n, k) + beta * C[m][n], with
 // A(m, k) = A[m * sam + k * sak] and B(n, k) = B[n * sbn + k * sbk] (BF16).
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+// blockIdx.z splits K: with split > 1 each slice writes its partial sum to
+// C + z * M * N (row-major [M][N], beta ignored) for split_reduce_kernel.
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, int kslice, const __nv_bfloat16* __restrict__ A,
                                                         int64_t sam, int64_t sak, const __nv_bfloat16* __restrict__ B,
                                                         int64_t sbn, int64_t sbk, float* __restrict__ C, int64_t ldc,
-                                                        float alpha, float beta) {
-    __shared__ __nv_bfloat16 As[BM][BK + PADK];
-    __shared__ __nv_bfloat16 Bs[BN][BK + PADK];
+                                                        float beta, bool avk, bool avr, bool bvk, bool bvr) {
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    if (gridDim.z > 1) {
+        C += (int64_t)blockIdx.z * M * N;
+        ldc = N;
+        beta = 0.f;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;     // 2 x 2 warps of 32 x 32
     const int grp = lane >> 2, tig = lane & 3;
@@ -48,18 +88,9 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int t = threadIdx.x; t < BM * BK; t += blockDim.x) {
-            const int r = sak == 1 ? t / BK : t % BM, c = sak == 1 ? t % BK : t / BM;
-            const int gm = m0 + r, gk = k0 + c;
-            As[r][c] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : zero;
-        }
-        for (int t = threadIdx.x; t < BN * BK; t += blockDim.x) {
-            const int r = sbk == 1 ? t / BK : t % BN, c = sbk == 1 ? t % BK : t / BN;
-            const int gn = n0 + r, gk = k0 + c;
-            Bs[r][c] = (gn < N && gk < K) ? B[gn * sbn + gk * sbk] : zero;
-        }
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        stage_tile(As, A, sam, sak, m0, M, k0, ke, avk, avr);
+        stage_tile(Bs, B, sbn, sbk, n0, N, k0, ke, bvk, bvr);
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
@@ -100,15 +131,45 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
                 const int c = n0 + wn + j * 8 + tig * 2 + (q & 1);
                 if (r < M && c < N) {
                     float* p = C + (int64_t)r * ldc + c;
-                    *p = alpha * acc[i][j][q] + (beta != 0.f ? beta * *p : 0.f);
+                    *p = acc[i][j][q] + (beta != 0.f ? beta * *p : 0.f);
                 }
             }
 }
 
+// C[m][n] = sum over the split slices of the partials, in slice order
+__global__ void split_reduce_kernel(const float* __restrict__ part, int split, int M, int N, float* __restrict__ C,
+                                    int64_t ldc) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M * N) return;
+    float s = 0.f;
+    for (int z = 0; z < split; ++z) s += part[(int64_t)z * M * N + t];
+    C[(t / N) * ldc + t % N] = s;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// K slices of a GEMM whose tiles alone do not fill the GPU (the weight
+// gradients: a few 64 x 64 tiles, K = the batch's rows): enough slices for
+// about two tiles per SM, each at least 8 k-steps long, within the workspace
+constexpr int kMaxSplit = 32;
+int split_of(int M, int N, int K) {
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int split = 1;
+    while (split < kMaxSplit && tiles * split < 304 && K / (split * 2) >= 8 * BK) split *= 2;
+    return split;
+}
+
 void gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak, const __nv_bfloat16* B, int64_t sbn,
-          int64_t sbk, float* C, int64_t ldc, float beta, cudaStream_t s) {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_bf16_kernel<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, 1.f, beta);
+          int64_t sbk, float* C, int64_t ldc, float beta, cudaStream_t s, float* ws = nullptr) {
+    const bool avk = sak == 1 && sam % 8 == 0 && aligned16(A), avr = sam == 1 && sak % 8 == 0 && aligned16(A);
+    const bool bvk = sbk == 1 && sbn % 8 == 0 && aligned16(B), bvr = sbn == 1 && sbk % 8 == 0 && aligned16(B);
+    const int split = (ws && beta == 0.f) ? split_of(M, N, K) : 1;
+    const int kslice = ((K + split * BK - 1) / (split * BK)) * BK;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, split);
+    gemm_bf16_kernel<<<grid, 128, 0, s>>>(M, N, K, kslice, A, sam, sak, B, sbn, sbk, split > 1 ? ws : C, ldc, beta,
+                                          avk, avr, bvk, bvr);
+    if (split > 1)
+        split_reduce_kernel<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, s>>>(ws, split, M, N, C, ldc);
 }
 
 // ------------------------------------------------------------------ elementwise
@@ -198,13 +259,23 @@ __global__ void act_bwd_kernel(float* __restrict__ G, const float* __restrict__ 
     Gb[p] = __float2bfloat16(gh);
 }
 
-// db[j] = sum over primal rows of G[r][j]
+// db[j] = sum over primal rows of G[r][j]: a block per 32 columns, its 8
+// warps over interleaved samples, then the 8 partial sums in order
 __global__ void bias_grad_kernel(const float* __restrict__ G, int B, int S, int width, float* __restrict__ db) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= width) return;
+    __shared__ float part[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int b = 0; b < B; ++b) s += G[(int64_t)b * S * width + j];
-    db[j] = s;
+    if (j < width)
+        for (int b = w; b < B; b += 8) s += G[(int64_t)b * S * width + j];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && j < width) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += part[q][lane];
+        db[j] = t;
+    }
 }
 
 __global__ void add_bias_primal_kernel(float* __restrict__ Y, const float* __restrict__ b, int R, int S, int n_out) {
@@ -310,6 +381,7 @@ struct ad_pic_mlp {
     std::vector<__nv_bfloat16*> A;           // per layer inputs [R][in] (BF16); A[0] = input rows
     float* G = nullptr;                      // gradient rows [R][max width] (FP32)
     float* G2 = nullptr;
+    float* ws = nullptr;                     // split-K partial sums of the weight gradients
     __nv_bfloat16* Gb = nullptr;
     float *x = nullptr, *t = nullptr, *dt = nullptr;
     double* loss = nullptr;
@@ -371,8 +443,8 @@ void loss_grad(ad_pic_mlp* h, int B, float lam) {
     for (int l = L - 1; l >= 0; --l) {
         const int in = h->in_dim[l], out = h->out_dim[l];
         // dW[o][i] = sum_r G[r][o] A[r][i]   (GEMM over the rows, both operands transposed in place)
-        gemm(out, in, R, h->Gb, 1, out, h->A[l], 1, in, h->g + h->w_off[l], in, 0.f, s);
-        bias_grad_kernel<<<nb(out), 256, 0, s>>>(G, B, S, out, h->g + h->b_off[l]);
+        gemm(out, in, R, h->Gb, 1, out, h->A[l], 1, in, h->g + h->w_off[l], in, 0.f, s, h->ws);
+        bias_grad_kernel<<<(unsigned)((out + 31) / 32), 256, 0, s>>>(G, B, S, out, h->g + h->b_off[l]);
         if (l == 0) break;
         // dA[r][i] = sum_o G[r][o] W[o][i]
         const __nv_bfloat16* W = h->pb + h->w_off[l];
@@ -442,6 +514,7 @@ int ad_pic_mlp_create(int n_in, int width, int hidden, int n_out, int max_batch,
     st |= mlp_alloc(h, (void**)&h->G, sizeof(float) * R * wmax);
     st |= mlp_alloc(h, (void**)&h->G2, sizeof(float) * R * wmax);
     st |= mlp_alloc(h, (void**)&h->Gb, sizeof(__nv_bfloat16) * R * wmax);
+    st |= mlp_alloc(h, (void**)&h->ws, sizeof(float) * kMaxSplit * (size_t)wmax * (width > n_in ? width : n_in));
     st |= mlp_alloc(h, (void**)&h->x, sizeof(float) * max_batch * n_in);
     st |= mlp_alloc(h, (void**)&h->t, sizeof(float) * max_batch * n_out);
     st |= mlp_alloc(h, (void**)&h->dt, sizeof(float) * max_batch * n_out * n_in);
