@@ -554,15 +554,17 @@ def run_track(args):
 
 
 def pipe2d(adpic, I, torch, n_part, cells, periods=1):
-    """The 2D conducting-pipe dual PIC (Sec. 4's solver): n_part particles, cells x cells, 100 A, one
-    FODO period per step, FP32-mixed and FP64; dual particle-steps/s (CUDA events around the run)."""
+    """The 2D conducting-pipe dual PIC (Sec. 4's solver): n_part particles, cells x cells on a 40 mm
+    pipe (the cell of the 128-cell, 20 mm parity case; the 1 mm beam's 5-sigma tails of a million
+    particles stay clear of the walls), 100 A, one FODO period per step, FP32-mixed and FP64; dual
+    particle-steps/s (wall clock around a synchronised run)."""
     beam = I.default_beam(7)
     lat = I.Lattice(deriv_slot=(-1, 1, 2, 3, 4, 5, 6))
     nrm = I.normals(53, n_part)[:4]
-    out = {"workload": f"2D pipe 20 x 20 mm, {cells}x{cells} cells, {n_part} particles, 100 A (current in slot 0), "
+    out = {"workload": f"2D pipe 40 x 40 mm, {cells}x{cells} cells, {n_part} particles, 100 A (current in slot 0), "
                        f"P=7, step = one period of 20 kicks"}
     for name, prec in (("fp32", adpic.AD_PIC_FP32_MIXED), ("fp64", adpic.AD_PIC_FP64)):
-        sim = adpic.Pipe2D((cells, cells), (0.02, 0.02), n_part, 7, prec)
+        sim = adpic.Pipe2D((cells, cells), (0.04, 0.04), n_part, 7, prec)
         sim.set_beam(beam, 100.0, 0, nrm)
         sim.set_lattice(lat)
         sim.run(20)
@@ -574,6 +576,35 @@ def pipe2d(adpic, I, torch, n_part, cells, periods=1):
         sim.close()
         out[name] = {"value": n_part * 20 / (ms / 1000.0), "ms_per_step": ms}
     return out
+
+
+def surrogate_training(adpic, peaks, steps=200, B=512):
+    """The surrogate's device-resident training (7 -> 256 x 3 -> 2, GELU, B samples x 8 rows of
+    primal and input tangents per step, Sobolev loss, Adam): ms per step by CUDA events inside the
+    library around the graph replays, and the GEMM work of a step (3 passes of 2 R K N per layer)
+    against the measured bf16 peak."""
+    import numpy as np
+
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, size=(4096, 7))
+    A = rng.standard_normal((2, 7)) * 0.4
+    z = X @ A.T
+    T, dT = np.sin(z), np.cos(z)[:, :, None] * A[None, :, :]
+    m = adpic.ad_pic_mlp_create(7, 256, 3, 2, B)
+    n = adpic.ad_pic_mlp_num_params(m)
+    adpic.ad_pic_mlp_set_params(m, (rng.standard_normal(n) * 0.05).astype(np.float32))
+    adpic.ad_pic_mlp_set_dataset(m, X, T, dT)
+    adpic.ad_pic_mlp_train(m, 5, B, 1.0, 1e-3, 1e-3)       # graph capture and warm-up
+    _, ms = adpic.ad_pic_mlp_train(m, steps, B, 1.0, 1e-3, 1e-4)
+    adpic.ad_pic_mlp_destroy(m)
+    R = B * 8
+    flops = 3 * 2 * R * (7 * 256 + 256 * 256 * 2 + 256 * 2)
+    tf = flops * steps / (ms * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops")
+    return {"workload": f"MLP 7-256-256-256-2, batch {B} samples x 8 rows (primal + 7 tangents), Sobolev loss, "
+                        f"Adam; {steps} steps", "ms_per_step": ms / steps, "gemm_flops_per_step": flops,
+            "gemm_tflops": tf, "bf16_peak_tflops": peak, "frac_of_measured_bf16": tf / peak if peak else None,
+            "ms_per_step_at_peak": flops / (peak * 1e12) * 1e3 if peak else None}
 
 
 def run_native(args):
@@ -611,6 +642,19 @@ def run_native(args):
         sim.set_beam(w.beam, nrm)
         sim.set_lattice(w.lattice)
         return sim
+
+    if args.fp64_only:
+        # the plain FP64 path alone (the run an FP64 instruction-count capture profiles): one
+        # untimed period, then --steps periods
+        sim64 = make(adpic.AD_PIC_FP64)
+        sim64.run(kicks)
+        barrier()
+        ms64, _, _ = timed_runs(sim64, args.steps, kicks, torch)
+        sim64.close()
+        if rank == 0:
+            print(json.dumps({"fp64_only": True, "workload": w.name, "ms_per_period": ms64,
+                              "periods": args.steps, "kicks_per_period": kicks}))
+        return 0
 
     # ---- FP32 bulk / compensated FP64 reductions (headline)
     sim = make(adpic.AD_PIC_FP32_MIXED)
@@ -699,9 +743,11 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{kicks_cpu} kicks of the {w.name} workload on the host cores ({dt:.1f} s)"}
 
-    large = batch = track = pipe = None
+    large = batch = track = pipe = surr = None
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_pipe2d:
-        pipe = pipe2d(adpic, I, torch, 1_048_576, 128)
+        pipe = pipe2d(adpic, I, torch, 1_048_576, 256)
+    if rank == 0 and w.name == "fodo_1m_64" and not args.no_surrogate:
+        surr = surrogate_training(adpic, peaks)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_track:
         fma64 = fp64["fma_peaks_tflops"]["fp64"] if fp64 else adpic.ad_pic_fma_peak(adpic.AD_PIC_FP64)
         track = tracking(adpic, 7, args.track_particles, 10, 100, fma64)
@@ -717,7 +763,7 @@ def run_native(args):
                 "roofline": roof, "roofline_step": roof_step, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64, "accuracy": acc,
                 "kernels": kernels, "large_instance": large, "batched_scan": batch,
-                "single_particle_tracking": track, "pipe2d": pipe}
+                "single_particle_tracking": track, "pipe2d": pipe, "surrogate_training": surr}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -760,6 +806,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--no-track", action="store_true", help="skip the single-particle tracking sub-result")
     ap.add_argument("--no-pipe2d", action="store_true", help="skip the 2D conducting-pipe sub-result")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate training sub-result")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="run only the plain FP64 path (one untimed period, then --steps periods)")
     ap.add_argument("--track-particles", type=int, default=65536)
     ap.add_argument("--workload", choices=["fodo_1m_64", "fodo_16m_128", "batch", "track"], default="fodo_1m_64")
     ap.add_argument("--batch-instances", type=int, default=256)
