@@ -31,7 +31,7 @@ class OrcConfig(ct.Structure):
         ("kicks", ct.c_int32 * 5), ("lat_slot", ct.c_int32 * 7),
         ("n_line", ct.c_int32), ("pad_line", ct.c_int32),
         ("line", ct.POINTER(OrcElement)), ("line_kicks", ct.POINTER(ct.c_int32)),
-        ("charge_slot", ct.c_int32), ("pad_q", ct.c_int32),
+        ("charge_slot", ct.c_int32), ("energy_slot", ct.c_int32),
     ]
 
 
@@ -51,6 +51,9 @@ def lib():
             "orc_testfn": (None, [dp, dp]),
             "orc_fft1d": (ct.c_int, [dp, dp, ct.c_int, ct.c_int]),
             "orc_igf": (ct.c_double, [ct.c_double] * 6),
+            "orc_igf_dhz": (None, [ct.c_double] * 6 + [dp]),
+            "orc_dual_constants": (None, [cp, dp]),
+            "orc_green_denergy": (None, [cp, dp, dp]),
             "orc_beam_init": (ct.c_int, [cp, dp, dp]),
             "orc_half_map": (None, [cp, ct.c_int64, dp]),
             "orc_apply_half_map": (None, [cp, dp, ct.c_int64]),
@@ -99,6 +102,7 @@ class Oracle:
         line_kicks kicks per element, in place of the FODO period."""
         c = OrcConfig()
         c.charge_slot = -1
+        c.energy_slot = -1
         if line is not None:
             self._line = elements(line)
             self._line_kicks = (ct.c_int32 * len(line))(*[int(v) for v in line_kicks])
@@ -127,6 +131,19 @@ class Oracle:
         self._L.orc_constants(self.ref, _p(out))
         keys = ["gamma0", "beta0", "p0", "brho", "kappa_perp", "kappa_z", "q_macro", "q"]
         return dict(zip(keys, out.tolist()))
+
+    def dual_constants(self):
+        """gamma0, beta0 gamma0, B rho, kappa_perp, kappa_z, gamma0^2 as duals [6][C]."""
+        out = np.zeros((6, self.C))
+        self._L.orc_dual_constants(self.ref, _p(out))
+        return out
+
+    def green_denergy(self, geom):
+        geom = np.ascontiguousarray(geom, dtype=np.float64)
+        nx, ny, nz = self.n
+        out = np.zeros((2 * nz, 2 * ny, 2 * nx))
+        self._L.orc_green_denergy(self.ref, _p(geom), _p(out))
+        return out
 
     def state_shape(self):
         return (6, self.N, self.C)
@@ -239,6 +256,13 @@ def fft1d(z, sign=-1):
 
 def igf(x, y, z, hx, hy, hz):
     return lib().orc_igf(x, y, z, hx, hy, hz)
+
+
+def igf_dhz(x, y, kz, hx, hy, hz):
+    """(G, dG/dhz) at the node offset (x, y, kz hz), the z offset moving with hz."""
+    out = np.zeros(2)
+    lib().orc_igf_dhz(x, y, kz, hx, hy, hz, _p(out))
+    return out[0], out[1]
 
 
 def threads():

@@ -86,6 +86,9 @@ static void d_exp(int C, const double* f, double* out) {
     d_fn(C, f, e, e, out);
 }
 
+static void d_log(int C, const double* f, double* out) { d_fn(C, f, log(f[0]), 1.0 / f[0], out); }
+static void d_atan(int C, const double* f, double* out) { d_fn(C, f, atan(f[0]), 1.0 / (1.0 + f[0] * f[0]), out); }
+
 /* a constant times a dual: Eq. 2 with g = (a, 0, ..., 0) */
 static void d_cmul(int C, double a, const double* f, double* out) {
     dual g;
@@ -168,6 +171,59 @@ void orc_constants(const orc_config* cfg, double out[8]) {
     out[4] = k.kperp; out[5] = k.kz; out[6] = k.qm; out[7] = k.q;
 }
 
+/* The reference-particle constants as duals of the kinetic energy E (slot
+   energy_slot): gamma0 = 1 + E / (m c^2), beta0 gamma0 = sqrt(gamma0^2 - 1),
+   p0 = beta0 gamma0 m c, B rho = p0 / q, v0 = beta0 c, and the kick constants
+   of get_consts. With energy_slot < 0 every derivative part is zero. The
+   value parts are those of get_consts (the same numbers as without the slot). */
+typedef struct {
+    dual gamma0, bg, brho, kperp, kz, g2;
+} dconsts;
+
+static int energy_active(const orc_config* cfg) {
+    return cfg->energy_slot >= 0 && cfg->energy_slot + 1 < cfg->P + 1;
+}
+
+static void get_dconsts(const orc_config* cfg, dconsts* k) {
+    const int C = cfg->P + 1;
+    const double mass_kg = cfg->mass_eV * Q_E / (C_LIGHT * C_LIGHT);
+    const double q = cfg->charge_e * Q_E;
+    dual E, t, one, p0, v0, den, qd;
+    d_var(C, cfg->kinetic_eV, cfg->energy_slot, E);
+    d_const(C, 1.0, one);
+    d_cmul(C, 1.0 / cfg->mass_eV, E, t);
+    d_add(C, one, t, k->gamma0);
+    d_mul(C, k->gamma0, k->gamma0, t);
+    d_sub(C, t, one, t);
+    d_sqrt(C, t, k->bg);
+    d_cmul(C, mass_kg * C_LIGHT, k->bg, p0);
+    d_cmul(C, 1.0 / q, p0, k->brho);
+    d_div(C, k->bg, k->gamma0, t);
+    d_cmul(C, C_LIGHT, t, v0);                 /* v0 = beta0 c */
+    d_const(C, q, qd);
+    d_mul(C, k->gamma0, p0, den);
+    d_mul(C, den, v0, den);
+    d_div(C, qd, den, k->kperp);               /* q / (gamma0 p0 v0) */
+    d_mul(C, p0, v0, den);
+    d_div(C, qd, den, k->kz);                  /* q / (p0 v0) */
+    d_mul(C, k->gamma0, k->gamma0, k->g2);
+    const consts K = get_consts(cfg);
+    k->gamma0[0] = K.gamma0;
+    k->bg[0] = K.beta0 * K.gamma0;
+    k->brho[0] = K.brho;
+    k->kperp[0] = K.kperp;
+    k->kz[0] = K.kz;
+    k->g2[0] = K.gamma0 * K.gamma0;
+}
+
+void orc_dual_constants(const orc_config* cfg, double* out) {
+    const int C = cfg->P + 1;
+    dconsts k;
+    get_dconsts(cfg, &k);
+    const double* v[6] = {k.gamma0, k.bg, k.brho, k.kperp, k.kz, k.g2};
+    for (int i = 0; i < 6; ++i) d_copy(C, v[i], out + i * C);
+}
+
 /* ------------------------------------------------------------------ */
 /* Lattice: element of a kick, dual step length, half-step maps         */
 /* ------------------------------------------------------------------ */
@@ -239,7 +295,8 @@ static void plane_map(int C, const double* kp, const double* t, double m[4][ORC_
    entries (m11, m12, m21, m22) for planes (x,px), (y,py), (z,delta). */
 void orc_half_map(const orc_config* cfg, int64_t kick, double* mflat) {
     const int C = cfg->P + 1;
-    consts K = get_consts(cfg);
+    dconsts K;
+    get_dconsts(cfg, &K);
     int e = element_of_kick(cfg, kick);
     dual tau, t, kx, ky, zero;
     double m[4][ORC_MAXC];
@@ -254,10 +311,9 @@ void orc_half_map(const orc_config* cfg, int64_t kick, double* mflat) {
     } else if (e == 1 || e == 3) {
         int gi = (e == 1) ? 0 : 1;
         int gslot = cfg->lat_slot[(e == 1) ? 2 : 5];
-        dual g, br;
+        dual g;
         d_var(C, cfg->g[gi], gslot, g);
-        d_const(C, K.brho, br);
-        d_div(C, g, br, kx);                  /* k = q g / p0 = g / Brho */
+        d_div(C, g, K.brho, kx);              /* k = q g / p0 = g / Brho (Brho dual in the energy) */
         for (int k = 0; k < C; ++k) ky[k] = -kx[k];
     } else {
         d_copy(C, zero, kx);
@@ -268,9 +324,8 @@ void orc_half_map(const orc_config* cfg, int64_t kick, double* mflat) {
     plane_map(C, ky, t, m);
     for (int i = 0; i < 4; ++i) d_copy(C, m[i], mflat + (1 * 4 + i) * C);
     /* longitudinal: z += t delta / gamma0^2 */
-    dual g2, tz;
-    d_const(C, K.gamma0 * K.gamma0, g2);
-    d_div(C, t, g2, tz);
+    dual tz;
+    d_div(C, t, K.g2, tz);
     d_const(C, 1.0, mflat + (2 * 4 + 0) * C);
     d_copy(C, tz, mflat + (2 * 4 + 1) * C);
     d_const(C, 0.0, mflat + (2 * 4 + 2) * C);
@@ -320,18 +375,17 @@ int orc_beam_init(const orc_config* cfg, const double* normals, double* state) {
     const int C = cfg->P + 1;
     const int64_t N = cfg->N;
     if (C < 1 || C > ORC_MAXC || N < 0) return -1;
-    consts K = get_consts(cfg);
-    double bg = K.beta0 * K.gamma0;
+    dconsts K;
+    get_dconsts(cfg, &K);
     for (int pl = 0; pl < 3; ++pl) {
-        dual al, be, ep, epsn, bgd, a, b, t;
+        dual al, be, ep, epsn, a, b, t;
         int sa = pl < 2 ? cfg->twiss_slot[3 * pl + 0] : -1;
         int sb = pl < 2 ? cfg->twiss_slot[3 * pl + 1] : -1;
         int se = pl < 2 ? cfg->twiss_slot[3 * pl + 2] : -1;
         d_var(C, cfg->alpha[pl], sa, al);
         d_var(C, cfg->beta[pl], sb, be);
         d_const(C, cfg->eps_n[pl], epsn);
-        d_const(C, bg, bgd);
-        d_div(C, epsn, bgd, ep);              /* geometric emittance */
+        d_div(C, epsn, K.bg, ep);             /* geometric emittance eps_n / (beta0 gamma0) */
         if (se >= 0) d_var(C, ep[0], se, ep);
         d_mul(C, ep, be, t);
         d_sqrt(C, t, a);                      /* sqrt(eps beta) */
@@ -509,6 +563,59 @@ double orc_igf(double x, double y, double z, double hx, double hy, double hz) {
     return s / (4.0 * PI * EPS0 * hx * hy * hz);
 }
 
+/* The antiderivative F of 1/r at (x, y, z) with z a dual number (C = 2):
+   Eq. 4 through every elementary function of F. */
+static void igf_F_dual(double x, double y, const double* z, double* out) {
+    const int C = 2;
+    dual X, Y, r, t, u, w, acc, a;
+    d_const(C, x, X);
+    d_const(C, y, Y);
+    d_mul(C, z, z, t);
+    d_const(C, x * x + y * y, u);
+    d_add(C, t, u, t);
+    d_sqrt(C, t, r);                                  /* r */
+    d_const(C, 0.0, acc);
+    /* y z log(x + r) */
+    d_add(C, X, r, t); d_log(C, t, t); d_mul(C, z, t, t); d_cmul(C, y, t, t); d_add(C, acc, t, acc);
+    /* x z log(y + r) */
+    d_add(C, Y, r, t); d_log(C, t, t); d_mul(C, z, t, t); d_cmul(C, x, t, t); d_add(C, acc, t, acc);
+    /* x y log(z + r) */
+    d_add(C, z, r, t); d_log(C, t, t); d_cmul(C, x * y, t, t); d_add(C, acc, t, acc);
+    /* - x^2/2 atan(y z / (x r)) */
+    d_cmul(C, y, z, u); d_cmul(C, x, r, w); d_div(C, u, w, t); d_atan(C, t, t);
+    d_cmul(C, -0.5 * x * x, t, t); d_add(C, acc, t, acc);
+    /* - y^2/2 atan(x z / (y r)) */
+    d_cmul(C, x, z, u); d_cmul(C, y, r, w); d_div(C, u, w, t); d_atan(C, t, t);
+    d_cmul(C, -0.5 * y * y, t, t); d_add(C, acc, t, acc);
+    /* - z^2/2 atan(x y / (z r)) */
+    d_const(C, x * y, u); d_mul(C, z, r, w); d_div(C, u, w, t); d_atan(C, t, t);
+    d_mul(C, z, z, a); d_cmul(C, -0.5, a, a); d_mul(C, a, t, t); d_add(C, acc, t, acc);
+    d_copy(C, acc, out);
+}
+
+void orc_igf_dhz(double x, double y, double kz, double hx, double hy, double hz, double out[2]) {
+    const int C = 2;
+    dual H, zc, Fv, sum, den, G;
+    d_var(C, hz, 0, H);                              /* hz as the variable */
+    d_const(C, 0.0, sum);
+    const double xs[2] = {x - 0.5 * hx, x + 0.5 * hx};
+    const double ys[2] = {y - 0.5 * hy, y + 0.5 * hy};
+    const double kc[2] = {kz - 0.5, kz + 0.5};         /* corner z = kc hz */
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                const double sgn = ((a + b + c) % 2 == 1) ? 1.0 : -1.0;
+                d_cmul(C, kc[c], H, zc);
+                igf_F_dual(xs[a], ys[b], zc, Fv);
+                d_cmul(C, sgn, Fv, Fv);
+                d_add(C, sum, Fv, sum);
+            }
+    d_cmul(C, 4.0 * PI * EPS0 * hx * hy, H, den);
+    d_div(C, sum, den, G);
+    out[0] = G[0];
+    out[1] = G[1];
+}
+
 /* G on the doubled grid (2nx x 2ny x 2nz), even extension: index i maps to
    offset i for i <= n and i - 2n above. Rest-frame spacings (hx, hy, gamma0 hz). */
 void orc_green(const orc_config* cfg, const double* geom, double* G) {
@@ -607,6 +714,28 @@ static void fft3d(double* re, double* im, int mx, int my, int mz, int sign) {
     }
 }
 
+/* dG/dE through the rest-frame spacing hz_r = gamma0 hz: dG/dhz_r (with the
+   node offsets k hz_r) times dhz_r/dE = hz / (m c^2) */
+void orc_green_denergy(const orc_config* cfg, const double* geom, double* GE) {
+    consts K = get_consts(cfg);
+    const int mx = 2 * cfg->nx, my = 2 * cfg->ny, mz = 2 * cfg->nz;
+    const double hx = geom[3], hy = geom[4], hz = geom[5] * K.gamma0;
+    const double dhz = geom[5] / cfg->mass_eV;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < mz; ++k) {
+        int ok = k <= cfg->nz ? k : k - mz;
+        for (int j = 0; j < my; ++j) {
+            int oj = j <= cfg->ny ? j : j - my;
+            for (int i = 0; i < mx; ++i) {
+                int oi = i <= cfg->nx ? i : i - mx;
+                double g[2];
+                orc_igf_dhz(fabs((double)oi) * hx, fabs((double)oj) * hy, fabs((double)ok), hx, hy, hz, g);
+                GE[((int64_t)k * my + j) * mx + i] = g[1] * dhz;
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Hockney convolution phi_c = G * rho_c for every channel (Sec. 4: the  */
 /* Poisson equation is solved for the value and for every derivative)   */
@@ -617,13 +746,28 @@ int orc_solve(const orc_config* cfg, const double* geom, const double* rho, doub
     const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
     const int mx = 2 * nx, my = 2 * ny, mz = 2 * nz;
     const int64_t M = (int64_t)mx * my * mz, nn = (int64_t)nx * ny * nz;
+    /* with the kinetic energy as a dual input G is dual too: the energy
+       channel gets phi_E = G * rho_E + (dG/dE) * rho_0 (Eq. 2 on the product
+       inside the convolution) */
+    const int ce = energy_active(cfg) ? cfg->energy_slot + 1 : -1;
     double* gr = (double*)malloc(sizeof(double) * M);
     double* gi = (double*)calloc(M, sizeof(double));
     double* ar = (double*)malloc(sizeof(double) * M);
     double* ai = (double*)malloc(sizeof(double) * M);
-    if (!gr || !gi || !ar || !ai) { free(gr); free(gi); free(ar); free(ai); return -1; }
+    double* er = ce > 0 ? (double*)malloc(sizeof(double) * M) : NULL;
+    double* ei = ce > 0 ? (double*)calloc(M, sizeof(double)) : NULL;
+    double* r0r = ce > 0 ? (double*)malloc(sizeof(double) * M) : NULL;
+    double* r0i = ce > 0 ? (double*)malloc(sizeof(double) * M) : NULL;
+    if (!gr || !gi || !ar || !ai || (ce > 0 && (!er || !ei || !r0r || !r0i))) {
+        free(gr); free(gi); free(ar); free(ai); free(er); free(ei); free(r0r); free(r0i);
+        return -1;
+    }
     orc_green(cfg, geom, gr);
     fft3d(gr, gi, mx, my, mz, -1);
+    if (ce > 0) {
+        orc_green_denergy(cfg, geom, er);
+        fft3d(er, ei, mx, my, mz, -1);
+    }
     for (int c = 0; c < C; ++c) {
         memset(ar, 0, sizeof(double) * M);
         memset(ai, 0, sizeof(double) * M);
@@ -632,9 +776,17 @@ int orc_solve(const orc_config* cfg, const double* geom, const double* rho, doub
                 for (int i = 0; i < nx; ++i)
                     ar[((int64_t)k * my + j) * mx + i] = rho[(int64_t)c * nn + ((int64_t)k * ny + j) * nx + i];
         fft3d(ar, ai, mx, my, mz, -1);
+        if (c == 0 && ce > 0) {
+            memcpy(r0r, ar, sizeof(double) * M);
+            memcpy(r0i, ai, sizeof(double) * M);
+        }
         for (int64_t q = 0; q < M; ++q) {
             double r = ar[q] * gr[q] - ai[q] * gi[q];
             double s = ar[q] * gi[q] + ai[q] * gr[q];
+            if (c == ce) {
+                r += r0r[q] * er[q] - r0i[q] * ei[q];
+                s += r0r[q] * ei[q] + r0i[q] * er[q];
+            }
             ar[q] = r;
             ai[q] = s;
         }
@@ -645,7 +797,7 @@ int orc_solve(const orc_config* cfg, const double* geom, const double* rho, doub
                     phi[(int64_t)c * nn + ((int64_t)k * ny + j) * nx + i] =
                         ar[((int64_t)k * my + j) * mx + i] / (double)M;
     }
-    free(gr); free(gi); free(ar); free(ai);
+    free(gr); free(gi); free(ar); free(ai); free(er); free(ei); free(r0r); free(r0i);
     return 0;
 }
 
@@ -656,6 +808,8 @@ int orc_solve_direct(const orc_config* cfg, const double* geom, const double* rh
     const int64_t nn = (int64_t)nx * ny * nz;
     consts K = get_consts(cfg);
     const double hx = geom[3], hy = geom[4], hz = geom[5] * K.gamma0;
+    const int ce = energy_active(cfg) ? cfg->energy_slot + 1 : -1;
+    const double dhz = geom[5] / cfg->mass_eV;
 #pragma omp parallel for schedule(static)
     for (int64_t a = 0; a < nn; ++a) {
         int ia = (int)(a % nx), ja = (int)((a / nx) % ny), ka = (int)(a / ((int64_t)nx * ny));
@@ -665,6 +819,12 @@ int orc_solve_direct(const orc_config* cfg, const double* geom, const double* rh
             double G = orc_igf(fabs((double)(ia - ib)) * hx, fabs((double)(ja - jb)) * hy,
                                fabs((double)(ka - kb)) * hz, hx, hy, hz);
             for (int c = 0; c < C; ++c) phi[(int64_t)c * nn + a] += G * rho[(int64_t)c * nn + b];
+            if (ce > 0) {
+                double g[2];
+                orc_igf_dhz(fabs((double)(ia - ib)) * hx, fabs((double)(ja - jb)) * hy, fabs((double)(ka - kb)),
+                            hx, hy, hz, g);
+                phi[(int64_t)ce * nn + a] += g[1] * dhz * rho[b];
+            }
         }
     }
     return 0;
@@ -693,6 +853,26 @@ void orc_field(const orc_config* cfg, const double* geom, const double* phi, dou
                     ex[a] = -(f[a + 1] - f[a - 1]) / (2.0 * hx);
                     ey[a] = -(f[a + nx] - f[a - nx]) / (2.0 * hy);
                     ez[a] = -(f[a + (int64_t)nx * ny] - f[a - (int64_t)nx * ny]) / (2.0 * hz);
+                }
+    }
+    if (energy_active(cfg)) {
+        /* the rest-frame spacing 2 gamma0 hz is dual in the energy: E_z is the
+           dual quotient (Eq. 3) of -(phi(k+1) - phi(k-1)) by it */
+        dconsts D;
+        get_dconsts(cfg, &D);
+        dual den;
+        d_cmul(C, 2.0 * geom[5], D.gamma0, den);
+        for (int k = 1; k < nz - 1; ++k)
+            for (int j = 1; j < ny - 1; ++j)
+                for (int i = 1; i < nx - 1; ++i) {
+                    const int64_t a = ((int64_t)k * ny + j) * nx + i;
+                    dual num, q;
+                    for (int c = 0; c < C; ++c) {
+                        const double* f = phi + (int64_t)c * nn;
+                        num[c] = -(f[a + (int64_t)nx * ny] - f[a - (int64_t)nx * ny]);
+                    }
+                    d_div(C, num, den, q);
+                    for (int c = 0; c < C; ++c) E[((int64_t)2 * C + c) * nn + a] = q[c];
                 }
     }
 }
@@ -741,16 +921,17 @@ int orc_gather(const orc_config* cfg, const double* state, const double* geom, c
 int orc_kick(const orc_config* cfg, double* state, const double* geom, const double* E, int64_t kick) {
     const int C = cfg->P + 1;
     const int64_t N = cfg->N;
-    consts K = get_consts(cfg);
+    dconsts K;
+    get_dconsts(cfg, &K);
     double* Ep = (double*)malloc(sizeof(double) * 3 * N * C + 8);
     if (!Ep) return -1;
     int st = orc_gather(cfg, state, geom, E, Ep);
     if (st) { free(Ep); return st; }
     dual tau, a[3];
     dual_tau(cfg, element_of_kick(cfg, kick), tau);
-    d_cmul(C, K.kperp, tau, a[0]);
-    d_cmul(C, K.kperp, tau, a[1]);
-    d_cmul(C, K.kz, tau, a[2]);
+    d_mul(C, tau, K.kperp, a[0]);        /* kappa tau, dual in the step and the energy */
+    d_mul(C, tau, K.kperp, a[1]);
+    d_mul(C, tau, K.kz, a[2]);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         for (int d = 0; d < 3; ++d) {
@@ -1061,6 +1242,7 @@ static orc_config as3d(const orc2d_config* c) {
     k.g[1] = c->g[1];
     for (int j = 0; j < 7; ++j) k.lat_slot[j] = c->lat_slot[j];
     k.charge_slot = -1;
+    k.energy_slot = -1;
     return k;
 }
 

@@ -68,11 +68,18 @@ typedef struct {
     /* slot of the bunch charge as an AD variable (Sec. 4: beam current as a
        dual input), -1 = constant: the macroparticle charge Q / N is then a
        dual number */
-    int32_t charge_slot, pad_q;
+    int32_t charge_slot;
+    /* slot of the kinetic energy as an AD variable (Sec. 4: beam parameters
+       as dual inputs), -1 = constant: gamma0, beta0 gamma0, B rho and the kick
+       constants are then dual, and so are the rest-frame z spacing gamma0 hz
+       of the Green's function and of the field */
+    int32_t energy_slot;
 } orc_config;
 
 /* derived constants: gamma0, beta0, p0 (kg m/s), Brho (T m), kappa_perp, kappa_z, q_macro (C), q (C) */
 void orc_constants(const orc_config* cfg, double out[8]);
+/* the same as duals (energy_slot): out[6][C] = gamma0, beta0 gamma0, Brho, kappa_perp, kappa_z, 1/gamma0^2 */
+void orc_dual_constants(const orc_config* cfg, double* out);
 
 /* dual arithmetic, exposed for the pins: op 0 add, 1 sub, 2 mul, 3 div,
    4 sqrt, 5 sin, 6 cos, 7 sinh, 8 cosh, 9 exp (g ignored for unary ops) */
@@ -86,6 +93,9 @@ int orc_fft1d(double* re, double* im, int n, int sign);
 
 /* cell-averaged 1/(4 pi eps0 r) over the box of size (hx,hy,hz) centred at (x,y,z) */
 double orc_igf(double x, double y, double z, double hx, double hy, double hz);
+/* the same at the node offset (x, y, kz hz) and its derivative with respect to
+   hz (the centre moves with hz): out[2] = (G, dG/dhz) */
+void orc_igf_dhz(double x, double y, double kz, double hx, double hy, double hz, double out[2]);
 
 int orc_beam_init(const orc_config* cfg, const double* normals /*[6][N]*/, double* state);
 void orc_half_map(const orc_config* cfg, int64_t kick, double* m /*[3][4][C]*/);
@@ -93,6 +103,9 @@ void orc_apply_half_map(const orc_config* cfg, double* state, int64_t kick);
 int orc_geometry(const orc_config* cfg, const double* state, double* geom);
 int orc_deposit(const orc_config* cfg, const double* state, const double* geom, double* rho);
 void orc_green(const orc_config* cfg, const double* geom, double* G /*[2nz][2ny][2nx]*/);
+/* dG/dE (E the kinetic energy, eV) on the same doubled grid, through the
+   rest-frame spacing gamma0 hz */
+void orc_green_denergy(const orc_config* cfg, const double* geom, double* GE);
 int orc_solve(const orc_config* cfg, const double* geom, const double* rho, double* phi);
 int orc_solve_direct(const orc_config* cfg, const double* geom, const double* rho, double* phi);
 void orc_field(const orc_config* cfg, const double* geom, const double* phi, double* E);

@@ -60,6 +60,7 @@ class Beam:
     beta: tuple = (0.0, 0.0, 0.0)
     twiss_slot: tuple = (-1, -1, -1, -1, -1, -1)
     charge_slot: int = -1          # derivative slot of the bunch charge (-1: constant)
+    energy_slot: int = -1          # derivative slot of the kinetic energy (-1: constant)
 
 
 @dataclass
@@ -189,4 +190,5 @@ def orc_kwargs(w: Workload, n_particles=None, grid=None, n_deriv=None, lattice=N
                 twiss_slot=[s if (0 <= s < P) else -1 for s in b.twiss_slot],
                 L=lat.L, g=lat.g, kicks=lat.kicks,
                 lat_slot=[s if (0 <= s < P) else -1 for s in lat.deriv_slot],
-                charge_slot=b.charge_slot if 0 <= b.charge_slot < P else -1)
+                charge_slot=b.charge_slot if 0 <= b.charge_slot < P else -1,
+                energy_slot=b.energy_slot if 0 <= b.energy_slot < P else -1)
