@@ -607,6 +607,37 @@ def surrogate_training(adpic, peaks, steps=200, B=512):
             "ms_per_step_at_peak": flops / (peak * 1e12) * 1e3 if peak else None}
 
 
+def cufft_comparison(torch, n=64, C=8, reps=20):
+    """For comparison only (not a product path): the same zero-padded Hockney convolution as one kick's
+    x / (y, z) / inverse-x kernels, done by cuFFT through torch.fft: the C channels of an n^3 density in a
+    (2n)^3 zero-padded FP32 buffer, batched R2C, times a real (2n, 2n, n+1) spectrum, C2R. Timed with
+    CUDA events on the current stream; the zero padding and the extraction of the n^3 result are not
+    timed (the library's kernels do them inside their passes)."""
+    M = 2 * n
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.zeros((C, M, M, M), device="cuda", dtype=torch.float32)
+    x[:, :n, :n, :n] = torch.randn((C, n, n, n), device="cuda", generator=g)
+    G = torch.rand((M, M, M // 2 + 1), device="cuda", generator=g)
+
+    def conv():
+        X = torch.fft.rfftn(x, dim=(1, 2, 3))
+        X *= G
+        return torch.fft.irfftn(X, s=(M, M, M), dim=(1, 2, 3))
+
+    for _ in range(3):
+        conv()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        conv()
+    e1.record()
+    torch.cuda.synchronize()
+    return {"what": f"cuFFT (torch.fft) R2C + spectrum product + C2R of {C} channels on the {M}^3 zero-padded "
+                    f"grid, comparison only", "ms_per_convolution": e0.elapsed_time(e1) / reps}
+
+
 def run_native(args):
     import torch
 
@@ -748,6 +779,13 @@ def run_native(args):
         pipe = pipe2d(adpic, I, torch, 1_048_576, 256)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_surrogate:
         surr = surrogate_training(adpic, peaks)
+    if rank == 0 and kernels is not None and "fft" in kernels:
+        try:
+            cf = cufft_comparison(torch, w.grid[0], C)
+            cf["ours_ms_per_convolution"] = kernels["fft"]["ms_per_launch"]
+            kernels["fft_vs_cufft"] = cf
+        except RuntimeError as e:          # torch built without cuFFT: the comparison is skipped
+            kernels["fft_vs_cufft"] = {"unavailable": str(e).splitlines()[0]}
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_track:
         fma64 = fp64["fma_peaks_tflops"]["fp64"] if fp64 else adpic.ad_pic_fma_peak(adpic.AD_PIC_FP64)
         track = tracking(adpic, 7, args.track_particles, 10, 100, fma64)

@@ -262,12 +262,12 @@ struct Impl {
         tbegin(h, K_MISC, cap);
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
         tend(h, K_MISC, cap);
-        cudaStreamWaitEvent(s, h->ev_join, 0);
         tbegin(h, K_FFT, cap);
         FFTDims d = dims(h);
+        // the forward x pass runs while the Green's spectrum is still being made
         launch_fft_conv<T>((T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
-                           (const Ord<T>*)h->chmax, s);
+                           (const Ord<T>*)h->chmax, s, h->ev_join);
         tend(h, K_FFT, cap);
         tbegin(h, K_FIELD, cap);
         launch_field<T>((const T*)h->phi, h->geom, h->nx, h->ny, h->nz, CP, (T*)h->E, s);

@@ -328,10 +328,13 @@ template <typename T>
 int fft_slab_yt(const FFTDims& d);
 template <typename T>
 size_t fft_slab_smem(const FFTDims& d, int which = -1);
-// rho is read and left zero (ready for the next deposit)
+// rho is read and left zero (ready for the next deposit). `spec`: an event
+// the stream waits for after the forward x pass, before Ghat is first read
+// (the spectrum made on another stream); null for none
 template <typename T>
 void launch_fft_conv(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d,
-                     const V2<T>* twx, const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s);
+                     const V2<T>* twx, const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s,
+                     cudaEvent_t spec = nullptr);
 template <typename T>
 void launch_field(const T* phi, const GeomDev* geom, int nx, int ny, int nz, int CP, T* E, cudaStream_t s);
 

@@ -45,10 +45,11 @@ struct Conv {
 
 template <typename T, int MX, int MY, int MZ>
 void conv_run(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
-              const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+              const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     const int rows = d.ny * d.nz;
     const unsigned gx = (unsigned)((rows + kRowsX - 1) / kRowsX);
     fftx_fwd_kernel<T, MX><<<gx, 256, Conv<T, MX>::sm_x(d), s>>>(rho, X1, d, twx, chmax);
+    if (spec) cudaStreamWaitEvent(s, spec, 0);
     ffty_kernel<T, MY, false><<<dim3(d.Mx / kTile, d.nz, d.npair), 256, Conv<T, MY>::sm_col(), s>>>(X1, X2, d, twy);
     fftz_kernel<T, MZ><<<dim3(d.Mx / kTile, d.My, d.npair), 256, Conv<T, MZ>::sm_col(), s>>>(X2, Ghat, d, twz);
     ffty_kernel<T, MY, true><<<dim3(d.Mx / kTile, d.nz, d.npair), 256, Conv<T, MY>::sm_col(), s>>>(X2, X1, d, twy);
@@ -56,25 +57,25 @@ void conv_run(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims
 }
 template <typename T, int MX, int MY>
 void conv_z(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
-            const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+            const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     switch (d.Mz) {
-        case 16: conv_run<T, MX, MY, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 32: conv_run<T, MX, MY, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 64: conv_run<T, MX, MY, 64>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 128: conv_run<T, MX, MY, 128>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        default: conv_run<T, MX, MY, 256>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 16: conv_run<T, MX, MY, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 32: conv_run<T, MX, MY, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 64: conv_run<T, MX, MY, 64>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 128: conv_run<T, MX, MY, 128>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        default: conv_run<T, MX, MY, 256>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
     }
 }
 
 template <typename T, int MX>
 void conv_y(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
-            const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+            const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     switch (d.My) {
-        case 16: conv_z<T, MX, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 32: conv_z<T, MX, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 64: conv_z<T, MX, 64>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 128: conv_z<T, MX, 128>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        default: conv_z<T, MX, 256>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 16: conv_z<T, MX, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 32: conv_z<T, MX, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 64: conv_z<T, MX, 64>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 128: conv_z<T, MX, 128>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        default: conv_z<T, MX, 256>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
     }
 }
 
@@ -134,53 +135,54 @@ size_t fft_slab_smem(const FFTDims& d, int which) {
 
 template <typename T, int MX, int MY, int MZ>
 void conv_slab(T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
-               const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+               const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     const int yt = slab_yt<T>(d);
     const dim3 gx((unsigned)(d.ny / yt), (unsigned)d.nz);
     fftx_fwd_t_kernel<T, MX><<<gx, 256, sm_fwd_t<T>(d, yt), s>>>(rho, X1, d, twx, chmax, yt);
+    if (spec) cudaStreamWaitEvent(s, spec, 0);
     fftyz_kernel<T, MY, MZ><<<dim3((unsigned)d.Mx, (unsigned)d.npair), 512, sm_yz<T>(d), s>>>(X1, Ghat, d, twy, twz);
     fftx_inv_t_kernel<T, MX><<<gx, 256, sm_inv_t<T>(d, yt), s>>>(X1, phi, d, twx, chmax, yt);
 }
 template <typename T, int MX, int MY>
 void conv_slab_z(T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
-                 const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+                 const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     switch (d.Mz) {
-        case 16: conv_slab<T, MX, MY, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 32: conv_slab<T, MX, MY, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 64: conv_slab<T, MX, MY, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        default: conv_slab<T, MX, MY, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 16: conv_slab<T, MX, MY, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 32: conv_slab<T, MX, MY, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 64: conv_slab<T, MX, MY, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        default: conv_slab<T, MX, MY, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
     }
 }
 template <typename T, int MX>
 void conv_slab_y(T* rho, V2<T>* X1, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx, const V2<T>* twy,
-                 const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+                 const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     switch (d.My) {
-        case 16: conv_slab_z<T, MX, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 32: conv_slab_z<T, MX, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 64: conv_slab_z<T, MX, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        default: conv_slab_z<T, MX, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 16: conv_slab_z<T, MX, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 32: conv_slab_z<T, MX, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 64: conv_slab_z<T, MX, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        default: conv_slab_z<T, MX, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
     }
 }
 
 template <typename T>
 void launch_fft_conv(T* rho, V2<T>* X1, V2<T>* X2, const T* Ghat, T* phi, const FFTDims& d, const V2<T>* twx,
-                     const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s) {
+                     const V2<T>* twy, const V2<T>* twz, const Ord<T>* chmax, cudaStream_t s, cudaEvent_t spec) {
     if (fft_slab_path<T>(d)) {
         switch (d.Mx) {
-            case 16: conv_slab_y<T, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-            case 32: conv_slab_y<T, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-            case 64: conv_slab_y<T, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-            case 128: conv_slab_y<T, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-            default: conv_slab_y<T, 256>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+            case 16: conv_slab_y<T, 16>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+            case 32: conv_slab_y<T, 32>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+            case 64: conv_slab_y<T, 64>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+            case 128: conv_slab_y<T, 128>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+            default: conv_slab_y<T, 256>(rho, X1, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
         }
         return;
     }
     switch (d.Mx) {
-        case 16: conv_y<T, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 32: conv_y<T, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 64: conv_y<T, 64>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        case 128: conv_y<T, 128>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
-        default: conv_y<T, 256>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s); break;
+        case 16: conv_y<T, 16>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 32: conv_y<T, 32>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 64: conv_y<T, 64>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        case 128: conv_y<T, 128>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
+        default: conv_y<T, 256>(rho, X1, X2, Ghat, phi, d, twx, twy, twz, chmax, s, spec); break;
     }
 }
 
@@ -216,10 +218,11 @@ void setup_fft() {
 }
 
 template void launch_fft_conv<float>(float*, float2*, float2*, const float*, float*, const FFTDims&,
-                                     const float2*, const float2*, const float2*, const unsigned int*, cudaStream_t);
+                                     const float2*, const float2*, const float2*, const unsigned int*, cudaStream_t,
+                                     cudaEvent_t);
 template void launch_fft_conv<double>(double*, double2*, double2*, const double*, double*, const FFTDims&,
                                       const double2*, const double2*, const double2*, const unsigned long long*,
-                                      cudaStream_t);
+                                      cudaStream_t, cudaEvent_t);
 template bool fft_slab_path<float>(const FFTDims&);
 template int fft_slab_yt<float>(const FFTDims&);
 template size_t fft_slab_smem<float>(const FFTDims&, int);
