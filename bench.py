@@ -578,6 +578,36 @@ def pipe2d(adpic, I, torch, n_part, cells, periods=1):
     return out
 
 
+def energy_slot_cost(adpic, I, torch, w, nrm, stream, periods=3):
+    """The kinetic energy as a dual input (slot 0, lattice in slots 1-6) on the headline workload:
+    period time against the same run without it (the energy adds one Green's spectrum on the side
+    stream and one single-pair convolution per kick). CUDA events on the library's stream."""
+    import dataclasses
+
+    lat = I.Lattice(deriv_slot=(-1, 1, 2, 3, 4, 5, 6))
+    out = {"workload": f"{w.name} with the energy in slot 0 and the lattice in slots 1-6, FP32-mixed"}
+    for name, slot in (("without", -1), ("with", 0)):
+        b = dataclasses.replace(w.beam, energy_slot=slot)
+        sim = adpic.ADPIC(w.grid, w.n_particles, w.n_deriv, adpic.AD_PIC_FP32_MIXED)
+        sim.set_stream(stream.cuda_stream)
+        sim.set_beam(b, nrm)
+        sim.set_lattice(lat)
+        sim.run(w.kicks_per_period)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(periods):
+            sim.run(w.kicks_per_period)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / periods
+        sim.close()
+        out[name] = {"ms_per_step": ms, "value": w.n_particles * w.kicks_per_period / (ms / 1000.0)}
+    out["cost"] = out["with"]["ms_per_step"] / out["without"]["ms_per_step"]
+    return out
+
+
 def surrogate_training(adpic, peaks, steps=200, B=512):
     """The surrogate's device-resident training (7 -> 256 x 3 -> 2, GELU, B samples x 8 rows of
     primal and input tangents per step, Sobolev loss, Adam): ms per step by CUDA events inside the
@@ -774,7 +804,9 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"{kicks_cpu} kicks of the {w.name} workload on the host cores ({dt:.1f} s)"}
 
-    large = batch = track = pipe = surr = None
+    large = batch = track = pipe = surr = energy = None
+    if rank == 0 and w.name == "fodo_1m_64" and not args.no_energy:
+        energy = energy_slot_cost(adpic, I, torch, w, nrm, stream)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_pipe2d:
         pipe = pipe2d(adpic, I, torch, 1_048_576, 256)
     if rank == 0 and w.name == "fodo_1m_64" and not args.no_surrogate:
@@ -801,7 +833,8 @@ def run_native(args):
                 "roofline": roof, "roofline_step": roof_step, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64, "accuracy": acc,
                 "kernels": kernels, "large_instance": large, "batched_scan": batch,
-                "single_particle_tracking": track, "pipe2d": pipe, "surrogate_training": surr}
+                "single_particle_tracking": track, "pipe2d": pipe, "surrogate_training": surr,
+                "energy_slot": energy}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -845,6 +878,7 @@ def main():
     ap.add_argument("--no-track", action="store_true", help="skip the single-particle tracking sub-result")
     ap.add_argument("--no-pipe2d", action="store_true", help="skip the 2D conducting-pipe sub-result")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate training sub-result")
+    ap.add_argument("--no-energy", action="store_true", help="skip the energy-slot sub-result")
     ap.add_argument("--fp64-only", action="store_true",
                     help="run only the plain FP64 path (one untimed period, then --steps periods)")
     ap.add_argument("--track-particles", type=int, default=65536)

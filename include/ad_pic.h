@@ -86,7 +86,14 @@ typedef struct {
    beta_y, eps_y), eps the geometric rms emittance, or -1.
    charge_deriv_slot is the slot of the bunch charge (Sec. 4: the beam
    current as an AD variable) or -1: the macroparticle charge Q / N is then a
-   dual number in the deposit, so every field and kick carries d/dQ. */
+   dual number in the deposit, so every field and kick carries d/dQ.
+   energy_deriv_slot is the slot of the kinetic energy (Sec. 4: beam
+   parameters as AD variables) or -1: gamma0, beta0 gamma0, B rho and the
+   kick constants are then duals of the energy, and so is the rest-frame z
+   spacing gamma0 hz, which enters the Green's function (one more convolution
+   per kick: dG/dE of channel 0 into the energy channel) and E_z. It must
+   differ from charge_deriv_slot. Only ad_pic_set_beam accepts it; the batched
+   runtime and the 2D pipe return AD_PIC_ERR_UNSUPPORTED for it. */
 typedef struct {
     double kinetic_eV, mass_eV, charge_e, bunch_charge_C;
     double eps_n[3];   /* normalised rms emittances (m rad), > 0 */
@@ -94,6 +101,7 @@ typedef struct {
     double beta[3];    /* m, > 0 */
     int twiss_deriv_slot[6];
     int charge_deriv_slot;
+    int energy_deriv_slot;
 } ad_pic_beam;
 
 /* Create a handle for n_particles in [1, 2^31 - 1] macroparticles (particle

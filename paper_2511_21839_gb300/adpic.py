@@ -32,7 +32,8 @@ class ad_pic_lattice(ct.Structure):
 class ad_pic_beam(ct.Structure):
     _fields_ = [("kinetic_eV", ct.c_double), ("mass_eV", ct.c_double), ("charge_e", ct.c_double),
                 ("bunch_charge_C", ct.c_double), ("eps_n", ct.c_double * 3), ("alpha", ct.c_double * 3),
-                ("beta", ct.c_double * 3), ("twiss_deriv_slot", ct.c_int * 6), ("charge_deriv_slot", ct.c_int)]
+                ("beta", ct.c_double * 3), ("twiss_deriv_slot", ct.c_int * 6), ("charge_deriv_slot", ct.c_int),
+                ("energy_deriv_slot", ct.c_int)]
 
 
 AD_PIC_DRIFT = 0
@@ -491,7 +492,7 @@ def make_beam(b) -> ad_pic_beam:
     """ad_pic_beam from any object with the fields of inputs.Beam."""
     return ad_pic_beam(b.kinetic_eV, b.mass_eV, b.charge_e, b.bunch_charge_C, (ct.c_double * 3)(*b.eps_n),
                        (ct.c_double * 3)(*b.alpha), (ct.c_double * 3)(*b.beta), (ct.c_int * 6)(*b.twiss_slot),
-                       int(getattr(b, "charge_slot", -1)))
+                       int(getattr(b, "charge_slot", -1)), int(getattr(b, "energy_slot", -1)))
 
 
 def make_lattice(lat) -> ad_pic_lattice:

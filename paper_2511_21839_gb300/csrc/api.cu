@@ -148,8 +148,43 @@ struct Impl {
         return to_map(I);
     }
 
+    // The reference-particle constants as host duals of the kinetic energy E
+    // (slot eslot, Sec. 4: beam parameters as AD variables): gamma0 = 1 + E/m,
+    // beta0 gamma0 = sqrt(gamma0^2 - 1), p0 = beta0 gamma0 m c, B rho = p0/q,
+    // v0 = c beta0 gamma0 / gamma0, kappa_perp = q/(gamma0 p0 v0), kappa_z =
+    // q/(p0 v0). The value parts are the handle's constants; without an energy
+    // slot the derivative parts are zero.
+    struct EConst {
+        HD g0, g2, bg, brho, kperp, kz;
+    };
+    static EConst energy_consts(const ad_pic* h) {
+        EConst e;
+        if (h->eslot >= 0) {
+            const double mass_kg = h->mass_eV * kQE / (kC * kC);
+            const HD E = hvar((h->gamma0 - 1.0) * h->mass_eV, h->eslot);
+            e.g0 = hadd(hc(1.0), hmul(E, hc(1.0 / h->mass_eV)));
+            e.g2 = hmul(e.g0, e.g0);
+            e.bg = hsqrt(hadd(e.g2, hc(-1.0)));
+            const HD p0 = hmul(e.bg, hc(mass_kg * kC));
+            e.brho = hdiv(p0, hc(h->q));
+            const HD v0 = hmul(hdiv(e.bg, e.g0), hc(kC));
+            e.kperp = hdiv(hc(h->q), hmul(hmul(e.g0, p0), v0));
+            e.kz = hdiv(hc(h->q), hmul(p0, v0));
+        } else {
+            e.g0 = e.g2 = e.bg = e.brho = e.kperp = e.kz = hc(0.0);
+        }
+        e.g0.v[0] = h->gamma0;
+        e.g2.v[0] = h->gamma0 * h->gamma0;
+        e.bg.v[0] = h->beta0 * h->gamma0;
+        e.brho.v[0] = h->brho;
+        e.kperp.v[0] = h->kperp;
+        e.kz.v[0] = h->kz;
+        return e;
+    }
+
     // per-kick dual coefficients of one period
     static void build_coef(ad_pic* h) {
+        const EConst ec = energy_consts(h);
         const ad_pic_lattice& L = h->lat;
         const int len_param[5] = {0, 1, 3, 4, 6};
         const bool use_line = !h->line.empty();
@@ -174,17 +209,17 @@ struct Impl {
             } else if (e == 1 || e == 3) {
                 const int gi = e == 1 ? 0 : 1;
                 HD g = hvar(L.g[gi], L.deriv_slot[e == 1 ? 2 : 5]);
-                kx = hdiv(g, hc(h->brho));                   // k = q g / p0
+                kx = hdiv(g, ec.brho);                       // k = q g / p0 (B rho dual in the energy)
                 ky = hneg(kx);
             }
             HMap m;
             plane_map(kx, t, m.m[0]);
             plane_map(ky, t, m.m[1]);
             m.m[2][0] = hc(1.0);
-            m.m[2][1] = hdiv(t, hc(h->gamma0 * h->gamma0));   // z += t delta / gamma0^2
+            m.m[2][1] = hdiv(t, ec.g2);                   // z += t delta / gamma0^2
             m.m[2][2] = hc(0.0);
             m.m[2][3] = hc(1.0);
-            HD ap = hmul(hc(h->kperp), tau), az = hmul(hc(h->kz), tau);
+            HD ap = hmul(ec.kperp, tau), az = hmul(ec.kz, tau);
             K kk;
             for (int k = 0; k < CP; ++k) { kk.a[0][k] = (T)ap.v[k]; kk.a[1][k] = (T)ap.v[k]; kk.a[2][k] = (T)az.v[k]; }
             for (int j = 0; j < kicks_of(e); ++j, ++s) { halfm[s] = m; kc[s] = kk; }
@@ -231,6 +266,28 @@ struct Impl {
         return f;
     }
 
+    // The kinetic energy as a dual input (eslot): the spectrum of dG/dE after
+    // the Green's function on stream s, and the extra convolution (dG/dE) *
+    // rho_0 added to the energy channel of phi. rho_0 was copied into the
+    // two-channel records rho_e before the main convolution cleared rho; the
+    // main convolution has waited for the spectra.
+    static void green_energy(ad_pic* h, cudaStream_t s) {
+        launch_green_energy<T>(h->geom, h->nx, h->ny, h->nz, h->corner, h->corner_e, (T*)h->G, (T*)h->Gtmp,
+                               (T*)h->Ghat_e, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2],
+                               fft_slab_path<T>(dims(h)) ? 1 : 0, 1.0 / h->mass_eV, s);
+    }
+    static void energy_term(ad_pic* h, cudaStream_t s) {
+        const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
+        FFTDims de = dims(h);
+        de.C = 2;
+        de.CP = 2;
+        de.npair = 1;
+        launch_fft_conv<T>((T*)h->rho_e, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat_e, (T*)h->phi_e, de,
+                           (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
+                           (const Ord<T>*)h->chmax, s);
+        launch_energy_add<T>((const T*)h->phi_e, nodes, (T*)h->phi, CP, h->eslot + 1, s);
+    }
+
     // deposit -> Green -> convolution -> field for the current state. The grid
     // geometry was derived by the last block of the kernel before (the push
     // that tracked the extrema, or the half map at a run or period start).
@@ -245,6 +302,7 @@ struct Impl {
         launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
                         (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2],
                         fft_slab_path<T>(dims(h)) ? 1 : 0, h->side);
+        if (h->eslot >= 0) green_energy(h, h->side);
         tend(h, K_GREEN, cap, h->side);
         cudaEventRecord(h->ev_join, h->side);
         tbegin(h, K_DEPOSIT, cap);
@@ -261,6 +319,7 @@ struct Impl {
         cudaEventRecord(h->ev_scan, h->side);
         tbegin(h, K_MISC, cap);
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
+        if (h->eslot >= 0) launch_energy_copy<T>((const T*)h->rho, CP, nodes, (T*)h->rho_e, s);
         tend(h, K_MISC, cap);
         tbegin(h, K_FFT, cap);
         FFTDims d = dims(h);
@@ -268,9 +327,12 @@ struct Impl {
         launch_fft_conv<T>((T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
                            (const Ord<T>*)h->chmax, s, h->ev_join);
+        if (h->eslot >= 0) energy_term(h, s);
         tend(h, K_FFT, cap);
         tbegin(h, K_FIELD, cap);
         launch_field<T>((const T*)h->phi, h->geom, h->nx, h->ny, h->nz, CP, (T*)h->E, s);
+        if (h->eslot >= 0)
+            launch_energy_field<T>((T*)h->E, nodes, CP, h->eslot + 1, 1.0 / (h->mass_eV * h->gamma0), s);
         tend(h, K_FIELD, cap);
         cudaStreamWaitEvent(s, h->ev_scan, 0);     // the push reads the cell offsets
     }
@@ -283,8 +345,13 @@ struct Impl {
 
     // kernels launched by one enqueue_field (deposit 1, scan 2, push slots 1,
     // chmax 1, Green's function 4: corners, cell averages with the first DCT
-    // pass, two DCT passes; convolution 3 or 5, field 1)
-    static int field_launches(ad_pic* h) { return 10 + fft_conv_launches(fft_slab_path<T>(dims(h))); }
+    // pass, two DCT passes; convolution 3 or 5, field 1); with the energy slot
+    // also its Green's spectrum (4), the copy of rho_0, its convolution, the
+    // add into phi and the E_z term
+    static int field_launches(ad_pic* h) {
+        const int conv = fft_conv_launches(fft_slab_path<T>(dims(h)));
+        return 10 + conv + (h->eslot >= 0 ? 7 + conv : 0);
+    }
 
     // the launch sequence of one run; returns the number of moment records
     // `from` is the buffer holding the particles at the start; each push moves
@@ -447,6 +514,19 @@ struct Impl {
         return 2 * e;
     }
 
+    // the energy term's buffers, once per handle
+    static int alloc_energy(ad_pic* h) {
+        if (h->Ghat_e) return AD_PIC_OK;
+        const int64_t nodes = (int64_t)h->nx * h->ny * h->nz;
+        const int64_t gnodes = (int64_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
+        int r = 0;
+        r |= dalloc(h, (void**)&h->corner_e, sizeof(double) * (h->nx + 2) * (h->ny + 2) * (h->nz + 2));
+        r |= dalloc(h, &h->rho_e, sizeof(T) * nodes * 2);
+        r |= dalloc(h, &h->phi_e, sizeof(T) * nodes * 2);
+        if (!r) r |= dalloc(h, &h->Ghat_e, sizeof(T) * gnodes);    // last: its pointer marks success
+        return r ? AD_PIC_ERR_OOM : AD_PIC_OK;
+    }
+
     static int set_beam(ad_pic* h, const ad_pic_beam* b, const double* normals) {
         h->q = b->charge_e * kQE;
         const double mass_kg = b->mass_eV * kQE / (kC * kC);
@@ -459,10 +539,17 @@ struct Impl {
         h->kz = h->q / (h->p0 * v0);
         h->qm = b->bunch_charge_C / (double)h->N;
         h->qslot = b->charge_deriv_slot;
+        h->mass_eV = b->mass_eV;
+        h->eslot = b->energy_deriv_slot;
+        if (h->eslot >= 0 && alloc_energy(h)) {
+            h->eslot = -1;
+            return AD_PIC_ERR_OOM;
+        }
         h->beam_set = true;
         h->coef_dirty = true;
         free_graphs(h);
         if (!normals) return AD_PIC_OK;
+        const EConst ec = energy_consts(h);
         // per-plane dual coefficients u = a n1, p = b (n2 - alpha n1)
         std::vector<double> coef(3 * 3 * CP + 6, 0.0);
         const double bg = h->beta0 * h->gamma0;
@@ -471,7 +558,8 @@ struct Impl {
             const int sb = pl < 2 ? b->twiss_deriv_slot[3 * pl + 1] : -1;
             const int se = pl < 2 ? b->twiss_deriv_slot[3 * pl + 2] : -1;
             HD al = hvar(b->alpha[pl], sa), be = hvar(b->beta[pl], sb);
-            HD ep = hvar(b->eps_n[pl] / bg, se);
+            // geometric emittance eps_n / (beta0 gamma0), dual in the energy unless eps is a slot itself
+            HD ep = (h->eslot >= 0 && se < 0) ? hdiv(hc(b->eps_n[pl]), ec.bg) : hvar(b->eps_n[pl] / bg, se);
             HD a = hsqrt(hmul(ep, be)), bb = hsqrt(hdiv(ep, be));
             for (int k = 0; k < CP; ++k) {
                 coef[(pl * 3 + 0) * CP + k] = a.v[k];
@@ -588,13 +676,16 @@ struct Impl {
             return check_err(h);
         }
         launch_chmax<T>((const T*)h->rho, nodes, CP, (Ord<T>*)h->chmax, s);
+        if (h->eslot >= 0) launch_energy_copy<T>((const T*)h->rho, CP, nodes, (T*)h->rho_e, s);
         launch_green<T>(h->geom, h->nx, h->ny, h->nz, sizeof(T) == 8, h->corner, (T*)h->G, (T*)h->Gtmp,
                         (T*)h->Ghat, (const T*)h->dct[0], (const T*)h->dct[1], (const T*)h->dct[2],
                         fft_slab_path<T>(dims(h)) ? 1 : 0, s);
+        if (h->eslot >= 0) green_energy(h, s);
         FFTDims d = dims(h);
         launch_fft_conv<T>((T*)h->rho, (V2<T>*)h->X1, (V2<T>*)h->X2, (const T*)h->Ghat, (T*)h->phi, d,
                            (const V2<T>*)h->tw[0], (const V2<T>*)h->tw[1], (const V2<T>*)h->tw[2],
                            (const Ord<T>*)h->chmax, s);
+        if (h->eslot >= 0) energy_term(h, s);
         if (which == 2) {
             buf.resize(nodes * CP);
             CK(cudaMemcpyAsync(buf.data(), h->phi, sizeof(T) * buf.size(), cudaMemcpyDeviceToHost, s));
@@ -603,6 +694,8 @@ struct Impl {
             return check_err(h);
         }
         launch_field<T>((const T*)h->phi, h->geom, h->nx, h->ny, h->nz, CP, (T*)h->E, s);
+        if (h->eslot >= 0)
+            launch_energy_field<T>((T*)h->E, nodes, CP, h->eslot + 1, 1.0 / (h->mass_eV * h->gamma0), s);
         if (which == 3) {
             buf.resize(nodes * 3 * CP);
             CK(cudaMemcpyAsync(buf.data(), h->E, sizeof(T) * buf.size(), cudaMemcpyDeviceToHost, s));
@@ -636,6 +729,8 @@ struct Impl {
         int64_t N, kick, hist_len, n_line;
         double consts[8];
         ad_pic_lattice lat;
+        int32_t eslot, pad;
+        double mass_eV;
     };
     static constexpr size_t kChunk = (size_t)64 << 20;   // bytes staged on the host at a time
 
@@ -643,7 +738,7 @@ struct Impl {
         if (!h->particles_set) return AD_PIC_ERR_STATE;
         FileHeader hd{};
         std::memcpy(hd.magic, "ADPICCK", 8);
-        hd.version = 2;
+        hd.version = 3;
         hd.elem = sizeof(T);
         hd.prec = h->prec; hd.n_deriv = h->P; hd.chans = C; hd.chans_padded = CP;
         hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz;
@@ -654,6 +749,8 @@ struct Impl {
         const double k[8] = {h->gamma0, h->beta0, h->p0, h->brho, h->kperp, h->kz, h->qm, h->q};
         std::memcpy(hd.consts, k, sizeof(k));
         hd.lat = h->lat;
+        hd.eslot = h->eslot;
+        hd.mass_eV = h->mass_eV;
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return AD_PIC_ERR_CUDA;
         FILE* f = std::fopen(path, "wb");
         if (!f) return AD_PIC_ERR_IO;
@@ -685,7 +782,7 @@ struct Impl {
         if (!f) return AD_PIC_ERR_IO;
         FileHeader hd{};
         int rc = AD_PIC_OK;
-        if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "ADPICCK", 8) != 0 || hd.version != 2)
+        if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "ADPICCK", 8) != 0 || hd.version != 3)
             rc = AD_PIC_ERR_IO;
         else if (hd.elem != sizeof(T) || hd.prec != h->prec || hd.n_deriv != h->P || hd.nx != h->nx || hd.ny != h->ny ||
                  hd.nz != h->nz || hd.N != h->N || hd.hist_len < 0 || hd.hist_len % (15 * C) != 0 || hd.n_line < 0 ||
@@ -731,6 +828,13 @@ struct Impl {
         h->gamma0 = hd.consts[0]; h->beta0 = hd.consts[1]; h->p0 = hd.consts[2]; h->brho = hd.consts[3];
         h->kperp = hd.consts[4]; h->kz = hd.consts[5]; h->qm = hd.consts[6]; h->q = hd.consts[7];
         h->qslot = hd.qslot >= -1 && hd.qslot < h->P ? hd.qslot : -1;
+        h->mass_eV = hd.mass_eV;
+        h->eslot = hd.eslot >= 0 && hd.eslot < h->P && hd.mass_eV > 0 ? hd.eslot : -1;
+        if (h->eslot >= 0 && alloc_energy(h)) {
+            h->eslot = -1;
+            h->particles_set = false;
+            return AD_PIC_ERR_OOM;
+        }
         h->beam_set = (hd.flags & 1) != 0;
         h->lattice_set = (hd.flags & 2) != 0;
         h->lat = hd.lat;
@@ -911,6 +1015,9 @@ int ad_pic_set_beam(ad_pic* h, const ad_pic_beam* b, const double* normals) {
     for (int j = 0; j < 6; ++j)
         if (b->twiss_deriv_slot[j] < -1 || b->twiss_deriv_slot[j] >= h->P) return AD_PIC_ERR_INVALID_ARG;
     if (b->charge_deriv_slot < -1 || b->charge_deriv_slot >= h->P) return AD_PIC_ERR_INVALID_ARG;
+    if (b->energy_deriv_slot < -1 || b->energy_deriv_slot >= h->P ||
+        (b->energy_deriv_slot >= 0 && b->energy_deriv_slot == b->charge_deriv_slot))
+        return AD_PIC_ERR_INVALID_ARG;
     DISPATCH(h, I::set_beam(h, b, normals));
 }
 

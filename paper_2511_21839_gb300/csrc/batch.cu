@@ -979,6 +979,7 @@ int ad_pic_batch_create(int n_inst, const ad_pic_grid* grids, const int64_t* n_p
 int ad_pic_batch_set_beam(ad_pic_batch* b, int inst, const ad_pic_beam* beam, const double* normals) {
     if (!b || inst < 0 || inst >= b->n_inst || !beam) return AD_PIC_ERR_INVALID_ARG;
     if (beam->charge_deriv_slot != -1) return AD_PIC_ERR_UNSUPPORTED;   // the batched deposit has no charge channel
+    if (beam->energy_deriv_slot != -1) return AD_PIC_ERR_UNSUPPORTED;   // nor the energy term of the convolution
     batch_free_graphs(b);
     return ad_pic_set_beam(b->h[inst], beam, normals);
 }

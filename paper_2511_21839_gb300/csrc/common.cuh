@@ -313,6 +313,18 @@ void launch_green(const GeomDev* geom, int nx, int ny, int nz, bool exact, doubl
                   T* Ghat, const T* dct_x, const T* dct_y, const T* dct_z, int order, cudaStream_t s);
 template <typename T>
 void setup_green();
+// the kinetic energy as a dual input: the spectrum of dG/dE (after launch_green
+// on the same stream), and the extra convolution's input and output records
+template <typename T>
+void launch_green_energy(const GeomDev* geom, int nx, int ny, int nz, const double* corner, double* corner_e, T* G,
+                         T* Gtmp, T* Ghat_e, const T* dct_x, const T* dct_y, const T* dct_z, int order,
+                         double inv_mass_eV, cudaStream_t s);
+template <typename T>
+void launch_energy_copy(const T* rho, int CP, int64_t nodes, T* rho_e, cudaStream_t s);
+template <typename T>
+void launch_energy_add(const T* phi_e, int64_t nodes, T* phi, int CP, int ce, cudaStream_t s);
+template <typename T>
+void launch_energy_field(T* E, int64_t nodes, int CP, int ce, double r, cudaStream_t s);
 template <typename T>
 void setup_fft();
 // twx/twy/twz: exp(-2 pi i j / M) for j < M of each axis (M = 2n)

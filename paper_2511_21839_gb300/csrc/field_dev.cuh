@@ -253,6 +253,30 @@ static __global__ void __launch_bounds__(64) green_corner_strided_kernel(const G
     }
 }
 
+// dF/dz of the antiderivative above, in closed form (differentiating F's six
+// terms and collecting): y log(x + r) + x log(y + r) - z atan(x y / (z r))
+// + z^2 (x + y)(x y + z^2) / ((x^2 + z^2)(y^2 + z^2)).
+__device__ __forceinline__ double igf_Fz(double x, double y, double z) {
+    const double r = sqrt(x * x + y * y + z * z);
+    const double z2 = z * z;
+    return y * log(x + r) + x * log(y + r) - z * atan(x * y / (z * r)) +
+           z2 * (x + y) * (x * y + z2) / ((x * x + z2) * (y * y + z2));
+}
+
+// The kinetic energy as a dual input moves the rest-frame spacing hzr =
+// gamma0 hz and with it every corner z = (k - 1/2) hzr: FE holds
+// dF/dhzr = (k - 1/2) dF/dz at the corners of the same near box as F.
+static __global__ void __launch_bounds__(64) green_corner_dz_kernel(const GeomDev* __restrict__ g, int nx, int ny,
+                                                                  int nz, double* __restrict__ FE) {
+    const int ex = g->R[0] + 2, ey = g->R[1] + 2, ez = g->R[2] + 2;
+    const int cx = nx + 2, cy = ny + 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ex * ey * ez; t += gridDim.x * blockDim.x) {
+        const int i = t % ex, j = (t / ex) % ey, k = t / (ex * ey);
+        FE[((int64_t)k * cy + j) * cx + i] =
+            (k - 0.5) * igf_Fz((i - 0.5) * g->hr[0], (j - 0.5) * g->hr[1], (k - 0.5) * g->hr[2]);
+    }
+}
+
 // Cell average of 1/(4 pi eps0 r) over the cell centred at offset (i, j, k):
 // the 8-corner difference of F in FP64 inside the near box (every cell on
 // the FP64 path), else the Taylor expansion of the box average of a smooth
@@ -291,6 +315,68 @@ __device__ __forceinline__ T green_cell_value(const GeomDev* __restrict__ g, int
         s22 += t2[d] * t2[e] * (T)3 * ((T)35 * c2[d] * c2[e] - (T)5 * (c2[d] + c2[e]) + (T)1);
     }
     return (T)k4 * ir * ((T)1 + s2 / (T)24 + s4 / (T)1920 + s22 / (T)576);
+}
+
+// a first-order dual of one variable (value, derivative), for the far-field
+// expansion of the cell average differentiated in hzr (Eqs. 1-4)
+template <typename T>
+struct D1 {
+    T v, d;
+};
+template <typename T> __device__ __forceinline__ D1<T> operator+(D1<T> a, D1<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename T> __device__ __forceinline__ D1<T> operator-(D1<T> a, D1<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename T> __device__ __forceinline__ D1<T> operator*(D1<T> a, D1<T> b) {
+    return {a.v * b.v, a.d * b.v + a.v * b.d};
+}
+template <typename T> __device__ __forceinline__ D1<T> operator*(T c, D1<T> a) { return {c * a.v, c * a.d}; }
+template <typename T> __device__ __forceinline__ D1<T> d1_rsqrt(D1<T> a) {
+    const T r = rsqrt(a.v);
+    return {r, (T)-0.5 * r * r * r * a.d};
+}
+
+// dG/dhzr of the cell average at offset (i, j, k), the offset k hzr moving
+// with hzr: inside the near box from the corner values, G = c S / (hx hy hzr)
+// with S the 8-corner difference of F, so dG/dhzr = c (S' - S / hzr) /
+// (hx hy hzr) with S' the same difference of FE; outside it the expansion of
+// green_cell_value carried through in dual arithmetic.
+template <typename T>
+__device__ __forceinline__ T green_cell_dvalue(const GeomDev* __restrict__ g, int nx, int ny,
+                                               const double* __restrict__ F, const double* __restrict__ FE, int i,
+                                               int j, int k) {
+    const double hx = g->hr[0], hy = g->hr[1], hz = g->hr[2];
+    const double k4 = 1.0 / (4.0 * 3.14159265358979323846 * 8.8541878128e-12);
+    if (i <= g->R[0] && j <= g->R[1] && k <= g->R[2]) {
+        const int cx = nx + 2, cy = ny + 2;
+        auto diff = [&](const double* A) {
+            auto at = [&](int a, int b, int c) { return A[((int64_t)c * cy + b) * cx + a]; };
+            return at(i + 1, j + 1, k + 1) - at(i, j + 1, k + 1) - at(i + 1, j, k + 1) - at(i + 1, j + 1, k) +
+                   at(i, j, k + 1) + at(i, j + 1, k) + at(i + 1, j, k) - at(i, j, k);
+        };
+        const double S = diff(F), Sd = diff(FE);
+        return (T)(k4 * (Sd - S / hz) / (hx * hy * hz));
+    }
+    const D1<T> H = {(T)hz, (T)1};
+    const T x = (T)i * (T)hx, y = (T)j * (T)hy;
+    const D1<T> z = (T)k * H;
+    const D1<T> r2 = D1<T>{x * x + y * y, (T)0} + z * z;
+    const D1<T> ir = d1_rsqrt(r2);
+    const D1<T> ir2 = ir * ir;
+    const D1<T> c2[3] = {(x * x) * ir2, (y * y) * ir2, z * z * ir2};
+    const D1<T> t2[3] = {((T)hx * (T)hx) * ir2, ((T)hy * (T)hy) * ir2, H * H * ir2};
+    const D1<T> one = {(T)1, (T)0};
+    D1<T> s2 = {(T)0, (T)0}, s4 = {(T)0, (T)0}, s22 = {(T)0, (T)0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        s2 = s2 + t2[d] * ((T)3 * c2[d] - one);
+        s4 = s4 + (T)3 * (t2[d] * t2[d] * ((T)35 * (c2[d] * c2[d]) - (T)30 * c2[d] + (T)3 * one));
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int e = (d + 1) % 3;
+        s22 = s22 + (T)3 * (t2[d] * t2[e] * ((T)35 * (c2[d] * c2[e]) - (T)5 * (c2[d] + c2[e]) + one));
+    }
+    const D1<T> bracket = one + ((T)1 / (T)24) * s2 + ((T)1 / (T)1920) * s4 + ((T)1 / (T)576) * s22;
+    return ((T)k4 * (ir * bracket)).d;
 }
 
 // (i, j, k) of element l of DCT line ba in G's layout: order 0 G[z][y][x]
@@ -341,10 +427,13 @@ constexpr int kDctAcc = 8;
 // CELL: the lines are not read from `in` but computed here as the cell
 // averages of the Green's function (green_cell_value; lines of G's layout for
 // `order`), so the cell pass and the first DCT pass are one launch.
-template <typename T, int ACC = kDctAcc, bool CELL = false>
+// CELL == 2: the lines are the energy derivative dG/dE = dG/dhzr * hz / (m c^2)
+// (escale = 1 / (m c^2) in 1/eV) from F and FE (green_cell_dvalue).
+template <typename T, int ACC = kDctAcc, int CELL = 0>
 __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
     const int bx_, const int by_, const int bz_, const int nbx_, const GeomDev* __restrict__ g = nullptr,
-    int nx = 0, int ny = 0, int nz = 0, const double* __restrict__ F = nullptr, int order = 0) {
+    int nx = 0, int ny = 0, int nz = 0, const double* __restrict__ F = nullptr, int order = 0,
+    const double* __restrict__ FE = nullptr, double escale = 0.0) {
     extern __shared__ unsigned char smraw[];
     T* Ds = reinterpret_cast<T*>(smraw);            // [L][L]
     T* xs = Ds + L * L;                             // [kDctLines][L] (room for [kDctLines][L + 1])
@@ -367,14 +456,16 @@ __device__ __forceinline__ void dct_kernel_body(const T* __restrict__ in, T* __r
         }
     };
     stage(D, Ds, L * L, L * L);
-    if constexpr (CELL) {
+    if constexpr (CELL != 0) {
+        const T es = CELL == 2 ? (T)(g->h[2] * escale) : (T)0;
         for (int t = threadIdx.x; t < kDctLines * L; t += blockDim.x) {
             const int line = t / L, lp = t - line * L;
             T v = (T)0;
             if (line < nl) {
                 int i, j, k;
                 green_cell_index((int)(ba0 + line), lp, nx, ny, nz, order, i, j, k);
-                v = green_cell_value<T>(g, nx, ny, F, i, j, k);
+                if constexpr (CELL == 2) v = green_cell_dvalue<T>(g, nx, ny, F, FE, i, j, k) * es;
+                else v = green_cell_value<T>(g, nx, ny, F, i, j, k);
             }
             xs[t] = v;
         }
@@ -416,8 +507,17 @@ template <typename T, int ACC>
 static __global__ void cell_dct_kernel(T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
                                        const GeomDev* __restrict__ g, int nx, int ny, int nz,
                                        const double* __restrict__ F, int order) {
-    dct_kernel_body<T, ACC, true>(nullptr, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
-                                  (int)gridDim.x, g, nx, ny, nz, F, order);
+    dct_kernel_body<T, ACC, 1>(nullptr, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                               (int)gridDim.x, g, nx, ny, nz, F, order);
+}
+// dG/dE's cell values and the first DCT pass in one launch
+template <typename T, int ACC>
+static __global__ void cell_dct_energy_kernel(T* __restrict__ out, const T* __restrict__ D, int L, int64_t BA,
+                                              const GeomDev* __restrict__ g, int nx, int ny, int nz,
+                                              const double* __restrict__ F, const double* __restrict__ FE,
+                                              double escale, int order) {
+    dct_kernel_body<T, ACC, 2>(nullptr, out, D, L, BA, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                               (int)gridDim.x, g, nx, ny, nz, F, order, FE, escale);
 }
 
 // ------------------------------------------------------------------ field

@@ -21,6 +21,15 @@ struct ad_pic {
     bool beam_set = false, particles_set = false, lattice_set = false, coef_dirty = true;
     double gamma0 = 0, beta0 = 0, p0 = 0, brho = 0, kperp = 0, kz = 0, qm = 0, q = 0;
     int qslot = -1;               // derivative slot of the bunch charge (-1: constant)
+    int eslot = -1;               // derivative slot of the kinetic energy (-1: constant)
+    double mass_eV = 0;           // rest energy: d gamma0 / dE = 1 / mass_eV
+    // the energy's term of the convolution, allocated with the first energy slot:
+    // dF/dhzr at the Green's corners, the spectrum of dG/dE, and the two-channel
+    // records [node][2] of rho_0 and of (dG/dE) * rho_0
+    double* corner_e = nullptr;
+    void* Ghat_e = nullptr;
+    void* rho_e = nullptr;
+    void* phi_e = nullptr;
     ad_pic_lattice lat{};
     // a general beamline in place of the FODO period (empty: the FODO lattice)
     std::vector<ad_pic_element> line;

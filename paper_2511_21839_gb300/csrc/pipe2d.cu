@@ -549,6 +549,7 @@ int ad_pic2d_set_beam(ad_pic2d* h, const ad_pic_beam* b, double current_A, int c
     if (!h || !b || !(b->kinetic_eV > 0) || !(b->mass_eV > 0) || b->charge_e == 0 || !(current_A >= 0) ||
         current_deriv_slot < -1 || current_deriv_slot >= h->P)
         return AD_PIC_ERR_INVALID_ARG;
+    if (b->energy_deriv_slot != -1) return AD_PIC_ERR_UNSUPPORTED;   // the pipe's energy derivative is not built
     for (int d = 0; d < 2; ++d)
         if (!(b->eps_n[d] > 0) || !(b->beta[d] > 0) || !std::isfinite(b->alpha[d])) return AD_PIC_ERR_INVALID_ARG;
     const double q = b->charge_e * kQE;
