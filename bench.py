@@ -379,24 +379,31 @@ def class_times(sim, kicks, periods):
 
 def e2e_measure(args, sim, w, kicks, ws, barrier):
     """End to end through the public API with host buffers: every step uploads the dual state from
-    pinned host memory, runs the period and reads the emittances back."""
+    pinned host memory, runs the period and reads the emittances back. The FP32-mixed handle takes
+    its state in FP32 (ad_pic_set_particles_f32: the device state it holds either way), the FP64
+    handle in FP64."""
     import torch
 
-    state = torch.empty((6, w.n_particles, w.n_deriv + 1), dtype=torch.float64, pin_memory=True)
+    from paper_2511_21839_gb300 import adpic
+
+    f32 = sim.precision == adpic.AD_PIC_FP32_MIXED
+    state = torch.empty((6, w.n_particles, w.n_deriv + 1), dtype=torch.float32 if f32 else torch.float64,
+                        pin_memory=True)
     state.numpy()[...] = sim.get_particles()
+    upload = sim.set_particles_f32 if f32 else sim.set_particles
     for _ in range(2):
-        sim.set_particles(state.numpy())
+        upload(state.numpy())
         sim.run(kicks)
         sim.moments()
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        sim.set_particles(state.numpy())
+        upload(state.numpy())
         sim.run(kicks)
         sim.moments()
     barrier()
     e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
-    h2d = state.numel() * 8
+    h2d = state.numel() * state.element_size()
     d2h = 8 * (2 + 2 * w.n_deriv) + 15 * 8 * (w.n_deriv + 1) + 4
     return ws * w.n_particles * kicks / (e2e_ms / 1000.0), e2e_ms, h2d, d2h
 

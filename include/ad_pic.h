@@ -124,6 +124,12 @@ int ad_pic_set_beam(ad_pic* h, const ad_pic_beam* beam, const double* normals);
    only in ad_pic_set_particles. */
 int ad_pic_set_particles(ad_pic* h, const double* state);
 int ad_pic_get_particles(const ad_pic* h, double* state);
+/* The same upload from FP32 host data [6][N][C] for an AD_PIC_FP32_MIXED
+   handle: the device state is the same as ad_pic_set_particles gives for the
+   FP64 values of these floats, with half the bytes over the host link (C ==
+   its padded record size: one copy straight into the state). An FP64 handle
+   returns AD_PIC_ERR_UNSUPPORTED. */
+int ad_pic_set_particles_f32(ad_pic* h, const float* state);
 
 /* Set the lattice and recompute the per-kick dual map coefficients (FP64 on
    the host, Eqs. 1-4 applied to the quad matrices of Sec. 4). */

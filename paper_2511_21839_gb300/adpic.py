@@ -67,6 +67,7 @@ def lib():
             "ad_pic_create": (ct.c_int, [ct.POINTER(ad_pic_grid), ct.c_int64, ct.c_int, ct.c_int, ct.POINTER(vp)]),
             "ad_pic_set_beam": (ct.c_int, [vp, ct.POINTER(ad_pic_beam), dp]),
             "ad_pic_set_particles": (ct.c_int, [vp, dp]),
+            "ad_pic_set_particles_f32": (ct.c_int, [vp, ct.POINTER(ct.c_float)]),
             "ad_pic_get_particles": (ct.c_int, [vp, dp]),
             "ad_pic_set_lattice": (ct.c_int, [vp, ct.POINTER(ad_pic_lattice)]),
             "ad_pic_run": (ct.c_int, [vp, ct.c_int]),
@@ -172,6 +173,11 @@ def ad_pic_set_beam(h, beam: ad_pic_beam, normals=None):
 def ad_pic_set_particles(h, state):
     s = np.ascontiguousarray(state, dtype=np.float64)
     _ck("ad_pic_set_particles", lib().ad_pic_set_particles(h, _p(s)))
+
+
+def ad_pic_set_particles_f32(h, state):
+    s = np.ascontiguousarray(state, dtype=np.float32)
+    _ck("ad_pic_set_particles_f32", lib().ad_pic_set_particles_f32(h, s.ctypes.data_as(ct.POINTER(ct.c_float))))
 
 
 def ad_pic_get_particles(h, out):
@@ -531,6 +537,9 @@ class ADPIC:
 
     def set_particles(self, state):
         ad_pic_set_particles(self.h, state)
+
+    def set_particles_f32(self, state):
+        ad_pic_set_particles_f32(self.h, state)
 
     def get_particles(self):
         return ad_pic_get_particles(self.h, np.zeros((6, self.N, self.C)))

@@ -61,6 +61,20 @@ bool fault_launch() {
     return f && std::strcmp(f, "launch") == 0;
 }
 
+// FP32 records [6 N][C] -> [6 N][CP] (padding channels zero)
+__global__ void pad_records_f32_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t rows, int C,
+                                       int CP) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= rows * CP) return;
+    const int64_t r = t / CP;
+    const int k = (int)(t % CP);
+    dst[t] = k < C ? src[r * C + k] : 0.0f;
+}
+void pad_records_f32(const float* src, float* dst, int64_t N, int C, int CP, cudaStream_t s) {
+    const int64_t rows = 6 * N;
+    pad_records_f32_kernel<<<(unsigned)((rows * CP + 255) / 256), 256, 0, s>>>(src, dst, rows, C, CP);
+}
+
 int dalloc(ad_pic* h, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
     const int after = fault_alloc_after();
@@ -625,6 +639,30 @@ struct Impl {
         return AD_PIC_OK;
     }
 
+    static int set_particles_f32(ad_pic* h, const float* src) {
+        if (sizeof(T) != 4) return AD_PIC_ERR_UNSUPPORTED;
+        const size_t bytes = sizeof(float) * 6 * h->N * C;
+        cudaError_t e1;
+        if (C == CP) {
+            e1 = cudaMemcpyAsync(st(h), src, bytes, cudaMemcpyHostToDevice, h->stream);
+        } else {
+            double* tmp = nullptr;
+            int r = staging(h, &tmp);                // holds 6 N C doubles: room for the floats
+            if (r) return r;
+            e1 = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, h->stream);
+            if (e1 == cudaSuccess) pad_records_f32(reinterpret_cast<const float*>(tmp), (float*)st(h), h->N, C, CP,
+                                                   h->stream);
+        }
+        if (e1 == cudaSuccess) launch_iota(h->ids[h->cur], h->N, h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || cudaGetLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
+        h->particles_set = true;
+        h->kick = 0;
+        h->first_record = true;
+        h->hist.clear();
+        return AD_PIC_OK;
+    }
+
     static int get_particles(const ad_pic* hc_, double* dst) {
         ad_pic* h = const_cast<ad_pic*>(hc_);
         double* tmp = nullptr;
@@ -1024,6 +1062,11 @@ int ad_pic_set_beam(ad_pic* h, const ad_pic_beam* b, const double* normals) {
 int ad_pic_set_particles(ad_pic* h, const double* state) {
     if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
     DISPATCH(h, I::set_particles(h, state));
+}
+
+int ad_pic_set_particles_f32(ad_pic* h, const float* state) {
+    if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::set_particles_f32(h, state));
 }
 
 int ad_pic_get_particles(const ad_pic* h, double* state) {

@@ -1041,16 +1041,14 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
     const bool head = sv && (lane == 0 || prev != cell);
     const unsigned heads = __ballot_sync(FULL, head);
     const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    // the run's counting atomic is issued here and its result consumed after
+    // the sums below, so its round trip to L2 overlaps them
+    int base = 0;
     if (sb.key) {
         const unsigned after = heads & ~(0xffffffffu >> (31 - lane));
         const int end = after ? __ffs(after) - 2 : nv - 1;
-        int base = 0;
         if (head) base = atomicAdd(&sb.hist[cell], end - lane + 1);
-        base = __shfl_sync(FULL, base, start & 31);
-        if (sv) {
-            sb.key[ps] = cell;
-            sb.rank[ps] = base + lane - start;
-        }
+        if (sv) sb.key[ps] = cell;
     }
     // Two halves of the stencil, the nodes of the lower (c = 0) then the upper
     // (c = 1) z plane: the tile holds one half (4 node records per row), so it
@@ -1117,6 +1115,10 @@ __device__ __forceinline__ void deposit_tile_body(const T* __restrict__ state, i
                 }
             }
         }
+    }
+    if (sb.key) {
+        base = __shfl_sync(FULL, base, start & 31);
+        if (sv) sb.rank[ps] = base + lane - start;
     }
     if (bad) atomicOr(err, bad);
 }

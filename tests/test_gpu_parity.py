@@ -406,3 +406,29 @@ def test_large_instance_fp32_vs_fp64(adpic):
         e32 = o.emittance(hs[1][r])[:2]
         ev, ed = report(f"large instance period {r} fp32 vs fp64", e32[:, 0], e32[:, 1:], e64)
         assert ev < 1e-5 and ed < 1e-4, r
+
+
+@pytest.mark.parametrize("P", [7, 13])
+def test_fp32_upload_matches_the_fp64_upload(adpic, P):
+    """ad_pic_set_particles_f32 gives an FP32 handle the state ad_pic_set_particles gives it for the
+    same values (P = 7: straight copy; P = 13: records padded to 16 channels); an FP64 handle refuses
+    it (AD_PIC_ERR_UNSUPPORTED)."""
+    N, grid = 2003, (16, 16, 16)
+    o, sim, w, b = make_pair(adpic, N, grid, P, 1)
+    st = o.beam_init(I.normals(71, N))
+    st32 = st.astype(np.float32)
+    sim.set_particles(st32.astype(np.float64))
+    a = sim.get_particles()
+    sim.run(3)
+    ra = sim.history()
+    sim.set_particles_f32(st32)
+    g = sim.get_particles()
+    np.testing.assert_array_equal(g, a)
+    sim.run(3)
+    np.testing.assert_allclose(sim.history(), ra, rtol=1e-6, atol=1e-6 * np.abs(ra).max())
+    sim.close()
+    s64 = adpic.ADPIC(grid, N, P, 0)
+    with pytest.raises(adpic.AdPicError) as e:
+        s64.set_particles_f32(st32)
+    assert e.value.status == -8                          # AD_PIC_ERR_UNSUPPORTED
+    s64.close()
