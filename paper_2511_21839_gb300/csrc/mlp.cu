@@ -61,14 +61,38 @@ __device__ __forceinline__ void stage_tile(__nv_bfloat16 (*Xs)[BK + PADK], const
     }
 }
 
+__device__ __forceinline__ float phi(float x) { return 0.3989422804014327f * __expf(-0.5f * x * x); }
+__device__ __forceinline__ float Phi(float x) { return 0.5f * (1.f + erff(x * 0.7071067811865476f)); }
+
+// What the GEMM does with its 64 x 64 tile after the products, on the rows
+// r = s S + c of the Sobolev network (c = 0 primal, c > 0 the tangent of input
+// c - 1; a tile holds whole samples, 64 % S == 0). EPI_STORE stores C. The
+// others store C and also do, on the tile:
+//   EPI_HIDDEN  (forward, hidden layer) primal rows h += b, a = GELU(h) =
+//               h Phi(h); tangent rows a = GELU'(h_primal) h (no bias);
+//               a goes to act (BF16 rows of the next layer's input);
+//   EPI_OUTPUT  (forward, output layer) primal rows += b;
+//   EPI_BACKWARD (backward into a hidden layer's pre-activations, from dL/da
+//               of that layer's output; Hp its pre-activations) per sample and
+//               unit: dL/dh = G_p GELU'(h) + sum_c G_c t_c GELU''(h), the
+//               tangent rows G_c GELU'(h); FP32 in C, BF16 copy in act.
+enum { EPI_STORE = 0, EPI_HIDDEN, EPI_OUTPUT, EPI_BACKWARD };
+struct Epi {
+    int S;
+    const float* bias;
+    __nv_bfloat16* act;
+    const float* Hp;
+};
+
 // C[m][n] (ldc) = sum_k A(m, k) B(n, k) + beta * C[m][n], with
 // A(m, k) = A[m * sam + k * sak] and B(n, k) = B[n * sbn + k * sbk] (BF16).
 // blockIdx.z splits K: with split > 1 each slice writes its partial sum to
 // C + z * M * N (row-major [M][N], beta ignored) for split_reduce_kernel.
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, int kslice, const __nv_bfloat16* __restrict__ A,
+template <int EPI>
+__global__ void __launch_bounds__(128, 4) gemm_bf16_kernel(int M, int N, int K, int kslice, const __nv_bfloat16* __restrict__ A,
                                                         int64_t sam, int64_t sak, const __nv_bfloat16* __restrict__ B,
                                                         int64_t sbn, int64_t sbk, float* __restrict__ C, int64_t ldc,
-                                                        float beta, bool avk, bool avr, bool bvk, bool bvr) {
+                                                        float beta, bool avk, bool avr, bool bvk, bool bvr, Epi ep) {
     __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -121,19 +145,76 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, int
         }
         __syncthreads();
     }
+    if constexpr (EPI == EPI_STORE) {
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = m0 + wm + i * 16 + grp + (q >= 2 ? 8 : 0);
-                const int c = n0 + wn + j * 8 + tig * 2 + (q & 1);
-                if (r < M && c < N) {
-                    float* p = C + (int64_t)r * ldc + c;
-                    *p = acc[i][j][q] + (beta != 0.f ? beta * *p : 0.f);
+                for (int q = 0; q < 4; ++q) {
+                    const int r = m0 + wm + i * 16 + grp + (q >= 2 ? 8 : 0);
+                    const int c = n0 + wn + j * 8 + tig * 2 + (q & 1);
+                    if (r < M && c < N) {
+                        float* p = C + (int64_t)r * ldc + c;
+                        *p = acc[i][j][q] + (beta != 0.f ? beta * *p : 0.f);
+                    }
+                }
+    } else {
+        // the tile through shared memory, so each sample's rows meet
+        __shared__ float Cs[BM][BN + 1];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    Cs[wm + i * 16 + grp + (q >= 2 ? 8 : 0)][wn + j * 8 + tig * 2 + (q & 1)] = acc[i][j][q];
+        __syncthreads();
+        const int S = ep.S;
+        if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUTPUT) {
+            for (int t = threadIdx.x; t < BM * BN; t += blockDim.x) {
+                const int rl = t / BN, cl = t % BN;
+                const int r = m0 + rl, c = n0 + cl;
+                if (r >= M || c >= N) continue;
+                const int cs = rl % S;
+                const float v = Cs[rl][cl];
+                const int64_t at = (int64_t)r * ldc + c;
+                if (EPI == EPI_OUTPUT) {
+                    C[at] = cs == 0 ? v + ep.bias[c] : v;
+                } else if (cs == 0) {
+                    const float hh = v + ep.bias[c];
+                    C[at] = hh;
+                    ep.act[(int64_t)r * N + c] = __float2bfloat16(hh * Phi(hh));
+                } else {
+                    const float hp = Cs[rl - cs][cl] + ep.bias[c];
+                    const float d1 = Phi(hp) + hp * phi(hp);
+                    C[at] = v;
+                    ep.act[(int64_t)r * N + c] = __float2bfloat16(d1 * v);
                 }
             }
+        } else {
+            for (int t = threadIdx.x; t < (BM / S) * BN; t += blockDim.x) {
+                const int sl = t / BN, cl = t % BN;
+                const int rp = m0 + sl * S, c = n0 + cl;
+                if (rp >= M || c >= N) continue;
+                const int64_t p = (int64_t)rp * ldc + c;
+                const float hh = ep.Hp[p];
+                const float d1 = Phi(hh) + hh * phi(hh);
+                const float d2 = phi(hh) * (2.f - hh * hh);
+                float gh = Cs[sl * S][cl] * d1;
+                for (int cc = 1; cc < S; ++cc) {
+                    const int64_t q = p + (int64_t)cc * ldc;
+                    const float g = Cs[sl * S + cc][cl];
+                    gh += g * ep.Hp[q] * d2;
+                    const float gt = g * d1;
+                    C[q] = gt;
+                    ep.act[q] = __float2bfloat16(gt);
+                }
+                C[p] = gh;
+                ep.act[p] = __float2bfloat16(gh);
+            }
+        }
+    }
 }
 
 // C[m][n] = sum over the split slices of the partials, in slice order
@@ -160,22 +241,29 @@ int split_of(int M, int N, int K) {
 }
 
 void gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak, const __nv_bfloat16* B, int64_t sbn,
-          int64_t sbk, float* C, int64_t ldc, float beta, cudaStream_t s, float* ws = nullptr) {
+          int64_t sbk, float* C, int64_t ldc, float beta, cudaStream_t s, float* ws = nullptr, int epi = EPI_STORE,
+          Epi ep = Epi{1, nullptr, nullptr, nullptr}) {
     const bool avk = sak == 1 && sam % 8 == 0 && aligned16(A), avr = sam == 1 && sak % 8 == 0 && aligned16(A);
     const bool bvk = sbk == 1 && sbn % 8 == 0 && aligned16(B), bvr = sbn == 1 && sbk % 8 == 0 && aligned16(B);
-    const int split = (ws && beta == 0.f) ? split_of(M, N, K) : 1;
+    const int split = (ws && beta == 0.f && epi == EPI_STORE) ? split_of(M, N, K) : 1;
     const int kslice = ((K + split * BK - 1) / (split * BK)) * BK;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, split);
-    gemm_bf16_kernel<<<grid, 128, 0, s>>>(M, N, K, kslice, A, sam, sak, B, sbn, sbk, split > 1 ? ws : C, ldc, beta,
-                                          avk, avr, bvk, bvr);
+    float* out = split > 1 ? ws : C;
+#define ADPIC_GEMM(E) gemm_bf16_kernel<E><<<grid, 128, 0, s>>>(M, N, K, kslice, A, sam, sak, B, sbn, sbk, out, ldc, \
+                                                                 beta, avk, avr, bvk, bvr, ep)
+    switch (epi) {
+        case EPI_HIDDEN: ADPIC_GEMM(EPI_HIDDEN); break;
+        case EPI_OUTPUT: ADPIC_GEMM(EPI_OUTPUT); break;
+        case EPI_BACKWARD: ADPIC_GEMM(EPI_BACKWARD); break;
+        default: ADPIC_GEMM(EPI_STORE); break;
+    }
+#undef ADPIC_GEMM
     if (split > 1)
         split_reduce_kernel<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, s>>>(ws, split, M, N, C, ldc);
 }
 
 // ------------------------------------------------------------------ elementwise
 
-__device__ __forceinline__ float phi(float x) { return 0.3989422804014327f * __expf(-0.5f * x * x); }
-__device__ __forceinline__ float Phi(float x) { return 0.5f * (1.f + erff(x * 0.7071067811865476f)); }
 
 // rows r = s * S + c (S = n_in + 1; c = 0 primal, c > 0 tangent of input c-1).
 // Primal rows of a hidden layer: h += b, a = GELU(h) (tangent rows follow in
@@ -418,8 +506,14 @@ void forward_rows(ad_pic_mlp* h, int B) {
     for (int l = 0; l < h->layers; ++l) {
         const int in = h->in_dim[l], out = h->out_dim[l];
         const __nv_bfloat16* W = h->pb + h->w_off[l];          // [out][in]
-        gemm(R, out, in, h->A[l], in, 1, W, in, 1, h->H[l], out, 0.f, s);
         const bool hidden = l < h->layers - 1;
+        if (BM % S == 0) {
+            // activations in the GEMM's epilogue
+            gemm(R, out, in, h->A[l], in, 1, W, in, 1, h->H[l], out, 0.f, s, nullptr,
+                 hidden ? EPI_HIDDEN : EPI_OUTPUT, Epi{S, h->p + h->b_off[l], hidden ? h->A[l + 1] : nullptr, nullptr});
+            continue;
+        }
+        gemm(R, out, in, h->A[l], in, 1, W, in, 1, h->H[l], out, 0.f, s);
         if (hidden) {
             act_fwd_kernel<<<nb((int64_t)R * out), 256, 0, s>>>(h->H[l], h->p + h->b_off[l], h->A[l + 1], R, S, out);
             act_fwd_tangent_kernel<<<nb((int64_t)R * out), 256, 0, s>>>(h->H[l], h->A[l + 1], R, S, out);
@@ -448,8 +542,13 @@ void loss_grad(ad_pic_mlp* h, int B, float lam) {
         if (l == 0) break;
         // dA[r][i] = sum_o G[r][o] W[o][i]
         const __nv_bfloat16* W = h->pb + h->w_off[l];
-        gemm(R, in, out, h->Gb, out, 1, W, 1, in, Gn, in, 0.f, s);
-        act_bwd_kernel<<<nb((int64_t)B * in), 256, 0, s>>>(Gn, h->H[l - 1], h->Gb, R, S, in);
+        if (BM % S == 0) {
+            gemm(R, in, out, h->Gb, out, 1, W, 1, in, Gn, in, 0.f, s, nullptr, EPI_BACKWARD,
+                 Epi{S, nullptr, h->Gb, h->H[l - 1]});
+        } else {
+            gemm(R, in, out, h->Gb, out, 1, W, 1, in, Gn, in, 0.f, s);
+            act_bwd_kernel<<<nb((int64_t)B * in), 256, 0, s>>>(Gn, h->H[l - 1], h->Gb, R, S, in);
+        }
         float* tmp = G;
         G = Gn;
         Gn = tmp;
