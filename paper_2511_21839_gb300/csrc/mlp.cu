@@ -29,32 +29,59 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
 
-// one operand tile [rows][BK] of X(r, k) = X[r * sr + k * sk] (BF16) into
-// shared memory: 16-byte vector loads along k (k contiguous) or along r (r
-// contiguous, the transposed operands of the backward pass) where the strides
-// and the tile allow, bounds-checked scalar loads otherwise
-__device__ __forceinline__ void stage_tile(__nv_bfloat16 (*Xs)[BK + PADK], const __nv_bfloat16* __restrict__ X,
-                                           int64_t sr, int64_t sk, int r0, int R, int k0, int K, bool vk, bool vr) {
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    if (vk && k0 + BK <= K) {
-        for (int t = threadIdx.x; t < BM * BK / 8; t += blockDim.x) {
-            const int r = t / (BK / 8), c = (t % (BK / 8)) * 8, gr = r0 + r;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gr < R) v = *reinterpret_cast<const uint4*>(X + gr * sr + (k0 + c));
-            *reinterpret_cast<uint4*>(&Xs[r][c]) = v;
-        }
-    } else if (vr && r0 + BM <= R) {
-        for (int t = threadIdx.x; t < BM * BK / 8; t += blockDim.x) {
-            const int c = t / (BM / 8), r = (t % (BM / 8)) * 8, gk = k0 + c;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gk < K) v = *reinterpret_cast<const uint4*>(X + (r0 + r) + gk * sk);
-            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+// One operand tile [rows][BK] of X(r, k) = X[r * sr + k * sk] (BF16) on its
+// way to shared memory, in two steps so the next tile's loads can be in flight
+// while the current one is multiplied: tile_load reads it into registers
+// (16-byte vectors along k, k contiguous, or along r, r contiguous: the
+// transposed operands of the backward pass, where the strides and the tile
+// allow), tile_store writes them to shared memory. Tiles that allow neither
+// (ragged edges, odd strides) are read with bounds-checked scalar loads in
+// tile_store itself. 128 threads: two vectors each.
+constexpr int kGemmThreads = 128;
+struct TileRegs {
+    uint4 v[BM * BK / 8 / kGemmThreads];
+    int mode;                 // 1 along k, 2 along r, 0 scalar in tile_store
+};
+__device__ __forceinline__ void tile_load(TileRegs& t, const __nv_bfloat16* __restrict__ X, int64_t sr, int64_t sk,
+                                          int r0, int R, int k0, int K, bool vk, bool vr) {
+    t.mode = (vk && k0 + BK <= K) ? 1 : ((vr && r0 + BM <= R) ? 2 : 0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) Xs[r + q][c] = e[q];
+    for (int i = 0; i < BM * BK / 8 / kGemmThreads; ++i) {
+        const int q = threadIdx.x + i * kGemmThreads;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (t.mode == 1) {
+            const int r = q / (BK / 8), c = (q % (BK / 8)) * 8, gr = r0 + r;
+            if (gr < R) v = *reinterpret_cast<const uint4*>(X + gr * sr + (k0 + c));
+        } else if (t.mode == 2) {
+            const int c = q / (BM / 8), r = (q % (BM / 8)) * 8, gk = k0 + c;
+            if (gk < K) v = *reinterpret_cast<const uint4*>(X + (r0 + r) + gk * sk);
+        }
+        t.v[i] = v;
+    }
+}
+__device__ __forceinline__ void tile_store(const TileRegs& t, __nv_bfloat16 (*Xs)[BK + PADK],
+                                           const __nv_bfloat16* __restrict__ X, int64_t sr, int64_t sk, int r0, int R,
+                                           int k0, int K) {
+    if (t.mode == 1) {
+#pragma unroll
+        for (int i = 0; i < BM * BK / 8 / kGemmThreads; ++i) {
+            const int q = threadIdx.x + i * kGemmThreads;
+            const int r = q / (BK / 8), c = (q % (BK / 8)) * 8;
+            *reinterpret_cast<uint4*>(&Xs[r][c]) = t.v[i];
+        }
+    } else if (t.mode == 2) {
+#pragma unroll
+        for (int i = 0; i < BM * BK / 8 / kGemmThreads; ++i) {
+            const int q = threadIdx.x + i * kGemmThreads;
+            const int c = q / (BM / 8), r = (q % (BM / 8)) * 8;
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&t.v[i]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Xs[r + j][c] = e[j];
         }
     } else {
-        for (int t = threadIdx.x; t < BM * BK; t += blockDim.x) {
-            const int r = sk == 1 ? t / BK : t % BM, c = sk == 1 ? t % BK : t / BM;
+        const __nv_bfloat16 zero = __float2bfloat16(0.f);
+        for (int q = threadIdx.x; q < BM * BK; q += kGemmThreads) {
+            const int r = sk == 1 ? q / BK : q % BM, c = sk == 1 ? q % BK : q / BM;
             const int gr = r0 + r, gk = k0 + c;
             Xs[r][c] = (gr < R && gk < K) ? X[gr * sr + gk * sk] : zero;
         }
@@ -89,7 +116,7 @@ struct Epi {
 // blockIdx.z splits K: with split > 1 each slice writes its partial sum to
 // C + z * M * N (row-major [M][N], beta ignored) for split_reduce_kernel.
 template <int EPI>
-__global__ void __launch_bounds__(128, 4) gemm_bf16_kernel(int M, int N, int K, int kslice, const __nv_bfloat16* __restrict__ A,
+__global__ void __launch_bounds__(kGemmThreads, 4) gemm_bf16_kernel(int M, int N, int K, int kslice, const __nv_bfloat16* __restrict__ A,
                                                         int64_t sam, int64_t sak, const __nv_bfloat16* __restrict__ B,
                                                         int64_t sbn, int64_t sbk, float* __restrict__ C, int64_t ldc,
                                                         float beta, bool avk, bool avr, bool bvk, bool bvr, Epi ep) {
@@ -112,10 +139,17 @@ __global__ void __launch_bounds__(128, 4) gemm_bf16_kernel(int M, int N, int K, 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    TileRegs ra, rb;
+    tile_load(ra, A, sam, sak, m0, M, kb, ke, avk, avr);
+    tile_load(rb, B, sbn, sbk, n0, N, kb, ke, bvk, bvr);
     for (int k0 = kb; k0 < ke; k0 += BK) {
-        stage_tile(As, A, sam, sak, m0, M, k0, ke, avk, avr);
-        stage_tile(Bs, B, sbn, sbk, n0, N, k0, ke, bvk, bvr);
+        tile_store(ra, As, A, sam, sak, m0, M, k0, ke);
+        tile_store(rb, Bs, B, sbn, sbk, n0, N, k0, ke);
         __syncthreads();
+        if (k0 + BK < ke) {                  // the next tile's loads overlap this tile's products
+            tile_load(ra, A, sam, sak, m0, M, k0 + BK, ke, avk, avr);
+            tile_load(rb, B, sbn, sbk, n0, N, k0 + BK, ke, bvk, bvr);
+        }
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             unsigned a[2][4], b[4][2];
@@ -249,7 +283,7 @@ void gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak,
     const int kslice = ((K + split * BK - 1) / (split * BK)) * BK;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, split);
     float* out = split > 1 ? ws : C;
-#define ADPIC_GEMM(E) gemm_bf16_kernel<E><<<grid, 128, 0, s>>>(M, N, K, kslice, A, sam, sak, B, sbn, sbk, out, ldc, \
+#define ADPIC_GEMM(E) gemm_bf16_kernel<E><<<grid, kGemmThreads, 0, s>>>(M, N, K, kslice, A, sam, sak, B, sbn, sbk, out, ldc, \
                                                                  beta, avk, avr, bvk, bvr, ep)
     switch (epi) {
         case EPI_HIDDEN: ADPIC_GEMM(EPI_HIDDEN); break;
