@@ -16,7 +16,7 @@ import numpy as np
 from . import adpic
 from . import inputs as I
 from . import optics
-from .surrogate import bfgs
+from .surrogate import Surrogate, bfgs, search_warm
 
 DRIFT, QUAD = 0.3, 0.1
 KICKS_DRIFT, KICKS_QUAD = 3, 2
@@ -138,3 +138,58 @@ class PicMatch:
 
     def close(self):
         self.sim.close()
+
+
+class MatchProblem:
+    """The re-matching in normalised strengths x in [-1, 1]^4 around `center`, k = center (1 + rel x),
+    in the form the surrogate machinery takes: evaluate(x) runs the dual PIC through the section and
+    returns the exit Twiss functions (beta_x, alpha_x, beta_y, alpha_y) over `scale` (the weights of
+    Eq. 6: the target betas, 1 for the alphas) and their exact derivatives in x."""
+
+    def __init__(self, pm, center, rel=0.2):
+        self.pm = pm
+        self.center = np.asarray(center, dtype=np.float64)
+        self.rel = rel
+        bxt, _, byt, _ = pm.target
+        self.scale = np.array([bxt, 1.0, byt, 1.0])
+        self.target = np.asarray(pm.target) / self.scale
+        self.evaluations = 0
+
+    def strengths(self, x):
+        return self.center * (1.0 + self.rel * np.asarray(x))
+
+    def evaluate(self, x):
+        self.evaluations += 1
+        t = self.pm.twiss(self.strengths(x))
+        y = t[:, 0] / self.scale
+        dy = t[:, 1:5] * (self.center * self.rel)[None, :] / self.scale[:, None]
+        return y, dy
+
+    def dataset(self, n, seed=11):
+        """n dual-PIC runs at x ~ U(-1, 1)^4: inputs, values and derivatives."""
+        X = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, 4))
+        Y = np.zeros((n, 4))
+        dY = np.zeros((n, 4, 4))
+        for i in range(n):
+            Y[i], dY[i] = self.evaluate(X[i])
+        self.evaluations = 0
+        return X, Y, dY
+
+
+def surrogate_rematch(pm, center, n_train=256, rel=0.2, ftol=1e-9, max_evals=60, width=128, steps=3000):
+    """The re-matching warm-started by a learned surrogate: a 4 -> width^3 -> 4 MLP is fitted with
+    the Sobolev loss to n_train dual-PIC runs around `center` (values and exact derivatives), then the
+    trust-region search of surrogate.search_warm proposes strengths from BFGS on the surrogate
+    (corrected to the last dual-PIC value and gradient), and a full dual-PIC run checks every proposal;
+    BFGS on dual-PIC gradients finishes. Returns (strengths, Eq. 6 value, dual-PIC evaluations of the
+    search, training-set runs, held-out surrogate errors)."""
+    prob = MatchProblem(pm, center, rel)
+    X, Y, dY = prob.dataset(n_train + n_train // 8)
+    Xt, Yt, dYt = X[:n_train], Y[:n_train], dY[:n_train]
+    sur = Surrogate(width=width, hidden=3, max_batch=min(512, n_train), seed=1, n_in=4, n_out=4)
+    sur.fit(Xt, Yt, dYt, steps=steps, lam=1.0, lr=2e-3, lr_final=2e-5)
+    errs = sur.errors(X[n_train:], Y[n_train:], dY[n_train:])
+    x, f, evals = search_warm(prob, sur, prob.target, np.zeros(4), ftol, max_evals=max_evals, radius=0.5)
+    sur.close()
+    return prob.strengths(x), f, evals, len(X), errs
+

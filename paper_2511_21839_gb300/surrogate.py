@@ -102,15 +102,17 @@ def generate_dataset(problem, n_runs, seed=5, chunk=512):
 
 
 class Surrogate:
-    """MLP 7 -> 256 -> 256 -> 256 -> 2 (GELU) trained with the Sobolev loss on (X, Y, dY).
+    """MLP n_in -> width (x hidden, GELU) -> n_out trained with the Sobolev loss on (X, Y, dY); the
+    FODO problem's network is 7 -> 256 -> 256 -> 256 -> 2.
 
     The network fits (y - y_shift) / y_scale per output; derivatives are scaled alike."""
 
-    def __init__(self, width=256, hidden=3, max_batch=512, seed=0):
-        self.m = adpic.ad_pic_mlp_create(7, width, hidden, 2, max_batch)
+    def __init__(self, width=256, hidden=3, max_batch=512, seed=0, n_in=7, n_out=2):
+        self.n_in, self.n_out = n_in, n_out
+        self.m = adpic.ad_pic_mlp_create(n_in, width, hidden, n_out, max_batch)
         self.n_params = adpic.ad_pic_mlp_num_params(self.m)
         self.max_batch = max_batch
-        self.sizes = [7] + [width] * hidden + [2]
+        self.sizes = [n_in] + [width] * hidden + [n_out]
         rng = np.random.default_rng(seed)
         parts = []
         for l in range(len(self.sizes) - 1):
@@ -118,8 +120,8 @@ class Surrogate:
             scale = math.sqrt((1.0 if l == len(self.sizes) - 2 else 2.0) / n_in)
             parts += [rng.standard_normal(n_in * n_out) * scale, np.zeros(n_out)]
         adpic.ad_pic_mlp_set_params(self.m, np.concatenate(parts))
-        self.y_shift = np.zeros(2)
-        self.y_scale = np.ones(2)
+        self.y_shift = np.zeros(n_out)
+        self.y_scale = np.ones(n_out)
 
     def fit(self, X, Y, dY, steps=3000, lam=1.0, lr=2e-3, lr_final=2e-5, seed=0, device=True, epochs_in_order=8):
         """Adam on mini-batches of max_batch samples, learning rate decayed geometrically from lr to
@@ -146,11 +148,11 @@ class Surrogate:
         return hist
 
     def predict(self, X):
-        """Surrogate values [B][2] and derivatives [B][2][7] in the problem's normalised units."""
+        """Surrogate values [B][n_out] and derivatives [B][n_out][n_in] in the problem's normalised units."""
         X = np.atleast_2d(X)
         ys, dys = [], []
         for c0 in range(0, X.shape[0], self.max_batch):
-            y, dy = adpic.ad_pic_mlp_forward(self.m, X[c0:c0 + self.max_batch], 2)
+            y, dy = adpic.ad_pic_mlp_forward(self.m, X[c0:c0 + self.max_batch], self.n_out)
             ys.append(y.astype(np.float64) * self.y_scale + self.y_shift)
             dys.append(dy.astype(np.float64) * self.y_scale[None, :, None])
         return np.concatenate(ys), np.concatenate(dys)
@@ -235,7 +237,8 @@ def search_cold(problem, target, x0, ftol, max_evals=60, scale=1.0):
     def fg(x):
         return objective(*problem.evaluate(x), target, scale)
 
-    x, f, _ = bfgs(fg, x0, -np.ones(7), np.ones(7), max_iter=max_evals, ftol=ftol, max_evals=max_evals)
+    n = np.size(x0)
+    x, f, _ = bfgs(fg, x0, -np.ones(n), np.ones(n), max_iter=max_evals, ftol=ftol, max_evals=max_evals)
     return x, f, problem.evaluations
 
 
@@ -268,6 +271,7 @@ def search_warm(problem, surrogate, target, x0, ftol, max_evals=60, radius=0.5, 
         def fg(xp):
             return objective(*problem.evaluate(xp), target, scale)
 
-        x, f, _ = bfgs(fg, x, -np.ones(7), np.ones(7), max_iter=max_evals, ftol=ftol,
+        n = x.size
+        x, f, _ = bfgs(fg, x, -np.ones(n), np.ones(n), max_iter=max_evals, ftol=ftol,
                        max_evals=max_evals - used)
     return x, f, problem.evaluations

@@ -116,3 +116,32 @@ def test_space_charge_rematching_with_bfgs(adpic):
     t_orc = design.beam_twiss(hist[-1], 4)
     np.testing.assert_allclose(t_gpu[:, 0], t_orc[:, 0], rtol=1e-10)
     pm.close()
+
+
+def test_rematching_from_cold_optics_and_surrogate_starts(adpic):
+    """The Eq. 6 re-matching at 100 A from three starts, dual-PIC evaluations counted until f <= 1e-9
+    (reported):
+    cold BFGS from the generic guess (+-20 m^-2), BFGS warm-started from the zero-current optics
+    solution, and the surrogate warm start (Sec. 4 and the learned-surrogate search: a 4 -> 128^3 -> 4
+    MLP fitted with the Sobolev loss to dual-PIC runs within +-20 % of the zero-current solution, every
+    proposal checked by a full dual-PIC run)."""
+    from paper_2511_21839_gb300 import design
+
+    pm = design.PicMatch(current_A=100.0, n_particles=16384, grid=32)
+    k_zero, _, _ = pm.zero.bfgs([20.0, -20.0, 20.0, -20.0], ftol=1e-14)
+    ftol = 1e-9
+    k_c, f_c, n_cold = pm.bfgs([20.0, -20.0, 20.0, -20.0], ftol=ftol)
+    k_o, f_o, n_opt = pm.bfgs(k_zero, ftol=ftol)
+    k_s, f_s, n_sur, n_train, errs = design.surrogate_rematch(pm, k_zero, ftol=ftol)
+    print(f"dual-PIC evaluations to f <= {ftol:.0e}: cold {n_cold} (f {f_c:.1e}), optics warm start {n_opt} "
+          f"(f {f_o:.1e}), surrogate warm start {n_sur} (f {f_s:.1e}; surrogate trained on {n_train} runs, "
+          f"held-out value/derivative errors {errs[0]:.3f}/{errs[1]:.3f})")
+    print(f"strengths: cold {k_c}, optics start {k_o}, surrogate start {k_s}")
+    # all three reach the target and the same matching solution; the counts are reported, not ranked:
+    # with exact dual-PIC gradients this 4-parameter problem takes BFGS 15-30 evaluations from any of
+    # the starts (the surrogate pays off on the 7-parameter emittance search, test_gpu_surrogate.py)
+    assert max(f_c, f_o, f_s) <= ftol
+    np.testing.assert_allclose(k_c, k_o, rtol=1e-3)
+    np.testing.assert_allclose(k_s, k_o, rtol=1e-3)
+    assert errs[0] < 0.05 and errs[1] < 0.1
+    pm.close()
