@@ -598,7 +598,8 @@ __device__ __forceinline__ void fftyz_kernel_body(V2<T>* __restrict__ X1, const 
                                                     const int bx_, const int by_) {
     using LY = Lay<MY>;
     using LZ = Lay<MZ>;
-    constexpr int KC = slab_kc<T>();
+    // columns per chunk, at most the MY columns there are (an 8-node y grid has 16)
+    constexpr int KC = slab_kc<T>() < MY ? slab_kc<T>() : MY;
     extern __shared__ unsigned char smraw[];
     V2<T>* tY = reinterpret_cast<V2<T>*>(smraw);
     V2<T>* tZ = tY + MY;

@@ -69,6 +69,7 @@ def make_pair(adpic, N, grid, P, prec, wname="fodo_10k_32", beam=None, q=None):
 STAGE_CASES = [
     ((16, 32, 16), 7, 5003),      # small anisotropic grid
     ((16, 32, 16), 13, 5003),
+    ((16, 8, 8), 7, 1501),        # the smallest dimensions: 16 y columns per slab, fewer than a chunk
     ((64, 64, 64), 7, 4099),      # the benched grid: slab convolution (x pass, one CTA per (y, z) slab)
     ((128, 128, 128), 13, 3001),  # the large instance's grid: five-pass convolution, 129-point DCTs
 ]
