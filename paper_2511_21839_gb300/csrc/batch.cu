@@ -142,7 +142,13 @@ JOB(job_deposit) {
     deposit_tile_body<T, kCP, kCP, 8>(in.state[st.from], in.N, in.geom, in.n, in.n, in.n, in.qm, in.rho, in.err,
                                       sort_of(in, st.from), lb);
 }
-JOB(job_corner) { green_corner_kernel_body(in.geom, in.n, in.n, in.n, in.corner, lb, 0, 0, 0); }
+// the near box's corners by a few blocks per instance striding over it (the
+// box is a small part of the corner lattice in FP32)
+constexpr int kCornerBlocks = 8;
+JOB(job_corner) {
+    if constexpr (sizeof(T) == 4) green_corner_strided_body(in.geom, in.n, in.n, in.corner, lb, kCornerBlocks);
+    else green_corner_kernel_body(in.geom, in.n, in.n, in.n, in.corner, lb, 0, 0, 0);
+}
 JOB(job_scansum) { scan_sum_kernel_body(in.cellcount, in.n * in.n * in.n, in.bsum, lb, 0, 0, 0); }
 JOB(job_chmax) {
     chmax_kernel_body<T>(in.rho, (int64_t)in.n * in.n * in.n, kCP, in.chmax, lb, 0, 0, in.tiles.chmax_blocks);
@@ -518,7 +524,7 @@ int build_tables(ad_pic_batch* b) {
         set(J_GEOM, 1);
         set(J_CLEAR, b->tiles.clear_blocks);
         set(J_DEPOSIT, ceil_div(h->N, 256));
-        set(J_CORNER, ceil_div((int64_t)(n + 2) * (n + 2) * (n + 2), 256));
+        set(J_CORNER, sizeof(T) == 4 ? kCornerBlocks : ceil_div((int64_t)(n + 2) * (n + 2) * (n + 2), 256));
         set(J_SCANSUM, scan_blocks((int)nodes));
         set(J_CHMAX, b->tiles.chmax_blocks);
         set(J_CELL, ceil_div((int64_t)(n + 1) * (n + 1) * (n + 1), 256));

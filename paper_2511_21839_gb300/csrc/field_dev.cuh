@@ -242,15 +242,21 @@ static __global__ void green_corner_kernel(const GeomDev* __restrict__ g, int nx
 
 // The same integrals from a fixed grid of blocks that strides over the near
 // box (its size is known on the device only), instead of one thread per
-// corner of the whole lattice of which all but the box return at once.
-static __global__ void __launch_bounds__(64) green_corner_strided_kernel(const GeomDev* __restrict__ g, int nx, int ny,
-                                                                       int nz, double* __restrict__ F) {
+// corner of the whole lattice of which all but the box return at once:
+// block b of nb.
+__device__ __forceinline__ void green_corner_strided_body(const GeomDev* __restrict__ g, int nx, int ny,
+                                                          double* __restrict__ F, int b, int nb) {
     const int ex = g->R[0] + 2, ey = g->R[1] + 2, ez = g->R[2] + 2;
     const int cx = nx + 2, cy = ny + 2;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ex * ey * ez; t += gridDim.x * blockDim.x) {
+    for (int t = b * blockDim.x + threadIdx.x; t < ex * ey * ez; t += nb * blockDim.x) {
         const int i = t % ex, j = (t / ex) % ey, k = t / (ex * ey);
         F[((int64_t)k * cy + j) * cx + i] = igf_F((i - 0.5) * g->hr[0], (j - 0.5) * g->hr[1], (k - 0.5) * g->hr[2]);
     }
+}
+static __global__ void __launch_bounds__(64) green_corner_strided_kernel(const GeomDev* __restrict__ g, int nx, int ny,
+                                                                       int nz, double* __restrict__ F) {
+    (void)nz;
+    green_corner_strided_body(g, nx, ny, F, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // dF/dz of the antiderivative above, in closed form (differentiating F's six
