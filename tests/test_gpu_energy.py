@@ -44,16 +44,24 @@ def chan_err(gpu, ref):
     return (np.abs(g - r) / np.where(scale > 0, scale, 1.0)).max(axis=1)
 
 
+ENERGY_STAGE_CASES = [
+    ((16, 32, 16), 7),
+    ((16, 32, 16), 13),     # 16-channel records: the energy term's copy and add stride over 16
+    ((64, 64, 64), 7),      # the benched grid (slab convolution)
+    ((128, 128, 128), 7),   # the five-pass convolution carries the energy term too
+]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("grid", [(16, 32, 16), (64, 64, 64)], ids=lambda g: "x".join(map(str, g)))
-def test_energy_stage_parity(adpic, prec, grid):
+@pytest.mark.parametrize("grid,P", ENERGY_STAGE_CASES, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_energy_stage_parity(adpic, prec, grid, P):
     """Potential, field and kick of one kick element-wise against the oracle on the same state: the
     energy channel of phi carries (dG/dE) * rho_0, that of E_z the dual rest-frame spacing."""
     N = 4099
     b = energy_beam()
     w = I.workload("fodo_10k_32")
-    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=N, grid=grid, beam=b, lattice=LAT))
-    sim = adpic.ADPIC(grid, N, 7, prec)
+    o = oracle.Oracle(**I.orc_kwargs(w, n_particles=N, grid=grid, n_deriv=P, beam=b, lattice=LAT))
+    sim = adpic.ADPIC(grid, N, P, prec)
     sim.set_beam(b)
     sim.set_lattice(LAT)
     st = o.beam_init(I.normals(61, N))
@@ -70,13 +78,13 @@ def test_energy_stage_parity(adpic, prec, grid):
     print(f"  phi per channel {np.array2string(e, precision=1)}")
     assert e.max() < tol
     # the energy term is a visible part of its channel
-    o0 = oracle.Oracle(**I.orc_kwargs(w, n_particles=N, grid=grid, beam=I.Beam(**{**b.__dict__, "energy_slot": -1}),
-                                      lattice=LAT))
+    o0 = oracle.Oracle(**I.orc_kwargs(w, n_particles=N, grid=grid, n_deriv=P,
+                                      beam=I.Beam(**{**b.__dict__, "energy_slot": -1}), lattice=LAT))
     plain = o0.solve(geom, rho_ref)
     assert np.abs(phi_ref[1] - plain[1]).max() > 10 * tol * np.abs(phi_ref[1]).max()
     E = sim.stage(3)
     E_ref = o.field(geom, phi_ref)
-    e = chan_err(E.reshape(3 * 8, -1), E_ref.reshape(3 * 8, -1))
+    e = chan_err(E.reshape(3 * (P + 1), -1), E_ref.reshape(3 * (P + 1), -1))
     print(f"  E per channel max {e.max():.2e}")
     assert e.max() < 5 * tol
     sim.stage(4, kick=5)
