@@ -476,7 +476,8 @@ struct Impl {
                 nrec = enqueue_run(h, g0, n, first, true, from);
                 CK(cudaStreamEndCapture(h->stream, &graph));
                 cudaGraphExec_t ex;
-                CK(cudaGraphInstantiate(&ex, graph, 0));
+                // captured launches keep their stream's priority
+                CK(cudaGraphInstantiateWithFlags(&ex, graph, cudaGraphInstantiateFlagUseNodePriority));
                 cudaGraphDestroy(graph);
                 it = h->graphs.emplace(key, ex).first;
             } else {
@@ -1027,7 +1028,12 @@ int ad_pic_create(const ad_pic_grid* grid, int64_t n_particles, int n_deriv, int
         return AD_PIC_ERR_CUDA;
     }
     h->stream = h->own_stream;
-    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // the side stream (Green's function, then the cell offsets) at the highest
+    // priority: the Green's spectrum is on the kick's critical path while its
+    // kernels share the GPU with the deposit, so their blocks go first
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_dep, cudaEventDisableTiming) != cudaSuccess ||
