@@ -130,6 +130,23 @@ int ad_pic_get_particles(const ad_pic* h, double* state);
    its padded record size: one copy straight into the state). An FP64 handle
    returns AD_PIC_ERR_UNSUPPORTED. */
 int ad_pic_set_particles_f32(ad_pic* h, const float* state);
+/* Asynchronous form of ad_pic_set_particles_f32, for streaming many beams
+   through one handle (the next beam's upload overlaps the current run).
+   ad_pic_prefetch_particles_f32 enqueues the copy of FP32 host data [6][N][C]
+   into a device buffer the handle allocates on first use (6 N C floats), on a
+   copy stream of its own, and returns without waiting for it. The copy starts
+   after the previous commit has read that buffer; a second prefetch before a
+   commit replaces the first. The caller keeps the host buffer unchanged until
+   the copy is done: until the next ad_pic_run, ad_pic_get_particles or
+   ad_pic_destroy returns after ad_pic_commit_particles (pinned host memory
+   makes the copy asynchronous; pageable memory is copied before the call
+   returns). ad_pic_commit_particles makes the prefetched data the particle
+   state, exactly as ad_pic_set_particles_f32 of the same data (kick counter
+   and moment history reset), ordered on the handle's stream after the copy,
+   without host synchronisation. Commit without a pending prefetch returns
+   AD_PIC_ERR_STATE; an FP64 handle returns AD_PIC_ERR_UNSUPPORTED from both. */
+int ad_pic_prefetch_particles_f32(ad_pic* h, const float* state);
+int ad_pic_commit_particles(ad_pic* h);
 
 /* Set the lattice and recompute the per-kick dual map coefficients (FP64 on
    the host, Eqs. 1-4 applied to the quad matrices of Sec. 4). */

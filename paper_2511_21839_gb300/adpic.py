@@ -68,6 +68,8 @@ def lib():
             "ad_pic_set_beam": (ct.c_int, [vp, ct.POINTER(ad_pic_beam), dp]),
             "ad_pic_set_particles": (ct.c_int, [vp, dp]),
             "ad_pic_set_particles_f32": (ct.c_int, [vp, ct.POINTER(ct.c_float)]),
+            "ad_pic_prefetch_particles_f32": (ct.c_int, [vp, ct.POINTER(ct.c_float)]),
+            "ad_pic_commit_particles": (ct.c_int, [vp]),
             "ad_pic_get_particles": (ct.c_int, [vp, dp]),
             "ad_pic_set_lattice": (ct.c_int, [vp, ct.POINTER(ad_pic_lattice)]),
             "ad_pic_run": (ct.c_int, [vp, ct.c_int]),
@@ -178,6 +180,19 @@ def ad_pic_set_particles(h, state):
 def ad_pic_set_particles_f32(h, state):
     s = np.ascontiguousarray(state, dtype=np.float32)
     _ck("ad_pic_set_particles_f32", lib().ad_pic_set_particles_f32(h, s.ctypes.data_as(ct.POINTER(ct.c_float))))
+
+
+def ad_pic_prefetch_particles_f32(h, state):
+    """Enqueue the asynchronous upload; returns the array whose memory is being
+    copied, which the caller keeps alive and unchanged until the copy is done."""
+    s = np.ascontiguousarray(state, dtype=np.float32)
+    _ck("ad_pic_prefetch_particles_f32",
+        lib().ad_pic_prefetch_particles_f32(h, s.ctypes.data_as(ct.POINTER(ct.c_float))))
+    return s
+
+
+def ad_pic_commit_particles(h):
+    _ck("ad_pic_commit_particles", lib().ad_pic_commit_particles(h))
 
 
 def ad_pic_get_particles(h, out):
@@ -540,6 +555,14 @@ class ADPIC:
 
     def set_particles_f32(self, state):
         ad_pic_set_particles_f32(self.h, state)
+
+    def prefetch_particles_f32(self, state):
+        # the source arrays of the copies that may still be in flight stay referenced
+        src = ad_pic_prefetch_particles_f32(self.h, state)
+        self._prefetch_src = (getattr(self, "_prefetch_src", (None, None))[-1], src)
+
+    def commit_particles(self):
+        ad_pic_commit_particles(self.h)
 
     def get_particles(self):
         return ad_pic_get_particles(self.h, np.zeros((6, self.N, self.C)))

@@ -664,6 +664,61 @@ struct Impl {
         return AD_PIC_OK;
     }
 
+    // Asynchronous FP32 upload: the copy into the handle's prefetch buffer runs
+    // on a copy stream of its own, after the previous commit has read that buffer
+    static int prefetch_particles_f32(ad_pic* h, const float* src) {
+        if (sizeof(T) != 4) return AD_PIC_ERR_UNSUPPORTED;
+        const size_t bytes = sizeof(float) * 6 * h->N * C;
+        if (!h->prefetch) {
+            int r = dalloc(h, (void**)&h->prefetch, bytes);
+            if (r) return r;
+        }
+        if (!h->copy) {
+            if (cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_consumed, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(h->ev_consumed, h->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return AD_PIC_ERR_CUDA;
+            }
+        }
+        if (cudaStreamWaitEvent(h->copy, h->ev_consumed, 0) != cudaSuccess ||
+            cudaMemcpyAsync(h->prefetch, src, bytes, cudaMemcpyHostToDevice, h->copy) != cudaSuccess ||
+            cudaEventRecord(h->ev_copied, h->copy) != cudaSuccess) {
+            cudaGetLastError();
+            h->prefetched = false;
+            return AD_PIC_ERR_CUDA;
+        }
+        h->prefetched = true;
+        return AD_PIC_OK;
+    }
+
+    // the prefetched data becomes the particle state (as set_particles_f32),
+    // ordered on the handle's stream after the copy; no host synchronisation
+    static int commit_particles(ad_pic* h) {
+        if (sizeof(T) != 4) return AD_PIC_ERR_UNSUPPORTED;
+        if (!h->prefetched) return AD_PIC_ERR_STATE;
+        const size_t bytes = sizeof(float) * 6 * h->N * C;
+        cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_copied, 0);
+        if (e == cudaSuccess) {
+            if (C == CP)
+                e = cudaMemcpyAsync(st(h), h->prefetch, bytes, cudaMemcpyDeviceToDevice, h->stream);
+            else
+                pad_records_f32(h->prefetch, (float*)st(h), h->N, C, CP, h->stream);
+        }
+        if (e == cudaSuccess) {
+            launch_iota(h->ids[h->cur], h->N, h->stream);
+            e = cudaEventRecord(h->ev_consumed, h->stream);
+        }
+        if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return AD_PIC_ERR_CUDA;
+        h->prefetched = false;
+        h->particles_set = true;
+        h->kick = 0;
+        h->first_record = true;
+        h->hist.clear();
+        return AD_PIC_OK;
+    }
+
     static int get_particles(const ad_pic* hc_, double* dst) {
         ad_pic* h = const_cast<ad_pic*>(hc_);
         double* tmp = nullptr;
@@ -1075,6 +1130,16 @@ int ad_pic_set_particles_f32(ad_pic* h, const float* state) {
     DISPATCH(h, I::set_particles_f32(h, state));
 }
 
+int ad_pic_prefetch_particles_f32(ad_pic* h, const float* state) {
+    if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::prefetch_particles_f32(h, state));
+}
+
+int ad_pic_commit_particles(ad_pic* h) {
+    if (!h) return AD_PIC_ERR_INVALID_ARG;
+    DISPATCH(h, I::commit_particles(h));
+}
+
 int ad_pic_get_particles(const ad_pic* h, double* state) {
     if (!h || !state) return AD_PIC_ERR_INVALID_ARG;
     if (!h->particles_set) return AD_PIC_ERR_STATE;
@@ -1270,6 +1335,7 @@ void ad_pic_destroy(ad_pic* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->side) cudaStreamSynchronize(h->side);
+    if (h->copy) cudaStreamSynchronize(h->copy);
     free_graphs(h);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (void* p : h->allocs)
@@ -1280,6 +1346,9 @@ void ad_pic_destroy(ad_pic* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_dep) cudaEventDestroy(h->ev_dep);
     if (h->ev_scan) cudaEventDestroy(h->ev_scan);
+    if (h->copy) cudaStreamDestroy(h->copy);
+    if (h->ev_copied) cudaEventDestroy(h->ev_copied);
+    if (h->ev_consumed) cudaEventDestroy(h->ev_consumed);
     cudaGetLastError();
     delete h;
 }

@@ -77,6 +77,12 @@ struct ad_pic {
     double* records = nullptr;
     int records_cap = 0;
     double* staging = nullptr;      // FP64 [6][N][C] staging buffer of set/get_particles
+    // asynchronous FP32 upload (prefetch / commit): its device buffer [6][N][C],
+    // the copy stream, the copy's completion and the commit's last read of the buffer
+    float* prefetch = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_copied = nullptr, ev_consumed = nullptr;
+    bool prefetched = false;
     int64_t launches = 0;           // kernels launched by ad_pic_run so far
     int wait_polls = -1;            // poll limit of the push's tile waits (< 0: the default)
     std::vector<void*> allocs;

@@ -433,3 +433,43 @@ def test_fp32_upload_matches_the_fp64_upload(adpic, P):
         s64.set_particles_f32(st32)
     assert e.value.status == -8                          # AD_PIC_ERR_UNSUPPORTED
     s64.close()
+
+
+@pytest.mark.parametrize("P", [7, 13])
+def test_prefetched_upload_matches_the_synchronous_one(adpic, P):
+    """ad_pic_prefetch_particles_f32 + ad_pic_commit_particles give the state and the run that
+    ad_pic_set_particles_f32 gives, also when the next beam's copy is enqueued while the current
+    beam runs (two pinned-or-not host buffers in turn, as a streaming caller uses them). A commit
+    with nothing prefetched is AD_PIC_ERR_STATE; an FP64 handle refuses both calls."""
+    N, grid = 3001, (16, 16, 16)
+    o, sim, w, b = make_pair(adpic, N, grid, P, 1)
+    beams = [o.beam_init(I.normals(81 + k, N)).astype(np.float32) for k in range(3)]
+    ref = []
+    for st in beams:
+        sim.set_particles_f32(st)
+        s0 = sim.get_particles()
+        sim.run(4)
+        ref.append((s0, sim.history(), sim.get_particles()))
+    with pytest.raises(adpic.AdPicError) as e:
+        sim.commit_particles()
+    assert e.value.status == -4                          # AD_PIC_ERR_STATE
+    sim.prefetch_particles_f32(beams[0])
+    for k in range(3):
+        sim.commit_particles()
+        if k == 0:
+            np.testing.assert_array_equal(sim.get_particles(), ref[0][0])
+        if k + 1 < 3:
+            sim.prefetch_particles_f32(beams[k + 1])     # overlaps the run below
+        sim.run(4)
+        # separate runs: the deposit's atomic order differs, so not bitwise
+        h = sim.history()
+        np.testing.assert_allclose(h, ref[k][1], rtol=1e-6, atol=1e-6 * np.abs(ref[k][1]).max())
+        g = sim.get_particles()
+        np.testing.assert_allclose(g, ref[k][2], rtol=1e-5, atol=1e-5 * np.abs(ref[k][2]).max())
+    sim.close()
+    s64 = adpic.ADPIC(grid, N, P, 0)
+    for call in (lambda: s64.prefetch_particles_f32(beams[0]), s64.commit_particles):
+        with pytest.raises(adpic.AdPicError) as e:
+            call()
+        assert e.value.status == -8                      # AD_PIC_ERR_UNSUPPORTED
+    s64.close()
