@@ -104,7 +104,7 @@ template <int M> struct Split;
 template <> struct Split<16> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Split<32> { static constexpr int R1 = 8, R2 = 4; };
 template <> struct Split<64> { static constexpr int R1 = 8, R2 = 8; };
-template <> struct Split<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct Split<128> { static constexpr int R1 = 8, R2 = 16; };
 template <> struct Split<256> { static constexpr int R1 = 16, R2 = 16; };
 
 template <int M>
