@@ -518,7 +518,7 @@ __device__ __forceinline__ void fftx_fwd_t_kernel_body(T* rho, V2<T>* __restrict
 }
 
 template <typename T, int M>
-static __global__ void __launch_bounds__(256) fftx_fwd_t_kernel(T* rho, V2<T>* __restrict__ X1,
+static __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) fftx_fwd_t_kernel(T* rho, V2<T>* __restrict__ X1,
                                                                   FFTDims d, const V2<T>* __restrict__ tw,
                                                                   const Ord<T>* __restrict__ chmax, int yt) {
     fftx_fwd_t_kernel_body<T, M>(rho, X1, d, tw, chmax, yt, true, (int)blockIdx.x, (int)blockIdx.y);
@@ -771,7 +771,7 @@ __device__ __forceinline__ void fftx_inv_t_kernel_body(const V2<T>* __restrict__
 }
 
 template <typename T, int M>
-static __global__ void __launch_bounds__(256) fftx_inv_t_kernel(const V2<T>* __restrict__ X1, T* __restrict__ phi,
+static __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) fftx_inv_t_kernel(const V2<T>* __restrict__ X1, T* __restrict__ phi,
                                                                   FFTDims d, const V2<T>* __restrict__ tw,
                                                                   const Ord<T>* __restrict__ chmax, int yt) {
     fftx_inv_t_kernel_body<T, M>(X1, phi, d, tw, chmax, yt, (int)blockIdx.x, (int)blockIdx.y);
