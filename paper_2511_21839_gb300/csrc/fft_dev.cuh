@@ -230,14 +230,29 @@ __device__ __forceinline__ void fftx_fwd_kernel_body(T* rho, V2<T>* __restrict__
     const int nrows = d.ny * d.nz;
     const int lcp = __ffs(d.CP) - 1;                  // nx = M/2 and CP are powers of two
     constexpr int LNX = log2_c(M) - 1;
-    for (int t = threadIdx.x; t < (kRowsX << (LNX + lcp)); t += blockDim.x) {
-        const int r = t >> (LNX + lcp);
-        const int x = (t >> lcp) & ((1 << LNX) - 1), c = t & (d.CP - 1);
-        if (row0 + r >= nrows || c >= d.C) continue;
-        const int64_t at = ((row0 + r) * d.nx + x) * d.CP + c;
-        const T v = rho[at] * chan_scale<T>(chmax, c, false);
-        V2<T>& dst = buf[(r * d.npair + (c >> 1)) * L::LS + L::pos(x)];
-        if (c & 1) dst.y = v; else dst.x = v;
+    __shared__ T scs[16];                             // channel scales
+    if (threadIdx.x < d.CP) scs[threadIdx.x] = chan_scale<T>(chmax, threadIdx.x, false);
+    __syncthreads();
+    // batches of NB independent loads per thread (one latency per batch)
+    constexpr int NB = 8;
+    const int total = kRowsX << (LNX + lcp);
+    for (int t0 = threadIdx.x; t0 < total; t0 += NB * blockDim.x) {
+        T v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, r = t >> (LNX + lcp);
+            const int x = (t >> lcp) & ((1 << LNX) - 1), c = t & (d.CP - 1);
+            v[b] = (t < total && row0 + r < nrows && c < d.C) ? rho[((row0 + r) * d.nx + x) * d.CP + c] : (T)0;
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, r = t >> (LNX + lcp);
+            const int x = (t >> lcp) & ((1 << LNX) - 1), c = t & (d.CP - 1);
+            if (t >= total || row0 + r >= nrows || c >= d.C) continue;
+            V2<T>& dst = buf[(r * d.npair + (c >> 1)) * L::LS + L::pos(x)];
+            const T sv = v[b] * scs[c];
+            if (c & 1) dst.y = sv; else dst.x = sv;
+        }
     }
     __syncthreads();
     if (clear) {
@@ -281,9 +296,19 @@ __device__ __forceinline__ void ffty_kernel_body(const V2<T>* __restrict__ in, V
     const int yin = INV ? M : d.ny, yout = INV ? d.ny : M;
     for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
     const int64_t plane_in = ((int64_t)p * d.nz + z) * yin;
-    for (int t = threadIdx.x; t < yin * kTile; t += blockDim.x) {
-        const int y = t / kTile, j = t % kTile;
-        buf[j * L::LS + L::pos(y)] = in[(plane_in + y) * d.Mx + kx0 + j];
+    constexpr int NB = 8;                             // independent loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < yin * kTile; t0 += NB * blockDim.x) {
+        V2<T> v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, y = t / kTile, j = t % kTile;
+            if (t < yin * kTile) v[b] = in[(plane_in + y) * d.Mx + kx0 + j];
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, y = t / kTile, j = t % kTile;
+            if (t < yin * kTile) buf[j * L::LS + L::pos(y)] = v[b];
+        }
     }
     __syncthreads();
     step1<T, M, INV>(buf, kTile, twM, !INV);
@@ -321,9 +346,19 @@ __device__ __forceinline__ void fftz_kernel_body(V2<T>* __restrict__ X2, const T
     for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
     const int64_t zstride = (int64_t)d.My * d.Mx;
     V2<T>* base = X2 + (int64_t)p * d.nz * zstride + (int64_t)ky * d.Mx + kx0;
-    for (int t = threadIdx.x; t < d.nz * kTile; t += blockDim.x) {
-        const int z = t / kTile, j = t % kTile;
-        buf[j * L::LS + L::pos(z)] = base[z * zstride + j];
+    constexpr int NB = 8;                             // independent loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < d.nz * kTile; t0 += NB * blockDim.x) {
+        V2<T> v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, z = t / kTile, j = t % kTile;
+            if (t < d.nz * kTile) v[b] = base[z * zstride + j];
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, z = t / kTile, j = t % kTile;
+            if (t < d.nz * kTile) buf[j * L::LS + L::pos(z)] = v[b];
+        }
     }
     __syncthreads();
     step1<T, M, false>(buf, kTile, twM, true);
@@ -392,31 +427,39 @@ __device__ __forceinline__ void fftx_inv_kernel_body(const V2<T>* __restrict__ X
     for (int j = threadIdx.x; j < M; j += blockDim.x) twM[j] = tw[j];
     const int64_t row0 = (int64_t)bx_ * kRowsX;
     const int nrows = d.ny * d.nz;
-    for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
-        const int line = t / M, kx = t % M;
-        const int r = line / d.npair, p = line % d.npair;
-        V2<T> v;
-        v.x = (T)0;
-        v.y = (T)0;
-        if (row0 + r < nrows) {
-            const int64_t z = (row0 + r) / d.ny, y = (row0 + r) % d.ny;
-            v = X1[(((int64_t)p * d.nz + z) * d.ny + y) * M + kx];
+    __shared__ T isc[16];                             // channel scales back, times 1/(Mx My Mz)
+    if (threadIdx.x < d.CP) isc[threadIdx.x] = (T)d.norm * chan_scale<T>(chmax, threadIdx.x, true);
+    constexpr int NB = 8;                             // independent loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < nl * M; t0 += NB * blockDim.x) {
+        V2<T> v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, line = t / M, kx = t % M;
+            const int r = line / d.npair, p = line % d.npair;
+            v[b].x = (T)0;
+            v[b].y = (T)0;
+            if (t < nl * M && row0 + r < nrows) {
+                const int64_t z = (row0 + r) / d.ny, y = (row0 + r) % d.ny;
+                v[b] = X1[(((int64_t)p * d.nz + z) * d.ny + y) * M + kx];
+            }
         }
-        buf[line * L::LS + L::pos(kx)] = v;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int t = t0 + b * blockDim.x, line = t / M, kx = t % M;
+            if (t < nl * M) buf[line * L::LS + L::pos(kx)] = v[b];
+        }
     }
     __syncthreads();
     step1<T, M, true>(buf, nl, twM, false);
     __syncthreads();
     // outputs x < nx of every line into a row-major staging area [r][x][CP]
     T* stage = reinterpret_cast<T*>(buf + nl * L::LS);
-    const T norm = (T)d.norm;
     for (int w = threadIdx.x; w < nl * L::R1; w += blockDim.x) {
         const int line = w % nl, k1 = w / nl;
         V2<T> v[L::R2];
         step2<T, M, true, true>(buf, line, k1, v);   // keeps x < nx
         const int r = line / d.npair, p = line % d.npair;
-        const T sa = norm * chan_scale<T>(chmax, 2 * p, true);
-        const T sb = norm * chan_scale<T>(chmax, 2 * p + 1, true);
+        const T sa = isc[2 * p], sb = isc[2 * p + 1];
 #pragma unroll
         for (int k2 = 0; k2 < L::R2; ++k2) {
             const int x = k1 + L::R1 * k2;

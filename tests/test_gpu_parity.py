@@ -426,7 +426,13 @@ def test_fp32_upload_matches_the_fp64_upload(adpic, P):
     g = sim.get_particles()
     np.testing.assert_array_equal(g, a)
     sim.run(3)
-    np.testing.assert_allclose(sim.history(), ra, rtol=1e-6, atol=1e-6 * np.abs(ra).max())
+    # separate runs (the deposit's atomic order differs): emittances within the FP32 bounds
+    h = sim.history()
+    assert len(h) == len(ra)
+    for r in range(len(h)):
+        e, er = o.emittance(h[r]), o.emittance(ra[r])
+        ev, ed = report(f"FP32 upload record {r}", e[:, 0], e[:, 1:], er)
+        assert ev < 1e-5 and ed < der_tol(1, N), r
     sim.close()
     s64 = adpic.ADPIC(grid, N, P, 0)
     with pytest.raises(adpic.AdPicError) as e:
@@ -461,9 +467,14 @@ def test_prefetched_upload_matches_the_synchronous_one(adpic, P):
         if k + 1 < 3:
             sim.prefetch_particles_f32(beams[k + 1])     # overlaps the run below
         sim.run(4)
-        # separate runs: the deposit's atomic order differs, so not bitwise
+        # separate runs: the deposit's atomic order differs, so not bitwise; the
+        # emittances and their derivatives agree within the FP32 bounds
         h = sim.history()
-        np.testing.assert_allclose(h, ref[k][1], rtol=1e-6, atol=1e-6 * np.abs(ref[k][1]).max())
+        assert len(h) == len(ref[k][1])
+        for r in range(len(h)):
+            e, er = o.emittance(h[r]), o.emittance(ref[k][1][r])
+            ev, ed = report(f"prefetched beam {k} record {r}", e[:, 0], e[:, 1:], er)
+            assert ev < 1e-5 and ed < der_tol(1, N), (k, r)
         g = sim.get_particles()
         np.testing.assert_allclose(g, ref[k][2], rtol=1e-5, atol=1e-5 * np.abs(ref[k][2]).max())
     sim.close()
