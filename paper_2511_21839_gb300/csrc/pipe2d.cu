@@ -18,6 +18,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "ad_pic.h"
 #include "common.cuh"
@@ -78,15 +79,137 @@ __global__ void __launch_bounds__(256) deposit2d_kernel(const T* __restrict__ st
             const T wx = a ? fx : (T)1 - fx, sx = a ? (T)1 : (T)-1;
             const T wy = b ? fy : (T)1 - fy, sy = b ? (T)1 : (T)-1;
             T* r = rho + ((int64_t)(iy + b) * (nx + 1) + (ix + a)) * CP;
-            atomicAdd(r, q * (wx * wy));
+            if constexpr (sizeof(T) == 4) {
+                // FP32: the node record in 16-byte vector reductions (records are
+                // 16-byte aligned, CP a multiple of 4), a quarter of the atomics
+                T rec[CP];
+                rec[0] = q * (wx * wy);
 #pragma unroll
-            for (int k = 1; k < C; ++k) atomicAdd(r + k, q * (sx * x[k] * ihx * wy + sy * y[k] * ihy * wx));
+                for (int k = 1; k < CP; ++k) rec[k] = k < C ? q * (sx * x[k] * ihx * wy + sy * y[k] * ihy * wx) : (T)0;
+                float4* r4 = reinterpret_cast<float4*>(r);
+#pragma unroll
+                for (int v = 0; v < CP / 4; ++v)
+                    atomicAdd(r4 + v, make_float4(rec[4 * v], rec[4 * v + 1], rec[4 * v + 2], rec[4 * v + 3]));
+            } else {
+                atomicAdd(r, q * (wx * wy));
+#pragma unroll
+                for (int k = 1; k < C; ++k) atomicAdd(r + k, q * (sx * x[k] * ihx * wy + sy * y[k] * ihy * wx));
+            }
         }
 }
 
+// Sine sums as small matrix products, one block per (line, 64 outputs): the
+// line's CP-channel records are staged in shared memory with 16-byte loads;
+// each thread accumulates all CP channels of one output in the order of the
+// sum index (one load of S per term, the records read as broadcast vectors).
+constexpr int kSineThreads = 64;
+template <typename T>
+using SineVec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+
 // out[j][l][c] = sum_i S[l][i] in[j][i][c] along the rows (x), S = sin(pi l i / nx)
 template <typename T, int CP>
-__global__ void sine_rows_kernel(const T* __restrict__ in, const T* __restrict__ S, int nx, int ny, T* __restrict__ out) {
+__global__ void __launch_bounds__(kSineThreads) sine_rows_kernel(const T* __restrict__ in, const T* __restrict__ S,
+                                                                 int nx, int ny, T* __restrict__ out) {
+    using V = SineVec<T>;
+    constexpr int EPV = 16 / (int)sizeof(T), VPR = CP / EPV;
+    extern __shared__ __align__(16) unsigned char sine_sm[];
+    V* rowv = reinterpret_cast<V*>(sine_sm);          // [nx + 1][VPR]
+    const int j = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nv = (nx + 1) * VPR;
+    const V* src = reinterpret_cast<const V*>(in + (int64_t)j * (nx + 1) * CP);
+    for (int t0 = threadIdx.x; t0 < nv; t0 += 8 * blockDim.x) {
+        V v[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (t0 + b * (int)blockDim.x < nv) v[b] = src[t0 + b * blockDim.x];
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (t0 + b * (int)blockDim.x < nv) rowv[t0 + b * blockDim.x] = v[b];
+    }
+    __syncthreads();
+    if (l > nx) return;
+    T acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = (T)0;
+    const T* sl = S + (int64_t)l * (nx + 1);
+    for (int i = 1; i < nx; ++i) {
+        const T w = sl[i];
+#pragma unroll
+        for (int q = 0; q < VPR; ++q) {
+            const V a = rowv[i * VPR + q];
+            T e[EPV];
+            memcpy(e, &a, sizeof(V));
+#pragma unroll
+            for (int k = 0; k < EPV; ++k) acc[q * EPV + k] = fma(w, e[k], acc[q * EPV + k]);
+        }
+    }
+    V* dst = reinterpret_cast<V*>(out + ((int64_t)j * (nx + 1) + l) * CP);
+#pragma unroll
+    for (int q = 0; q < VPR; ++q) {
+        V a;
+        memcpy(&a, acc + q * EPV, sizeof(V));
+        dst[q] = a;
+    }
+}
+
+// out[m][l][c] = scale[m][l] sum_j S[m][j] in[j][l][c] along the columns (y)
+template <typename T, int CP>
+__global__ void __launch_bounds__(kSineThreads) sine_cols_kernel(const T* __restrict__ in, const T* __restrict__ S,
+                                                                 const T* __restrict__ scale, int nx, int ny,
+                                                                 T* __restrict__ out) {
+    using V = SineVec<T>;
+    constexpr int EPV = 16 / (int)sizeof(T), VPR = CP / EPV;
+    extern __shared__ __align__(16) unsigned char sine_sm[];
+    V* colv = reinterpret_cast<V*>(sine_sm);          // [ny + 1][VPR]
+    const int l = blockIdx.y, m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nv = (ny + 1) * VPR;
+    const V* src = reinterpret_cast<const V*>(in);
+    for (int t0 = threadIdx.x; t0 < nv; t0 += 8 * blockDim.x) {
+        V v[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int t = t0 + b * blockDim.x;
+            if (t < nv) v[b] = src[((int64_t)(t / VPR) * (nx + 1) + l) * VPR + t % VPR];
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (t0 + b * (int)blockDim.x < nv) colv[t0 + b * blockDim.x] = v[b];
+    }
+    __syncthreads();
+    if (m > ny) return;
+    T acc[CP];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) acc[c] = (T)0;
+    const T* sm = S + (int64_t)m * (ny + 1);
+    for (int jj = 1; jj < ny; ++jj) {
+        const T w = sm[jj];
+#pragma unroll
+        for (int q = 0; q < VPR; ++q) {
+            const V a = colv[jj * VPR + q];
+            T e[EPV];
+            memcpy(e, &a, sizeof(V));
+#pragma unroll
+            for (int k = 0; k < EPV; ++k) acc[q * EPV + k] = fma(w, e[k], acc[q * EPV + k]);
+        }
+    }
+    const T f = scale ? scale[(int64_t)m * (nx + 1) + l] : (T)1;
+    V* dst = reinterpret_cast<V*>(out + ((int64_t)m * (nx + 1) + l) * CP);
+#pragma unroll
+    for (int q = 0; q < VPR; ++q) {
+        T e[EPV];
+#pragma unroll
+        for (int k = 0; k < EPV; ++k) e[k] = scale ? acc[q * EPV + k] * f : acc[q * EPV + k];
+        V a;
+        memcpy(&a, e, sizeof(V));
+        dst[q] = a;
+    }
+}
+
+// FP64: one thread per (output, channel) (the FP64 units bound these sums,
+// and this form keeps more of them busy than the staged one)
+// out[j][l][c] = sum_i S[l][i] in[j][i][c] along the rows (x), S = sin(pi l i / nx)
+template <typename T, int CP>
+__global__ void sine_rows_point_kernel(const T* __restrict__ in, const T* __restrict__ S, int nx, int ny, T* __restrict__ out) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)(ny + 1) * (nx + 1) * CP;
     if (t >= tot) return;
@@ -102,7 +225,7 @@ __global__ void sine_rows_kernel(const T* __restrict__ in, const T* __restrict__
 
 // out[m][l][c] = scale[m][l] sum_j S[m][j] in[j][l][c] along the columns (y)
 template <typename T, int CP>
-__global__ void sine_cols_kernel(const T* __restrict__ in, const T* __restrict__ S, const T* __restrict__ scale, int nx,
+__global__ void sine_cols_point_kernel(const T* __restrict__ in, const T* __restrict__ S, const T* __restrict__ scale, int nx,
                                  int ny, T* __restrict__ out) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)(ny + 1) * (nx + 1) * CP;
@@ -356,6 +479,11 @@ struct Impl2 {
                 const double al = kPi * l / h->a, be = kPi * m / h->b;
                 sc[(size_t)m * (h->nx + 1) + l] = (T)(4.0 / ((double)h->nx * h->ny) / (al * al + be * be));
             }
+        // the staged line of the sine sums: up to 513 records of CP values
+        if constexpr (sizeof(T) == 4) {
+            cudaFuncSetAttribute(sine_rows_kernel<T, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+            cudaFuncSetAttribute(sine_cols_kernel<T, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        }
         if (cudaMemcpy(h->Sx, Sx.data(), sizeof(T) * Sx.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->Sy, Sy.data(), sizeof(T) * Sy.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->scale, sc.data(), sizeof(T) * sc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -374,11 +502,28 @@ struct Impl2 {
             (const T*)h->state, h->N, h->nx, h->ny, (T)(0.5 * h->a), (T)(0.5 * h->b), (T)1 / hx, (T)1 / hy,
             (T)(1.0 / ((double)h->N * (h->a / h->nx) * (h->b / h->ny))), (T*)h->rho, h->err);
         // rho^lm (rows, then columns with the spectral factor), then phi by the sine sums back
-        sine_rows_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->rho, (const T*)h->Sx, h->nx, h->ny, (T*)h->T1);
-        sine_cols_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->T1, (const T*)h->Sy, (const T*)h->scale, h->nx, h->ny,
-                                                  (T*)h->T2);
-        sine_cols_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->T2, (const T*)h->Sy, nullptr, h->nx, h->ny, (T*)h->T1);
-        sine_rows_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->T1, (const T*)h->Sx, h->nx, h->ny, (T*)h->phi);
+        if constexpr (sizeof(T) == 4) {
+            const dim3 gr((unsigned)((h->nx + kSineThreads) / kSineThreads), (unsigned)(h->ny + 1));
+            const dim3 gc((unsigned)((h->ny + kSineThreads) / kSineThreads), (unsigned)(h->nx + 1));
+            const size_t smr = sizeof(T) * (size_t)(h->nx + 1) * CP, smc = sizeof(T) * (size_t)(h->ny + 1) * CP;
+            sine_rows_kernel<T, CP><<<gr, kSineThreads, smr, s>>>((const T*)h->rho, (const T*)h->Sx, h->nx, h->ny,
+                                                                  (T*)h->T1);
+            sine_cols_kernel<T, CP><<<gc, kSineThreads, smc, s>>>((const T*)h->T1, (const T*)h->Sy,
+                                                                  (const T*)h->scale, h->nx, h->ny, (T*)h->T2);
+            sine_cols_kernel<T, CP><<<gc, kSineThreads, smc, s>>>((const T*)h->T2, (const T*)h->Sy, nullptr, h->nx,
+                                                                  h->ny, (T*)h->T1);
+            sine_rows_kernel<T, CP><<<gr, kSineThreads, smr, s>>>((const T*)h->T1, (const T*)h->Sx, h->nx, h->ny,
+                                                                  (T*)h->phi);
+        } else {
+            sine_rows_point_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->rho, (const T*)h->Sx, h->nx, h->ny,
+                                                            (T*)h->T1);
+            sine_cols_point_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->T1, (const T*)h->Sy, (const T*)h->scale,
+                                                            h->nx, h->ny, (T*)h->T2);
+            sine_cols_point_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->T2, (const T*)h->Sy, nullptr, h->nx, h->ny,
+                                                            (T*)h->T1);
+            sine_rows_point_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->T1, (const T*)h->Sx, h->nx, h->ny,
+                                                            (T*)h->phi);
+        }
         field2d_kernel<T, CP><<<g, 256, 0, s>>>((const T*)h->phi, h->nx, h->ny, (T)0.5 / hx, (T)0.5 / hy, (T*)h->E);
     }
 
