@@ -367,15 +367,17 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 
 // particles per tile (one thread each) and resident CTAs per SM the register
 // budget is sized for: 2 KB coordinate runs and six 64-thread CTAs for the
-// 32-byte records (168 registers, no spills; two warps per tile barrier), 8 KB
-// runs and two CTAs otherwise
+// 32-byte records (168 registers, no spills; two warps per tile barrier); 4 KB
+// runs and four 64-thread CTAs for the FP32 64-byte records (255 registers:
+// the 8 warps per SM of two 128-thread CTAs, with two warps per tile barrier);
+// 8 KB runs and two CTAs otherwise
 template <typename T, int CP>
 __host__ __device__ constexpr int push_tile() {
-    return CP * sizeof(T) == 32 ? 64 : (int)(8192 / (CP * sizeof(T)));
+    return (CP * sizeof(T) == 32 || (sizeof(T) == 4 && CP == 16)) ? 64 : (int)(8192 / (CP * sizeof(T)));
 }
 template <typename T, int CP>
 __host__ __device__ constexpr int push_min_blocks() {
-    return CP * sizeof(T) == 32 ? 6 : 2;
+    return CP * sizeof(T) == 32 ? 6 : ((sizeof(T) == 4 && CP == 16) ? 4 : 2);
 }
 // Field stencils staged in shared memory per warp and tile (FP32, P = 7): the
 // distinct cells of a warp's particles, up to this many, each as its eight
