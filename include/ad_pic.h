@@ -51,7 +51,7 @@ enum {
     AD_PIC_ERR_NONFINITE = -5,   /* a particle coordinate became NaN or Inf */
     AD_PIC_ERR_OUT_OF_GRID = -6, /* a particle fell outside the grid stencil */
     AD_PIC_ERR_TIMEOUT = -7,     /* a bounded device wait gave up */
-    AD_PIC_ERR_UNSUPPORTED = -8, /* valid request this build does not implement */
+    AD_PIC_ERR_UNSUPPORTED = -8, /* valid request the library does not implement */
     AD_PIC_ERR_IO = -9,          /* a checkpoint file could not be read or written */
     AD_PIC_ERR_UNSTABLE = -10    /* a cell has no periodic Twiss solution (|cos mu| >= 1) */
 };

@@ -11,7 +11,7 @@ to agree with the dual PIC in value and gradient at the current point (the
 exact derivatives make this first-order correction possible), inside a trust
 region; the proposed point is then checked by a full dual-PIC run and kept
 only if it improves the objective. When the proposals stop improving, BFGS
-continues on dual-PIC gradients alone, so the PIC stays both the judge of the
+continues on dual-PIC gradients alone, so the PIC stays both the arbiter of the
 surrogate's error and the fallback.
 
 Coordinates: x = (p / p_nominal - 1) / rel in [-1, 1]^7; outputs
